@@ -1,0 +1,415 @@
+"""Python side of the FP64 CPU oracle (test infrastructure only).
+
+Only the tests, the package smoke check and the benchmark's CPU-baseline /
+reference legs may import this module. It never touches the CUDA library and
+shares no code with it; both sides read the same seeded inputs from
+``paper_2408_12479_gb300.inputs`` (data recipes only) and nothing else.
+
+Contents
+--------
+* 1D rules: Gauss-Lobatto-Legendre nodal points and Gauss-Legendre
+  quadrature on [0, 1] (numpy's Legendre routines serve as library steps).
+* Fibre dispersion constants H11, H22, H33 from (a, b) (Sec. 3, bivariate von
+  Mises dispersion; scipy's Bessel and error functions as library steps).
+* ctypes wrappers of hx_oracle.c: residual, tangent apply, diagonal, dense
+  element matrices, energy, node coordinates, pointwise material evaluation.
+* Plain global algorithms built on those: Dirichlet-constrained operators,
+  sparse assembly, the Chebyshev-Jacobi smoother (Chebyshev acceleration as
+  in Saad, "Iterative Methods for Sparse Linear Systems", Sec. 12.3, applied
+  to D^-1 K), and preconditioned CG (Saad, Alg. 9.1, with the Polak-Ribiere
+  beta so an inexact preconditioner is tolerated) -- the paper's Sec. 5
+  smoother and outer Krylov solver.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hx_oracle.c")
+_LIBDIR = os.path.join(_HERE, "_lib")
+_LIB = os.path.join(_LIBDIR, "libhx_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile hx_oracle.c with gcc (OpenMP) into oracle/_lib."""
+    os.makedirs(_LIBDIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", _SRC,
+                               "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Material(C.Structure):
+    _fields_ = [("law", C.c_int), ("mu", C.c_double), ("lam", C.c_double), ("kappa", C.c_double),
+                ("k1", C.c_double), ("k2", C.c_double), ("Hd", C.c_double * 3), ("phi", C.c_double)]
+
+
+class _Mesh(C.Structure):
+    _fields_ = [("p", C.c_int), ("g", C.c_int), ("n_elem", C.c_int), ("n_nodes", C.c_int64),
+                ("geo_nodes", C.c_void_p), ("geo_conn", C.c_void_p), ("dof_conn", C.c_void_p),
+                ("frames", C.c_void_p), ("xi_node", C.c_void_p), ("xi_q", C.c_void_p),
+                ("w_q", C.c_void_p), ("xi_geo", C.c_void_p)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB)
+            P = C.c_void_p
+            for name in ("orc_residual", "orc_apply", "orc_diagonal", "orc_assemble"):
+                f = getattr(L, name)
+                f.restype = C.c_int
+            L.orc_residual.argtypes = [P, P, P, P, P, C.c_int]
+            L.orc_apply.argtypes = [P, P, P, P, P, P, C.c_int]
+            L.orc_diagonal.argtypes = [P, P, P, P, P, C.c_int]
+            L.orc_assemble.argtypes = [P, P, P, P, P, C.c_int]
+            L.orc_energy.restype = C.c_double
+            L.orc_energy.argtypes = [P, P, P]
+            L.orc_node_coords.restype = C.c_int
+            L.orc_node_coords.argtypes = [P, P]
+            L.orc_qp_fields.restype = C.c_int
+            L.orc_qp_fields.argtypes = [P, P, P, C.c_int, P, P, P]
+            L.orc_material_point.restype = C.c_double
+            L.orc_material_point.argtypes = [P, P, P, P, P, P, P, P, P]
+            L.orc_num_threads.restype = C.c_int
+            L.orc_set_num_threads.argtypes = [C.c_int]
+            _lib = L
+    return _lib
+
+
+# ---------------------------------------------------------------------------
+# 1D rules and material constants
+# ---------------------------------------------------------------------------
+
+def gll_points(p: int) -> np.ndarray:
+    """p+1 Gauss-Lobatto-Legendre points on [0, 1]: the end points and the
+    roots of P_p'."""
+    if p == 1:
+        x = np.array([-1.0, 1.0])
+    else:
+        inner = np.polynomial.legendre.Legendre.basis(p).deriv().roots()
+        x = np.concatenate([[-1.0], np.sort(inner.real), [1.0]])
+    return 0.5 * (x + 1.0)
+
+
+def gauss_rule(nq: int):
+    """nq-point Gauss-Legendre points and weights on [0, 1] (weights sum to 1)."""
+    x, w = np.polynomial.legendre.leggauss(nq)
+    return 0.5 * (x + 1.0), 0.5 * w
+
+
+def equispaced(g: int) -> np.ndarray:
+    return np.linspace(0.0, 1.0, g + 1)
+
+
+def dispersion_H(a: float, b: float):
+    """H11, H22, H33 of the generalized structure tensor from the in-plane and
+    out-of-plane concentration parameters (a, b) (Sec. 3)."""
+    from scipy.special import erf, i0, i1
+    H33 = 1.0 / (4.0 * b) - math.exp(-2.0 * b) / (math.sqrt(2.0 * math.pi * b) * erf(math.sqrt(2.0 * b)))
+    r = i1(a) / i0(a)
+    H11 = 0.5 * (1.0 - H33) * (1.0 + r)
+    H22 = 0.5 * (1.0 - H33) * (1.0 - r)
+    return float(H11), float(H22), float(H33)
+
+
+@dataclass
+class Material:
+    law: int            # 0 cNH, 1 iNH, 2 fiber
+    mu: float = 1.0
+    lam: float = 0.0
+    kappa: float = 0.0
+    k1: float = 0.0
+    k2: float = 0.0
+    Hd: tuple = (0.0, 0.0, 0.0)
+    phi: float = 0.0
+
+    @classmethod
+    def from_dict(cls, d: dict) -> "Material":
+        Hd = (0.0, 0.0, 0.0)
+        if d.get("law") == 2:
+            Hd = dispersion_H(d["a"], d["b"])
+        return cls(law=d["law"], mu=d.get("mu", 1.0), lam=d.get("lam", 0.0), kappa=d.get("kappa", 0.0),
+                   k1=d.get("k1", 0.0), k2=d.get("k2", 0.0), Hd=Hd, phi=d.get("phi", 0.0))
+
+    def c(self) -> _Material:
+        return _Material(self.law, self.mu, self.lam, self.kappa, self.k1, self.k2,
+                         (C.c_double * 3)(*self.Hd), self.phi)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+class OracleMesh:
+    """Holds the arrays of a mesh in the layout hx_oracle.c expects."""
+
+    def __init__(self, mesh_input):
+        m = mesh_input
+        self.src = m
+        self.p, self.g = m.p, m.geo_degree
+        self.geo_nodes = np.ascontiguousarray(m.geo_nodes, dtype=np.float64)
+        self.geo_conn = np.ascontiguousarray(m.geo_conn, dtype=np.int32)
+        self.dof_conn = np.ascontiguousarray(m.dof_conn, dtype=np.int32)
+        self.frames = None if m.frames is None else np.ascontiguousarray(m.frames, dtype=np.float64)
+        self.xi_node = gll_points(m.p)
+        self.xi_q, self.w_q = gauss_rule(m.p + 1)
+        self.xi_geo = equispaced(m.geo_degree)
+        self.n_nodes = int(m.n_nodes)
+        self.n_elem = int(self.geo_conn.shape[0])
+        self.dirichlet = np.asarray(m.dirichlet, dtype=bool)
+        self._c = _Mesh(self.p, self.g, self.n_elem, self.n_nodes, _ptr(self.geo_nodes), _ptr(self.geo_conn),
+                        _ptr(self.dof_conn), _ptr(self.frames), _ptr(self.xi_node), _ptr(self.xi_q),
+                        _ptr(self.w_q), _ptr(self.xi_geo))
+
+    @property
+    def n_dofs(self):
+        return 3 * self.n_nodes
+
+    @property
+    def nloc(self):
+        return 3 * (self.p + 1) ** 3
+
+    def cref(self):
+        return C.byref(self._c)
+
+
+def _vec(x, n):
+    x = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    assert x.shape[0] == n, (x.shape, n)
+    return x
+
+
+def _elems(elems):
+    if elems is None:
+        return None, 0
+    e = np.ascontiguousarray(elems, dtype=np.int32)
+    return e, int(e.shape[0])
+
+
+class NonInvertible(RuntimeError):
+    pass
+
+
+def _check(nbad, what):
+    if nbad < 0:
+        raise MemoryError(what)
+    if nbad > 0:
+        raise NonInvertible(f"{what}: {nbad} element(s) with J <= 0 or det J0 <= 0")
+
+
+# ---------------------------------------------------------------------------
+# operators (pure operator, no constraints)
+# ---------------------------------------------------------------------------
+
+def node_coords(M: OracleMesh) -> np.ndarray:
+    X = np.zeros((M.n_nodes, 3))
+    if lib().orc_node_coords(M.cref(), X.ctypes.data) != 0:
+        raise MemoryError("node_coords")
+    return X
+
+
+def residual(M: OracleMesh, mat: Material, u, elems=None) -> np.ndarray:
+    u = _vec(u, M.n_dofs)
+    r = np.zeros(M.n_dofs)
+    e, ne = _elems(elems)
+    mc = mat.c()
+    _check(lib().orc_residual(M.cref(), C.byref(mc), u.ctypes.data, r.ctypes.data, _ptr(e), ne), "residual")
+    return r
+
+
+def apply(M: OracleMesh, mat: Material, u, du, elems=None) -> np.ndarray:
+    u = _vec(u, M.n_dofs)
+    du = _vec(du, M.n_dofs)
+    out = np.zeros(M.n_dofs)
+    e, ne = _elems(elems)
+    mc = mat.c()
+    _check(lib().orc_apply(M.cref(), C.byref(mc), u.ctypes.data, du.ctypes.data, out.ctypes.data, _ptr(e), ne),
+           "apply")
+    return out
+
+
+def diagonal(M: OracleMesh, mat: Material, u, elems=None) -> np.ndarray:
+    u = _vec(u, M.n_dofs)
+    d = np.zeros(M.n_dofs)
+    e, ne = _elems(elems)
+    mc = mat.c()
+    _check(lib().orc_diagonal(M.cref(), C.byref(mc), u.ctypes.data, d.ctypes.data, _ptr(e), ne), "diagonal")
+    return d
+
+
+def element_matrices(M: OracleMesh, mat: Material, u, elems=None) -> np.ndarray:
+    u = _vec(u, M.n_dofs)
+    e, ne = _elems(elems)
+    n_list = ne if e is not None else M.n_elem
+    Ke = np.zeros((n_list, M.nloc, M.nloc))
+    mc = mat.c()
+    _check(lib().orc_assemble(M.cref(), C.byref(mc), u.ctypes.data, Ke.ctypes.data, _ptr(e), ne), "assemble")
+    return Ke
+
+
+def energy(M: OracleMesh, mat: Material, u) -> float:
+    u = _vec(u, M.n_dofs)
+    mc = mat.c()
+    return float(lib().orc_energy(M.cref(), C.byref(mc), u.ctypes.data))
+
+
+def qp_fields(M: OracleMesh, u, elems):
+    u = _vec(u, M.n_dofs)
+    e = np.ascontiguousarray(elems, dtype=np.int32)
+    qq = (M.p + 1) ** 3
+    JxW = np.zeros((len(e), qq))
+    J0 = np.zeros((len(e), qq, 9))
+    F = np.zeros((len(e), qq, 9))
+    lib().orc_qp_fields(M.cref(), u.ctypes.data, e.ctypes.data, len(e), JxW.ctypes.data, J0.ctypes.data,
+                        F.ctypes.data)
+    return JxW, J0, F
+
+
+def material_point(mat: Material, F, H=None, frame=None):
+    """Psi, S, P, dP (and fibre auxiliaries) at one deformation gradient."""
+    F = np.ascontiguousarray(np.asarray(F, dtype=np.float64).reshape(9))
+    Hh = None if H is None else np.ascontiguousarray(np.asarray(H, dtype=np.float64).reshape(9))
+    fr = None if frame is None else np.ascontiguousarray(np.asarray(frame, dtype=np.float64).reshape(9))
+    psi = C.c_double(0.0)
+    S = np.zeros(9)
+    P = np.zeros(9)
+    dP = np.zeros(9)
+    aux = np.zeros(6)
+    mc = mat.c()
+    J = lib().orc_material_point(C.byref(mc), _ptr(fr), F.ctypes.data, _ptr(Hh), C.byref(psi), S.ctypes.data,
+                                 P.ctypes.data, dP.ctypes.data if Hh is not None else None, aux.ctypes.data)
+    return dict(J=J, psi=psi.value, S=S.reshape(3, 3), P=P.reshape(3, 3),
+                dP=dP.reshape(3, 3) if Hh is not None else None, aux=aux)
+
+
+def set_threads(n: int):
+    lib().orc_set_num_threads(int(n))
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+# ---------------------------------------------------------------------------
+# global assembly and constrained operators
+# ---------------------------------------------------------------------------
+
+def assemble_sparse(M: OracleMesh, mat: Material, u):
+    """Global sparse K(u) (pure operator, no constraints) from the dense
+    element matrices."""
+    import scipy.sparse as sp
+    Ke = element_matrices(M, mat, u)
+    nn = (M.p + 1) ** 3
+    dofs = (3 * M.dof_conn[:, :, None] + np.arange(3)[None, None, :]).reshape(M.n_elem, 3 * nn)
+    rows = np.repeat(dofs, 3 * nn, axis=1).ravel()
+    cols = np.tile(dofs, (1, 3 * nn)).ravel()
+    return sp.csr_matrix((Ke.ravel(), (rows, cols)), shape=(M.n_dofs, M.n_dofs))
+
+
+def constrain_matrix(K, mask):
+    """Replace constrained rows/columns by identity rows (out_c = du_c)."""
+    import scipy.sparse as sp
+    free = sp.diags((~mask).astype(np.float64))
+    fix = sp.diags(mask.astype(np.float64))
+    return (free @ K @ free + fix).tocsr()
+
+
+def apply_constrained(M: OracleMesh, mat: Material, u, du):
+    """K_c du: free rows of K applied to du with constrained entries zeroed;
+    constrained rows return du itself."""
+    mask = M.dirichlet
+    d = np.where(mask, 0.0, _vec(du, M.n_dofs))
+    out = apply(M, mat, u, d)
+    return np.where(mask, _vec(du, M.n_dofs), out)
+
+
+def residual_constrained(M: OracleMesh, mat: Material, u):
+    r = residual(M, mat, u)
+    r[M.dirichlet] = 0.0
+    return r
+
+
+def diagonal_constrained(M: OracleMesh, mat: Material, u):
+    d = diagonal(M, mat, u)
+    d[M.dirichlet] = 1.0
+    return d
+
+
+# ---------------------------------------------------------------------------
+# Chebyshev-Jacobi smoother and preconditioned CG (Sec. 5)
+# ---------------------------------------------------------------------------
+
+def chebyshev_smooth(Kop, rhs, x, inv_diag, degree, lambda_max, smoothing_range, zero_initial=False):
+    """Chebyshev acceleration of the Jacobi iteration on D^-1 K x = D^-1 rhs
+    with eigenvalue interval [lambda_max/smoothing_range, lambda_max]; degree
+    steps, each using one residual rhs - K x (the first is rhs itself when x
+    starts at zero). Written as the three-term recurrence
+        d_0 = r_0 / theta,  rho_0 = delta/theta,
+        rho_k = 1/(2 theta/delta - rho_{k-1}),
+        d_k = rho_k rho_{k-1} d_{k-1} + (2 rho_k/delta) r_k,
+        x_{k+1} = x_k + d_k,  r_k = D^-1 (rhs - K x_k)."""
+    a = lambda_max / smoothing_range
+    b = lambda_max
+    theta = 0.5 * (b + a)
+    delta = 0.5 * (b - a)
+    x = np.array(x, dtype=np.float64, copy=True)
+    if zero_initial:
+        x[:] = 0.0
+    d = None
+    rho_prev = None
+    for k in range(degree):
+        if k == 0 and zero_initial:
+            r = inv_diag * rhs
+        else:
+            r = inv_diag * (rhs - Kop(x))
+        if k == 0:
+            rho = delta / theta
+            d = r / theta
+        else:
+            rho_new = 1.0 / (2.0 * theta / delta - rho_prev)
+            d = rho_new * rho_prev * d + (2.0 * rho_new / delta) * r
+            rho = rho_new
+        x = x + d
+        rho_prev = rho
+    return x
+
+
+def pcg(Kop, b, Mop, tol=1e-8, maxit=10000, x0=None):
+    """Preconditioned CG with the Polak-Ribiere beta; stops when
+    ||b - K x|| <= tol ||b|| (recomputed residual checked at exit)."""
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
+    r = b - Kop(x)
+    bn = np.linalg.norm(b)
+    z = Mop(r)
+    p = z.copy()
+    rz = r @ z
+    it = 0
+    hist = [np.linalg.norm(r) / bn]
+    while it < maxit and hist[-1] > tol:
+        Ap = Kop(p)
+        alpha = rz / (p @ Ap)
+        x += alpha * p
+        r_new = r - alpha * Ap
+        z_new = Mop(r_new)
+        beta = (r_new @ (z_new - z)) / rz
+        rz = r_new @ z_new
+        p = z_new + beta * p
+        r, z = r_new, z_new
+        it += 1
+        hist.append(np.linalg.norm(r) / bn)
+    true_rel = np.linalg.norm(b - Kop(x)) / bn
+    return x, it, true_rel, hist
