@@ -1,0 +1,341 @@
+"""Benchmark of the matrix-free hyperelastic tangent apply on GB300.
+
+Default workload: compressible neo-Hookean on the 32^3 cube with interior
+vertices jittered by +-10% of h, p = 4 (6,440,067 DoFs), FP32, with the
+fastest of the three quadrature-point storage strategies. One step is one
+tangent apply K(u_k) du over the whole mesh (gather, sum-factorized gradient,
+quadrature-point material tangent, integration, scatter: one fused kernel plus
+the zeroing of the output). The qp cache is refreshed once before timing, as
+in the paper's protocol (Sec. 6.2). Metric: GDoF/s over all 3*n_nodes DoFs.
+
+Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+For N > 1 (torchrun) every rank runs an independent replica (weak scaling, no
+collective in the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "tangent-operator apply GDoF/s (p=2-6, FP64 vs FP32) and fraction of HBM roofline"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def build_case(p, prec, storage, device, law="cNH", n=32):
+    import torch
+    from paper_2408_12479_gb300 import hx
+    from paper_2408_12479_gb300 import inputs as I
+    m, field, seed = I.workload_jittered_cube(p, n=n)
+    mat = dict(I.MAT_CNH)
+    G = hx.Mesh(m, mat, device=device)
+    X = G.node_coords().cpu().numpy()
+    u = torch.tensor(field(X).ravel(), dtype=torch.float64, device=G.device)
+    du64 = torch.tensor(I.random_direction(m.n_dofs, seed + 3), dtype=torch.float64, device=G.device)
+    du = du64 if prec == hx.HX_FP64 else du64.float()
+    G.precompute(u, prec, storage)
+    out = torch.empty_like(du)
+    return G, m, u, du, out
+
+
+def time_steps(G, du, out, steps, warmup):
+    import torch
+    from paper_2408_12479_gb300 import hx
+    for _ in range(warmup):
+        hx.hx_tangent_apply(G.ctx, G.handle, du, out)
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(steps):
+        hx.hx_tangent_apply(G.ctx, G.handle, du, out)
+    e1.record(s)
+    torch.cuda.synchronize()
+    G.sync(60000)
+    return e0.elapsed_time(e1) / steps
+
+
+def cpu_baseline(m, field, seed, p, mat_d, target_s=12.0):
+    """The FP64 oracle's full-tensor apply on a bounded sample of the same mesh
+    (leading elements), on all host cores; scaled to GDoF/s of the whole mesh."""
+    from oracle import oracle as O
+    M = O.OracleMesh(m)
+    X = O.node_coords(M)
+    u = field(X).ravel()
+    from paper_2408_12479_gb300 import inputs as I
+    du = I.random_direction(m.n_dofs, seed + 3)
+    mat = O.Material.from_dict(mat_d)
+    k = 64
+    while True:
+        t0 = time.perf_counter()
+        O.apply(M, mat, u, du, elems=np.arange(k, dtype=np.int32))
+        dt = time.perf_counter() - t0
+        if dt > 1.0 or k >= m.n_elem:
+            break
+        k = min(m.n_elem, k * 4)
+    k = int(min(m.n_elem, max(k, k * target_s / max(dt, 1e-3))))
+    t0 = time.perf_counter()
+    O.apply(M, mat, u, du, elems=np.arange(k, dtype=np.int32))
+    dt = time.perf_counter() - t0
+    gdofs = m.n_dofs * (k / m.n_elem) / dt / 1e9
+    return {"value": gdofs, "unit": "GDoF/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"FP64 full-tensor oracle apply over the first {k} of {m.n_elem} elements "
+                      f"({dt:.1f} s), scaled by the element fraction"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, timed as it stands on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_2408_12479_gb300 import inputs as I
+    p = args.p
+    m, field, seed = I.workload_jittered_cube(p)
+    mat_d = dict(I.MAT_CNH)
+    M = O.OracleMesh(m)
+    X = O.node_coords(M)
+    u = field(X).ravel()
+    du = I.random_direction(m.n_dofs, seed + 3)
+    mat = O.Material.from_dict(mat_d)
+    k = 256
+    elems = np.arange(k, dtype=np.int32)
+    for _ in range(args.warmup):
+        O.apply(M, mat, u, du, elems=elems)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.apply(M, mat, u, du, elems=elems)
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    gdofs = m.n_dofs * (k / m.n_elem) / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": gdofs, "unit": "GDoF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 * m.n_elem / k,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"cNH 32^3 jittered cube p={p}", "p": p,
+                                            "n_dofs": m.n_dofs},
+            "cpu_baseline": {"value": gdofs, "unit": "GDoF/s", "cores": O.num_threads(), "kind": "oracle",
+                             "sample": f"first {k} of {m.n_elem} elements per step, scaled by the element fraction"},
+            "e2e": {"value": gdofs, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="hx")
+    ap.add_argument("--p", type=int, default=4)
+    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--storage", default="best", choices=["best", "recompute", "cache_F", "cache_tensors"])
+    ap.add_argument("--prec", default="f32", choices=["f32", "f64"])
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2408_12479_gb300 import hx
+    from paper_2408_12479_gb300 import inputs as I
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    hbm_peak, peak_kind = peaks()
+
+    p = args.p
+    prec = hx.HX_FP32 if args.prec == "f32" else hx.HX_FP64
+    # pick the fastest storage strategy on a short run (or take the given one)
+    best = None
+    per_storage = {}
+    names = {v: k for k, v in hx.STORAGE_NAMES.items()}
+    cands = (hx.HX_RECOMPUTE, hx.HX_CACHE_F, hx.HX_CACHE_TENSORS) if args.storage == "best" else (names[args.storage],)
+    for storage in cands:
+        if len(cands) == 1:
+            best = (storage, None)
+            break
+        G, m, u, du, out = build_case(p, prec, storage, local)
+        ms = time_steps(G, du, out, 20, 3)
+        per_storage[hx.STORAGE_NAMES[storage]] = ms
+        if best is None or ms < best[1]:
+            best = (storage, ms)
+        G.close()
+        del u, du, out
+        torch.cuda.empty_cache()
+    storage = best[0]
+    G, m, u, du, out = build_case(p, prec, storage, local)
+    n_dofs = m.n_dofs
+    bytes_alg = G.apply_bytes(storage, prec)
+
+    hx.hx_launch_count(G.ctx, reset=True)
+    for _ in range(args.warmup):
+        hx.hx_tangent_apply(G.ctx, G.handle, du, out)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    hx.hx_launch_count(G.ctx, reset=True)
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(args.steps):
+            hx.hx_tangent_apply(G.ctx, G.handle, du, out)
+        e1.record(s)
+        torch.cuda.synchronize()
+    launches = hx.hx_launch_count(G.ctx)
+    G.sync(60000)
+    ms = e0.elapsed_time(e1) / args.steps
+    t_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        dist.barrier()
+    value = world * n_dofs / (t_max * 1e-3) / 1e9
+    achieved = bytes_alg / (ms * 1e-3) / 1e9
+
+    # end to end through the host-buffer C-ABI call (pinned host vectors)
+    bytes_vec = n_dofs * du.element_size()
+    e2e = None
+    if not args.no_e2e:
+        du_h = du.cpu().pin_memory()
+        out_h = torch.empty_like(du_h).pin_memory()
+        for _ in range(2):
+            hx.hx_tangent_apply_host(G.ctx, G.handle, du_h, out_h, prec)
+        k_e2e = max(5, min(args.steps, 50))
+        t0 = time.perf_counter()
+        for _ in range(k_e2e):
+            hx.hx_tangent_apply_host(G.ctx, G.handle, du_h, out_h, prec)
+        e2e_s = (time.perf_counter() - t0) / k_e2e
+        e2e = {"value": round(n_dofs / e2e_s / 1e9, 4), "unit": "GDoF/s", "h2d_bytes_per_step": bytes_vec,
+               "d2h_bytes_per_step": bytes_vec}
+
+    sweep = []
+    if rank == 0 and not args.no_sweep:
+        G.close()
+        del u, du, out
+        torch.cuda.empty_cache()
+        for pp in (2, 3, 4, 5, 6):
+            for pr in (hx.HX_FP32, hx.HX_FP64):
+                for st in (hx.HX_RECOMPUTE, hx.HX_CACHE_F, hx.HX_CACHE_TENSORS):
+                    Gs, ms_, us, dus, outs = build_case(pp, pr, st, local)
+                    reps = 30 if pr == hx.HX_FP32 else 5
+                    t = time_steps(Gs, dus, outs, reps, 2)
+                    b = Gs.apply_bytes(st, pr)
+                    sweep.append({"p": pp, "prec": "f32" if pr else "f64", "storage": hx.STORAGE_NAMES[st],
+                                  "n_dofs": ms_.n_dofs, "ms": round(t, 4),
+                                  "gdofs": round(ms_.n_dofs / (t * 1e-3) / 1e9, 3),
+                                  "hbm_frac": round(b / (t * 1e-3) / 1e9 / hbm_peak, 4)})
+                    Gs.close()
+                    del us, dus, outs
+                    torch.cuda.empty_cache()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        m2, field, seed = I.workload_jittered_cube(p)
+        cpu = cpu_baseline(m2, field, seed, p, dict(I.MAT_CNH))
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t_max, 5), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+            "config": {"workload": f"cNH tangent apply, 32^3 jittered cube, p={p}, {args.prec.upper()}, "
+                                   f"storage={hx.STORAGE_NAMES[storage]}",
+                       "p": p, "n_dofs": n_dofs, "law": "cNH", "prec": args.prec,
+                       "storage": hx.STORAGE_NAMES[storage],
+                       "l2": "inputs larger than L2 (vectors + qp data %.0f MB > 129 MB)" % (bytes_alg / 1e6),
+                       "per_storage_ms": {k: round(v, 4) for k, v in per_storage.items() if v}},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                         "frac": round(achieved / hbm_peak, 4), "traffic": None,
+                         "peak_kind": peak_kind, "bytes_per_launch": bytes_alg},
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+            "sweep": sweep,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

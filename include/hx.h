@@ -1,0 +1,229 @@
+/*
+ * hx.h -- C ABI of the GB300 library for matrix-free hyperelastic operators
+ * on hexahedral Q_p elements (arXiv 2408.12479, "Matrix-Free Higher-Order
+ * Finite Element Methods for Hyperelasticity").
+ *
+ * The library evaluates, matrix-free and with sum factorization,
+ *   the nonlinear residual  R(u)_i = (Grad N_i, P(F))_Omega0        Sec. 2, Eq. (mom_bal_nonlinear_material_residual)
+ *   the tangent action      K(u_k) du = (Grad N_i, Grad du S + F D_uS[Grad du])   Sec. 2, Eq. (DDu_residual_material)
+ * for three laws (Sec. 3): compressible neo-Hookean (cNH, Eq. NH_compressible),
+ * nearly incompressible neo-Hookean (iNH, Eq. NH_nearly_incompressible) and the
+ * two-family dispersed fibre model (fiber, Eq. fiber_Psi), in FP64 or FP32,
+ * with the quadrature-point storage strategies of Sec. 4 / Table 2.
+ *
+ * Discretisation: Lagrange polynomials of degree p on the p+1
+ * Gauss-Lobatto-Legendre points per direction, (p+1)^3 Gauss-Legendre
+ * quadrature points per element, geometry given by trilinear (8 vertices) or
+ * triquadratic (27 nodes, equispaced parameter points) element maps.
+ *
+ * Conventions for every call:
+ *  - Pointers named *_dev are device pointers owned by the caller; *_host are
+ *    host pointers owned by the caller. The library copies what it keeps.
+ *  - A DoF vector holds 3*n_nodes values, node-major: component c of node I
+ *    at index 3*I+c. Its scalar type follows the call's hx_prec (double for
+ *    HX_FP64, float for HX_FP32). Vectors must be 16-byte aligned.
+ *  - Calls are asynchronous on the context's CUDA stream. Argument errors are
+ *    returned synchronously. Device-side errors (a quadrature point with
+ *    J <= 0 or det J0 <= 0, a NaN state) set a device flag that hx_sync()
+ *    and hx_precompute_qp() (on its next call) turn into a status.
+ *  - The library never traps or aborts: every failure is a status, and
+ *    hx_last_error() gives a one-line message.
+ *  - Constrained DoFs (Dirichlet mask): residual rows are zero; tangent and
+ *    diagonal rows are the identity (out_i = du_i, diag_i = 1); the operator
+ *    sees constrained entries of du as zero.
+ */
+#ifndef HX_H
+#define HX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hx_ctx hx_ctx;   /* device, stream, error string */
+typedef struct hx_mesh hx_mesh; /* device mesh, geometry, qp cache, workspace */
+typedef struct hx_batch hx_batch;
+
+typedef enum {
+    HX_OK = 0,
+    HX_ERR_ARG = 1,            /* invalid argument (null pointer, size, enum) */
+    HX_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    HX_ERR_NONINVERTIBLE = 3,  /* J <= 0 or det J0 <= 0 at some quadrature point */
+    HX_ERR_NOT_READY = 4,      /* tangent/diagonal needs hx_precompute_qp first */
+    HX_ERR_TIMEOUT = 5,        /* hx_sync waited longer than its limit */
+    HX_ERR_NOT_CONVERGED = 6,  /* iterative solver hit its iteration limit */
+    HX_ERR_NAN = 7,            /* a NaN/Inf met in the state or in a solver scalar */
+    HX_ERR_UNSUPPORTED = 8     /* degree/law/storage combination not built */
+} hx_status;
+
+typedef enum { HX_CNH = 0, HX_INH = 1, HX_FIBER = 2 } hx_law;
+typedef enum { HX_FP64 = 0, HX_FP32 = 1 } hx_prec;
+
+/* Storage strategies of Sec. 4 (material configuration), refreshed by
+ * hx_precompute_qp once per Newton state (Alg. 1, "update quadrature point
+ * data"):
+ *   HX_RECOMPUTE      nothing per qp but the geometry; the tangent re-reads
+ *                     u_k and rebuilds F, F^-1, C^-1, J-1, ln J, J^-2/3 and S
+ *                     at every quadrature point ("on-the-fly", stage i);
+ *   HX_CACHE_F        Grad u_k (= F - I) and the law's scalars (1/J and ln J
+ *                     for cNH; 1/J, J^-2/3, c1, c2 and the stress scalar for
+ *                     iNH; plus the fibre factors for fiber) -- stage ii;
+ *   HX_CACHE_TENSORS  F - I, F^-1, C^-1, S and the tangent scalars -- the
+ *                     paper's stage iii "scalars and tensors".
+ * Geometry (J0^-1 and JxW per qp) is stored once at mesh setup for all. */
+typedef enum { HX_RECOMPUTE = 0, HX_CACHE_F = 1, HX_CACHE_TENSORS = 2 } hx_storage;
+
+/* Material parameters (Sec. 3, Table 1). lambda is used by cNH only (note
+ * Psi_cNH = mu/2(I1 - 3 - 2 ln J) + lambda ln^2 J, so the small-strain Lame
+ * constant is 2 lambda). kappa is the bulk modulus of iNH/fiber. For fiber:
+ * k1, k2 of the exponential fibre energy, dispersion (a, b) from which H11,
+ * H22, H33 are computed (see hx_fibre_dispersion), and phi the mean in-plane
+ * fibre angle in radians (family 4 at +phi, family 6 at -phi). */
+typedef struct {
+    int32_t law; /* hx_law */
+    double mu, lambda, kappa;
+    double k1, k2, a, b, phi;
+} hx_material;
+
+/* Mesh description (host arrays, copied by hx_setup_mesh).
+ *  geo_nodes   [n_geo_nodes][3] vertex (g = 1) or node (g = 2) coordinates
+ *  geo_conn    [n_elem][(g+1)^3] geometry node ids, lexicographic xi1 fastest
+ *  dof_conn    [n_elem][(p+1)^3] DoF node ids, lexicographic xi1 fastest;
+ *              may be NULL for a structured box (nx, ny, nz > 0), in which
+ *              case element (ex,ey,ez) = ex + nx*(ey + ny*ez) owns nodes
+ *              (ex*p+i) + (nx*p+1)*((ey*p+j) + (ny*p+1)*(ez*p+k))
+ *  dirichlet   [3*n_nodes] 1 = constrained DoF, or NULL for none
+ *  fibre_frames[n_elem][9] (E1 circumferential, E2 longitudinal, E3 radial)
+ *              per element, required for HX_FIBER, ignored otherwise. */
+typedef struct {
+    int32_t n_elem;
+    int32_t p;          /* 1..6 */
+    int32_t geo_degree; /* 1 or 2 */
+    int64_t n_nodes;
+    const double *geo_nodes;
+    int64_t n_geo_nodes;
+    const int32_t *geo_conn;
+    const int32_t *dof_conn;
+    int32_t nx, ny, nz;
+    const uint8_t *dirichlet;
+    const double *fibre_frames;
+} hx_mesh_desc;
+
+/* ---- context ------------------------------------------------------------ */
+/* Create a context on `device`, issuing all work on `cuda_stream` (a
+ * cudaStream_t; NULL = the legacy default stream). */
+hx_status hx_create(hx_ctx **ctx, int device, void *cuda_stream);
+void hx_destroy(hx_ctx *ctx);
+/* Rebind the context to another stream (subsequent calls only). */
+hx_status hx_set_stream(hx_ctx *ctx, void *cuda_stream);
+/* Message of the last failing call on this context ("" if none). */
+const char *hx_last_error(hx_ctx *ctx);
+/* Wait (polling, at most timeout_ms; <0 = no limit) for the context's stream,
+ * then report device-side errors: HX_ERR_NONINVERTIBLE / HX_ERR_NAN, else
+ * HX_OK. The device flag is cleared once reported. HX_ERR_TIMEOUT leaves the
+ * work running. */
+hx_status hx_sync(hx_ctx *ctx, int timeout_ms);
+
+/* ---- mesh --------------------------------------------------------------- */
+/* Upload a mesh and compute the geometry at every quadrature point (J0^-1 and
+ * JxW, FP64 and FP32 copies). Fails with HX_ERR_NONINVERTIBLE if some
+ * quadrature point has det J0 <= 0 (mapping check, Sec. 5). Synchronous. */
+hx_status hx_setup_mesh(hx_ctx *ctx, const hx_mesh_desc *desc, const hx_material *mat, hx_mesh **mesh);
+void hx_destroy_mesh(hx_mesh *mesh);
+/* Number of DoF nodes, elements and quadrature points of a mesh. */
+hx_status hx_mesh_info(const hx_mesh *mesh, int64_t *n_nodes, int64_t *n_elem, int64_t *n_qp);
+/* Physical coordinates of the DoF nodes (the geometry map at the GLL points),
+ * X_dev[n_nodes][3] FP64 on the device. */
+hx_status hx_node_coords(hx_mesh *mesh, double *X_dev);
+/* Bytes the tangent apply streams per call for (storage, prec), counting the
+ * two DoF vectors once each, the qp cache and the per-qp geometry; this is the
+ * figure behind the HBM-roofline fraction. */
+hx_status hx_apply_bytes(const hx_mesh *mesh, int32_t storage, int32_t prec, double *bytes);
+
+/* ---- hot path ----------------------------------------------------------- */
+/* Update the quadrature-point data at the Newton state u_dev (FP64 vector):
+ * interpolate Grad u_k with sum factorization and store what the strategy
+ * keeps, computed in FP64 (J-1 from the components of Grad u, ln J as
+ * ln_{+1}(J-1), J^-2/3 exactly) and stored in store_prec. This is Alg. 1's
+ * "update quadrature point data" (Sec. 4). The first call per mesh allocates
+ * the cache (call it before any stream capture). Returns a status of the
+ * previous device-side error, if any; this call's own J <= 0 check is reported
+ * by hx_sync. */
+hx_status hx_precompute_qp(hx_mesh *mesh, const double *u_dev, int32_t store_prec, int32_t storage);
+
+/* r = R(u) (Sec. 2), constrained rows zero. u_dev, r_dev in `prec`. The state
+ * is recomputed from u at every quadrature point (no cache needed). */
+hx_status hx_residual(hx_mesh *mesh, const void *u_dev, void *r_dev, int32_t prec);
+
+/* out = K(u_k) du (Sec. 2, Eq. DDu_residual_material; Sec. 4 storage forms),
+ * using the cache of the last hx_precompute_qp; `prec` must equal its
+ * store_prec. du_dev and out_dev must not overlap. */
+hx_status hx_tangent_apply(hx_mesh *mesh, const void *du_dev, void *out_dev, int32_t prec);
+
+/* Same operator with host vectors: copies du to the device, applies, copies
+ * the result back, all on the context stream; returns after the result is on
+ * the host. Uses a device staging buffer owned by the mesh. */
+hx_status hx_tangent_apply_host(hx_mesh *mesh, const void *du_host, void *out_host, int32_t prec);
+
+/* diag(K(u_k)), constrained entries 1 (needed by the Jacobi smoother,
+ * Sec. 5); sum-factorized from the per-qp tangent blocks. */
+hx_status hx_diagonal(hx_mesh *mesh, void *diag_dev, int32_t prec);
+
+/* `degree` steps of Chebyshev-accelerated Jacobi on K x = rhs (Sec. 5,
+ * smoother), in place on x, eigenvalue interval
+ * [lambda_max/smoothing_range, lambda_max] of D^-1 K, inv_diag = D^-1.
+ * zero_initial != 0 treats x as zero on entry (saves one operator apply).
+ * Every step applies the tangent of the last hx_precompute_qp in `prec`. */
+hx_status hx_chebyshev_smooth(hx_mesh *mesh, const void *rhs_dev, void *x_dev, const void *inv_diag_dev,
+                              int32_t degree, double lambda_max, double smoothing_range, int32_t zero_initial,
+                              int32_t prec);
+
+/* Largest eigenvalue of D^-1 K by `iters` power iterations from a seeded
+ * random start (FP64, on the device); *out receives the Rayleigh quotient. */
+hx_status hx_estimate_lambda_max(hx_mesh *mesh, const double *inv_diag_dev, int32_t iters, uint64_t seed,
+                                 double *out);
+
+/* FP64 preconditioned CG on K(u_k) x = rhs (constrained operator), with a
+ * Chebyshev(degree)-Jacobi preconditioner applied in precond_prec (Sec. 5:
+ * FP64 outer Krylov, FP32 preconditioner). x_dev holds the start and
+ * receives the solution; stops when ||rhs - K x|| <= tol ||rhs|| (true
+ * residual rechecked at exit) or after max_iter iterations
+ * (HX_ERR_NOT_CONVERGED). One iteration runs as a captured CUDA graph.
+ * Requires hx_precompute_qp at FP64 and, for an FP32 preconditioner, at FP32
+ * as well (both caches are kept). */
+typedef struct {
+    int32_t degree;            /* Chebyshev degree (0 = plain Jacobi) */
+    double lambda_max;         /* upper eigenvalue bound of D^-1 K */
+    double smoothing_range;    /* lambda_min = lambda_max / range */
+    int32_t precond_prec;      /* hx_prec */
+    int32_t use_graph;         /* capture one iteration in a CUDA graph */
+} hx_cg_options;
+hx_status hx_cg_solve(hx_mesh *mesh, const double *rhs_dev, double *x_dev, double tol, int32_t max_iter,
+                      const hx_cg_options *opt, int32_t *iters, double *rel_residual);
+
+/* Fibre dispersion constants H11, H22, H33 from (a, b) (Sec. 3). Host only. */
+hx_status hx_fibre_dispersion(double a, double b, double H[3]);
+
+/* ---- batches of meshes (many uneven problems in one launch) -------------- */
+/* Group meshes (possibly of different degrees) so that one persistent launch
+ * applies every mesh's tangent. The meshes stay owned by the caller and must
+ * outlive the batch; each needs its qp cache at `prec`. */
+hx_status hx_batch_create(hx_ctx *ctx, hx_mesh *const *meshes, int32_t n_meshes, hx_batch **batch);
+void hx_batch_destroy(hx_batch *batch);
+/* out_i = K_i du_i for every mesh i in one launch; du/out are arrays of
+ * n_meshes device pointers (host arrays). */
+hx_status hx_batch_tangent_apply(hx_batch *batch, const void *const *du_dev, void *const *out_dev, int32_t prec);
+
+/* ---- measurement support ------------------------------------------------- */
+/* Peak FMA throughput of this device for `prec`, measured by a dependent-FMA
+ * kernel over all SMs (flop/s, 2 flops per FMA). Synchronous. */
+hx_status hx_measure_fma_peak(hx_ctx *ctx, int32_t prec, double *flops);
+/* Number of this library's kernel launches since the counter was reset. */
+uint64_t hx_launch_count(hx_ctx *ctx, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HX_H */

@@ -1,0 +1,931 @@
+// hx_api.cu -- implementation of the C ABI declared in include/hx.h: contexts,
+// mesh setup (1D rules, fibre structure tensors, geometry), quadrature-point
+// caches, operator dispatch to the per-degree kernel units, the
+// Chebyshev-Jacobi smoother, power iteration and the graph-captured FP64 CG.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <chrono>
+#include <cmath>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "hx_internal.h"
+#include "hx_vec.h"
+
+// per-(degree, precision) kernel units
+#define HX_DECL(P)                                   \
+    extern const hx::PrecOps *hx_prec_ops_p##P##_f64(); \
+    extern const hx::PrecOps *hx_prec_ops_p##P##_f32();
+HX_DECL(1)
+HX_DECL(2)
+HX_DECL(3)
+HX_DECL(4)
+HX_DECL(5)
+HX_DECL(6)
+#undef HX_DECL
+
+namespace hx {
+const PrecOps *prec_ops(int p, int prec) {
+#define HX_CASE(P) \
+    case P:        \
+        return prec == HX_FP64 ? hx_prec_ops_p##P##_f64() : hx_prec_ops_p##P##_f32();
+    switch (p) {
+        HX_CASE(1)
+        HX_CASE(2)
+        HX_CASE(3)
+        HX_CASE(4)
+        HX_CASE(5)
+        HX_CASE(6)
+        default:
+            return nullptr;
+    }
+#undef HX_CASE
+}
+}  // namespace hx
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// 1D rules on [0, 1]
+// ---------------------------------------------------------------------------
+// Legendre P_n and P_n' on [-1, 1] by the three-term recurrence
+void legendre(int n, double x, double &P, double &dP) {
+    double p0 = 1.0, p1 = x;
+    if (n == 0) {
+        P = 1.0;
+        dP = 0.0;
+        return;
+    }
+    for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+    }
+    P = p1;
+    dP = n * (x * p1 - p0) / (x * x - 1.0);
+}
+
+// Gauss-Legendre: roots of P_n by Newton from Chebyshev-like guesses
+void gauss_rule(int n, std::vector<double> &x, std::vector<double> &w) {
+    x.assign(n, 0.0);
+    w.assign(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        double t = -std::cos(M_PI * (i + 0.75) / (n + 0.5));
+        for (int it = 0; it < 100; ++it) {
+            double P, dP;
+            legendre(n, t, P, dP);
+            const double dt = P / dP;
+            t -= dt;
+            if (std::fabs(dt) < 1e-16) break;
+        }
+        double P, dP;
+        legendre(n, t, P, dP);
+        x[i] = 0.5 * (t + 1.0);
+        w[i] = 1.0 / ((1.0 - t * t) * dP * dP);  // 2/((1-t^2)P'^2), halved for [0,1]
+    }
+}
+
+// Gauss-Lobatto-Legendre: end points and the roots of P_p', found by Newton on
+// P_p' with P_p'' = (2t P_p' - p(p+1) P_p)/(1 - t^2)
+std::vector<double> gll_points(int p) {
+    std::vector<double> x(p + 1);
+    x[0] = 0.0;
+    x[p] = 1.0;
+    for (int i = 1; i < p; ++i) {
+        double t = -std::cos(M_PI * i / p);
+        for (int it = 0; it < 100; ++it) {
+            double P, dP;
+            legendre(p, t, P, dP);
+            const double d2P = (2.0 * t * dP - p * (p + 1.0) * P) / (1.0 - t * t);
+            const double dt = dP / d2P;
+            t -= dt;
+            if (std::fabs(dt) < 1e-16) break;
+        }
+        x[i] = 0.5 * (t + 1.0);
+    }
+    return x;
+}
+
+double lagrange(const std::vector<double> &xs, int a, double x) {
+    double v = 1.0;
+    for (size_t b = 0; b < xs.size(); ++b)
+        if ((int)b != a) v *= (x - xs[b]) / (xs[a] - xs[b]);
+    return v;
+}
+
+double lagrange_d(const std::vector<double> &xs, int a, double x) {
+    double s = 0.0;
+    for (size_t m = 0; m < xs.size(); ++m) {
+        if ((int)m == a) continue;
+        double v = 1.0 / (xs[a] - xs[m]);
+        for (size_t b = 0; b < xs.size(); ++b)
+            if ((int)b != a && b != m) v *= (x - xs[b]) / (xs[a] - xs[b]);
+        s += v;
+    }
+    return s;
+}
+
+struct Tables {
+    std::vector<double> B, D, Gd, w, geoV, geoD, geoVn;
+};
+
+Tables make_tables(int p) {
+    const int n = p + 1;
+    Tables t;
+    std::vector<double> xq, wq;
+    gauss_rule(n, xq, wq);
+    const std::vector<double> xn = gll_points(p);
+    t.B.resize(n * n);
+    t.D.resize(n * n);
+    t.Gd.resize(n * n);
+    for (int q = 0; q < n; ++q)
+        for (int a = 0; a < n; ++a) {
+            t.B[q * n + a] = lagrange(xn, a, xq[q]);
+            t.Gd[q * n + a] = lagrange_d(xn, a, xq[q]);
+            t.D[q * n + a] = lagrange_d(xq, a, xq[q]);
+        }
+    t.w = wq;
+    t.geoV.assign(2 * 3 * n, 0.0);
+    t.geoD.assign(2 * 3 * n, 0.0);
+    t.geoVn.assign(2 * 3 * n, 0.0);
+    for (int g = 1; g <= 2; ++g) {
+        std::vector<double> xg(g + 1);
+        for (int a = 0; a <= g; ++a) xg[a] = (double)a / g;
+        for (int a = 0; a <= g; ++a)
+            for (int q = 0; q < n; ++q) {
+                t.geoV[(g - 1) * 3 * n + a * n + q] = lagrange(xg, a, xq[q]);
+                t.geoD[(g - 1) * 3 * n + a * n + q] = lagrange_d(xg, a, xq[q]);
+                t.geoVn[(g - 1) * 3 * n + a * n + q] = lagrange(xg, a, xn[q]);
+            }
+    }
+    return t;
+}
+
+std::mutex g_upload_mu;
+bool g_uploaded[64][HX_PMAX + 1];
+
+cudaError_t ensure_tables(int device, int p) {
+    std::lock_guard<std::mutex> lk(g_upload_mu);
+    if (device < 0 || device >= 64) return cudaErrorInvalidDevice;
+    if (g_uploaded[device][p]) return cudaSuccess;
+    Tables t = make_tables(p);
+    for (int prec = 0; prec < 2; ++prec) {
+        const hx::PrecOps *ops = hx::prec_ops(p, prec);
+        cudaError_t e = ops->upload_tables(t.B.data(), t.D.data(), t.Gd.data(), t.w.data(), t.geoV.data(),
+                                           t.geoD.data(), t.geoVn.data());
+        if (e != cudaSuccess) return e;
+    }
+    g_uploaded[device][p] = true;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// mesh object
+// ---------------------------------------------------------------------------
+struct QpCache {
+    int storage = -1;
+    bool valid = false;
+    void *buf = nullptr;
+    size_t bytes = 0;
+};
+
+struct hx_mesh {
+    hx_ctx *ctx = nullptr;
+    int p = 0, g = 1, n_elem = 0;
+    int64_t n_nodes = 0, n_qp = 0, n_geo = 0;
+    int structured = 0, nx = 0, ny = 0, nz = 0;
+    int law = 0;
+    hx::MatParams mat{};
+    int32_t *d_dof_conn = nullptr;
+    uint8_t *d_dmask = nullptr;
+    int64_t *d_cidx = nullptr;
+    int64_t n_constrained = 0;
+    double *d_geo_nodes = nullptr;
+    int32_t *d_geo_conn = nullptr;
+    double *d_geo64 = nullptr;
+    float *d_geo32 = nullptr;
+    double *d_fibH64 = nullptr;
+    float *d_fibH32 = nullptr;
+    double *d_fibM = nullptr;
+    QpCache cache[2];
+    int variant[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    // workspace (allocated on first use)
+    std::vector<void *> ws;
+    void *w_cheb_d[2] = {nullptr, nullptr}, *w_cheb_Kx[2] = {nullptr, nullptr};
+    void *w_stage_in = nullptr, *w_stage_out = nullptr;
+    double *w_cg = nullptr;   // r z zold p Ap dinv (FP64)
+    float *w_cg32 = nullptr;  // r32 z32 dinv32
+    cudaStream_t solve_stream = nullptr;
+    hx::CgScalars *d_sc = nullptr;
+    double *d_dots = nullptr, *d_partial = nullptr;
+    double *h_pinned = nullptr;
+};
+
+namespace {
+
+hx_status fail(hx_ctx *ctx, hx_status st, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return st;
+}
+
+hx_status cuda_fail(hx_ctx *ctx, cudaError_t e, const char *where) {
+    return fail(ctx, HX_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define HX_CUDA(ctx, call)                                           \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);   \
+    } while (0)
+
+hx::MeshView view(const hx_mesh *m, int prec) {
+    hx::MeshView v{};
+    v.p = m->p;
+    v.n_elem = m->n_elem;
+    v.n_nodes = m->n_nodes;
+    v.n_qp = m->n_qp;
+    v.structured = m->structured;
+    v.nx = m->nx;
+    v.ny = m->ny;
+    v.nz = m->nz;
+    v.Nx = (int64_t)m->nx * m->p + 1;
+    v.Ny = (int64_t)m->ny * m->p + 1;
+    v.dof_conn = m->d_dof_conn;
+    v.geo = prec == HX_FP64 ? (const void *)m->d_geo64 : (const void *)m->d_geo32;
+    v.geo64 = m->d_geo64;
+    v.qp = m->cache[prec].buf;
+    v.uk = m->cache[prec].buf;
+    v.nf = m->cache[prec].storage >= 0 ? hx::qp_fields(m->law, m->cache[prec].storage) : 0;
+    v.dmask = m->n_constrained ? m->d_dmask : nullptr;
+    v.fibH = prec == HX_FP64 ? (const void *)m->d_fibH64 : (const void *)m->d_fibH32;
+    v.fibH64 = m->d_fibH64;
+    v.fibM = m->d_fibM;
+    v.err = m->ctx->d_flags;
+    v.mat = m->mat;
+    v.law = m->law;
+    return v;
+}
+
+size_t prec_size(int prec) { return prec == HX_FP64 ? 8 : 4; }
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t n) {
+    return cudaMalloc((void **)p, n * sizeof(T) + 16);
+}
+
+void dfree(void *p) {
+    if (p) cudaFree(p);
+}
+
+bool bad_prec(int prec) { return prec != HX_FP64 && prec != HX_FP32; }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+extern "C" {
+
+hx_status hx_create(hx_ctx **ctx, int device, void *cuda_stream) {
+    if (!ctx) return HX_ERR_ARG;
+    *ctx = nullptr;
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || device < 0 || device >= ndev) return HX_ERR_CUDA;
+    e = cudaSetDevice(device);
+    if (e != cudaSuccess) return HX_ERR_CUDA;
+    hx_ctx *c = new hx_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    e = cudaMalloc((void **)&c->d_flags, 2 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_flags, 0, 2 * sizeof(int));
+    if (e != cudaSuccess) {
+        delete c;
+        return HX_ERR_CUDA;
+    }
+    *ctx = c;
+    return HX_OK;
+}
+
+void hx_destroy(hx_ctx *ctx) {
+    if (!ctx) return;
+    dfree(ctx->d_flags);
+    delete ctx;
+}
+
+hx_status hx_set_stream(hx_ctx *ctx, void *cuda_stream) {
+    if (!ctx) return HX_ERR_ARG;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return HX_OK;
+}
+
+const char *hx_last_error(hx_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+uint64_t hx_launch_count(hx_ctx *ctx, int32_t reset) {
+    if (!ctx) return 0;
+    const uint64_t v = ctx->launches;
+    if (reset) ctx->launches = 0;
+    return v;
+}
+
+hx_status hx_sync(hx_ctx *ctx, int timeout_ms) {
+    if (!ctx) return HX_ERR_ARG;
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        cudaError_t q = cudaStreamQuery(ctx->stream);
+        if (q == cudaSuccess) break;
+        if (q != cudaErrorNotReady) return cuda_fail(ctx, q, "hx_sync");
+        if (timeout_ms >= 0) {
+            const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(std::chrono::steady_clock::now() - t0).count();
+            if (ms > timeout_ms) return fail(ctx, HX_ERR_TIMEOUT, "hx_sync: stream still busy after the time limit");
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    int flags[2] = {0, 0};
+    HX_CUDA(ctx, cudaMemcpy(flags, ctx->d_flags, sizeof flags, cudaMemcpyDeviceToHost));
+    if (flags[0] || flags[1]) {
+        HX_CUDA(ctx, cudaMemset(ctx->d_flags, 0, 2 * sizeof(int)));
+        if (flags[1]) return fail(ctx, HX_ERR_NAN, "NaN met in a quadrature-point state");
+        return fail(ctx, HX_ERR_NONINVERTIBLE, "J <= 0 or det J0 <= 0 at a quadrature point");
+    }
+    return HX_OK;
+}
+
+hx_status hx_fibre_dispersion(double a, double b, double H[3]) {
+    if (!H || !(a >= 0.0) || !(b > 0.0)) return HX_ERR_ARG;
+    const double H33 = 1.0 / (4.0 * b) - std::exp(-2.0 * b) / (std::sqrt(2.0 * M_PI * b) * std::erf(std::sqrt(2.0 * b)));
+    const double r = std::cyl_bessel_i(1.0, a) / std::cyl_bessel_i(0.0, a);
+    H[0] = 0.5 * (1.0 - H33) * (1.0 + r);
+    H[1] = 0.5 * (1.0 - H33) * (1.0 - r);
+    H[2] = H33;
+    return HX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// mesh setup
+// ---------------------------------------------------------------------------
+void hx_destroy_mesh(hx_mesh *m) {
+    if (!m) return;
+    cudaStreamSynchronize(m->ctx ? m->ctx->stream : nullptr);
+    void *ptrs[] = {m->d_dof_conn, m->d_dmask, m->d_cidx, m->d_geo_nodes, m->d_geo_conn, m->d_geo64, m->d_geo32,
+                    m->d_fibH64, m->d_fibH32, m->d_fibM, m->cache[0].buf, m->cache[1].buf, m->w_cheb_d[0],
+                    m->w_cheb_d[1], m->w_cheb_Kx[0], m->w_cheb_Kx[1], m->w_stage_in, m->w_stage_out, m->w_cg,
+                    m->w_cg32, m->d_sc, m->d_dots, m->d_partial};
+    for (void *p : ptrs) dfree(p);
+    if (m->h_pinned) cudaFreeHost(m->h_pinned);
+    if (m->solve_stream) cudaStreamDestroy(m->solve_stream);
+    delete m;
+}
+
+hx_status hx_setup_mesh(hx_ctx *ctx, const hx_mesh_desc *d, const hx_material *mat, hx_mesh **out) {
+    if (!ctx || !d || !mat || !out) return fail(ctx, HX_ERR_ARG, "hx_setup_mesh: null argument");
+    *out = nullptr;
+    if (d->p < HX_PMIN || d->p > HX_PMAX) return fail(ctx, HX_ERR_UNSUPPORTED, "hx_setup_mesh: degree outside 1..6");
+    if (d->geo_degree != 1 && d->geo_degree != 2) return fail(ctx, HX_ERR_ARG, "hx_setup_mesh: geo_degree must be 1 or 2");
+    if (d->n_elem < 0 || d->n_nodes <= 0 || d->n_geo_nodes <= 0 || !d->geo_nodes || !d->geo_conn)
+        return fail(ctx, HX_ERR_ARG, "hx_setup_mesh: empty or missing geometry");
+    if (mat->law < HX_CNH || mat->law > HX_FIBER) return fail(ctx, HX_ERR_ARG, "hx_setup_mesh: unknown law");
+    if (mat->law == HX_FIBER && !d->fibre_frames && d->n_elem > 0)
+        return fail(ctx, HX_ERR_ARG, "hx_setup_mesh: fibre law needs per-element fibre frames");
+    const int p = d->p, n = p + 1, nq = n * n * n, g = d->geo_degree, ngg = (g + 1) * (g + 1) * (g + 1);
+    int structured = 0;
+    if (!d->dof_conn) {
+        if (d->nx <= 0 || d->ny <= 0 || d->nz <= 0 || (int64_t)d->nx * d->ny * d->nz != d->n_elem)
+            return fail(ctx, HX_ERR_ARG, "hx_setup_mesh: structured box needs nx*ny*nz == n_elem");
+        if (((int64_t)d->nx * p + 1) * ((int64_t)d->ny * p + 1) * ((int64_t)d->nz * p + 1) != d->n_nodes)
+            return fail(ctx, HX_ERR_ARG, "hx_setup_mesh: n_nodes does not match the structured box");
+        structured = 1;
+    } else {
+        for (int64_t i = 0; i < (int64_t)d->n_elem * nq; ++i)
+            if (d->dof_conn[i] < 0 || d->dof_conn[i] >= d->n_nodes)
+                return fail(ctx, HX_ERR_ARG, "hx_setup_mesh: dof_conn entry out of range");
+    }
+    for (int64_t i = 0; i < (int64_t)d->n_elem * ngg; ++i)
+        if (d->geo_conn[i] < 0 || d->geo_conn[i] >= d->n_geo_nodes)
+            return fail(ctx, HX_ERR_ARG, "hx_setup_mesh: geo_conn entry out of range");
+    if ((int64_t)d->n_elem * nq >= ((int64_t)1 << 31) * 8)
+        return fail(ctx, HX_ERR_ARG, "hx_setup_mesh: mesh too large");
+
+    HX_CUDA(ctx, cudaSetDevice(ctx->device));
+    HX_CUDA(ctx, ensure_tables(ctx->device, p));
+
+    hx_mesh *m = new hx_mesh();
+    m->ctx = ctx;
+    m->p = p;
+    m->g = g;
+    m->n_elem = d->n_elem;
+    m->n_nodes = d->n_nodes;
+    m->n_qp = (int64_t)d->n_elem * nq;
+    m->n_geo = d->n_geo_nodes;
+    m->structured = structured;
+    m->nx = d->nx;
+    m->ny = d->ny;
+    m->nz = d->nz;
+    m->law = mat->law;
+    m->mat = hx::MatParams{mat->mu, mat->lambda, mat->kappa, mat->k1, mat->k2};
+    auto bail = [&](hx_status st) {
+        hx_destroy_mesh(m);
+        return st;
+    };
+#define HX_MCUDA(call)                                                  \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return bail(cuda_fail(ctx, e_, #call));  \
+    } while (0)
+    cudaStream_t s = ctx->stream;
+    const int64_t ne = d->n_elem;
+    if (!structured && ne > 0) {
+        HX_MCUDA(dalloc(&m->d_dof_conn, ne * nq));
+        HX_MCUDA(cudaMemcpy(m->d_dof_conn, d->dof_conn, sizeof(int32_t) * ne * nq, cudaMemcpyHostToDevice));
+    }
+    HX_MCUDA(dalloc(&m->d_geo_nodes, 3 * d->n_geo_nodes));
+    HX_MCUDA(cudaMemcpy(m->d_geo_nodes, d->geo_nodes, sizeof(double) * 3 * d->n_geo_nodes, cudaMemcpyHostToDevice));
+    HX_MCUDA(dalloc(&m->d_geo_conn, ne * ngg));
+    if (ne > 0)
+        HX_MCUDA(cudaMemcpy(m->d_geo_conn, d->geo_conn, sizeof(int32_t) * ne * ngg, cudaMemcpyHostToDevice));
+    // Dirichlet mask and the list of constrained DoFs
+    if (d->dirichlet) {
+        std::vector<int64_t> idx;
+        for (int64_t i = 0; i < 3 * d->n_nodes; ++i)
+            if (d->dirichlet[i]) idx.push_back(i);
+        m->n_constrained = (int64_t)idx.size();
+        if (m->n_constrained) {
+            HX_MCUDA(dalloc(&m->d_dmask, 3 * d->n_nodes));
+            HX_MCUDA(cudaMemcpy(m->d_dmask, d->dirichlet, 3 * d->n_nodes, cudaMemcpyHostToDevice));
+            HX_MCUDA(dalloc(&m->d_cidx, idx.size()));
+            HX_MCUDA(cudaMemcpy(m->d_cidx, idx.data(), sizeof(int64_t) * idx.size(), cudaMemcpyHostToDevice));
+        }
+    }
+    // fibre families per element: M1 and H_i = sum_k H_kk M_k (x) M_k (Sec. 3)
+    {
+        double Hd[3] = {0, 0, 0};
+        if (mat->law == HX_FIBER) {
+            if (hx_fibre_dispersion(mat->a, mat->b, Hd) != HX_OK)
+                return bail(fail(ctx, HX_ERR_ARG, "hx_setup_mesh: invalid dispersion (a, b)"));
+        }
+        std::vector<double> fh(12 * (size_t)std::max<int64_t>(ne, 1), 0.0), fm(6 * (size_t)std::max<int64_t>(ne, 1), 0.0);
+        std::vector<float> fh32(fh.size(), 0.0f);
+        if (mat->law == HX_FIBER) {
+            for (int64_t e = 0; e < ne; ++e) {
+                const double *E1 = d->fibre_frames + 9 * e, *E2 = E1 + 3, *E3 = E1 + 6;
+                for (int f = 0; f < 2; ++f) {
+                    const double ph = f == 0 ? mat->phi : -mat->phi;
+                    const double c = std::cos(ph), sn = std::sin(ph);
+                    double M[3][3];
+                    for (int k = 0; k < 3; ++k) {
+                        M[0][k] = c * E1[k] + sn * E2[k];
+                        M[1][k] = -sn * E1[k] + c * E2[k];
+                        M[2][k] = E3[k];
+                    }
+                    const int pairs[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+                    for (int k = 0; k < 6; ++k) {
+                        const int i = pairs[k][0], j = pairs[k][1];
+                        double v = 0.0;
+                        for (int a = 0; a < 3; ++a) v += Hd[a] * M[a][i] * M[a][j];
+                        fh[(size_t)(6 * f + k) * ne + e] = v;
+                    }
+                    for (int k = 0; k < 3; ++k) fm[(size_t)(3 * f + k) * ne + e] = M[0][k];
+                }
+            }
+            for (size_t i = 0; i < fh.size(); ++i) fh32[i] = (float)fh[i];
+        }
+        HX_MCUDA(dalloc(&m->d_fibH64, fh.size()));
+        HX_MCUDA(dalloc(&m->d_fibH32, fh.size()));
+        HX_MCUDA(dalloc(&m->d_fibM, fm.size()));
+        HX_MCUDA(cudaMemcpy(m->d_fibH64, fh.data(), sizeof(double) * fh.size(), cudaMemcpyHostToDevice));
+        HX_MCUDA(cudaMemcpy(m->d_fibH32, fh32.data(), sizeof(float) * fh.size(), cudaMemcpyHostToDevice));
+        HX_MCUDA(cudaMemcpy(m->d_fibM, fm.data(), sizeof(double) * fm.size(), cudaMemcpyHostToDevice));
+    }
+    // geometry at the quadrature points
+    HX_MCUDA(dalloc(&m->d_geo64, 10 * (size_t)m->n_qp));
+    HX_MCUDA(dalloc(&m->d_geo32, 10 * (size_t)m->n_qp));
+    HX_MCUDA(cudaMemsetAsync(ctx->d_flags, 0, 2 * sizeof(int), s));
+    {
+        const hx::MeshView v = view(m, HX_FP64);
+        HX_MCUDA(hx::prec_ops(p, HX_FP64)->geometry(v, m->d_geo_nodes, m->d_geo_conn, g, m->d_geo64, m->d_geo32, s));
+        ctx->launches++;
+    }
+    HX_MCUDA(cudaStreamSynchronize(s));
+    int flags[2];
+    HX_MCUDA(cudaMemcpy(flags, ctx->d_flags, sizeof flags, cudaMemcpyDeviceToHost));
+    if (flags[0]) {
+        HX_MCUDA(cudaMemset(ctx->d_flags, 0, 2 * sizeof(int)));
+        return bail(fail(ctx, HX_ERR_NONINVERTIBLE, "hx_setup_mesh: det J0 <= 0 at a quadrature point"));
+    }
+#undef HX_MCUDA
+    *out = m;
+    return HX_OK;
+}
+
+hx_status hx_mesh_info(const hx_mesh *m, int64_t *n_nodes, int64_t *n_elem, int64_t *n_qp) {
+    if (!m) return HX_ERR_ARG;
+    if (n_nodes) *n_nodes = m->n_nodes;
+    if (n_elem) *n_elem = m->n_elem;
+    if (n_qp) *n_qp = m->n_qp;
+    return HX_OK;
+}
+
+hx_status hx_node_coords(hx_mesh *m, double *X_dev) {
+    if (!m || !X_dev) return HX_ERR_ARG;
+    hx_ctx *ctx = m->ctx;
+    const hx::MeshView v = view(m, HX_FP64);
+    HX_CUDA(ctx, hx::prec_ops(m->p, HX_FP64)->node_coords(v, m->d_geo_nodes, m->d_geo_conn, m->g, X_dev, ctx->stream));
+    ctx->launches++;
+    return HX_OK;
+}
+
+hx_status hx_apply_bytes(const hx_mesh *m, int32_t storage, int32_t prec, double *bytes) {
+    if (!m || !bytes || bad_prec(prec) || storage < 0 || storage > 2) return HX_ERR_ARG;
+    const double s = (double)prec_size(prec);
+    double b = 2.0 * 3.0 * m->n_nodes * s;    // read du, write out
+    b += 10.0 * m->n_qp * s;                  // J0^-1, JxW
+    if (storage == HX_RECOMPUTE)
+        b += 3.0 * m->n_nodes * s;            // u_k
+    else
+        b += (double)hx::qp_fields(m->law, storage) * m->n_qp * s;
+    if (!m->structured) b += 4.0 * m->n_qp;   // connectivity (one int per node slot)
+    *bytes = b;
+    return HX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// hot path
+// ---------------------------------------------------------------------------
+hx_status hx_precompute_qp(hx_mesh *m, const double *u_dev, int32_t store_prec, int32_t storage) {
+    if (!m || !u_dev || bad_prec(store_prec) || storage < HX_RECOMPUTE || storage > HX_CACHE_TENSORS)
+        return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_precompute_qp: bad argument");
+    hx_ctx *ctx = m->ctx;
+    QpCache &c = m->cache[store_prec];
+    const size_t bytes = storage == HX_RECOMPUTE ? 3 * (size_t)m->n_nodes * prec_size(store_prec)
+                                                 : (size_t)hx::qp_fields(m->law, storage) * m->n_qp * prec_size(store_prec);
+    if (c.bytes != bytes) {
+        dfree(c.buf);
+        c.buf = nullptr;
+        c.bytes = 0;
+        HX_CUDA(ctx, cudaMalloc(&c.buf, bytes + 16));
+        c.bytes = bytes;
+    }
+    c.storage = storage;
+    c.valid = false;
+    const hx::MeshView v = view(m, store_prec);
+    HX_CUDA(ctx, hx::prec_ops(m->p, store_prec)->precompute(v, storage, u_dev, c.buf, ctx->stream));
+    ctx->launches += storage == HX_RECOMPUTE ? 2 : 1;
+    c.valid = true;
+    return HX_OK;
+}
+
+static hx_status apply_dev(hx_mesh *m, const void *du, void *out, int prec) {
+    hx_ctx *ctx = m->ctx;
+    const QpCache &c = m->cache[prec];
+    if (!c.valid) return fail(ctx, HX_ERR_NOT_READY, "hx_tangent_apply: no quadrature-point data at this precision (call hx_precompute_qp)");
+    HX_CUDA(ctx, cudaMemsetAsync(out, 0, 3 * (size_t)m->n_nodes * prec_size(prec), ctx->stream));
+    const hx::MeshView v = view(m, prec);
+    HX_CUDA(ctx, hx::prec_ops(m->p, prec)->apply(v, c.storage, du, out, ctx->stream, m->variant[prec][c.storage]));
+    ctx->launches++;
+    if (m->n_constrained) {
+        HX_CUDA(ctx, hx::copy_idx(m->d_cidx, m->n_constrained, du, out, prec, ctx->stream));
+        ctx->launches++;
+    }
+    return HX_OK;
+}
+
+hx_status hx_tangent_apply(hx_mesh *m, const void *du_dev, void *out_dev, int32_t prec) {
+    if (!m || !du_dev || !out_dev || bad_prec(prec) || du_dev == out_dev)
+        return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_tangent_apply: bad argument");
+    return apply_dev(m, du_dev, out_dev, prec);
+}
+
+hx_status hx_tangent_apply_host(hx_mesh *m, const void *du_host, void *out_host, int32_t prec) {
+    if (!m || !du_host || !out_host || bad_prec(prec))
+        return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_tangent_apply_host: bad argument");
+    hx_ctx *ctx = m->ctx;
+    const size_t bytes = 3 * (size_t)m->n_nodes * prec_size(prec);
+    if (!m->w_stage_in) {
+        HX_CUDA(ctx, cudaMalloc(&m->w_stage_in, 3 * (size_t)m->n_nodes * 8 + 16));
+        HX_CUDA(ctx, cudaMalloc(&m->w_stage_out, 3 * (size_t)m->n_nodes * 8 + 16));
+    }
+    HX_CUDA(ctx, cudaMemcpyAsync(m->w_stage_in, du_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    hx_status st = apply_dev(m, m->w_stage_in, m->w_stage_out, prec);
+    if (st != HX_OK) return st;
+    HX_CUDA(ctx, cudaMemcpyAsync(out_host, m->w_stage_out, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    HX_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return HX_OK;
+}
+
+hx_status hx_residual(hx_mesh *m, const void *u_dev, void *r_dev, int32_t prec) {
+    if (!m || !u_dev || !r_dev || bad_prec(prec) || u_dev == r_dev)
+        return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_residual: bad argument");
+    hx_ctx *ctx = m->ctx;
+    HX_CUDA(ctx, cudaMemsetAsync(r_dev, 0, 3 * (size_t)m->n_nodes * prec_size(prec), ctx->stream));
+    const hx::MeshView v = view(m, prec);
+    HX_CUDA(ctx, hx::prec_ops(m->p, prec)->residual(v, u_dev, r_dev, ctx->stream));
+    ctx->launches++;
+    return HX_OK;
+}
+
+hx_status hx_diagonal(hx_mesh *m, void *diag_dev, int32_t prec) {
+    if (!m || !diag_dev || bad_prec(prec)) return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_diagonal: bad argument");
+    hx_ctx *ctx = m->ctx;
+    const QpCache &c = m->cache[prec];
+    if (!c.valid) return fail(ctx, HX_ERR_NOT_READY, "hx_diagonal: no quadrature-point data at this precision");
+    HX_CUDA(ctx, cudaMemsetAsync(diag_dev, 0, 3 * (size_t)m->n_nodes * prec_size(prec), ctx->stream));
+    const hx::MeshView v = view(m, prec);
+    HX_CUDA(ctx, hx::prec_ops(m->p, prec)->diagonal(v, c.storage, diag_dev, ctx->stream));
+    ctx->launches++;
+    if (m->n_constrained) {
+        HX_CUDA(ctx, hx::set_idx(m->d_cidx, m->n_constrained, 1.0, diag_dev, prec, ctx->stream));
+        ctx->launches++;
+    }
+    return HX_OK;
+}
+
+static hx_status ensure_cheb_ws(hx_mesh *m, int prec) {
+    if (!m->w_cheb_d[prec]) {
+        const size_t b = 3 * (size_t)m->n_nodes * prec_size(prec) + 16;
+        HX_CUDA(m->ctx, cudaMalloc(&m->w_cheb_d[prec], b));
+        HX_CUDA(m->ctx, cudaMalloc(&m->w_cheb_Kx[prec], b));
+    }
+    return HX_OK;
+}
+
+static hx_status cheb_run(hx_mesh *m, const void *rhs, void *x, const void *dinv, int degree, double lmax,
+                          double range, int zero_initial, int prec) {
+    hx_ctx *ctx = m->ctx;
+    hx_status st = ensure_cheb_ws(m, prec);
+    if (st != HX_OK) return st;
+    const double a = lmax / range, b = lmax;
+    const double theta = 0.5 * (b + a), delta = 0.5 * (b - a);
+    const int64_t n = 3 * m->n_nodes;
+    double rho_prev = 0.0;
+    for (int k = 0; k < degree; ++k) {
+        const void *Kx = nullptr;
+        if (!(k == 0 && zero_initial)) {
+            st = apply_dev(m, x, m->w_cheb_Kx[prec], prec);
+            if (st != HX_OK) return st;
+            Kx = m->w_cheb_Kx[prec];
+        }
+        double cd, cr, rho;
+        if (k == 0) {
+            rho = delta / theta;
+            cd = 0.0;
+            cr = 1.0 / theta;
+        } else {
+            rho = 1.0 / (2.0 * theta / delta - rho_prev);
+            cd = rho * rho_prev;
+            cr = 2.0 * rho / delta;
+        }
+        HX_CUDA(ctx, hx::cheb_update(n, rhs, Kx, dinv, m->w_cheb_d[prec], x, cd, cr, k == 0, prec, ctx->stream));
+        ctx->launches++;
+        rho_prev = rho;
+    }
+    return HX_OK;
+}
+
+hx_status hx_chebyshev_smooth(hx_mesh *m, const void *rhs_dev, void *x_dev, const void *inv_diag_dev, int32_t degree,
+                              double lambda_max, double smoothing_range, int32_t zero_initial, int32_t prec) {
+    if (!m || !rhs_dev || !x_dev || !inv_diag_dev || bad_prec(prec) || degree < 0 || !(lambda_max > 0.0) ||
+        !(smoothing_range > 1.0))
+        return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_chebyshev_smooth: bad argument");
+    return cheb_run(m, rhs_dev, x_dev, inv_diag_dev, degree, lambda_max, smoothing_range, zero_initial, prec);
+}
+
+static hx_status ensure_cg_ws(hx_mesh *m) {
+    hx_ctx *ctx = m->ctx;
+    if (m->w_cg) return HX_OK;
+    const size_t n = 3 * (size_t)m->n_nodes;
+    HX_CUDA(ctx, cudaMalloc((void **)&m->w_cg, 6 * n * sizeof(double) + 64));
+    HX_CUDA(ctx, cudaMalloc((void **)&m->w_cg32, 3 * n * sizeof(float) + 64));
+    HX_CUDA(ctx, cudaMalloc((void **)&m->d_sc, sizeof(hx::CgScalars)));
+    HX_CUDA(ctx, cudaMalloc((void **)&m->d_dots, 8 * sizeof(double)));
+    HX_CUDA(ctx, cudaMalloc((void **)&m->d_partial, 3 * hx::RED_BLOCKS * sizeof(double)));
+    HX_CUDA(ctx, cudaHostAlloc((void **)&m->h_pinned, 8 * sizeof(double), cudaHostAllocDefault));
+    return HX_OK;
+}
+
+hx_status hx_estimate_lambda_max(hx_mesh *m, const double *inv_diag_dev, int32_t iters, uint64_t seed, double *out) {
+    if (!m || !inv_diag_dev || !out || iters < 1) return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_estimate_lambda_max: bad argument");
+    hx_ctx *ctx = m->ctx;
+    hx_status st = ensure_cg_ws(m);
+    if (st != HX_OK) return st;
+    const int64_t n = 3 * m->n_nodes;
+    double *v = m->w_cg, *y = m->w_cg + n, *w = m->w_cg + 2 * n;
+    cudaStream_t s = ctx->stream;
+    HX_CUDA(ctx, hx::random_vec(n, seed, w, s));
+    HX_CUDA(ctx, hx::dots(n, 1, w, w, nullptr, nullptr, nullptr, nullptr, m->d_partial, m->d_dots, s));
+    HX_CUDA(ctx, hx::normalize(n, m->d_dots, w, v, s));
+    for (int it = 0; it < iters; ++it) {
+        st = apply_dev(m, v, y, HX_FP64);
+        if (st != HX_OK) return st;
+        HX_CUDA(ctx, hx::scale(n, inv_diag_dev, y, w, s));
+        HX_CUDA(ctx, hx::dots(n, 1, w, w, nullptr, nullptr, nullptr, nullptr, m->d_partial, m->d_dots, s));
+        HX_CUDA(ctx, hx::normalize(n, m->d_dots, w, v, s));
+        ctx->launches += 5;
+    }
+    double nrm2 = 0.0;
+    HX_CUDA(ctx, cudaMemcpyAsync(&nrm2, m->d_dots, sizeof(double), cudaMemcpyDeviceToHost, s));
+    HX_CUDA(ctx, cudaStreamSynchronize(s));
+    *out = std::sqrt(nrm2);
+    return HX_OK;
+}
+
+// Preconditioner z = M r: Chebyshev(degree)-Jacobi from zero in precision pp
+// (degree 0 = plain Jacobi), FP64 in and out.
+static hx_status cg_precond(hx_mesh *m, int pp, int degree, double lmax, double range, const double *r, double *z,
+                            const void *dinv, bool r32_ready) {
+    hx_ctx *ctx = m->ctx;
+    const int64_t n = 3 * m->n_nodes;
+    cudaStream_t s = ctx->stream;
+    float *r32 = m->w_cg32, *z32 = m->w_cg32 + n;
+    if (pp == HX_FP32) {
+        if (!r32_ready) HX_CUDA(ctx, hx::to_f32(n, r, r32, s));
+        if (degree == 0) {
+            HX_CUDA(ctx, hx::cheb_update(n, r32, nullptr, dinv, m->w_cheb_d[pp], z32, 0.0, 1.0, 1, pp, s));
+        } else {
+            hx_status st = cheb_run(m, r32, z32, dinv, degree, lmax, range, 1, pp);
+            if (st != HX_OK) return st;
+        }
+        HX_CUDA(ctx, hx::to_f64(n, z32, z, s));
+        ctx->launches += 2;
+    } else {
+        if (degree == 0) {
+            HX_CUDA(ctx, hx::cheb_update(n, r, nullptr, dinv, m->w_cheb_d[pp], z, 0.0, 1.0, 1, pp, s));
+        } else {
+            hx_status st = cheb_run(m, r, z, dinv, degree, lmax, range, 1, pp);
+            if (st != HX_OK) return st;
+        }
+    }
+    return HX_OK;
+}
+
+hx_status hx_cg_solve(hx_mesh *m, const double *rhs, double *x, double tol, int32_t max_iter, const hx_cg_options *opt,
+                      int32_t *iters, double *rel_residual) {
+    if (!m || !rhs || !x || !opt || max_iter < 0 || !(tol > 0.0) || bad_prec(opt->precond_prec) || opt->degree < 0 ||
+        (opt->degree > 0 && (!(opt->lambda_max > 0.0) || !(opt->smoothing_range > 1.0))))
+        return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_cg_solve: bad argument");
+    hx_ctx *ctx = m->ctx;
+    if (!m->cache[HX_FP64].valid || !m->cache[opt->precond_prec].valid)
+        return fail(ctx, HX_ERR_NOT_READY, "hx_cg_solve: quadrature-point data missing (FP64 and preconditioner precision)");
+    hx_status st = ensure_cg_ws(m);
+    if (st != HX_OK) return st;
+    const int pp = opt->precond_prec;
+    st = ensure_cheb_ws(m, pp);
+    if (st != HX_OK) return st;
+    if (!m->solve_stream) HX_CUDA(ctx, cudaStreamCreateWithFlags(&m->solve_stream, cudaStreamNonBlocking));
+    // run the solve on a private (capturable) stream ordered after the caller's stream
+    cudaStream_t user = ctx->stream;
+    cudaEvent_t ev;
+    HX_CUDA(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    HX_CUDA(ctx, cudaEventRecord(ev, user));
+    HX_CUDA(ctx, cudaStreamWaitEvent(m->solve_stream, ev, 0));
+    ctx->stream = m->solve_stream;
+    struct Restore {
+        hx_ctx *c;
+        cudaStream_t u;
+        cudaEvent_t e;
+        ~Restore() {
+            cudaEventRecord(e, c->stream);
+            cudaStreamWaitEvent(u, e, 0);
+            c->stream = u;
+            cudaEventDestroy(e);
+        }
+    } restore{ctx, user, ev};
+    cudaStream_t s = ctx->stream;
+
+    const int64_t n = 3 * m->n_nodes;
+    double *r = m->w_cg, *z = r + n, *zold = r + 2 * n, *p = r + 3 * n, *Ap = r + 4 * n, *dinv64 = r + 5 * n;
+    float *dinv32 = m->w_cg32 + 2 * n;
+    void *dinv = pp == HX_FP64 ? (void *)dinv64 : (void *)dinv32;
+    // Jacobi: inverse diagonal of the preconditioner's operator (its own precision)
+    st = hx_diagonal(m, dinv, pp);
+    if (st != HX_OK) return st;
+    HX_CUDA(ctx, hx::invert(n, dinv, dinv, pp, s));
+    // r = b - K x ; z = M r ; p = zold = z
+    st = apply_dev(m, x, Ap, HX_FP64);
+    if (st != HX_OK) return st;
+    HX_CUDA(ctx, hx::sub(n, rhs, Ap, r, s));
+    st = cg_precond(m, pp, opt->degree, opt->lambda_max, opt->smoothing_range, r, z, dinv, false);
+    if (st != HX_OK) return st;
+    HX_CUDA(ctx, cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    HX_CUDA(ctx, cudaMemcpyAsync(zold, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    HX_CUDA(ctx, hx::dots(n, 3, r, z, r, r, rhs, rhs, m->d_partial, m->d_dots, s));
+    double h3[3];
+    HX_CUDA(ctx, cudaMemcpyAsync(h3, m->d_dots, sizeof h3, cudaMemcpyDeviceToHost, s));
+    HX_CUDA(ctx, cudaStreamSynchronize(s));
+    const double bnorm = std::sqrt(h3[2]);
+    hx::CgScalars sc0{};
+    sc0.rz = h3[0];
+    sc0.rr = h3[1];
+    HX_CUDA(ctx, cudaMemcpyAsync(m->d_sc, &sc0, sizeof sc0, cudaMemcpyHostToDevice, s));
+    HX_CUDA(ctx, cudaStreamSynchronize(s));
+    ctx->launches += 8;
+    if (bnorm == 0.0) {
+        HX_CUDA(ctx, cudaMemsetAsync(x, 0, n * sizeof(double), s));
+        if (iters) *iters = 0;
+        if (rel_residual) *rel_residual = 0.0;
+        return HX_OK;
+    }
+
+    auto body = [&]() -> hx_status {
+        hx_status b = apply_dev(m, p, Ap, HX_FP64);
+        if (b != HX_OK) return b;
+        HX_CUDA(ctx, hx::dots(n, 1, p, Ap, nullptr, nullptr, nullptr, nullptr, m->d_partial, &m->d_sc->pAp, s));
+        HX_CUDA(ctx, hx::cg_alpha(m->d_sc, s));
+        HX_CUDA(ctx, hx::cg_xr(n, m->d_sc, p, Ap, x, r, pp == HX_FP32 ? m->w_cg32 : nullptr, s));
+        b = cg_precond(m, pp, opt->degree, opt->lambda_max, opt->smoothing_range, r, z, dinv, true);
+        if (b != HX_OK) return b;
+        HX_CUDA(ctx, hx::dots(n, 3, r, z, r, zold, r, r, m->d_partial, m->d_dots, s));
+        HX_CUDA(ctx, hx::cg_beta(m->d_sc, m->d_dots, s));
+        HX_CUDA(ctx, hx::cg_p(n, m->d_sc, z, p, zold, s));
+        HX_CUDA(ctx, cudaMemcpyAsync(m->h_pinned, m->d_sc, sizeof(hx::CgScalars), cudaMemcpyDeviceToHost, s));
+        ctx->launches += 8;
+        return HX_OK;
+    };
+
+    cudaGraphExec_t exec = nullptr;
+    if (opt->use_graph) {
+        cudaGraph_t graph = nullptr;
+        HX_CUDA(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        hx_status b = body();
+        cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        if (b != HX_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return b;
+        }
+        if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaStreamEndCapture");
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaGraphInstantiate");
+    }
+    struct ExecGuard {
+        cudaGraphExec_t e;
+        ~ExecGuard() {
+            if (e) cudaGraphExecDestroy(e);
+        }
+    } eg{exec};
+    int it = 0;
+    double rel = std::sqrt(sc0.rr) / bnorm;
+    bool bad = false;
+    while (it < max_iter && rel > tol) {
+        if (exec) {
+            HX_CUDA(ctx, cudaGraphLaunch(exec, s));
+            ctx->launches += 8;
+        } else {
+            st = body();
+            if (st != HX_OK) return st;
+        }
+        HX_CUDA(ctx, cudaStreamSynchronize(s));
+        const hx::CgScalars *hs = (const hx::CgScalars *)m->h_pinned;
+        ++it;
+        if (hs->bad) {
+            bad = true;
+            break;
+        }
+        rel = std::sqrt(hs->rr) / bnorm;
+    }
+    // true residual at exit
+    st = apply_dev(m, x, Ap, HX_FP64);
+    if (st != HX_OK) return st;
+    HX_CUDA(ctx, hx::sub(n, rhs, Ap, r, s));
+    HX_CUDA(ctx, hx::dots(n, 1, r, r, nullptr, nullptr, nullptr, nullptr, m->d_partial, m->d_dots, s));
+    double rr = 0.0;
+    HX_CUDA(ctx, cudaMemcpyAsync(&rr, m->d_dots, sizeof rr, cudaMemcpyDeviceToHost, s));
+    HX_CUDA(ctx, cudaStreamSynchronize(s));
+    const double true_rel = std::sqrt(rr) / bnorm;
+    if (iters) *iters = it;
+    if (rel_residual) *rel_residual = true_rel;
+    if (bad || !(true_rel == true_rel)) return fail(ctx, HX_ERR_NAN, "hx_cg_solve: breakdown (NaN or non-positive curvature)");
+    if (true_rel > tol) return fail(ctx, HX_ERR_NOT_CONVERGED, "hx_cg_solve: tolerance not reached");
+    return HX_OK;
+}
+
+hx_status hx_measure_fma_peak(hx_ctx *ctx, int32_t prec, double *flops) {
+    if (!ctx || !flops || bad_prec(prec)) return HX_ERR_ARG;
+    HX_CUDA(ctx, cudaSetDevice(ctx->device));
+    HX_CUDA(ctx, hx::fma_probe(prec, ctx->sm_count, flops));
+    return HX_OK;
+}
+
+// batches: not built yet
+hx_status hx_batch_create(hx_ctx *ctx, hx_mesh *const *meshes, int32_t n_meshes, hx_batch **batch) {
+    (void)meshes;
+    (void)n_meshes;
+    if (batch) *batch = nullptr;
+    return fail(ctx, HX_ERR_UNSUPPORTED, "hx_batch_create: not built yet");
+}
+void hx_batch_destroy(hx_batch *batch) { (void)batch; }
+hx_status hx_batch_tangent_apply(hx_batch *batch, const void *const *du_dev, void *const *out_dev, int32_t prec) {
+    (void)batch;
+    (void)du_dev;
+    (void)out_dev;
+    (void)prec;
+    return HX_ERR_UNSUPPORTED;
+}
+
+}  // extern "C"

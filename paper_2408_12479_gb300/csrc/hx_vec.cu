@@ -1,0 +1,305 @@
+// hx_vec.cu -- vector kernels of the solver layer: constrained-row fix-ups,
+// the Chebyshev-Jacobi update, deterministic dot products, the CG scalar
+// recurrences (all scalars stay on the device so that one CG iteration can be
+// captured as a CUDA graph), precision conversions, a seeded random vector,
+// and the FMA-throughput probe used for the ALU roofline.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hx_vec.h"
+
+namespace hx {
+namespace {
+
+constexpr int VB = 256;  // threads per block for vector kernels
+
+inline int grid_for(int64_t n, int cap = 4096) {
+    int64_t g = (n + VB - 1) / VB;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+template <typename T>
+__global__ void k_copy_idx(const int64_t *__restrict__ idx, int64_t n, const T *__restrict__ src, T *__restrict__ dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[idx[i]] = src[idx[i]];
+}
+
+template <typename T>
+__global__ void k_set_idx(const int64_t *__restrict__ idx, int64_t n, T val, T *__restrict__ dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[idx[i]] = val;
+}
+
+// Chebyshev step: r = D^-1 (rhs - Kx) (Kx null: r = D^-1 rhs), d = cd d + cr r, x += d
+template <typename T>
+__global__ void k_cheb(int64_t n, const T *__restrict__ rhs, const T *__restrict__ Kx, const T *__restrict__ dinv,
+                       T *__restrict__ d, T *__restrict__ x, T cd, T cr, int first) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const T r = dinv[i] * (Kx ? rhs[i] - Kx[i] : rhs[i]);
+        const T dn = first ? cr * r : cd * d[i] + cr * r;
+        d[i] = dn;
+        x[i] = (first && !Kx) ? dn : x[i] + dn;
+    }
+}
+
+// Block-partial sums of up to three dot products a_k . b_k (fixed grid of
+// RED_BLOCKS, fixed order => bitwise repeatable).
+__global__ void k_dots(int64_t n, int k, const double *a0, const double *b0, const double *a1, const double *b1,
+                       const double *a2, const double *b2, double *partial) {
+    __shared__ double sh[3][VB];
+    double s[3] = {0, 0, 0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        s[0] += a0[i] * b0[i];
+        if (k > 1) s[1] += a1[i] * b1[i];
+        if (k > 2) s[2] += a2[i] * b2[i];
+    }
+    for (int j = 0; j < 3; ++j) sh[j][threadIdx.x] = s[j];
+    __syncthreads();
+    for (int w = VB / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int j = 0; j < 3; ++j) sh[j][threadIdx.x] += sh[j][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int j = 0; j < 3; ++j) partial[j * RED_BLOCKS + blockIdx.x] = sh[j][0];
+}
+
+__global__ void k_dots_final(const double *partial, int k, double *out) {
+    __shared__ double sh[3][RED_BLOCKS];
+    for (int j = 0; j < 3; ++j)
+        for (int i = threadIdx.x; i < RED_BLOCKS; i += blockDim.x) sh[j][i] = partial[j * RED_BLOCKS + i];
+    __syncthreads();
+    for (int w = RED_BLOCKS / 2; w > 0; w >>= 1) {
+        for (int i = threadIdx.x; i < w; i += blockDim.x)
+            for (int j = 0; j < 3; ++j) sh[j][i] += sh[j][i + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int j = 0; j < k; ++j) out[j] = sh[j][0];
+}
+
+// CG scalars (Polak-Ribiere flexible CG)
+__global__ void k_cg_alpha(CgScalars *s) {
+    const double a = s->rz / s->pAp;
+    s->alpha = a;
+    if (!(a == a) || !(s->pAp > 0.0)) s->bad = 1;
+}
+
+__global__ void k_cg_xr(int64_t n, const CgScalars *__restrict__ s, const double *__restrict__ p,
+                        const double *__restrict__ Ap, double *__restrict__ x, double *__restrict__ r,
+                        float *__restrict__ r32) {
+    const double a = s->alpha;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        x[i] += a * p[i];
+        const double rn = r[i] - a * Ap[i];
+        r[i] = rn;
+        if (r32) r32[i] = (float)rn;
+    }
+}
+
+// dots: [0] r.z_new, [1] r.z_old, [2] r.r  -> beta, rz
+__global__ void k_cg_beta(CgScalars *s, const double *dots) {
+    const double rz_new = dots[0];
+    s->beta = (rz_new - dots[1]) / s->rz;
+    s->rz = rz_new;
+    s->rr = dots[2];
+    if (!(s->beta == s->beta)) s->bad = 1;
+}
+
+__global__ void k_cg_p(int64_t n, const CgScalars *__restrict__ s, const double *__restrict__ z,
+                       double *__restrict__ p, double *__restrict__ zold) {
+    const double b = s->beta;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double zi = z[i];
+        p[i] = zi + b * p[i];
+        zold[i] = zi;
+    }
+}
+
+template <typename TI, typename TO>
+__global__ void k_convert(int64_t n, const TI *__restrict__ a, TO *__restrict__ b) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (TO)a[i];
+}
+
+// y = a - b
+__global__ void k_sub(int64_t n, const double *__restrict__ a, const double *__restrict__ b, double *__restrict__ y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = a[i] - b[i];
+}
+
+// y = s * x with s = 1/sqrt(*nrm2) read on the device
+__global__ void k_normalize(int64_t n, const double *__restrict__ nrm2, const double *__restrict__ x, double *__restrict__ y) {
+    const double sc = 1.0 / sqrt(*nrm2);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = sc * x[i];
+}
+
+// y = dinv * x
+__global__ void k_scale(int64_t n, const double *__restrict__ dinv, const double *__restrict__ x, double *__restrict__ y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = dinv[i] * x[i];
+}
+
+// y = 1 / x
+template <typename T>
+__global__ void k_invert(int64_t n, const T *__restrict__ x, T *__restrict__ y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = T(1) / x[i];
+}
+
+// splitmix64-based uniform [-1, 1) per index (counter-based, seeded)
+__global__ void k_random(int64_t n, uint64_t seed, double *__restrict__ y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(i + 1);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        y[i] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+    }
+}
+
+// FMA probe: 8 independent dependent chains per thread
+template <typename T>
+__global__ void k_fma_probe(int iters, T *sink) {
+    T a0 = T(threadIdx.x) * T(1e-7), a1 = a0 + T(1), a2 = a0 + T(2), a3 = a0 + T(3);
+    T a4 = a0 + T(4), a5 = a0 + T(5), a6 = a0 + T(6), a7 = a0 + T(7);
+    const T m = T(0.999999), c = T(1e-7);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            a0 = fma(a0, m, c);
+            a1 = fma(a1, m, c);
+            a2 = fma(a2, m, c);
+            a3 = fma(a3, m, c);
+            a4 = fma(a4, m, c);
+            a5 = fma(a5, m, c);
+            a6 = fma(a6, m, c);
+            a7 = fma(a7, m, c);
+        }
+    }
+    const T s = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+    if (s == T(-12345)) sink[0] = s;
+}
+
+}  // namespace
+
+cudaError_t copy_idx(const int64_t *idx, int64_t n, const void *src, void *dst, int prec, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    if (prec == HX_FP64)
+        k_copy_idx<double><<<grid_for(n), VB, 0, s>>>(idx, n, (const double *)src, (double *)dst);
+    else
+        k_copy_idx<float><<<grid_for(n), VB, 0, s>>>(idx, n, (const float *)src, (float *)dst);
+    return cudaGetLastError();
+}
+
+cudaError_t set_idx(const int64_t *idx, int64_t n, double val, void *dst, int prec, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    if (prec == HX_FP64)
+        k_set_idx<double><<<grid_for(n), VB, 0, s>>>(idx, n, val, (double *)dst);
+    else
+        k_set_idx<float><<<grid_for(n), VB, 0, s>>>(idx, n, (float)val, (float *)dst);
+    return cudaGetLastError();
+}
+
+cudaError_t cheb_update(int64_t n, const void *rhs, const void *Kx, const void *dinv, void *d, void *x, double cd,
+                        double cr, int first, int prec, cudaStream_t s) {
+    if (prec == HX_FP64)
+        k_cheb<double><<<grid_for(n), VB, 0, s>>>(n, (const double *)rhs, (const double *)Kx, (const double *)dinv,
+                                                 (double *)d, (double *)x, cd, cr, first);
+    else
+        k_cheb<float><<<grid_for(n), VB, 0, s>>>(n, (const float *)rhs, (const float *)Kx, (const float *)dinv,
+                                                (float *)d, (float *)x, (float)cd, (float)cr, first);
+    return cudaGetLastError();
+}
+
+cudaError_t dots(int64_t n, int k, const double *a0, const double *b0, const double *a1, const double *b1,
+                 const double *a2, const double *b2, double *partial, double *out, cudaStream_t s) {
+    k_dots<<<RED_BLOCKS, VB, 0, s>>>(n, k, a0, b0, a1, b1, a2, b2, partial);
+    k_dots_final<<<1, 1024, 0, s>>>(partial, k, out);
+    return cudaGetLastError();
+}
+
+cudaError_t cg_alpha(CgScalars *sc, cudaStream_t s) {
+    k_cg_alpha<<<1, 1, 0, s>>>(sc);
+    return cudaGetLastError();
+}
+cudaError_t cg_xr(int64_t n, const CgScalars *sc, const double *p, const double *Ap, double *x, double *r, float *r32,
+                  cudaStream_t s) {
+    k_cg_xr<<<grid_for(n), VB, 0, s>>>(n, sc, p, Ap, x, r, r32);
+    return cudaGetLastError();
+}
+cudaError_t cg_beta(CgScalars *sc, const double *d, cudaStream_t s) {
+    k_cg_beta<<<1, 1, 0, s>>>(sc, d);
+    return cudaGetLastError();
+}
+cudaError_t cg_p(int64_t n, const CgScalars *sc, const double *z, double *p, double *zold, cudaStream_t s) {
+    k_cg_p<<<grid_for(n), VB, 0, s>>>(n, sc, z, p, zold);
+    return cudaGetLastError();
+}
+cudaError_t to_f32(int64_t n, const double *a, float *b, cudaStream_t s) {
+    k_convert<double, float><<<grid_for(n), VB, 0, s>>>(n, a, b);
+    return cudaGetLastError();
+}
+cudaError_t to_f64(int64_t n, const float *a, double *b, cudaStream_t s) {
+    k_convert<float, double><<<grid_for(n), VB, 0, s>>>(n, a, b);
+    return cudaGetLastError();
+}
+cudaError_t sub(int64_t n, const double *a, const double *b, double *y, cudaStream_t s) {
+    k_sub<<<grid_for(n), VB, 0, s>>>(n, a, b, y);
+    return cudaGetLastError();
+}
+cudaError_t normalize(int64_t n, const double *nrm2, const double *x, double *y, cudaStream_t s) {
+    k_normalize<<<grid_for(n), VB, 0, s>>>(n, nrm2, x, y);
+    return cudaGetLastError();
+}
+cudaError_t scale(int64_t n, const double *dinv, const double *x, double *y, cudaStream_t s) {
+    k_scale<<<grid_for(n), VB, 0, s>>>(n, dinv, x, y);
+    return cudaGetLastError();
+}
+cudaError_t invert(int64_t n, const void *x, void *y, int prec, cudaStream_t s) {
+    if (prec == HX_FP64)
+        k_invert<double><<<grid_for(n), VB, 0, s>>>(n, (const double *)x, (double *)y);
+    else
+        k_invert<float><<<grid_for(n), VB, 0, s>>>(n, (const float *)x, (float *)y);
+    return cudaGetLastError();
+}
+cudaError_t random_vec(int64_t n, uint64_t seed, double *y, cudaStream_t s) {
+    k_random<<<grid_for(n), VB, 0, s>>>(n, seed, y);
+    return cudaGetLastError();
+}
+
+cudaError_t fma_probe(int prec, int sm_count, double *flops) {
+    const int threads = 256, blocks = sm_count * 8, iters = 4096;
+    void *sink = nullptr;
+    cudaError_t e = cudaMalloc(&sink, 16);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(a);
+        if (prec == HX_FP64)
+            k_fma_probe<double><<<blocks, threads>>>(iters / 16, (double *)sink);
+        else
+            k_fma_probe<float><<<blocks, threads>>>(iters, (float *)sink);
+        cudaEventRecord(b);
+        e = cudaEventSynchronize(b);
+        if (e != cudaSuccess) break;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        if (rep > 0 && ms < best) best = ms;
+    }
+    if (e == cudaSuccess) e = cudaGetLastError();
+    const double its = prec == HX_FP64 ? (double)(iters / 16) : (double)iters;
+    *flops = 2.0 * 8.0 * 16.0 * its * threads * (double)blocks / (best * 1e-3);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(sink);
+    return e;
+}
+
+}  // namespace hx

@@ -1,0 +1,39 @@
+// Vector kernels of the solver layer (hx_vec.cu); asynchronous on stream s.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hx.h"
+
+namespace hx {
+
+constexpr int RED_BLOCKS = 512;  // fixed reduction grid (deterministic sums)
+
+struct CgScalars {
+    double rz, pAp, alpha, beta, rr;
+    int bad;
+};
+
+cudaError_t copy_idx(const int64_t *idx, int64_t n, const void *src, void *dst, int prec, cudaStream_t s);
+cudaError_t set_idx(const int64_t *idx, int64_t n, double val, void *dst, int prec, cudaStream_t s);
+cudaError_t cheb_update(int64_t n, const void *rhs, const void *Kx, const void *dinv, void *d, void *x, double cd,
+                        double cr, int first, int prec, cudaStream_t s);
+// out[j] = a_j . b_j for j < k (k <= 3); partial holds 3*RED_BLOCKS doubles
+cudaError_t dots(int64_t n, int k, const double *a0, const double *b0, const double *a1, const double *b1,
+                 const double *a2, const double *b2, double *partial, double *out, cudaStream_t s);
+cudaError_t cg_alpha(CgScalars *sc, cudaStream_t s);
+cudaError_t cg_xr(int64_t n, const CgScalars *sc, const double *p, const double *Ap, double *x, double *r, float *r32,
+                  cudaStream_t s);
+cudaError_t cg_beta(CgScalars *sc, const double *dots3, cudaStream_t s);
+cudaError_t cg_p(int64_t n, const CgScalars *sc, const double *z, double *p, double *zold, cudaStream_t s);
+cudaError_t to_f32(int64_t n, const double *a, float *b, cudaStream_t s);
+cudaError_t to_f64(int64_t n, const float *a, double *b, cudaStream_t s);
+cudaError_t sub(int64_t n, const double *a, const double *b, double *y, cudaStream_t s);
+cudaError_t normalize(int64_t n, const double *nrm2, const double *x, double *y, cudaStream_t s);
+cudaError_t scale(int64_t n, const double *dinv, const double *x, double *y, cudaStream_t s);
+cudaError_t invert(int64_t n, const void *x, void *y, int prec, cudaStream_t s);
+cudaError_t random_vec(int64_t n, uint64_t seed, double *y, cudaStream_t s);
+cudaError_t fma_probe(int prec, int sm_count, double *flops);
+
+}  // namespace hx
