@@ -900,7 +900,9 @@ hx_status hx_cg_solve(hx_mesh *m, const double *rhs, double *x, double tol, int3
     const double true_rel = std::sqrt(rr) / bnorm;
     if (iters) *iters = it;
     if (rel_residual) *rel_residual = true_rel;
-    if (bad || !(true_rel == true_rel)) return fail(ctx, HX_ERR_NAN, "hx_cg_solve: breakdown (NaN or non-positive curvature)");
+    if (bad || !(true_rel == true_rel))
+        return fail(ctx, HX_ERR_NAN, "hx_cg_solve: breakdown (NaN or non-positive curvature p.Kp <= 0) at iteration " +
+                                         std::to_string(it));
     if (true_rel > tol) return fail(ctx, HX_ERR_NOT_CONVERGED, "hx_cg_solve: tolerance not reached");
     return HX_OK;
 }

@@ -347,3 +347,45 @@ class Mesh:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# autograd: R(u) with the hand-written tangent as its backward
+# ---------------------------------------------------------------------------
+
+def _residual_function():
+    import torch
+
+    class HxResidual(torch.autograd.Function):
+        """r = R(u) (forward: hx_precompute_qp at u, then hx_residual); the
+        backward applies K(u)^T g = K(u) g with hx_tangent_apply (the tangent
+        of a hyperelastic residual is symmetric)."""
+
+        @staticmethod
+        def forward(ctx, u, mesh, storage):
+            prec = _prec_of(u)
+            u64 = u if u.dtype == torch.float64 else u.double()
+            mesh.precompute(u64.contiguous(), prec, storage)
+            r = torch.empty_like(u)
+            hx_residual(mesh.ctx, mesh.handle, u.contiguous(), r)
+            ctx.mesh = mesh
+            return r
+
+        @staticmethod
+        def backward(ctx, g):
+            out = torch.empty_like(g)
+            hx_tangent_apply(ctx.mesh.ctx, ctx.mesh.handle, g.contiguous(), out)
+            return out, None, None
+
+    return HxResidual
+
+
+_HxResidual = None
+
+
+def residual_autograd(mesh: Mesh, u, storage=HX_CACHE_TENSORS):
+    """Differentiable R(u) on a Mesh; u is a CUDA tensor (float64 or float32)."""
+    global _HxResidual
+    if _HxResidual is None:
+        _HxResidual = _residual_function()
+    return _HxResidual.apply(u, mesh, storage)
