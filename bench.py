@@ -105,6 +105,7 @@ def build_case(p, prec, storage, device, law="cNH", n=32):
     du = du64 if prec == hx.HX_FP64 else du64.float()
     G.precompute(u, prec, storage)
     out = torch.empty_like(du)
+    G.tune = hx.hx_autotune(G.ctx, G.handle, du, out, reps=5)
     return G, m, u, du, out
 
 
@@ -302,6 +303,7 @@ def main():
                     sweep.append({"p": pp, "prec": "f32" if pr else "f64", "storage": hx.STORAGE_NAMES[st],
                                   "n_dofs": ms_.n_dofs, "ms": round(t, 4),
                                   "gdofs": round(ms_.n_dofs / (t * 1e-3) / 1e9, 3),
+                                  "tile_variant": Gs.tune[0], "variant_ms": [round(x, 4) for x in Gs.tune[1]],
                                   "hbm_frac": round(b / (t * 1e-3) / 1e9 / hbm_peak, 4)})
                     Gs.close()
                     del us, dus, outs
@@ -322,7 +324,8 @@ def main():
                        "p": p, "n_dofs": n_dofs, "law": "cNH", "prec": args.prec,
                        "storage": hx.STORAGE_NAMES[storage],
                        "l2": "inputs larger than L2 (vectors + qp data %.0f MB > 129 MB)" % (bytes_alg / 1e6),
-                       "per_storage_ms": {k: round(v, 4) for k, v in per_storage.items() if v}},
+                       "per_storage_ms": {k: round(v, 4) for k, v in per_storage.items() if v},
+                       "tile_variant": G.tune[0], "variant_ms": [round(x, 4) for x in G.tune[1]]},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                          "frac": round(achieved / hbm_peak, 4), "traffic": None,
                          "peak_kind": peak_kind, "bytes_per_launch": bytes_alg},

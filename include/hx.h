@@ -167,6 +167,16 @@ hx_status hx_tangent_apply(hx_mesh *mesh, const void *du_dev, void *out_dev, int
  * the host. Uses a device staging buffer owned by the mesh. */
 hx_status hx_tangent_apply_host(hx_mesh *mesh, const void *du_host, void *out_host, int32_t prec);
 
+/* Autotuner: time every compiled variant of the tangent apply for the mesh's
+ * current cache at `prec` -- tile shape (elements per CTA: default, half,
+ * double) times L2 prefetch of the next tile's quadrature-point data (on for
+ * variants 0-2, off for 3-5) -- keep the fastest for later hx_tangent_apply
+ * calls, and return its index and the six mean times in ms (a variant that
+ * cannot launch reports a negative time). Uses du_dev/out_dev as scratch
+ * vectors of the mesh's size; synchronous. */
+hx_status hx_autotune(hx_mesh *mesh, int32_t prec, const void *du_dev, void *out_dev, int32_t reps,
+                      int32_t *best_variant, double times_ms[6]);
+
 /* diag(K(u_k)), constrained entries 1 (needed by the Jacobi smoother,
  * Sec. 5); sum-factorized from the per-qp tangent blocks. */
 hx_status hx_diagonal(hx_mesh *mesh, void *diag_dev, int32_t prec);

@@ -268,6 +268,8 @@ hx::MeshView view(const hx_mesh *m, int prec) {
     v.fibM = m->d_fibM;
     v.err = m->ctx->d_flags;
     v.mat = m->mat;
+    v.matf = hx::MatParamsF{(float)m->mat.mu, (float)m->mat.lambda, (float)m->mat.kappa, (float)m->mat.k1,
+                            (float)m->mat.k2};
     v.law = m->law;
     return v;
 }
@@ -600,6 +602,54 @@ hx_status hx_tangent_apply(hx_mesh *m, const void *du_dev, void *out_dev, int32_
     if (!m || !du_dev || !out_dev || bad_prec(prec) || du_dev == out_dev)
         return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_tangent_apply: bad argument");
     return apply_dev(m, du_dev, out_dev, prec);
+}
+
+hx_status hx_autotune(hx_mesh *m, int32_t prec, const void *du_dev, void *out_dev, int32_t reps, int32_t *best_variant,
+                      double times_ms[3]) {
+    if (!m || bad_prec(prec) || !du_dev || !out_dev || du_dev == out_dev || reps < 1)
+        return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_autotune: bad argument");
+    hx_ctx *ctx = m->ctx;
+    const QpCache &c = m->cache[prec];
+    if (!c.valid) return fail(ctx, HX_ERR_NOT_READY, "hx_autotune: no quadrature-point data at this precision");
+    const hx::PrecOps *ops = hx::prec_ops(m->p, prec);
+    const hx::MeshView v = view(m, prec);
+    cudaEvent_t a, b;
+    HX_CUDA(ctx, cudaEventCreate(&a));
+    HX_CUDA(ctx, cudaEventCreate(&b));
+    int best = 0;
+    double tbest = 1e30, t[8];
+    for (int var = 0; var < ops->n_variants && var < 8; ++var) {
+        cudaError_t e = ops->apply(v, c.storage, du_dev, out_dev, ctx->stream, var);  // warm-up
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            t[var] = -1.0;
+            continue;
+        }
+        cudaEventRecord(a, ctx->stream);
+        for (int r = 0; r < reps; ++r) ops->apply(v, c.storage, du_dev, out_dev, ctx->stream, var);
+        cudaEventRecord(b, ctx->stream);
+        e = cudaEventSynchronize(b);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            return cuda_fail(ctx, e, "hx_autotune");
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, b);
+        t[var] = ms / reps;
+        ctx->launches += reps + 1;
+        if (t[var] < tbest) {
+            tbest = t[var];
+            best = var;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    m->variant[prec][c.storage] = best;
+    if (best_variant) *best_variant = best;
+    if (times_ms)
+        for (int i = 0; i < 6; ++i) times_ms[i] = i < ops->n_variants ? t[i] : -1.0;
+    return HX_OK;
 }
 
 hx_status hx_tangent_apply_host(hx_mesh *m, const void *du_host, void *out_host, int32_t prec) {

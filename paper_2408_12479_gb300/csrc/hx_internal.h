@@ -21,7 +21,7 @@ enum Op { OP_APPLY = 0, OP_RESIDUAL = 1, OP_PRECOMPUTE = 2, OP_DIAG = 3 };
 // Number of stored quadrature-point fields per (law, storage); the layout of
 // each field set is documented in hx_kernels.cuh next to the code that
 // writes it.
-inline int qp_fields(int law, int storage) {
+__host__ __device__ constexpr int qp_fields(int law, int storage) {
     if (storage == HX_RECOMPUTE) return 0;
     if (storage == HX_CACHE_F) return law == HX_CNH ? 11 : (law == HX_INH ? 14 : 18);
     return law == HX_CNH ? 31 : (law == HX_INH ? 33 : 35);
@@ -29,6 +29,9 @@ inline int qp_fields(int law, int storage) {
 
 struct MatParams {
     double mu, lambda, kappa, k1, k2;
+};
+struct MatParamsF {
+    float mu, lambda, kappa, k1, k2;
 };
 
 // Plain-old-data view of a device mesh, passed by value to every kernel.
@@ -49,7 +52,9 @@ struct MeshView {
     const double *fibM;          // [6][n_elem] mean fibre directions M1 of families 4, 6
     int *err;                    // device error flags: [0] non-invertible, [1] NaN
     MatParams mat;
+    MatParamsF matf;  // the same constants rounded once to FP32
     int law;
+    int l2pf;         // apply kernel: prefetch the next tile's qp data into L2
 };
 
 // Kernel entry points provided by each (degree, precision) translation unit

@@ -44,7 +44,36 @@ constexpr int NQ = N * N * N;      // nodes (and Gauss points) per element
 constexpr int R = (N % 2) ? N : N + 1;  // padded row length (odd)
 constexpr int SZ = R * N * N;      // padded cube size
 
+// Column-layout cubes of the apply kernel: element e of an array starts at
+// e*ES, component c at +c*CZ, point (i,j,k) at +i + j*RS + k*PS. The strides
+// were chosen by an exhaustive bank-conflict search over the three line-sweep
+// access patterns of a warp (lanes spanning several elements), separately for
+// 4- and 8-byte words.
+struct ColLayout {
+    int RS, PS, CZ, ES;
+};
+constexpr ColLayout col_layout() {
+    if (sizeof(Real) == 4) {
+        return N == 2 ? ColLayout{2, 5, 10, 36}
+             : N == 3 ? ColLayout{3, 14, 42, 137}
+             : N == 4 ? ColLayout{4, 19, 76, 240}
+             : N == 5 ? ColLayout{5, 25, 125, 377}
+             : N == 6 ? ColLayout{7, 42, 252, 764}
+                      : ColLayout{7, 56, 392, 1201};
+    }
+    return N == 2 ? ColLayout{2, 5, 10, 36}
+         : N == 3 ? ColLayout{3, 18, 54, 169}
+         : N == 4 ? ColLayout{4, 19, 76, 228}
+         : N == 5 ? ColLayout{5, 25, 125, 377}
+         : N == 6 ? ColLayout{9, 54, 324, 980}
+                  : ColLayout{7, 52, 364, 1105};
+}
+constexpr int CRS = col_layout().RS, CPS = col_layout().PS, CCZ = col_layout().CZ, CES = col_layout().ES;
+
 enum { TB = 0, TD = 1, TG = 2 };
+
+// threads per CTA of the column-layout apply: n^2 threads per element
+__host__ __device__ constexpr int col_threads(int epb) { return (epb * NN + 31) / 32 * 32; }
 
 // threads per CTA for a tile of epb elements: one thread per sweep line
 __host__ __device__ constexpr int threads_for(int epb) {
@@ -306,6 +335,19 @@ struct State {
     T Jm1;
 };
 
+// material constants in the compute precision (no per-point conversions)
+template <typename T>
+struct Mat {
+    T mu, lambda, kappa, k1, k2;
+};
+template <typename T>
+__device__ __forceinline__ Mat<T> mat_of(const hx::MeshView &m) {
+    if constexpr (std::is_same<T, double>::value)
+        return Mat<T>{m.mat.mu, m.mat.lambda, m.mat.kappa, m.mat.k1, m.mat.k2};
+    else
+        return Mat<T>{m.matf.mu, m.matf.lambda, m.matf.kappa, m.matf.k1, m.matf.k2};
+}
+
 template <typename T>
 __device__ __forceinline__ void load_fibH(const hx::MeshView &m, int e, State<T> &st) {
     const T *fh = std::is_same<T, double>::value ? (const T *)m.fibH64 : (const T *)m.fibH;
@@ -320,8 +362,8 @@ __device__ __forceinline__ void load_fibH(const hx::MeshView &m, int e, State<T>
 // on-the-fly paths); otherwise J^-2/3 = exp(-2/3 ln_{+1}(J-1)).
 template <typename T, int LAW, bool FAST>
 __device__ __forceinline__ void state_from_Hk(const hx::MeshView &m, int e, State<T> &st) {
-    const hx::MatParams &mp = m.mat;
-    const T mu = (T)mp.mu;
+    const Mat<T> mp = mat_of<T>(m);
+    const T mu = mp.mu;
     st.Jm1 = J_minus_1(st.Hk);
     const T J = T(1) + st.Jm1;
     st.invJ = T(1) / J;
@@ -331,29 +373,29 @@ __device__ __forceinline__ void state_from_Hk(const hx::MeshView &m, int e, Stat
     green_strain(st.Hk, E);
     st.lnJ = log1p_T(st.Jm1);  // ln J = ln_{+1}(J - 1)
     if constexpr (LAW == HX_CNH) {
-        const T lam = (T)mp.lambda;
+        const T lam = mp.lambda;
         stress_CiX(st.Ci, E, T(2) * mu, T(2) * lam * st.lnJ, st.S);
         st.al = T(2) * (mu - T(2) * lam * st.lnJ);
         st.be = T(2) * lam;
         st.ga = T(0);
         st.ph4 = st.ph6 = T(0);
     } else {
-        const T kap = (T)mp.kappa;
+        const T kap = mp.kappa;
         st.j23 = FAST ? fast_jpow(st.Jm1, 3) : exp_T(T(-2.0 / 3.0) * st.lnJ);
         const T trE = E[0] + E[1] + E[2];
         const T vol = T(0.5) * kap * st.Jm1 * (st.Jm1 + T(2));  // kappa/2 (J^2 - 1), stable
-        st.c1 = vol - mu / T(3) * st.j23 * (T(3) + T(2) * trE);
-        st.c2 = T(2) * mu / T(9) * st.j23 * (T(3) + T(2) * trE) + kap * J * J;
-        st.s0 = vol - T(2) * mu / T(3) * st.j23 * trE;
+        st.c1 = vol - mu * T(1.0 / 3.0) * st.j23 * (T(3) + T(2) * trE);
+        st.c2 = mu * T(2.0 / 9.0) * st.j23 * (T(3) + T(2) * trE) + kap * J * J;
+        st.s0 = vol - mu * T(2.0 / 3.0) * st.j23 * trE;
         stress_CiX(st.Ci, E, T(2) * mu * st.j23, st.s0, st.S);
         st.al = T(-2) * st.c1;
         st.be = st.c2;
-        st.ga = T(-2) * mu / T(3) * st.j23;
+        st.ga = mu * T(-2.0 / 3.0) * st.j23;
         st.ph4 = st.ph6 = T(0);
         st.sg4 = st.sg6 = T(0);
         if constexpr (LAW == HX_FIBER) {
             load_fibH(m, e, st);
-            const T k1 = (T)mp.k1, k2 = (T)mp.k2;
+            const T k1 = mp.k1, k2 = mp.k2;
 #pragma unroll
             for (int f = 0; f < 2; ++f) {
                 const T *Hf = f ? st.H6 : st.H4;
@@ -429,13 +471,11 @@ __device__ __forceinline__ void store_state(TS *qp, int64_t nq, int64_t g, const
     }
 }
 
-template <typename T, int LAW, int STORAGE>
-__device__ __forceinline__ void load_state(const hx::MeshView &m, int e, int64_t g, State<T> &st) {
-    const T *qp = (const T *)m.qp;
-    const int64_t nq = m.n_qp;
-    auto get = [&](int f) { return qp[(int64_t)f * nq + g]; };
-    const hx::MatParams &mp = m.mat;
-    const T mu = (T)mp.mu;
+// state of the cache strategies from the stored fields; get(f) returns field f
+template <typename T, int LAW, int STORAGE, typename Get>
+__device__ __forceinline__ void build_state(const hx::MeshView &m, int e, Get get, State<T> &st) {
+    const Mat<T> mp = mat_of<T>(m);
+    const T mu = mp.mu;
 #pragma unroll
     for (int k = 0; k < 9; ++k) st.Hk[k] = get(k);
     st.ph4 = st.ph6 = T(0);
@@ -446,7 +486,7 @@ __device__ __forceinline__ void load_state(const hx::MeshView &m, int e, int64_t
         T E[6];
         green_strain(st.Hk, E);
         if constexpr (LAW == HX_CNH) {
-            const T lam = (T)mp.lambda;
+            const T lam = mp.lambda;
             const T lnJ = get(10);
             stress_CiX(st.Ci, E, T(2) * mu, T(2) * lam * lnJ, st.S);
             st.al = T(2) * (mu - T(2) * lam * lnJ);
@@ -460,7 +500,7 @@ __device__ __forceinline__ void load_state(const hx::MeshView &m, int e, int64_t
             stress_CiX(st.Ci, E, T(2) * mu * j23, s0, st.S);
             st.al = T(-2) * st.c1;
             st.be = st.c2;
-            st.ga = T(-2) * mu / T(3) * j23;
+            st.ga = mu * T(-2.0 / 3.0) * j23;
             if constexpr (LAW == HX_FIBER) {
                 load_fibH(m, e, st);
                 const T sg4 = get(14), sg6 = get(15);
@@ -479,7 +519,7 @@ __device__ __forceinline__ void load_state(const hx::MeshView &m, int e, int64_t
         for (int k = 0; k < 6; ++k) st.S[k] = get(24 + k);
         st.al = get(30);
         if constexpr (LAW == HX_CNH) {
-            st.be = T(2) * (T)mp.lambda;
+            st.be = T(2) * mp.lambda;
             st.ga = T(0);
         } else {
             st.be = get(31);
@@ -491,6 +531,13 @@ __device__ __forceinline__ void load_state(const hx::MeshView &m, int e, int64_t
             }
         }
     }
+}
+
+template <typename T, int LAW, int STORAGE>
+__device__ __forceinline__ void load_state(const hx::MeshView &m, int e, int64_t g, State<T> &st) {
+    const T *qp = (const T *)m.qp;
+    const int64_t nq = m.n_qp;
+    build_state<T, LAW, STORAGE>(m, e, [&](int f) { return __ldcs(qp + (int64_t)f * nq + g); }, st);
 }
 
 // dP = H S + F D_uS[H] for a physical displacement-gradient direction H
@@ -557,8 +604,8 @@ template <typename T>
 __device__ __forceinline__ void load_geo(const hx::MeshView &m, int64_t g, T *Ji, T &JxW) {
     const T *geo = (const T *)m.geo;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) Ji[k] = geo[(int64_t)k * m.n_qp + g];
-    JxW = geo[(int64_t)9 * m.n_qp + g];
+    for (int k = 0; k < 9; ++k) Ji[k] = __ldcs(geo + (int64_t)k * m.n_qp + g);
+    JxW = __ldcs(geo + (int64_t)9 * m.n_qp + g);
 }
 
 // physical gradient H = G J0^-1 from the reference gradient G (G_{cd} = du_c/dxi_d)
@@ -591,60 +638,388 @@ __device__ __forceinline__ void flag_state(const hx::MeshView &m, double Jm1) {
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
-template <int EPB, int LAW, int STORAGE>
+// ---------------------------------------------------------------------------
+// column-layout building blocks of the apply kernel: every element has n^2
+// threads; thread (a0, a1) owns one line of each direction (x-line (j,k) =
+// (a0,a1), y-line (i,k), z-line (i,j)), and the z-line also carries the
+// quadrature-point column (a0, a1, *) through the material phase in registers
+// ---------------------------------------------------------------------------
+template <int DIR>
+__device__ __forceinline__ int line_off(int a0, int a1) {
+    if constexpr (DIR == 0) return a0 * CRS + a1 * CPS;
+    else if constexpr (DIR == 1) return a0 + a1 * CPS;
+    else return a0 + a1 * CRS;
+}
+template <int DIR>
+__device__ __forceinline__ constexpr int line_str() {
+    return DIR == 0 ? 1 : (DIR == 1 ? CRS : CPS);
+}
+template <int DIR>
+__device__ __forceinline__ void ld_line(const Real *p, Real *x) {
+#pragma unroll
+    for (int t = 0; t < N; ++t) x[t] = p[t * line_str<DIR>()];
+}
+template <int DIR>
+__device__ __forceinline__ void st_line(Real *p, const Real *y) {
+#pragma unroll
+    for (int t = 0; t < N; ++t) p[t * line_str<DIR>()] = y[t];
+}
+// y = M x (TR: y = M^T x) with a 1D table from constant memory
+template <int TAB, bool TR>
+__device__ __forceinline__ void mv(const Real *x, Real *y) {
+#pragma unroll
+    for (int o = 0; o < N; ++o) {
+        Real s = Real(0);
+#pragma unroll
+        for (int t = 0; t < N; ++t) s = fma(tab<TAB>(TR ? t * N + o : o * N + t), x[t], s);
+        y[o] = s;
+    }
+}
+
+// node numbering base of an element (structured box: lattice index of its
+// first node; otherwise the element index for the connectivity lookup)
+__device__ __forceinline__ int64_t elem_base(const hx::MeshView &m, int e) {
+    if (e >= m.n_elem) return 0;
+    if (m.structured) {
+        const int ex = e % m.nx;
+        const int t = e / m.nx;
+        const int ey = t % m.ny, ez = t / m.ny;
+        return (int64_t)ex * HX_P + m.Nx * ((int64_t)ey * HX_P + m.Ny * (int64_t)ez * HX_P);
+    }
+    return e;
+}
+__device__ __forceinline__ int64_t node_at(const hx::MeshView &m, int64_t base, int i, int j, int k) {
+    if (m.structured) return base + i + m.Nx * (j + m.Ny * (int64_t)k);
+    return m.dof_conn[base * NQ + i + N * (j + N * k)];
+}
+
+// L2 cache policies: the quadrature-point stream is read once per apply
+// (evict first); the DoF vectors are gathered and scattered by up to eight
+// elements each and should stay resident (evict last)
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes, uint64_t pol) {
+    asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(p), "r"(bytes), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ float ld_stream(const float *p, uint64_t pol) {
+    float v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double ld_stream(const double *p, uint64_t pol) {
+    double v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void red_add(float *p, float v, uint64_t pol) {
+    asm volatile("red.global.add.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void red_add(double *p, double v, uint64_t pol) {
+    asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
+}
+
+
+// Load the x-row (j = a0, k = a1) of element e of vector v into registers:
+// row[3*i + c] = v_c at node (i, a0, a1). In a structured box the row is 3*N
+// contiguous values; otherwise the N node ids come from the connectivity.
+// Constrained DoFs (mask) and elements past the end read zero.
+__device__ __forceinline__ void load_row(const hx::MeshView &m, int e, int64_t base, int a0, int a1,
+                                         const Real *__restrict__ v, bool mask, Real *row) {
+    if (e >= m.n_elem) {
+#pragma unroll
+        for (int t = 0; t < 3 * N; ++t) row[t] = Real(0);
+        return;
+    }
+    if (m.structured) {
+        const int64_t off = 3 * (base + m.Nx * (a0 + m.Ny * (int64_t)a1));
+        const Real *p = v + off;
+#pragma unroll
+        for (int t = 0; t < 3 * N; ++t) row[t] = p[t];
+        if (mask && m.dmask) {
+            const uint8_t *q = m.dmask + off;
+#pragma unroll
+            for (int t = 0; t < 3 * N; ++t)
+                if (q[t]) row[t] = Real(0);
+        }
+    } else {
+        const int32_t *cn = m.dof_conn + (int64_t)e * NQ + N * (a0 + N * a1);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const int64_t d = 3 * (int64_t)cn[i];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                row[3 * i + c] = v[d + c];
+                if (mask && m.dmask && m.dmask[d + c]) row[3 * i + c] = Real(0);
+            }
+        }
+    }
+}
+
+// forward sum factorization of an element whose x-rows are in the threads'
+// registers (row[3*i + c], x-line (a0, a1)): writes the x-, y- and
+// z-reference derivatives at the Gauss points to GXo, GYo, GZo. A and W are
+// scratch. The caller synchronises before the first call of a tile.
+__device__ __forceinline__ void col_forward(const Real *row, Real *A, Real *W, Real *GXo, Real *GYo, Real *GZo,
+                                            bool act, int eoff, int a0, int a1) {
+    Real x[N], y[N], z[N];
+    if (act) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) x[i] = row[3 * i + c];
+            mv<TB, false>(x, y);
+            st_line<0>(W + eoff + c * CCZ + line_off<0>(a0, a1), y);
+        }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int o = eoff + c * CCZ + line_off<1>(a0, a1);
+            ld_line<1>(W + o, x);
+            mv<TB, false>(x, y);
+            st_line<1>(A + o, y);
+        }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int o = eoff + c * CCZ + line_off<2>(a0, a1);
+            ld_line<2>(A + o, x);
+            mv<TB, false>(x, y);   // values at the Gauss points of this column
+            st_line<2>(W + o, y);
+            mv<TD, false>(y, z);
+            st_line<2>(GZo + o, z);
+        }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int o0 = eoff + c * CCZ + line_off<0>(a0, a1);
+            ld_line<0>(W + o0, x);
+            mv<TD, false>(x, y);
+            st_line<0>(GXo + o0, y);
+            const int o1 = eoff + c * CCZ + line_off<1>(a0, a1);
+            ld_line<1>(W + o1, x);
+            mv<TD, false>(x, y);
+            st_line<1>(GYo + o1, y);
+        }
+    }
+    __syncthreads();
+}
+
+
+
+// L2 prefetch of a tile's quadrature-point data (geometry + cache), one
+// contiguous chunk per field; skipped where a chunk is not 16-byte aligned
+template <int EPB, int STORAGE>
+__device__ __forceinline__ void prefetch_tile(const hx::MeshView &m, int tile) {
+    const int e0 = tile * EPB;
+    if (e0 >= m.n_elem) return;
+    const int cnt = min(EPB, m.n_elem - e0);
+    const unsigned bytes = (unsigned)(cnt * NQ * sizeof(Real));
+    const int nfc = STORAGE == HX_RECOMPUTE ? 0 : m.nf;
+    const int f = threadIdx.x;
+    if (f >= 10 + nfc || (bytes & 15u)) return;
+    const Real *p = f < 10 ? (const Real *)m.geo + (int64_t)f * m.n_qp + (int64_t)e0 * NQ
+                           : (const Real *)m.qp + (int64_t)(f - 10) * m.n_qp + (int64_t)e0 * NQ;
+    if (((uintptr_t)p & 15u) == 0) prefetch_l2(p, bytes, policy_evict_first());
+}
+
+template <int EPB, int STORAGE>
 struct ApplySmem {
-    static constexpr int cubes = (STORAGE == HX_RECOMPUTE ? 24 : 15) * EPB;
-    static constexpr size_t bytes = (size_t)cubes * SZ * sizeof(Real);
+    // U, W, GX, GY, GZ; recompute adds KX, KY, KZ
+    static constexpr int arrays = STORAGE == HX_RECOMPUTE ? 8 : 5;
+    static constexpr size_t bytes = (size_t)arrays * EPB * CES * sizeof(Real);
 };
 
-// out += K(u_k) du over all elements (out zeroed by the caller)
+// out += K(u_k) du over all elements (out zeroed by the caller). Persistent:
+// CTAs walk tiles of EPB elements with stride gridDim.x. Each thread loads
+// its element x-row of du (and u_k) straight into registers, one tile ahead.
 template <int EPB, int LAW, int STORAGE>
-__global__ void __launch_bounds__(threads_for(EPB)) k_apply(const hx::MeshView m, const Real *__restrict__ du, Real *__restrict__ out) {
+__global__ void __launch_bounds__(col_threads(EPB)) k_apply(const hx::MeshView m, const Real *__restrict__ du,
+                                                            Real *__restrict__ out, int ntiles) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Real *U = (Real *)smem_raw;
-    Real *W = U + 3 * EPB * SZ;
-    Real *G = W + 3 * EPB * SZ;
-    Real *Gk = G + 9 * EPB * SZ;
-    const int e0 = blockIdx.x * EPB;
-    constexpr int nc = 3 * EPB;
-    if constexpr (STORAGE == HX_RECOMPUTE) {
-        gather(m, e0, EPB, (const Real *)m.uk, U, false);
-        __syncthreads();
-        forward_grad(U, W, Gk, nc);
+    Real *W = U + EPB * CES;
+    Real *GX = W + EPB * CES;
+    Real *GY = GX + EPB * CES;
+    Real *GZ = GY + EPB * CES;
+    Real *KX = GZ + EPB * CES;  // recompute strategy: gradients of u_k
+    Real *KY = KX + EPB * CES;
+    Real *KZ = KY + EPB * CES;
+    const int t = threadIdx.x;
+    const int el = t / NN;
+    const int a = t - el * NN;
+    const int a0 = a % N, a1 = a / N;
+    const bool act = el < EPB;
+    const int eoff = (act ? el : 0) * CES;
+    const uint64_t pol_keep = policy_evict_last();
+    const uint64_t pol_stream = policy_evict_first();
+    constexpr bool RC = STORAGE == HX_RECOMPUTE;
+    Real rowd[3 * N], rowk[RC ? 3 * N : 1];
+    if (act && (int)blockIdx.x < ntiles) {
+        const int e1 = blockIdx.x * EPB + el;
+        const int64_t b1 = elem_base(m, e1);
+        load_row(m, e1, b1, a0, a1, du, true, rowd);
+        if constexpr (RC) load_row(m, e1, b1, a0, a1, (const Real *)m.uk, false, rowk);
     }
-    gather(m, e0, EPB, du, U, true);
-    __syncthreads();
-    forward_grad(U, W, G, nc);
-    for (int it = threadIdx.x; it < EPB * NQ; it += blockDim.x) {
-        const int el = it / NQ;
-        const int q = it - el * NQ;
-        const int e = e0 + el;
-        if (e >= m.n_elem) continue;
-        const int ci = cidx(q % N, (q / N) % N, q / NN);
-        const int64_t g = (int64_t)e * NQ + q;
-        Real Ji[9], JxW, Gr[9], H[9], dP[9], Q[9];
-        load_geo(m, g, Ji, JxW);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int e0 = tile * EPB;
+        const int ntile = tile + gridDim.x;
+        if (m.l2pf) prefetch_tile<EPB, STORAGE>(m, ntile);
+        // this tile's rows; the next tile's rows are requested now
+        Real cd[3 * N], ck[RC ? 3 * N : 1];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) Gr[k] = G[(el * 9 + k) * SZ + ci];
-        State<Real> st;
-        if constexpr (STORAGE == HX_RECOMPUTE) {
-            Real Gu[9];
+        for (int i = 0; i < 3 * N; ++i) cd[i] = rowd[i];
+        if constexpr (RC) {
 #pragma unroll
-            for (int k = 0; k < 9; ++k) Gu[k] = Gk[(el * 9 + k) * SZ + ci];
-            push_grad(Gu, Ji, st.Hk);
-            state_from_Hk<Real, LAW, (bool)HX_UNIT_F32>(m, e, st);
-        } else {
-            load_state<Real, LAW, STORAGE>(m, e, g, st);
+            for (int i = 0; i < 3 * N; ++i) ck[i] = rowk[i];
         }
-        push_grad(Gr, Ji, H);
-        tangent_dP<Real, LAW>(st, H, dP);
-        pull_flux(dP, Ji, JxW, Q);
+        if (act && ntile < ntiles) {
+            const int e1 = ntile * EPB + el;
+            const int64_t b1 = elem_base(m, e1);
+            load_row(m, e1, b1, a0, a1, du, true, rowd);
+            if constexpr (RC) load_row(m, e1, b1, a0, a1, (const Real *)m.uk, false, rowk);
+        }
+        __syncthreads();  // the previous tile is done with the shared arrays
+        const int e = e0 + el;
+        const bool valid = act && e < m.n_elem;
+        // quadrature-point phase: flat over the tile's EPB*NQ points (consecutive
+        // threads read consecutive points of every field: coalesced, no sector
+        // shared between iterations); the data of a thread's next point is
+        // requested one iteration ahead, the first before the forward sweeps
+        constexpr int NFC = STORAGE == HX_RECOMPUTE ? 0 : hx::qp_fields(LAW, STORAGE);
+        constexpr int NR = 10 + NFC;
+        constexpr int NT = col_threads(EPB);
+        const int nval = min(EPB, m.n_elem - e0) * NQ;  // valid points of this tile
+        const int64_t g0 = (int64_t)e0 * NQ;
+        Real rc[NR], rn[NR];
+        auto load_raw = [&](int q, Real *r) {
+            const Real *geo = (const Real *)m.geo + g0 + q;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) G[(el * 9 + k) * SZ + ci] = Q[k];
+            for (int f = 0; f < 10; ++f) r[f] = ld_stream(geo + (int64_t)f * m.n_qp, pol_stream);
+            if constexpr (NFC > 0) {
+                const Real *qp = (const Real *)m.qp + g0 + q;
+#pragma unroll
+                for (int f = 0; f < NFC; ++f) r[10 + f] = ld_stream(qp + (int64_t)f * m.n_qp, pol_stream);
+            }
+        };
+        if (t < nval) load_raw(t, rc);
+        if constexpr (RC) col_forward(ck, U, W, KX, KY, KZ, act, eoff, a0, a1);
+        col_forward(cd, U, W, GX, GY, GZ, act, eoff, a0, a1);
+#pragma unroll 1
+        for (int q = t; q < nval; q += NT) {
+            if (q + NT < nval) load_raw(q + NT, rn);
+            const int qel = q / NQ;
+            const int ql = q - qel * NQ;
+            const int pos = qel * CES + (ql % N) + ((ql / N) % N) * CRS + (ql / NN) * CPS;
+            Real Ji[9], Gr[9], H[9], dP[9], Q[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) Ji[k] = rc[k];
+            const Real JxW = rc[9];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                Gr[c * 3 + 0] = GX[pos + c * CCZ];
+                Gr[c * 3 + 1] = GY[pos + c * CCZ];
+                Gr[c * 3 + 2] = GZ[pos + c * CCZ];
+            }
+            State<Real> st;
+            if constexpr (STORAGE == HX_RECOMPUTE) {
+                Real Gu[9];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    Gu[c * 3 + 0] = KX[pos + c * CCZ];
+                    Gu[c * 3 + 1] = KY[pos + c * CCZ];
+                    Gu[c * 3 + 2] = KZ[pos + c * CCZ];
+                }
+                push_grad(Gu, Ji, st.Hk);
+                state_from_Hk<Real, LAW, (bool)HX_UNIT_F32>(m, e0 + qel, st);
+            } else {
+                build_state<Real, LAW, STORAGE>(m, e0 + qel, [&](int f) { return rc[10 + f]; }, st);
+            }
+            push_grad(Gr, Ji, H);
+            tangent_dP<Real, LAW>(st, H, dP);
+            pull_flux(dP, Ji, JxW, Q);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                GX[pos + c * CCZ] = Q[c * 3 + 0];
+                GY[pos + c * CCZ] = Q[c * 3 + 1];
+                GZ[pos + c * CCZ] = Q[c * 3 + 2];
+            }
+#pragma unroll
+            for (int f = 0; f < NR; ++f) rc[f] = rn[f];
+        }
+        __syncthreads();
+        Real x[N], y[N], w[N];
+        if (act) {  // in place: z-lines (qx, qy) GZ = Dz^T GZ, y-lines (qx, qz) GY = Dy^T GY
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int oz = eoff + c * CCZ + line_off<2>(a0, a1);
+                ld_line<2>(GZ + oz, x);
+                mv<TD, true>(x, y);
+                st_line<2>(GZ + oz, y);
+                const int oy = eoff + c * CCZ + line_off<1>(a0, a1);
+                ld_line<1>(GY + oy, x);
+                mv<TD, true>(x, y);
+                st_line<1>(GY + oy, y);
+            }
+        }
+        __syncthreads();
+        if (act) {  // x-lines (qy, qz): U = Bx^T (Dx^T Qx + GY + GZ)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int o = eoff + c * CCZ + line_off<0>(a0, a1);
+                ld_line<0>(GX + o, x);
+                mv<TD, true>(x, y);
+                ld_line<0>(GY + o, w);
+#pragma unroll
+                for (int k = 0; k < N; ++k) y[k] += w[k];
+                ld_line<0>(GZ + o, w);
+#pragma unroll
+                for (int k = 0; k < N; ++k) w[k] += y[k];
+                mv<TB, true>(w, y);
+                st_line<0>(U + o, y);
+            }
+        }
+        __syncthreads();
+        if (act) {  // y-lines (i, qz): W = By^T U
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int o = eoff + c * CCZ + line_off<1>(a0, a1);
+                ld_line<1>(U + o, x);
+                mv<TB, true>(x, y);
+                st_line<1>(W + o, y);
+            }
+        }
+        __syncthreads();
+        if (valid) {  // z-lines (i, j): r = Bz^T W, scattered from registers
+            const int64_t base = elem_base(m, e);
+            const bool msk = m.dmask != nullptr;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int o = eoff + c * CCZ + line_off<2>(a0, a1);
+                ld_line<2>(W + o, x);
+                mv<TB, true>(x, y);
+#pragma unroll
+                for (int k = 0; k < N; ++k) {
+                    const int64_t d = 3 * node_at(m, base, a0, a1, k) + c;
+                    if (!(msk && m.dmask[d])) red_add(out + d, y[k], pol_keep);
+                }
+            }
+        }
     }
-    __syncthreads();
-    backward_int(G, W, U, nc);
-    scatter_add(m, e0, EPB, U, out, true);
 }
 
 // r += R(u): state recomputed from u at every point, P = (I + Hk) S
@@ -943,7 +1318,9 @@ __global__ void k_convert_uk(const double *__restrict__ u, Real *__restrict__ uk
 constexpr int epb_default() {
     return N <= 3 ? 16 : (N == 4 ? 8 : (N == 5 ? 4 : 2));
 }
-constexpr int EPB_A = (sizeof(Real) == 4 && N >= 5) ? 2 * epb_default() : epb_default();
+// elements per CTA of the column-layout apply (n^2 threads each)
+constexpr int EPB_A = sizeof(Real) == 4 ? (N <= 2 ? 32 : (N == 3 ? 16 : (N <= 5 ? 8 : 4)))
+                                         : (N <= 2 ? 16 : (N == 3 ? 8 : (N <= 5 ? 4 : 2)));
 
 template <typename K>
 cudaError_t set_smem(K kern, size_t bytes) {
@@ -951,21 +1328,43 @@ cudaError_t set_smem(K kern, size_t bytes) {
     return cudaSuccess;
 }
 
+int sm_count() {
+    static int n = [] {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 1;
+    }();
+    return n;
+}
+
 template <int EPB, int LAW, int STORAGE>
 cudaError_t launch_apply_t(const hx::MeshView &m, const void *du, void *out, cudaStream_t s) {
     auto kern = k_apply<EPB, LAW, STORAGE>;
-    const size_t smem = ApplySmem<EPB, LAW, STORAGE>::bytes;
-    static cudaError_t attr = set_smem(kern, smem);
-    if (attr != cudaSuccess) return attr;
-    const int grid = (m.n_elem + EPB - 1) / EPB;
-    if (grid == 0) return cudaSuccess;
-    kern<<<grid, threads_for(EPB), smem, s>>>(m, (const Real *)du, (Real *)out);
+    constexpr size_t smem = ApplySmem<EPB, STORAGE>::bytes;
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    static int per_sm = [&] {
+        if (set_smem(kern, smem) != cudaSuccess) return 0;
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, col_threads(EPB), smem) != cudaSuccess) return 0;
+        return b;
+    }();
+    if (per_sm <= 0) return cudaErrorInvalidConfiguration;
+    const int ntiles = (m.n_elem + EPB - 1) / EPB;
+    if (ntiles == 0) return cudaSuccess;
+    const int grid = ntiles < per_sm * sm_count() ? ntiles : per_sm * sm_count();
+    kern<<<grid, col_threads(EPB), smem, s>>>(m, (const Real *)du, (Real *)out, ntiles);
     return cudaGetLastError();
 }
 
+// variants: tile shape (default, half, double elements per CTA) x L2
+// prefetch of the next tile's qp data (on for 0-2, off for 3-5)
 template <int LAW, int STORAGE>
-cudaError_t apply_variant(const hx::MeshView &m, const void *du, void *out, cudaStream_t s, int variant) {
-    switch (variant) {
+cudaError_t apply_variant(const hx::MeshView &m0, const void *du, void *out, cudaStream_t s, int variant) {
+    hx::MeshView m = m0;
+    m.l2pf = variant < 3;
+    switch (variant % 3) {
         case 1:
             return launch_apply_t<(EPB_A > 1 ? EPB_A / 2 : 1), LAW, STORAGE>(m, du, out, s);
         case 2:
@@ -1121,7 +1520,7 @@ extern "C++" const hx::PrecOps *HX_OPS_NAME() {
         op_apply,
         op_residual,
         op_diagonal,
-        3,
+        6,
     };
     return &ops;
 }

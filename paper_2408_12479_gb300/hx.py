@@ -33,7 +33,8 @@ EXPORTS = ["hx_create", "hx_destroy", "hx_set_stream", "hx_last_error", "hx_sync
            "hx_destroy_mesh", "hx_mesh_info", "hx_node_coords", "hx_apply_bytes", "hx_precompute_qp",
            "hx_residual", "hx_tangent_apply", "hx_tangent_apply_host", "hx_diagonal", "hx_chebyshev_smooth",
            "hx_estimate_lambda_max", "hx_cg_solve", "hx_fibre_dispersion", "hx_batch_create",
-           "hx_batch_destroy", "hx_batch_tangent_apply", "hx_measure_fma_peak", "hx_launch_count"]
+           "hx_batch_destroy", "hx_batch_tangent_apply", "hx_measure_fma_peak", "hx_launch_count",
+           "hx_autotune"]
 
 
 class HxError(RuntimeError):
@@ -98,6 +99,7 @@ def lib():
             "hx_batch_tangent_apply": (I32, [P, C.POINTER(P), C.POINTER(P), I32]),
             "hx_measure_fma_peak": (I32, [P, I32, C.POINTER(D)]),
             "hx_launch_count": (U64, [P, I32]),
+            "hx_autotune": (I32, [P, I32, P, P, I32, C.POINTER(I32), C.POINTER(D)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -269,6 +271,14 @@ def hx_cg_solve(ctx, mesh, rhs, x, tol, max_iter, degree, lambda_max, smoothing_
     if st not in (HX_OK, HX_ERR_NOT_CONVERGED):
         _check(st, ctx)
     return it.value, rel.value, st
+
+
+def hx_autotune(ctx, mesh, du, out, reps=10):
+    """Pick the fastest tile shape of the apply for the mesh's current cache."""
+    best = C.c_int32()
+    t = (C.c_double * 6)()
+    _check(lib().hx_autotune(mesh, _prec_of(du), _ptr(du), _ptr(out), int(reps), C.byref(best), t), ctx)
+    return best.value, list(t)
 
 
 def hx_measure_fma_peak(ctx, prec):

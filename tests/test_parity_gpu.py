@@ -291,3 +291,21 @@ def test_empty_mesh_gives_zero():
         G.sync(60000)
     finally:
         G.close()
+
+
+def test_autotune_keeps_results():
+    """Every tile shape the autotuner may pick computes the same operator."""
+    m = cases.small_cube(5, 4, "cNH", seed=121)
+    M, X, u = cases.state_for(m, "cNH", seed=122)
+    du = cuda(I.random_direction(m.n_dofs, 123), hx.HX_FP32)
+    G = hx.Mesh(m, cases.MATS["cNH"])
+    try:
+        G.precompute(cuda(u), hx.HX_FP32, hx.HX_CACHE_F)
+        out = torch.empty_like(du)
+        best, times = hx.hx_autotune(G.ctx, G.handle, du, out, reps=2)
+        assert best in range(6) and times[best] > 0
+        res = host(G.apply(du))
+        ref = O.apply(M, cases.oracle_material("cNH"), u, host(du))
+        assert rel_inf(res, ref) < 1e-5
+    finally:
+        G.close()
