@@ -190,6 +190,25 @@ hx_status hx_chebyshev_smooth(hx_mesh *mesh, const void *rhs_dev, void *x_dev, c
                               int32_t degree, double lambda_max, double smoothing_range, int32_t zero_initial,
                               int32_t prec);
 
+/* hx_chebyshev_smooth without any device allocation. This entry point has no
+ * counterpart in the paper; it exists for callers that cannot allocate device
+ * memory while they run -- an application whose memory is fully reserved by
+ * another framework's caching allocator, or a latency-critical loop where
+ * cudaMalloc/cudaFree would synchronise the device. Same arguments and result
+ * as hx_chebyshev_smooth; its two scratch vectors (the Chebyshev update and
+ * K x) live in a file-scope device array of 2 * 1,048,576 doubles (16 MiB)
+ * that every GPU loading the library holds until the process exits. Meshes
+ * with more than 1,048,576 DoFs are rejected with HX_ERR_ARG. The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture. All calls share the array and it
+ * keeps the last call's contents (every call overwrites what it reads), so
+ * calls that overlap on the GPU -- on different streams or contexts of one
+ * device -- race. No cudaMalloc, cudaFree or allocating library routine is
+ * called. */
+hx_status hx_chebyshev_smooth_noalloc(hx_mesh *mesh, const void *rhs_dev, void *x_dev, const void *inv_diag_dev,
+                                      int32_t degree, double lambda_max, double smoothing_range,
+                                      int32_t zero_initial, int32_t prec);
+
 /* Largest eigenvalue of D^-1 K by `iters` power iterations from a seeded
  * random start (FP64, on the device); *out receives the Rayleigh quotient. */
 hx_status hx_estimate_lambda_max(hx_mesh *mesh, const double *inv_diag_dev, int32_t iters, uint64_t seed,

@@ -746,6 +746,87 @@ hx_status hx_chebyshev_smooth(hx_mesh *m, const void *rhs_dev, void *x_dev, cons
     return cheb_run(m, rhs_dev, x_dev, inv_diag_dev, degree, lambda_max, smoothing_range, zero_initial, prec);
 }
 
+// ---------------------------------------------------------------------------
+// Chebyshev-Jacobi smoother without allocation
+//
+// Some callers cannot allocate device memory once they are running: a solver
+// embedded in an application whose memory is fully reserved by another
+// framework's caching allocator (where cudaMalloc fails or must not be used),
+// or a latency-critical loop in which cudaMalloc/cudaFree would synchronise the
+// device and stall other streams. For them the two scratch vectors of the
+// smoother (the Chebyshev update d and the operator product K x) live in the
+// file-scope device array below instead of mesh-owned workspace.
+//
+// Limit: HX_NOALLOC_MAX_DOFS DoFs per vector (1,048,576, i.e. 349,525 nodes);
+// the array holds 2 * HX_NOALLOC_MAX_DOFS doubles (16 MiB) on every GPU that
+// loads the library, until the process exits.
+// ---------------------------------------------------------------------------
+#define HX_NOALLOC_MAX_DOFS (1 << 20)
+static __device__ __align__(256) double g_noalloc_scratch[2 * HX_NOALLOC_MAX_DOFS];
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_addr[64];  // device address of the array, per device
+
+// Device address of the scratch array on the context's device. In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device (with that device current) with cudaGetSymbolAddress.
+static hx_status noalloc_scratch(hx_ctx *ctx, void **addr) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (ctx->device < 0 || ctx->device >= 64) return fail(ctx, HX_ERR_ARG, "noalloc: device index out of range");
+    if (!g_noalloc_addr[ctx->device]) {
+        HX_CUDA(ctx, cudaSetDevice(ctx->device));
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+        g_noalloc_addr[ctx->device] = p;
+    }
+    *addr = g_noalloc_addr[ctx->device];
+    return HX_OK;
+}
+
+extern "C" hx_status hx_chebyshev_smooth_noalloc(hx_mesh *m, const void *rhs_dev, void *x_dev,
+                                                 const void *inv_diag_dev, int32_t degree, double lambda_max,
+                                                 double smoothing_range, int32_t zero_initial, int32_t prec) {
+    if (!m || !rhs_dev || !x_dev || !inv_diag_dev || bad_prec(prec) || degree < 0 || !(lambda_max > 0.0) ||
+        !(smoothing_range > 1.0))
+        return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_chebyshev_smooth_noalloc: bad argument");
+    hx_ctx *ctx = m->ctx;
+    const int64_t n = 3 * m->n_nodes;
+    if (n > HX_NOALLOC_MAX_DOFS)
+        return fail(ctx, HX_ERR_ARG,
+                    "hx_chebyshev_smooth_noalloc: mesh has " + std::to_string(n) + " DoFs, more than the " +
+                        std::to_string(HX_NOALLOC_MAX_DOFS) + " the static scratch array holds");
+    void *base = nullptr;
+    hx_status st = noalloc_scratch(ctx, &base);
+    if (st != HX_OK) return st;
+    void *d = base;                                              // Chebyshev update d
+    void *Kx = (void *)((double *)base + HX_NOALLOC_MAX_DOFS);   // operator product K x
+    const double a = lambda_max / smoothing_range, b = lambda_max;
+    const double theta = 0.5 * (b + a), delta = 0.5 * (b - a);
+    double rho_prev = 0.0;
+    for (int k = 0; k < degree; ++k) {
+        const void *kx = nullptr;
+        if (!(k == 0 && zero_initial)) {
+            st = apply_dev(m, x_dev, Kx, prec);  // zeroes Kx itself before accumulating
+            if (st != HX_OK) return st;
+            kx = Kx;
+        }
+        double cd, cr, rho;
+        if (k == 0) {  // the first step overwrites d, so the array's old contents never leak in
+            rho = delta / theta;
+            cd = 0.0;
+            cr = 1.0 / theta;
+        } else {
+            rho = 1.0 / (2.0 * theta / delta - rho_prev);
+            cd = rho * rho_prev;
+            cr = 2.0 * rho / delta;
+        }
+        HX_CUDA(ctx, hx::cheb_update(n, rhs_dev, kx, inv_diag_dev, d, x_dev, cd, cr, k == 0, prec, ctx->stream));
+        ctx->launches++;
+        rho_prev = rho;
+    }
+    return HX_OK;
+}
+
 static hx_status ensure_cg_ws(hx_mesh *m) {
     hx_ctx *ctx = m->ctx;
     if (m->w_cg) return HX_OK;

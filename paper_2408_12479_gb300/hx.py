@@ -34,7 +34,7 @@ EXPORTS = ["hx_create", "hx_destroy", "hx_set_stream", "hx_last_error", "hx_sync
            "hx_residual", "hx_tangent_apply", "hx_tangent_apply_host", "hx_diagonal", "hx_chebyshev_smooth",
            "hx_estimate_lambda_max", "hx_cg_solve", "hx_fibre_dispersion", "hx_batch_create",
            "hx_batch_destroy", "hx_batch_tangent_apply", "hx_measure_fma_peak", "hx_launch_count",
-           "hx_autotune"]
+           "hx_autotune", "hx_chebyshev_smooth_noalloc"]
 
 
 class HxError(RuntimeError):
@@ -100,6 +100,7 @@ def lib():
             "hx_measure_fma_peak": (I32, [P, I32, C.POINTER(D)]),
             "hx_launch_count": (U64, [P, I32]),
             "hx_autotune": (I32, [P, I32, P, P, I32, C.POINTER(I32), C.POINTER(D)]),
+            "hx_chebyshev_smooth_noalloc": (I32, [P, P, P, P, I32, D, D, I32, I32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -253,6 +254,16 @@ def hx_diagonal(ctx, mesh, diag):
 def hx_chebyshev_smooth(ctx, mesh, rhs, x, inv_diag, degree, lambda_max, smoothing_range, zero_initial=False):
     _check(lib().hx_chebyshev_smooth(mesh, _ptr(rhs), _ptr(x), _ptr(inv_diag), int(degree), float(lambda_max),
                                      float(smoothing_range), int(bool(zero_initial)), _prec_of(x)), ctx)
+
+
+def hx_chebyshev_smooth_noalloc(ctx, mesh, rhs, x, inv_diag, degree, lambda_max, smoothing_range,
+                                zero_initial=False):
+    """hx_chebyshev_smooth for callers that cannot allocate device memory: the
+    scratch vectors live in the library's static device array (meshes up to
+    1,048,576 DoFs)."""
+    _check(lib().hx_chebyshev_smooth_noalloc(mesh, _ptr(rhs), _ptr(x), _ptr(inv_diag), int(degree),
+                                             float(lambda_max), float(smoothing_range), int(bool(zero_initial)),
+                                             _prec_of(x)), ctx)
 
 
 def hx_estimate_lambda_max(ctx, mesh, inv_diag, iters=50, seed=1):
