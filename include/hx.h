@@ -236,13 +236,18 @@ hx_status hx_cg_solve(hx_mesh *mesh, const double *rhs_dev, double *x_dev, doubl
 hx_status hx_fibre_dispersion(double a, double b, double H[3]);
 
 /* ---- batches of meshes (many uneven problems in one launch) -------------- */
-/* Group meshes (possibly of different degrees) so that one persistent launch
- * applies every mesh's tangent. The meshes stay owned by the caller and must
- * outlive the batch; each needs its qp cache at `prec`. */
+/* Group meshes of one context and one law (possibly of different degrees,
+ * sizes and Newton states) so that one persistent launch applies every mesh's
+ * tangent: the kernel walks a device work list of (mesh, element tile) items
+ * sorted by degree and dispatches each to the code of its degree. The meshes
+ * stay owned by the caller and must outlive the batch. */
 hx_status hx_batch_create(hx_ctx *ctx, hx_mesh *const *meshes, int32_t n_meshes, hx_batch **batch);
 void hx_batch_destroy(hx_batch *batch);
-/* out_i = K_i du_i for every mesh i in one launch; du/out are arrays of
- * n_meshes device pointers (host arrays). */
+/* out_i = K_i du_i for every mesh i in one launch (plus one launch that zeroes
+ * the outputs); du/out are host arrays of n_meshes device pointers. Every mesh
+ * needs a cache at `prec` from hx_precompute_qp, all with the same caching
+ * strategy (HX_CACHE_F or HX_CACHE_TENSORS; HX_RECOMPUTE gives
+ * HX_ERR_UNSUPPORTED). */
 hx_status hx_batch_tangent_apply(hx_batch *batch, const void *const *du_dev, void *const *out_dev, int32_t prec);
 
 /* ---- measurement support ------------------------------------------------- */

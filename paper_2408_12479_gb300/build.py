@@ -61,11 +61,15 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
             obj = os.path.join(objdir, f"hx_ops_p{p}_{'f32' if f32 else 'f64'}.o")
             jobs_list.append([nvcc] + flags + [f"-DHX_P={p}", f"-DHX_UNIT_F32={f32}", "-c",
                                                os.path.join(CSRC, "hx_ops.cu"), "-o", obj])
+    for f32 in (0, 1):
+        jobs_list.append([nvcc] + flags + [f"-DHX_UNIT_F32={f32}", "-c", os.path.join(CSRC, "hx_batch.cu"), "-o",
+                                           os.path.join(objdir, f"hx_batch_{'f32' if f32 else 'f64'}.o")])
     for name in ("hx_vec", "hx_api"):
         jobs_list.append([nvcc] + flags + ["-c", os.path.join(CSRC, name + ".cu"), "-o",
                                            os.path.join(objdir, name + ".o")])
-    # longest units first
-    jobs_list.sort(key=lambda c: -int(next((a.split("=")[1] for a in c if a.startswith("-DHX_P=")), "0")))
+    # longest units first (the batch units include every degree)
+    jobs_list.sort(key=lambda c: -(99 if any("hx_batch" in a for a in c) else
+                                   int(next((a.split("=")[1] for a in c if a.startswith("-DHX_P=")), "0"))))
     n = jobs or max(1, min(len(jobs_list), os.cpu_count() or 4))
 
     def run(cmd):

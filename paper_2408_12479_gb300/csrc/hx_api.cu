@@ -27,8 +27,11 @@ HX_DECL(4)
 HX_DECL(5)
 HX_DECL(6)
 #undef HX_DECL
+extern const hx::BatchOps *hx_batch_ops_f64();
+extern const hx::BatchOps *hx_batch_ops_f32();
 
 namespace hx {
+const BatchOps *batch_ops(int prec) { return prec == HX_FP64 ? hx_batch_ops_f64() : hx_batch_ops_f32(); }
 const PrecOps *prec_ops(int p, int prec) {
 #define HX_CASE(P) \
     case P:        \
@@ -177,6 +180,10 @@ cudaError_t ensure_tables(int device, int p) {
         const hx::PrecOps *ops = hx::prec_ops(p, prec);
         cudaError_t e = ops->upload_tables(t.B.data(), t.D.data(), t.Gd.data(), t.w.data(), t.geoV.data(),
                                            t.geoD.data(), t.geoVn.data());
+        if (e != cudaSuccess) return e;
+        // the batch unit keeps its own copy of every degree's tables
+        e = hx::batch_ops(prec)->upload_tables(p, t.B.data(), t.D.data(), t.Gd.data(), t.w.data(), t.geoV.data(),
+                                               t.geoD.data(), t.geoVn.data());
         if (e != cudaSuccess) return e;
     }
     g_uploaded[device][p] = true;
@@ -1045,20 +1052,106 @@ hx_status hx_measure_fma_peak(hx_ctx *ctx, int32_t prec, double *flops) {
     return HX_OK;
 }
 
-// batches: not built yet
+// ---------------------------------------------------------------------------
+// batches of meshes: one persistent launch over a degree-sorted work list
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct hx_batch {
+    hx_ctx *ctx = nullptr;
+    std::vector<hx_mesh *> meshes;
+    int law = 0;
+    hx::BatchMesh *d_meshes = nullptr;
+    std::vector<hx::BatchMesh> h;
+    int2 *d_items[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    int nitems[2][3] = {{-1, -1, -1}, {-1, -1, -1}};
+};
+
+extern "C" {
+
 hx_status hx_batch_create(hx_ctx *ctx, hx_mesh *const *meshes, int32_t n_meshes, hx_batch **batch) {
-    (void)meshes;
-    (void)n_meshes;
-    if (batch) *batch = nullptr;
-    return fail(ctx, HX_ERR_UNSUPPORTED, "hx_batch_create: not built yet");
+    if (!ctx || !meshes || n_meshes < 1 || !batch) return fail(ctx, HX_ERR_ARG, "hx_batch_create: bad argument");
+    *batch = nullptr;
+    for (int i = 0; i < n_meshes; ++i) {
+        if (!meshes[i] || meshes[i]->ctx != ctx)
+            return fail(ctx, HX_ERR_ARG, "hx_batch_create: every mesh must belong to the batch's context");
+        if (meshes[i]->law != meshes[0]->law) return fail(ctx, HX_ERR_ARG, "hx_batch_create: meshes of one batch share a law");
+    }
+    hx_batch *b = new hx_batch();
+    b->ctx = ctx;
+    b->meshes.assign(meshes, meshes + n_meshes);
+    b->law = meshes[0]->law;
+    b->h.resize(n_meshes);
+    cudaError_t e = cudaMalloc((void **)&b->d_meshes, sizeof(hx::BatchMesh) * n_meshes);
+    if (e != cudaSuccess) {
+        delete b;
+        return cuda_fail(ctx, e, "hx_batch_create");
+    }
+    *batch = b;
+    return HX_OK;
 }
-void hx_batch_destroy(hx_batch *batch) { (void)batch; }
-hx_status hx_batch_tangent_apply(hx_batch *batch, const void *const *du_dev, void *const *out_dev, int32_t prec) {
-    (void)batch;
-    (void)du_dev;
-    (void)out_dev;
-    (void)prec;
-    return HX_ERR_UNSUPPORTED;
+
+void hx_batch_destroy(hx_batch *b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->ctx->stream);
+    dfree(b->d_meshes);
+    for (auto &row : b->d_items)
+        for (auto *p : row) dfree(p);
+    delete b;
+}
+
+hx_status hx_batch_tangent_apply(hx_batch *b, const void *const *du_dev, void *const *out_dev, int32_t prec) {
+    if (!b || !du_dev || !out_dev || bad_prec(prec)) return fail(b ? b->ctx : nullptr, HX_ERR_ARG, "hx_batch_tangent_apply: bad argument");
+    hx_ctx *ctx = b->ctx;
+    const int n = (int)b->meshes.size();
+    const int storage = b->meshes[0]->cache[prec].storage;
+    for (int i = 0; i < n; ++i) {
+        const QpCache &c = b->meshes[i]->cache[prec];
+        if (!c.valid) return fail(ctx, HX_ERR_NOT_READY, "hx_batch_tangent_apply: a mesh has no quadrature-point data at this precision");
+        if (c.storage != storage) return fail(ctx, HX_ERR_ARG, "hx_batch_tangent_apply: meshes of a batch must share the storage strategy");
+        if (!du_dev[i] || !out_dev[i] || du_dev[i] == out_dev[i]) return fail(ctx, HX_ERR_ARG, "hx_batch_tangent_apply: bad vector");
+    }
+    if (storage == HX_RECOMPUTE)
+        return fail(ctx, HX_ERR_UNSUPPORTED, "hx_batch_tangent_apply: batches run the caching strategies");
+    const hx::BatchOps *ops = hx::batch_ops(prec);
+    // work list of (mesh, tile), highest degree first, built once per (prec, storage)
+    if (b->nitems[prec][storage] < 0) {
+        std::vector<int2> items;
+        for (int p = HX_PMAX; p >= HX_PMIN; --p)
+            for (int i = 0; i < n; ++i) {
+                const hx_mesh *m = b->meshes[i];
+                if (m->p != p) continue;
+                const int epb = ops->epb(p, storage);
+                if (epb < 1) return fail(ctx, HX_ERR_UNSUPPORTED, "hx_batch_tangent_apply: degree not in the batch unit");
+                const int nt = (m->n_elem + epb - 1) / epb;
+                for (int t = 0; t < nt; ++t) items.push_back(make_int2(i, t));
+            }
+        HX_CUDA(ctx, cudaMalloc((void **)&b->d_items[prec][storage], sizeof(int2) * (items.size() + 1)));
+        if (!items.empty())
+            HX_CUDA(ctx, cudaMemcpy(b->d_items[prec][storage], items.data(), sizeof(int2) * items.size(),
+                                    cudaMemcpyHostToDevice));
+        b->nitems[prec][storage] = (int)items.size();
+    }
+    for (int i = 0; i < n; ++i) {
+        hx_mesh *m = b->meshes[i];
+        b->h[i].m = view(m, prec);
+        b->h[i].du = du_dev[i];
+        b->h[i].out = out_dev[i];
+        b->h[i].n_dofs = 3 * m->n_nodes;
+    }
+    // pageable source: the copy is staged before the call returns
+    HX_CUDA(ctx, cudaMemcpyAsync(b->d_meshes, b->h.data(), sizeof(hx::BatchMesh) * n, cudaMemcpyHostToDevice, ctx->stream));
+    HX_CUDA(ctx, ops->zero(b->d_meshes, n, ctx->stream));
+    HX_CUDA(ctx, ops->apply(b->law, storage, b->d_meshes, b->d_items[prec][storage], b->nitems[prec][storage], ctx->stream));
+    ctx->launches += 2;
+    for (int i = 0; i < n; ++i) {
+        hx_mesh *m = b->meshes[i];
+        if (m->n_constrained) {
+            HX_CUDA(ctx, hx::copy_idx(m->d_cidx, m->n_constrained, du_dev[i], out_dev[i], prec, ctx->stream));
+            ctx->launches++;
+        }
+    }
+    return HX_OK;
 }
 
 }  // extern "C"

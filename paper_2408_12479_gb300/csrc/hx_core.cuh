@@ -1,0 +1,1340 @@
+// hx_core.cuh -- per-degree body of the operator kernels, included once per
+// (degree, precision) by hx_ops.cu and once per degree by hx_batch.cu. The
+// includer defines HX_P, HX_UNIT_F32 and the scalar type Real and opens the
+// enclosing namespaces; this file has no include guard on purpose.
+//
+// Per element the operators follow the same pipeline (Sec. 2 weak forms,
+// sum factorization as in the paper's matrix-free setting, Sec. 5):
+//   gather      x-rows of u_e <- u[conn(e)] into registers
+//   interpolate V = (B (x) B (x) B) u_e                  three 1D sweeps
+//   gradient    dV/dxi_d = D_d V (collocation on the Gauss points, q = p+1)
+//   qp operator H = (dV/dxi) J0^-1, material law, Q = JxW * dP J0^-T
+//   integrate   r_e = sum_d D_d^T Q_d, then (B^T (x) B^T (x) B^T)
+//   scatter     out[conn(e)] += r_e  (atomic adds into a zeroed vector)
+
+constexpr int N = HX_P + 1;        // nodes (and Gauss points) per direction
+constexpr int NN = N * N;
+constexpr int NQ = N * N * N;      // nodes (and Gauss points) per element
+constexpr int R = (N % 2) ? N : N + 1;  // padded row length (odd)
+constexpr int SZ = R * N * N;      // padded cube size
+
+// Column-layout cubes of the apply kernel: element e of an array starts at
+// e*ES, component c at +c*CZ, point (i,j,k) at +i + j*RS + k*PS. The strides
+// were chosen by an exhaustive bank-conflict search over the three line-sweep
+// access patterns of a warp (lanes spanning several elements), separately for
+// 4- and 8-byte words.
+struct ColLayout {
+    int RS, PS, CZ, ES;
+};
+constexpr ColLayout col_layout() {
+    if (sizeof(Real) == 4) {
+        return N == 2 ? ColLayout{2, 5, 10, 36}
+             : N == 3 ? ColLayout{3, 14, 42, 137}
+             : N == 4 ? ColLayout{4, 19, 76, 240}
+             : N == 5 ? ColLayout{5, 25, 125, 377}
+             : N == 6 ? ColLayout{7, 42, 252, 764}
+                      : ColLayout{7, 56, 392, 1201};
+    }
+    return N == 2 ? ColLayout{2, 5, 10, 36}
+         : N == 3 ? ColLayout{3, 18, 54, 169}
+         : N == 4 ? ColLayout{4, 19, 76, 228}
+         : N == 5 ? ColLayout{5, 25, 125, 377}
+         : N == 6 ? ColLayout{9, 54, 324, 980}
+                  : ColLayout{7, 52, 364, 1105};
+}
+constexpr int CRS = col_layout().RS, CPS = col_layout().PS, CCZ = col_layout().CZ, CES = col_layout().ES;
+
+enum { TB = 0, TD = 1, TG = 2 };
+
+// threads per CTA of the column-layout apply: n^2 threads per element
+__host__ __device__ constexpr int col_threads(int epb) { return (epb * NN + 31) / 32 * 32; }
+
+// threads per CTA for a tile of epb elements: one thread per sweep line
+__host__ __device__ constexpr int threads_for(int epb) {
+    return (3 * epb * NN + 31) / 32 * 32 < 64 ? 64 : ((3 * epb * NN + 31) / 32 * 32 > 1024 ? 1024 : (3 * epb * NN + 31) / 32 * 32);
+}
+
+__constant__ Real cTab[3][NN];       // B[q][a], D[q][r], Gd[q][a]
+__constant__ double cW[N];           // Gauss weights on [0,1]
+__constant__ double cGeoV[2][3 * N]; // geometry bases at Gauss points [g-1][a*N+q]
+__constant__ double cGeoD[2][3 * N];
+__constant__ double cGeoVn[2][3 * N];  // geometry bases at the nodal points
+
+template <int TAB>
+__device__ __forceinline__ Real tab(int i) {
+    return cTab[TAB][i];
+}
+
+__device__ __forceinline__ int cidx(int i, int j, int k) { return i + R * (j + N * k); }
+
+// sym6 index of (i,j): xx yy zz xy xz yz
+__host__ __device__ constexpr int SI(int i, int j) {
+    return (i == j) ? i : ((i + j == 1) ? 3 : ((i + j == 2) ? 4 : 5));
+}
+
+// ---------------------------------------------------------------------------
+// 1D line sweeps over padded cubes in shared memory. Lines along DIR of cube
+// (cube*IM + IO) are contracted with table TAB (transposed if TR) and written
+// (or added, ACC) to cube (cube*OM + OO). One thread per line, register
+// blocked: N loads, N*N FMAs, N stores.
+// ---------------------------------------------------------------------------
+template <typename T, int DIR, int TAB, bool TR, bool ACC, int IM, int IO, int OM, int OO>
+__device__ __forceinline__ void sweep(const T *__restrict__ in, T *__restrict__ out, int ncubes) {
+    const int nlines = ncubes * NN;
+    for (int l = threadIdx.x; l < nlines; l += blockDim.x) {
+        const int cube = l / NN;
+        const int r = l - cube * NN;
+        const int a = r % N, b = r / N;
+        int off, str;
+        if constexpr (DIR == 0) {
+            off = R * (a + N * b);
+            str = 1;
+        } else if constexpr (DIR == 1) {
+            off = a + R * N * b;
+            str = R;
+        } else {
+            off = a + R * b;
+            str = R * N;
+        }
+        const T *ip = in + (cube * IM + IO) * SZ + off;
+        T *op = out + (cube * OM + OO) * SZ + off;
+        T x[N];
+#pragma unroll
+        for (int t = 0; t < N; ++t) x[t] = ip[t * str];
+#pragma unroll
+        for (int o = 0; o < N; ++o) {
+            T s = T(0);
+#pragma unroll
+            for (int t = 0; t < N; ++t) s = fma((T)tab<TAB>(TR ? t * N + o : o * N + t), x[t], s);
+            if constexpr (ACC)
+                op[o * str] += s;
+            else
+                op[o * str] = s;
+        }
+    }
+}
+
+// values u_e (3*EPB cubes in U) -> reference gradients at Gauss points in G
+// (cube (e*3+c)*3+d holds d u_c / d xi_d). W is scratch; U is clobbered.
+template <typename T>
+__device__ __forceinline__ void forward_grad(T *U, T *W, T *G, int nc) {
+    sweep<T, 0, TB, false, false, 1, 0, 1, 0>(U, W, nc);
+    __syncthreads();
+    sweep<T, 1, TB, false, false, 1, 0, 1, 0>(W, U, nc);
+    __syncthreads();
+    sweep<T, 2, TB, false, false, 1, 0, 1, 0>(U, W, nc);
+    __syncthreads();
+    sweep<T, 0, TD, false, false, 1, 0, 3, 0>(W, G, nc);
+    sweep<T, 1, TD, false, false, 1, 0, 3, 1>(W, G, nc);
+    sweep<T, 2, TD, false, false, 1, 0, 3, 2>(W, G, nc);
+    __syncthreads();
+}
+
+// test-gradient integration: G (per-qp coefficients Q_{c,d}) -> nodal values in U
+template <typename T>
+__device__ __forceinline__ void backward_int(T *G, T *W, T *U, int nc) {
+    sweep<T, 0, TD, true, false, 3, 0, 1, 0>(G, W, nc);
+    __syncthreads();
+    sweep<T, 1, TD, true, true, 3, 1, 1, 0>(G, W, nc);
+    __syncthreads();
+    sweep<T, 2, TD, true, true, 3, 2, 1, 0>(G, W, nc);
+    __syncthreads();
+    sweep<T, 2, TB, true, false, 1, 0, 1, 0>(W, U, nc);
+    __syncthreads();
+    sweep<T, 1, TB, true, false, 1, 0, 1, 0>(U, W, nc);
+    __syncthreads();
+    sweep<T, 0, TB, true, false, 1, 0, 1, 0>(W, U, nc);
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// gather / scatter
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t node_of(const hx::MeshView &m, int e, int i, int j, int k) {
+    if (m.structured) {
+        const int ex = e % m.nx;
+        const int t = e / m.nx;
+        const int ey = t % m.ny, ez = t / m.ny;
+        return (int64_t)(ex * HX_P + i) + m.Nx * ((int64_t)(ey * HX_P + j) + m.Ny * (int64_t)(ez * HX_P + k));
+    }
+    return m.dof_conn[(int64_t)e * NQ + i + N * (j + N * k)];
+}
+
+// EPB elements starting at e0 -> cubes (el*3 + c) of U; zero for padding
+// elements and (if mask) constrained DoFs.
+template <typename TV, typename T>
+__device__ __forceinline__ void gather(const hx::MeshView &m, int e0, int epb, const TV *__restrict__ v, T *U,
+                                       bool mask) {
+    const int n = epb * NQ * 3;
+    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+        const int c = idx % 3;
+        const int a = (idx / 3) % NQ;
+        const int el = idx / (3 * NQ);
+        const int e = e0 + el;
+        const int i = a % N, j = (a / N) % N, k = a / NN;
+        T val = T(0);
+        if (e < m.n_elem) {
+            const int64_t d = 3 * node_of(m, e, i, j, k) + c;
+            val = (T)v[d];
+            if (mask && m.dmask && m.dmask[d]) val = T(0);
+        }
+        U[(el * 3 + c) * SZ + cidx(i, j, k)] = val;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void scatter_add(const hx::MeshView &m, int e0, int epb, const T *U, T *__restrict__ out,
+                                            bool mask) {
+    const int n = epb * NQ * 3;
+    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+        const int c = idx % 3;
+        const int a = (idx / 3) % NQ;
+        const int el = idx / (3 * NQ);
+        const int e = e0 + el;
+        if (e >= m.n_elem) continue;
+        const int i = a % N, j = (a / N) % N, k = a / NN;
+        const int64_t d = 3 * node_of(m, e, i, j, k) + c;
+        if (mask && m.dmask && m.dmask[d]) continue;
+        atomicAdd(out + d, U[(el * 3 + c) * SZ + cidx(i, j, k)]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// small tensor algebra (row-major 3x3, sym6 = xx yy zz xy xz yz)
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void mm(const T *A, const T *B, T *C) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) C[r * 3 + c] = fma(A[r * 3 + 0], B[0 * 3 + c], fma(A[r * 3 + 1], B[1 * 3 + c], A[r * 3 + 2] * B[2 * 3 + c]));
+}
+
+// 1/J-free inverse of F = I + Hk: adj(F) * invJ
+template <typename T>
+__device__ __forceinline__ void inv_F(const T *Hk, T invJ, T *Fi) {
+    const T f00 = T(1) + Hk[0], f01 = Hk[1], f02 = Hk[2];
+    const T f10 = Hk[3], f11 = T(1) + Hk[4], f12 = Hk[5];
+    const T f20 = Hk[6], f21 = Hk[7], f22 = T(1) + Hk[8];
+    Fi[0] = (f11 * f22 - f12 * f21) * invJ;
+    Fi[1] = (f02 * f21 - f01 * f22) * invJ;
+    Fi[2] = (f01 * f12 - f02 * f11) * invJ;
+    Fi[3] = (f12 * f20 - f10 * f22) * invJ;
+    Fi[4] = (f00 * f22 - f02 * f20) * invJ;
+    Fi[5] = (f02 * f10 - f00 * f12) * invJ;
+    Fi[6] = (f10 * f21 - f11 * f20) * invJ;
+    Fi[7] = (f01 * f20 - f00 * f21) * invJ;
+    Fi[8] = (f00 * f11 - f01 * f10) * invJ;
+}
+
+// J - 1 from the components of H = Grad u without forming det(I + H) - 1
+// (Sec. "Stable and fast numerics"): det(I+H) - 1 = tr H + (tr^2 H - tr H^2)/2 + det H.
+template <typename T>
+__device__ __forceinline__ T J_minus_1(const T *H) {
+    const T tr = H[0] + H[4] + H[8];
+    const T tr2 = H[0] * H[0] + H[4] * H[4] + H[8] * H[8] + T(2) * (H[1] * H[3] + H[2] * H[6] + H[5] * H[7]);
+    const T det = H[0] * (H[4] * H[8] - H[5] * H[7]) - H[1] * (H[3] * H[8] - H[5] * H[6]) +
+                  H[2] * (H[3] * H[7] - H[4] * H[6]);
+    return tr + T(0.5) * (tr * tr - tr2) + det;
+}
+
+// Green-Lagrange strain in stable form E = (H + H^T + H^T H)/2  (Eq. E_stable)
+template <typename T>
+__device__ __forceinline__ void green_strain(const T *H, T *E) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            T s = H[i * 3 + j] + H[j * 3 + i];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) s = fma(H[k * 3 + i], H[k * 3 + j], s);
+            E[SI(i, j)] = T(0.5) * s;
+        }
+}
+
+// C^-1 = F^-1 F^-T (sym)
+template <typename T>
+__device__ __forceinline__ void cinv_from_Fi(const T *Fi, T *Ci) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j)
+            Ci[SI(i, j)] = fma(Fi[i * 3 + 0], Fi[j * 3 + 0], fma(Fi[i * 3 + 1], Fi[j * 3 + 1], Fi[i * 3 + 2] * Fi[j * 3 + 2]));
+}
+
+// S = C^-1 (s1 E + s0 I) (the two factors commute; upper triangle kept)
+template <typename T>
+__device__ __forceinline__ void stress_CiX(const T *Ci, const T *E, T s1, T s0, T *S) {
+    T X[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) X[k] = s1 * E[k];
+    X[0] += s0;
+    X[1] += s0;
+    X[2] += s0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j)
+            S[SI(i, j)] = fma(Ci[SI(i, 0)], X[SI(0, j)], fma(Ci[SI(i, 1)], X[SI(1, j)], Ci[SI(i, 2)] * X[SI(2, j)]));
+}
+
+// Alg. 2 (FastApproxJpow): J^-2/3 from J-1 by N_it Newton steps on x^-3 = J^2 from x0 = 1
+template <typename T>
+__device__ __forceinline__ T fast_jpow(T Jm1, int N_it) {
+    const T alpha = ((Jm1 + T(2)) * Jm1 + T(1)) * T(1.0 / 3.0);
+    T beta = T(4.0 / 3.0) - alpha;
+    for (int n = 1; n < N_it; ++n) {
+        const T b2 = beta * beta;
+        beta = T(4.0 / 3.0) * beta - alpha * (b2 * b2);
+    }
+    return beta;
+}
+
+__device__ __forceinline__ double log1p_T(double x) { return log1p(x); }
+__device__ __forceinline__ float log1p_T(float x) { return log1pf(x); }
+__device__ __forceinline__ double exp_T(double x) { return exp(x); }
+__device__ __forceinline__ float exp_T(float x) { return expf(x); }
+
+// ---------------------------------------------------------------------------
+// quadrature-point state of a law at Grad u_k = Hk (Sec. 4 stable forms)
+// ---------------------------------------------------------------------------
+template <typename T>
+struct State {
+    T Hk[9], Fi[9], Ci[6], S[6];
+    T al, be, ga;       // D_uS = al sym(F^-1 H C^-1) + (be t + ga F:H) C^-1 + ga t I
+    T ph4, ph6;         // fibre tangent factors c3 (2 k2 E_i^2 + 1) (0 if inactive)
+    T H4[6], H6[6];     // structure tensors of the element
+    // scalars kept by the cache-F strategy
+    T invJ, lnJ, j23, c1, c2, s0, sg4, sg6;
+    T Jm1;
+};
+
+// material constants in the compute precision (no per-point conversions)
+template <typename T>
+struct Mat {
+    T mu, lambda, kappa, k1, k2;
+};
+template <typename T>
+__device__ __forceinline__ Mat<T> mat_of(const hx::MeshView &m) {
+    if constexpr (std::is_same<T, double>::value)
+        return Mat<T>{m.mat.mu, m.mat.lambda, m.mat.kappa, m.mat.k1, m.mat.k2};
+    else
+        return Mat<T>{m.matf.mu, m.matf.lambda, m.matf.kappa, m.matf.k1, m.matf.k2};
+}
+
+template <typename T>
+__device__ __forceinline__ void load_fibH(const hx::MeshView &m, int e, State<T> &st) {
+    const T *fh = std::is_same<T, double>::value ? (const T *)m.fibH64 : (const T *)m.fibH;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        st.H4[k] = fh[(int64_t)k * m.n_elem + e];
+        st.H6[k] = fh[(int64_t)(6 + k) * m.n_elem + e];
+    }
+}
+
+// Full state from Hk, computed in T. FAST selects Alg. 2 for J^-2/3 (FP32
+// on-the-fly paths); otherwise J^-2/3 = exp(-2/3 ln_{+1}(J-1)).
+template <typename T, int LAW, bool FAST>
+__device__ __forceinline__ void state_from_Hk(const hx::MeshView &m, int e, State<T> &st) {
+    const Mat<T> mp = mat_of<T>(m);
+    const T mu = mp.mu;
+    st.Jm1 = J_minus_1(st.Hk);
+    const T J = T(1) + st.Jm1;
+    st.invJ = T(1) / J;
+    inv_F(st.Hk, st.invJ, st.Fi);
+    cinv_from_Fi(st.Fi, st.Ci);
+    T E[6];
+    green_strain(st.Hk, E);
+    st.lnJ = log1p_T(st.Jm1);  // ln J = ln_{+1}(J - 1)
+    if constexpr (LAW == HX_CNH) {
+        const T lam = mp.lambda;
+        stress_CiX(st.Ci, E, T(2) * mu, T(2) * lam * st.lnJ, st.S);
+        st.al = T(2) * (mu - T(2) * lam * st.lnJ);
+        st.be = T(2) * lam;
+        st.ga = T(0);
+        st.ph4 = st.ph6 = T(0);
+    } else {
+        const T kap = mp.kappa;
+        st.j23 = FAST ? fast_jpow(st.Jm1, 3) : exp_T(T(-2.0 / 3.0) * st.lnJ);
+        const T trE = E[0] + E[1] + E[2];
+        const T vol = T(0.5) * kap * st.Jm1 * (st.Jm1 + T(2));  // kappa/2 (J^2 - 1), stable
+        st.c1 = vol - mu * T(1.0 / 3.0) * st.j23 * (T(3) + T(2) * trE);
+        st.c2 = mu * T(2.0 / 9.0) * st.j23 * (T(3) + T(2) * trE) + kap * J * J;
+        st.s0 = vol - mu * T(2.0 / 3.0) * st.j23 * trE;
+        stress_CiX(st.Ci, E, T(2) * mu * st.j23, st.s0, st.S);
+        st.al = T(-2) * st.c1;
+        st.be = st.c2;
+        st.ga = mu * T(-2.0 / 3.0) * st.j23;
+        st.ph4 = st.ph6 = T(0);
+        st.sg4 = st.sg6 = T(0);
+        if constexpr (LAW == HX_FIBER) {
+            load_fibH(m, e, st);
+            const T k1 = mp.k1, k2 = mp.k2;
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {
+                const T *Hf = f ? st.H6 : st.H4;
+                // E_i = 2 H_i : E, I_i* - 1 = 2 M1.E.M1 (stable fibre invariants)
+                T Ei = T(2) * (Hf[0] * E[0] + Hf[1] * E[1] + Hf[2] * E[2] +
+                               T(2) * (Hf[3] * E[3] + Hf[4] * E[4] + Hf[5] * E[5]));
+                T M[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) M[d] = (T)m.fibM[(int64_t)(3 * f + d) * m.n_elem + e];
+                T mEm = M[0] * M[0] * E[0] + M[1] * M[1] * E[1] + M[2] * M[2] * E[2] +
+                        T(2) * (M[0] * M[1] * E[3] + M[0] * M[2] * E[4] + M[1] * M[2] * E[5]);
+                const T c3 = (mEm > T(0)) ? T(2) * k1 * exp_T(k2 * Ei * Ei) : T(0);
+                const T sg = c3 * Ei, ph = c3 * (T(2) * k2 * Ei * Ei + T(1));
+#pragma unroll
+                for (int k = 0; k < 6; ++k) st.S[k] = fma(sg, Hf[k], st.S[k]);
+                if (f) {
+                    st.sg6 = sg;
+                    st.ph6 = ph;
+                } else {
+                    st.sg4 = sg;
+                    st.ph4 = ph;
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// cache layouts (SoA [field][n_qp])
+//  cache-F:      0-8 Hk, 9 1/J, then cNH: 10 ln J
+//                iNH/fiber: 10 J^-2/3, 11 c1, 12 c2, 13 s0 (stress scalar);
+//                fiber: 14 sigma_4, 15 sigma_6, 16 phi_4, 17 phi_6
+//  cache-tensors: 0-8 Hk, 9-17 F^-1, 18-23 C^-1, 24-29 S, 30 alpha,
+//                iNH/fiber: 31 beta, 32 gamma; fiber: 33 phi_4, 34 phi_6
+// ---------------------------------------------------------------------------
+template <typename TS, int LAW, int STORAGE>
+__device__ __forceinline__ void store_state(TS *qp, int64_t nq, int64_t g, const State<double> &st) {
+    auto put = [&](int f, double v) { qp[(int64_t)f * nq + g] = (TS)v; };
+#pragma unroll
+    for (int k = 0; k < 9; ++k) put(k, st.Hk[k]);
+    if constexpr (STORAGE == HX_CACHE_F) {
+        put(9, st.invJ);
+        if constexpr (LAW == HX_CNH) {
+            put(10, st.lnJ);
+        } else {
+            put(10, st.j23);
+            put(11, st.c1);
+            put(12, st.c2);
+            put(13, st.s0);
+            if constexpr (LAW == HX_FIBER) {
+                put(14, st.sg4);
+                put(15, st.sg6);
+                put(16, st.ph4);
+                put(17, st.ph6);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) put(9 + k, st.Fi[k]);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) put(18 + k, st.Ci[k]);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) put(24 + k, st.S[k]);
+        put(30, st.al);
+        if constexpr (LAW != HX_CNH) {
+            put(31, st.be);
+            put(32, st.ga);
+            if constexpr (LAW == HX_FIBER) {
+                put(33, st.ph4);
+                put(34, st.ph6);
+            }
+        }
+    }
+}
+
+// state of the cache strategies from the stored fields; get(f) returns field f
+template <typename T, int LAW, int STORAGE, typename Get>
+__device__ __forceinline__ void build_state(const hx::MeshView &m, int e, Get get, State<T> &st) {
+    const Mat<T> mp = mat_of<T>(m);
+    const T mu = mp.mu;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) st.Hk[k] = get(k);
+    st.ph4 = st.ph6 = T(0);
+    if constexpr (STORAGE == HX_CACHE_F) {
+        st.invJ = get(9);
+        inv_F(st.Hk, st.invJ, st.Fi);
+        cinv_from_Fi(st.Fi, st.Ci);
+        T E[6];
+        green_strain(st.Hk, E);
+        if constexpr (LAW == HX_CNH) {
+            const T lam = mp.lambda;
+            const T lnJ = get(10);
+            stress_CiX(st.Ci, E, T(2) * mu, T(2) * lam * lnJ, st.S);
+            st.al = T(2) * (mu - T(2) * lam * lnJ);
+            st.be = T(2) * lam;
+            st.ga = T(0);
+        } else {
+            const T j23 = get(10);
+            st.c1 = get(11);
+            st.c2 = get(12);
+            const T s0 = get(13);
+            stress_CiX(st.Ci, E, T(2) * mu * j23, s0, st.S);
+            st.al = T(-2) * st.c1;
+            st.be = st.c2;
+            st.ga = mu * T(-2.0 / 3.0) * j23;
+            if constexpr (LAW == HX_FIBER) {
+                load_fibH(m, e, st);
+                const T sg4 = get(14), sg6 = get(15);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) st.S[k] = fma(sg4, st.H4[k], fma(sg6, st.H6[k], st.S[k]));
+                st.ph4 = get(16);
+                st.ph6 = get(17);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) st.Fi[k] = get(9 + k);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) st.Ci[k] = get(18 + k);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) st.S[k] = get(24 + k);
+        st.al = get(30);
+        if constexpr (LAW == HX_CNH) {
+            st.be = T(2) * mp.lambda;
+            st.ga = T(0);
+        } else {
+            st.be = get(31);
+            st.ga = get(32);
+            if constexpr (LAW == HX_FIBER) {
+                load_fibH(m, e, st);
+                st.ph4 = get(33);
+                st.ph6 = get(34);
+            }
+        }
+    }
+}
+
+template <typename T, int LAW, int STORAGE>
+__device__ __forceinline__ void load_state(const hx::MeshView &m, int e, int64_t g, State<T> &st) {
+    const T *qp = (const T *)m.qp;
+    const int64_t nq = m.n_qp;
+    build_state<T, LAW, STORAGE>(m, e, [&](int f) { return __ldcs(qp + (int64_t)f * nq + g); }, st);
+}
+
+// dP = H S + F D_uS[H] for a physical displacement-gradient direction H
+// (Sec. 2 Eq. DDu_residual_material; D_uS from App. A with the sign of the
+// D_uC^-1 term that follows from differentiating S).
+template <typename T, int LAW>
+__device__ __forceinline__ void tangent_dP(const State<T> &st, const T *H, T *dP) {
+    T A[9];
+    mm(st.Fi, H, A);  // F^-1 H
+    const T t = A[0] + A[4] + A[8];
+    T D[6];
+    // sym(F^-1 H C^-1)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            const T bij = fma(A[i * 3 + 0], st.Ci[SI(0, j)], fma(A[i * 3 + 1], st.Ci[SI(1, j)], A[i * 3 + 2] * st.Ci[SI(2, j)]));
+            const T bji = fma(A[j * 3 + 0], st.Ci[SI(0, i)], fma(A[j * 3 + 1], st.Ci[SI(1, i)], A[j * 3 + 2] * st.Ci[SI(2, i)]));
+            D[SI(i, j)] = T(0.5) * st.al * (bij + bji);
+        }
+    T cC = st.be * t;
+    if constexpr (LAW != HX_CNH) {
+        T FH = H[0] + H[4] + H[8];  // F : H = tr H + Hk : H
+#pragma unroll
+        for (int k = 0; k < 9; ++k) FH = fma(st.Hk[k], H[k], FH);
+        cC = fma(st.ga, FH, cC);
+        const T gt = st.ga * t;
+        D[0] += gt;
+        D[1] += gt;
+        D[2] += gt;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) D[k] = fma(cC, st.Ci[k], D[k]);
+    if constexpr (LAW == HX_FIBER) {
+        // H_i : D_uC with D_uC = 2 sym(F^T H), F^T H = H + Hk^T H
+        T FtH[9];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                FtH[i * 3 + j] = H[i * 3 + j] + fma(st.Hk[0 * 3 + i], H[0 * 3 + j], fma(st.Hk[1 * 3 + i], H[1 * 3 + j], st.Hk[2 * 3 + i] * H[2 * 3 + j]));
+        auto contract = [&](const T *Hs) {
+            return T(2) * (Hs[0] * FtH[0] + Hs[1] * FtH[4] + Hs[2] * FtH[8] + Hs[3] * (FtH[1] + FtH[3]) +
+                           Hs[4] * (FtH[2] + FtH[6]) + Hs[5] * (FtH[5] + FtH[7]));
+        };
+        const T f4 = st.ph4 * contract(st.H4);
+        const T f6 = st.ph6 * contract(st.H6);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) D[k] = fma(f4, st.H4[k], fma(f6, st.H6[k], D[k]));
+    }
+    // dP = H S + D + Hk D
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            T s = D[SI(c, d)];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) s = fma(H[c * 3 + k], st.S[SI(k, d)], fma(st.Hk[c * 3 + k], D[SI(k, d)], s));
+            dP[c * 3 + d] = s;
+        }
+}
+
+template <typename T>
+__device__ __forceinline__ void load_geo(const hx::MeshView &m, int64_t g, T *Ji, T &JxW) {
+    const T *geo = (const T *)m.geo;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Ji[k] = __ldcs(geo + (int64_t)k * m.n_qp + g);
+    JxW = __ldcs(geo + (int64_t)9 * m.n_qp + g);
+}
+
+// physical gradient H = G J0^-1 from the reference gradient G (G_{cd} = du_c/dxi_d)
+template <typename T>
+__device__ __forceinline__ void push_grad(const T *G, const T *Ji, T *H) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) H[c * 3 + d] = fma(G[c * 3 + 0], Ji[0 * 3 + d], fma(G[c * 3 + 1], Ji[1 * 3 + d], G[c * 3 + 2] * Ji[2 * 3 + d]));
+}
+
+// test-side pull back Q = JxW P J0^-T (Q_{ce} = JxW sum_d P_cd (J0^-1)_{ed})
+template <typename T>
+__device__ __forceinline__ void pull_flux(const T *P, const T *Ji, T JxW, T *Q) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int e = 0; e < 3; ++e) Q[c * 3 + e] = JxW * fma(P[c * 3 + 0], Ji[e * 3 + 0], fma(P[c * 3 + 1], Ji[e * 3 + 1], P[c * 3 + 2] * Ji[e * 3 + 2]));
+}
+
+__device__ __forceinline__ void flag_state(const hx::MeshView &m, double Jm1) {
+    if (!(Jm1 > -1.0)) {
+        if (Jm1 != Jm1)
+            atomicOr(m.err + 1, 1);
+        else
+            atomicOr(m.err + 0, 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// column-layout building blocks of the apply kernel: every element has n^2
+// threads; thread (a0, a1) owns one line of each direction (x-line (j,k) =
+// (a0,a1), y-line (i,k), z-line (i,j)), and the z-line also carries the
+// quadrature-point column (a0, a1, *) through the material phase in registers
+// ---------------------------------------------------------------------------
+template <int DIR>
+__device__ __forceinline__ int line_off(int a0, int a1) {
+    if constexpr (DIR == 0) return a0 * CRS + a1 * CPS;
+    else if constexpr (DIR == 1) return a0 + a1 * CPS;
+    else return a0 + a1 * CRS;
+}
+template <int DIR>
+__device__ __forceinline__ constexpr int line_str() {
+    return DIR == 0 ? 1 : (DIR == 1 ? CRS : CPS);
+}
+template <int DIR>
+__device__ __forceinline__ void ld_line(const Real *p, Real *x) {
+#pragma unroll
+    for (int t = 0; t < N; ++t) x[t] = p[t * line_str<DIR>()];
+}
+template <int DIR>
+__device__ __forceinline__ void st_line(Real *p, const Real *y) {
+#pragma unroll
+    for (int t = 0; t < N; ++t) p[t * line_str<DIR>()] = y[t];
+}
+// y = M x (TR: y = M^T x) with a 1D table from constant memory
+template <int TAB, bool TR>
+__device__ __forceinline__ void mv(const Real *x, Real *y) {
+#pragma unroll
+    for (int o = 0; o < N; ++o) {
+        Real s = Real(0);
+#pragma unroll
+        for (int t = 0; t < N; ++t) s = fma(tab<TAB>(TR ? t * N + o : o * N + t), x[t], s);
+        y[o] = s;
+    }
+}
+
+// node numbering base of an element (structured box: lattice index of its
+// first node; otherwise the element index for the connectivity lookup)
+__device__ __forceinline__ int64_t elem_base(const hx::MeshView &m, int e) {
+    if (e >= m.n_elem) return 0;
+    if (m.structured) {
+        const int ex = e % m.nx;
+        const int t = e / m.nx;
+        const int ey = t % m.ny, ez = t / m.ny;
+        return (int64_t)ex * HX_P + m.Nx * ((int64_t)ey * HX_P + m.Ny * (int64_t)ez * HX_P);
+    }
+    return e;
+}
+__device__ __forceinline__ int64_t node_at(const hx::MeshView &m, int64_t base, int i, int j, int k) {
+    if (m.structured) return base + i + m.Nx * (j + m.Ny * (int64_t)k);
+    return m.dof_conn[base * NQ + i + N * (j + N * k)];
+}
+
+// L2 cache policies: the quadrature-point stream is read once per apply
+// (evict first); the DoF vectors are gathered and scattered by up to eight
+// elements each and should stay resident (evict last)
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes, uint64_t pol) {
+    asm volatile("cp.async.bulk.prefetch.L2.global.L2::cache_hint [%0], %1, %2;" ::"l"(p), "r"(bytes), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ float ld_stream(const float *p, uint64_t pol) {
+    float v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ double ld_stream(const double *p, uint64_t pol) {
+    double v;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void red_add(float *p, float v, uint64_t pol) {
+    asm volatile("red.global.add.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
+}
+__device__ __forceinline__ void red_add(double *p, double v, uint64_t pol) {
+    asm volatile("red.global.add.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(p), "d"(v), "l"(pol) : "memory");
+}
+
+
+// Load the x-row (j = a0, k = a1) of element e of vector v into registers:
+// row[3*i + c] = v_c at node (i, a0, a1). In a structured box the row is 3*N
+// contiguous values; otherwise the N node ids come from the connectivity.
+// Constrained DoFs (mask) and elements past the end read zero.
+__device__ __forceinline__ void load_row(const hx::MeshView &m, int e, int64_t base, int a0, int a1,
+                                         const Real *__restrict__ v, bool mask, Real *row) {
+    if (e >= m.n_elem) {
+#pragma unroll
+        for (int t = 0; t < 3 * N; ++t) row[t] = Real(0);
+        return;
+    }
+    if (m.structured) {
+        const int64_t off = 3 * (base + m.Nx * (a0 + m.Ny * (int64_t)a1));
+        const Real *p = v + off;
+#pragma unroll
+        for (int t = 0; t < 3 * N; ++t) row[t] = p[t];
+        if (mask && m.dmask) {
+            const uint8_t *q = m.dmask + off;
+#pragma unroll
+            for (int t = 0; t < 3 * N; ++t)
+                if (q[t]) row[t] = Real(0);
+        }
+    } else {
+        const int32_t *cn = m.dof_conn + (int64_t)e * NQ + N * (a0 + N * a1);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const int64_t d = 3 * (int64_t)cn[i];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                row[3 * i + c] = v[d + c];
+                if (mask && m.dmask && m.dmask[d + c]) row[3 * i + c] = Real(0);
+            }
+        }
+    }
+}
+
+// forward sum factorization of an element whose x-rows are in the threads'
+// registers (row[3*i + c], x-line (a0, a1)): writes the x-, y- and
+// z-reference derivatives at the Gauss points to GXo, GYo, GZo. A and W are
+// scratch. The caller synchronises before the first call of a tile.
+__device__ __forceinline__ void col_forward(const Real *row, Real *A, Real *W, Real *GXo, Real *GYo, Real *GZo,
+                                            bool act, int eoff, int a0, int a1) {
+    Real x[N], y[N], z[N];
+    if (act) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) x[i] = row[3 * i + c];
+            mv<TB, false>(x, y);
+            st_line<0>(W + eoff + c * CCZ + line_off<0>(a0, a1), y);
+        }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int o = eoff + c * CCZ + line_off<1>(a0, a1);
+            ld_line<1>(W + o, x);
+            mv<TB, false>(x, y);
+            st_line<1>(A + o, y);
+        }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int o = eoff + c * CCZ + line_off<2>(a0, a1);
+            ld_line<2>(A + o, x);
+            mv<TB, false>(x, y);   // values at the Gauss points of this column
+            st_line<2>(W + o, y);
+            mv<TD, false>(y, z);
+            st_line<2>(GZo + o, z);
+        }
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int o0 = eoff + c * CCZ + line_off<0>(a0, a1);
+            ld_line<0>(W + o0, x);
+            mv<TD, false>(x, y);
+            st_line<0>(GXo + o0, y);
+            const int o1 = eoff + c * CCZ + line_off<1>(a0, a1);
+            ld_line<1>(W + o1, x);
+            mv<TD, false>(x, y);
+            st_line<1>(GYo + o1, y);
+        }
+    }
+    __syncthreads();
+}
+
+
+
+// L2 prefetch of a tile's quadrature-point data (geometry + cache), one
+// contiguous chunk per field; skipped where a chunk is not 16-byte aligned
+template <int EPB, int STORAGE>
+__device__ __forceinline__ void prefetch_tile(const hx::MeshView &m, int tile) {
+    const int e0 = tile * EPB;
+    if (e0 >= m.n_elem) return;
+    const int cnt = min(EPB, m.n_elem - e0);
+    const unsigned bytes = (unsigned)(cnt * NQ * sizeof(Real));
+    const int nfc = STORAGE == HX_RECOMPUTE ? 0 : m.nf;
+    const int f = threadIdx.x;
+    if (f >= 10 + nfc || (bytes & 15u)) return;
+    const Real *p = f < 10 ? (const Real *)m.geo + (int64_t)f * m.n_qp + (int64_t)e0 * NQ
+                           : (const Real *)m.qp + (int64_t)(f - 10) * m.n_qp + (int64_t)e0 * NQ;
+    if (((uintptr_t)p & 15u) == 0) prefetch_l2(p, bytes, policy_evict_first());
+}
+
+template <int EPB, int STORAGE>
+struct ApplySmem {
+    // U, W, GX, GY, GZ; recompute adds KX, KY, KZ
+    static constexpr int arrays = STORAGE == HX_RECOMPUTE ? 8 : 5;
+    static constexpr size_t bytes = (size_t)arrays * EPB * CES * sizeof(Real);
+};
+
+// One tile (EPB elements, starting at element tile*EPB) of the tangent apply
+// on NT threads: forward sum factorization from the x-rows of du (and u_k) that
+// each thread holds in cd (ck), the quadrature-point phase, the transposed
+// sweeps and the atomic scatter into out. The caller synchronises the CTA
+// before each call (the shared arrays of the previous tile are reused).
+template <int EPB, int NT, int LAW, int STORAGE>
+__device__ __forceinline__ void apply_tile(const hx::MeshView &m, int tile, Real *__restrict__ out, const Real *cd,
+                                           const Real *ck, unsigned char *smem_raw, uint64_t pol_keep,
+                                           uint64_t pol_stream) {
+    Real *U = (Real *)smem_raw;
+    Real *W = U + EPB * CES;
+    Real *GX = W + EPB * CES;
+    Real *GY = GX + EPB * CES;
+    Real *GZ = GY + EPB * CES;
+    Real *KX = GZ + EPB * CES;  // recompute strategy: gradients of u_k
+    Real *KY = KX + EPB * CES;
+    Real *KZ = KY + EPB * CES;
+    const int t = threadIdx.x;
+    const int el = t / NN;
+    const int a = t - el * NN;
+    const int a0 = a % N, a1 = a / N;
+    const bool act = el < EPB;
+    const int eoff = (act ? el : 0) * CES;
+    constexpr bool RC = STORAGE == HX_RECOMPUTE;
+    const int e0 = tile * EPB;
+    const int e = e0 + el;
+    const bool valid = act && e < m.n_elem;
+    // quadrature-point phase: flat over the tile's EPB*NQ points (consecutive
+    // threads read consecutive points of every field: coalesced, no sector
+    // shared between iterations); the data of a thread's next point is
+    // requested one iteration ahead, the first before the forward sweeps
+    constexpr int NFC = STORAGE == HX_RECOMPUTE ? 0 : hx::qp_fields(LAW, STORAGE);
+    constexpr int NR = 10 + NFC;
+        const int nval = min(EPB, m.n_elem - e0) * NQ;  // valid points of this tile
+    const int64_t g0 = (int64_t)e0 * NQ;
+    Real rc[NR], rn[NR];
+    auto load_raw = [&](int q, Real *r) {
+        const Real *geo = (const Real *)m.geo + g0 + q;
+#pragma unroll
+        for (int f = 0; f < 10; ++f) r[f] = ld_stream(geo + (int64_t)f * m.n_qp, pol_stream);
+        if constexpr (NFC > 0) {
+            const Real *qp = (const Real *)m.qp + g0 + q;
+#pragma unroll
+            for (int f = 0; f < NFC; ++f) r[10 + f] = ld_stream(qp + (int64_t)f * m.n_qp, pol_stream);
+        }
+    };
+    if (t < nval) load_raw(t, rc);
+    if constexpr (RC) col_forward(ck, U, W, KX, KY, KZ, act, eoff, a0, a1);
+    col_forward(cd, U, W, GX, GY, GZ, act, eoff, a0, a1);
+#pragma unroll 1
+    for (int q = t; q < nval; q += NT) {
+        if (q + NT < nval) load_raw(q + NT, rn);
+        const int qel = q / NQ;
+        const int ql = q - qel * NQ;
+        const int pos = qel * CES + (ql % N) + ((ql / N) % N) * CRS + (ql / NN) * CPS;
+        Real Ji[9], Gr[9], H[9], dP[9], Q[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Ji[k] = rc[k];
+        const Real JxW = rc[9];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            Gr[c * 3 + 0] = GX[pos + c * CCZ];
+            Gr[c * 3 + 1] = GY[pos + c * CCZ];
+            Gr[c * 3 + 2] = GZ[pos + c * CCZ];
+        }
+        State<Real> st;
+        if constexpr (STORAGE == HX_RECOMPUTE) {
+            Real Gu[9];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                Gu[c * 3 + 0] = KX[pos + c * CCZ];
+                Gu[c * 3 + 1] = KY[pos + c * CCZ];
+                Gu[c * 3 + 2] = KZ[pos + c * CCZ];
+            }
+            push_grad(Gu, Ji, st.Hk);
+            state_from_Hk<Real, LAW, (bool)HX_UNIT_F32>(m, e0 + qel, st);
+        } else {
+            build_state<Real, LAW, STORAGE>(m, e0 + qel, [&](int f) { return rc[10 + f]; }, st);
+        }
+        push_grad(Gr, Ji, H);
+        tangent_dP<Real, LAW>(st, H, dP);
+        pull_flux(dP, Ji, JxW, Q);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            GX[pos + c * CCZ] = Q[c * 3 + 0];
+            GY[pos + c * CCZ] = Q[c * 3 + 1];
+            GZ[pos + c * CCZ] = Q[c * 3 + 2];
+        }
+#pragma unroll
+        for (int f = 0; f < NR; ++f) rc[f] = rn[f];
+    }
+    __syncthreads();
+    Real x[N], y[N], w[N];
+    if (act) {  // in place: z-lines (qx, qy) GZ = Dz^T GZ, y-lines (qx, qz) GY = Dy^T GY
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int oz = eoff + c * CCZ + line_off<2>(a0, a1);
+            ld_line<2>(GZ + oz, x);
+            mv<TD, true>(x, y);
+            st_line<2>(GZ + oz, y);
+            const int oy = eoff + c * CCZ + line_off<1>(a0, a1);
+            ld_line<1>(GY + oy, x);
+            mv<TD, true>(x, y);
+            st_line<1>(GY + oy, y);
+        }
+    }
+    __syncthreads();
+    if (act) {  // x-lines (qy, qz): U = Bx^T (Dx^T Qx + GY + GZ)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int o = eoff + c * CCZ + line_off<0>(a0, a1);
+            ld_line<0>(GX + o, x);
+            mv<TD, true>(x, y);
+            ld_line<0>(GY + o, w);
+#pragma unroll
+            for (int k = 0; k < N; ++k) y[k] += w[k];
+            ld_line<0>(GZ + o, w);
+#pragma unroll
+            for (int k = 0; k < N; ++k) w[k] += y[k];
+            mv<TB, true>(w, y);
+            st_line<0>(U + o, y);
+        }
+    }
+    __syncthreads();
+    if (act) {  // y-lines (i, qz): W = By^T U
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int o = eoff + c * CCZ + line_off<1>(a0, a1);
+            ld_line<1>(U + o, x);
+            mv<TB, true>(x, y);
+            st_line<1>(W + o, y);
+        }
+    }
+    __syncthreads();
+    if (valid) {  // z-lines (i, j): r = Bz^T W, scattered from registers
+        const int64_t base = elem_base(m, e);
+        const bool msk = m.dmask != nullptr;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int o = eoff + c * CCZ + line_off<2>(a0, a1);
+            ld_line<2>(W + o, x);
+            mv<TB, true>(x, y);
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                const int64_t d = 3 * node_at(m, base, a0, a1, k) + c;
+                if (!(msk && m.dmask[d])) red_add(out + d, y[k], pol_keep);
+            }
+        }
+    }
+}
+
+// out += K(u_k) du over all elements (out zeroed by the caller). Persistent:
+// CTAs walk tiles of EPB elements with stride gridDim.x. Each thread loads
+// its element x-row of du (and u_k) straight into registers, one tile ahead.
+template <int EPB, int LAW, int STORAGE>
+__global__ void __launch_bounds__(col_threads(EPB)) k_apply(const hx::MeshView m, const Real *__restrict__ du,
+                                                            Real *__restrict__ out, int ntiles) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int t = threadIdx.x;
+    const int el = t / NN;
+    const int a = t - el * NN;
+    const int a0 = a % N, a1 = a / N;
+    const bool act = el < EPB;
+    const uint64_t pol_keep = policy_evict_last();
+    const uint64_t pol_stream = policy_evict_first();
+    constexpr bool RC = STORAGE == HX_RECOMPUTE;
+    Real rowd[3 * N], rowk[RC ? 3 * N : 1];
+    if (act && (int)blockIdx.x < ntiles) {
+        const int e1 = blockIdx.x * EPB + el;
+        const int64_t b1 = elem_base(m, e1);
+        load_row(m, e1, b1, a0, a1, du, true, rowd);
+        if constexpr (RC) load_row(m, e1, b1, a0, a1, (const Real *)m.uk, false, rowk);
+    }
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int ntile = tile + gridDim.x;
+        if (m.l2pf) prefetch_tile<EPB, STORAGE>(m, ntile);
+        // this tile's rows; the next tile's rows are requested now
+        Real cd[3 * N], ck[RC ? 3 * N : 1];
+#pragma unroll
+        for (int i = 0; i < 3 * N; ++i) cd[i] = rowd[i];
+        if constexpr (RC) {
+#pragma unroll
+            for (int i = 0; i < 3 * N; ++i) ck[i] = rowk[i];
+        }
+        if (act && ntile < ntiles) {
+            const int e1 = ntile * EPB + el;
+            const int64_t b1 = elem_base(m, e1);
+            load_row(m, e1, b1, a0, a1, du, true, rowd);
+            if constexpr (RC) load_row(m, e1, b1, a0, a1, (const Real *)m.uk, false, rowk);
+        }
+        __syncthreads();  // the previous tile is done with the shared arrays
+        apply_tile<EPB, col_threads(EPB), LAW, STORAGE>(m, tile, out, cd, ck, smem_raw, pol_keep, pol_stream);
+    }
+}
+
+// One work item of a batch (one tile of one mesh) on NT threads: the rows are
+// loaded at the start of the item (no prefetch across items, which may belong
+// to meshes of other degrees).
+template <int EPB, int NT, int LAW, int STORAGE>
+__device__ __forceinline__ void batch_tile(const hx::MeshView &m, int tile, const Real *__restrict__ du,
+                                           Real *__restrict__ out, unsigned char *smem_raw) {
+    const int t = threadIdx.x;
+    const int el = t / NN;
+    const int a = t - el * NN;
+    const int a0 = a % N, a1 = a / N;
+    constexpr bool RC = STORAGE == HX_RECOMPUTE;
+    Real cd[3 * N], ck[RC ? 3 * N : 1];
+    if (el < EPB) {
+        const int e1 = tile * EPB + el;
+        const int64_t b1 = elem_base(m, e1);
+        load_row(m, e1, b1, a0, a1, du, true, cd);
+        if constexpr (RC) load_row(m, e1, b1, a0, a1, (const Real *)m.uk, false, ck);
+    }
+    apply_tile<EPB, NT, LAW, STORAGE>(m, tile, out, cd, ck, smem_raw, policy_evict_last(), policy_evict_first());
+}
+
+// r += R(u): state recomputed from u at every point, P = (I + Hk) S
+template <int EPB, int LAW>
+__global__ void __launch_bounds__(threads_for(EPB)) k_residual(const hx::MeshView m, const Real *__restrict__ u, Real *__restrict__ r) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real *U = (Real *)smem_raw;
+    Real *W = U + 3 * EPB * SZ;
+    Real *G = W + 3 * EPB * SZ;
+    const int e0 = blockIdx.x * EPB;
+    constexpr int nc = 3 * EPB;
+    gather(m, e0, EPB, u, U, false);
+    __syncthreads();
+    forward_grad(U, W, G, nc);
+    for (int it = threadIdx.x; it < EPB * NQ; it += blockDim.x) {
+        const int el = it / NQ;
+        const int q = it - el * NQ;
+        const int e = e0 + el;
+        if (e >= m.n_elem) continue;
+        const int ci = cidx(q % N, (q / N) % N, q / NN);
+        const int64_t g = (int64_t)e * NQ + q;
+        Real Ji[9], JxW, Gr[9], P[9], Q[9];
+        load_geo(m, g, Ji, JxW);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Gr[k] = G[(el * 9 + k) * SZ + ci];
+        State<Real> st;
+        push_grad(Gr, Ji, st.Hk);
+        state_from_Hk<Real, LAW, (bool)HX_UNIT_F32>(m, e, st);
+        flag_state(m, (double)st.Jm1);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                Real s = st.S[SI(c, d)];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) s = fma(st.Hk[c * 3 + k], st.S[SI(k, d)], s);
+                P[c * 3 + d] = s;
+            }
+        pull_flux(P, Ji, JxW, Q);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) G[(el * 9 + k) * SZ + ci] = Q[k];
+    }
+    __syncthreads();
+    backward_int(G, W, U, nc);
+    scatter_add(m, e0, EPB, U, r, true);
+}
+
+// qp cache at state u: interpolation and state in FP64, stored as Real
+template <int EPB, int LAW, int STORAGE>
+__global__ void __launch_bounds__(threads_for(EPB)) k_precompute(const hx::MeshView m, const double *__restrict__ u, Real *__restrict__ qp) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *U = (double *)smem_raw;
+    double *W = U + 3 * EPB * SZ;
+    double *G = W + 3 * EPB * SZ;
+    const int e0 = blockIdx.x * EPB;
+    constexpr int nc = 3 * EPB;
+    gather(m, e0, EPB, u, U, false);
+    __syncthreads();
+    forward_grad(U, W, G, nc);
+    const double *geo = m.geo64;  // FP64 geometry always
+    for (int it = threadIdx.x; it < EPB * NQ; it += blockDim.x) {
+        const int el = it / NQ;
+        const int q = it - el * NQ;
+        const int e = e0 + el;
+        if (e >= m.n_elem) continue;
+        const int ci = cidx(q % N, (q / N) % N, q / NN);
+        const int64_t g = (int64_t)e * NQ + q;
+        double Ji[9], Gr[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Ji[k] = geo[(int64_t)k * m.n_qp + g];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Gr[k] = G[(el * 9 + k) * SZ + ci];
+        State<double> st;
+        push_grad(Gr, Ji, st.Hk);
+        state_from_Hk<double, LAW, false>(m, e, st);
+        flag_state(m, st.Jm1);
+        if constexpr (STORAGE != HX_RECOMPUTE) store_state<Real, LAW, STORAGE>(qp, m.n_qp, g, st);
+    }
+}
+
+// Diagonal: per qp the 3 blocks A_c[d][f] = d(dP_cd)/d(H_cf) pulled back to
+// reference coordinates, M_c = JxW J0^-1 A_c J0^-T (symmetric), then
+// diag_c(a) = sum_q grad_xi N_a^T M_c grad_xi N_a by sum factorization with
+// products of the 1D tables.
+template <int LAW, int STORAGE>
+__global__ void __launch_bounds__(threads_for(2)) k_diagonal(const hx::MeshView m, Real *__restrict__ diag) {
+    constexpr int EPB = 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real *U = (Real *)smem_raw;
+    Real *W = U + 3 * SZ;
+    Real *Gk = W + 3 * SZ;
+    Real *Mc = Gk + 9 * SZ;   // 18 cubes: (c*6 + pair)
+    Real *T1 = Mc + 18 * SZ;  // 18 cubes
+    __shared__ Real tabs[3][NN];  // BB, BG, GG  [q][a]
+    const int e0 = blockIdx.x;
+    for (int i = threadIdx.x; i < NN; i += blockDim.x) {
+        const Real b = tab<TB>(i), gd = tab<TG>(i);
+        tabs[0][i] = b * b;
+        tabs[1][i] = b * gd;
+        tabs[2][i] = gd * gd;
+    }
+    if constexpr (STORAGE == HX_RECOMPUTE) {
+        gather(m, e0, EPB, (const Real *)m.uk, U, false);
+        __syncthreads();
+        forward_grad(U, W, Gk, 3);
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < NQ; q += blockDim.x) {
+        const int e = e0;
+        const int ci = cidx(q % N, (q / N) % N, q / NN);
+        const int64_t g = (int64_t)e * NQ + q;
+        Real Ji[9], JxW;
+        load_geo(m, g, Ji, JxW);
+        State<Real> st;
+        if constexpr (STORAGE == HX_RECOMPUTE) {
+            Real Gu[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) Gu[k] = Gk[k * SZ + ci];
+            push_grad(Gu, Ji, st.Hk);
+            state_from_Hk<Real, LAW, (bool)HX_UNIT_F32>(m, e, st);
+        } else {
+            load_state<Real, LAW, STORAGE>(m, e, g, st);
+        }
+#pragma unroll 1
+        for (int c = 0; c < 3; ++c) {
+            Real A[9];  // A[d*3+f] = dP_cd for H = e_c (x) e_f
+#pragma unroll 1
+            for (int f = 0; f < 3; ++f) {
+                Real H[9], dP[9];
+#pragma unroll
+                for (int k = 0; k < 9; ++k) H[k] = Real(0);
+                H[c * 3 + f] = Real(1);
+                tangent_dP<Real, LAW>(st, H, dP);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) A[d * 3 + f] = dP[c * 3 + d];
+            }
+            // M = JxW Ji A Ji^T
+            Real T9[9];
+#pragma unroll
+            for (int e1 = 0; e1 < 3; ++e1)
+#pragma unroll
+                for (int f = 0; f < 3; ++f) T9[e1 * 3 + f] = fma(Ji[e1 * 3 + 0], A[0 * 3 + f], fma(Ji[e1 * 3 + 1], A[1 * 3 + f], Ji[e1 * 3 + 2] * A[2 * 3 + f]));
+#pragma unroll
+            for (int e1 = 0; e1 < 3; ++e1)
+#pragma unroll
+                for (int e2 = e1; e2 < 3; ++e2) {
+                    const Real v = JxW * fma(T9[e1 * 3 + 0], Ji[e2 * 3 + 0], fma(T9[e1 * 3 + 1], Ji[e2 * 3 + 1], T9[e1 * 3 + 2] * Ji[e2 * 3 + 2]));
+                    Mc[(c * 6 + SI(e1, e2)) * SZ + ci] = (e1 == e2) ? v : Real(2) * v;
+                }
+        }
+    }
+    __syncthreads();
+    // pair (e1,e2) by sym index: 0 (0,0) 1 (1,1) 2 (2,2) 3 (0,1) 4 (0,2) 5 (1,2);
+    // for direction d the 1D table is BB, BG or GG by how many of e1, e2 equal d
+    auto tsel = [](int pair, int d) {
+        const int e1 = pair < 3 ? pair : (pair == 5 ? 1 : 0);
+        const int e2 = pair < 3 ? pair : (pair == 3 ? 1 : 2);
+        return (e1 == d) + (e2 == d);
+    };
+    // x then y contraction (q -> a) per cube
+#pragma unroll 1
+    for (int pass = 0; pass < 2; ++pass) {
+        const Real *in = pass == 0 ? Mc : T1;
+        Real *out = pass == 0 ? T1 : Mc;
+        for (int l = threadIdx.x; l < 18 * NN; l += blockDim.x) {
+            const int cube = l / NN;
+            const int r = l - cube * NN;
+            const int a = r % N, b = r / N;
+            const int off = pass == 0 ? R * (a + N * b) : a + R * N * b;
+            const int str = pass == 0 ? 1 : R;
+            const Real *tb = tabs[tsel(cube % 6, pass)];
+            Real x[N];
+#pragma unroll
+            for (int t = 0; t < N; ++t) x[t] = in[cube * SZ + off + t * str];
+#pragma unroll
+            for (int o = 0; o < N; ++o) {
+                Real s = Real(0);
+#pragma unroll
+                for (int t = 0; t < N; ++t) s = fma(tb[t * N + o], x[t], s);
+                out[cube * SZ + off + o * str] = s;
+            }
+        }
+        __syncthreads();
+    }
+    // z contraction summed over the six pairs -> U cube c
+    for (int l = threadIdx.x; l < 3 * NN; l += blockDim.x) {
+        const int c = l / NN;
+        const int r = l - c * NN;
+        const int off = (r % N) + R * (r / N);
+        Real acc[N];
+#pragma unroll
+        for (int o = 0; o < N; ++o) acc[o] = Real(0);
+#pragma unroll 1
+        for (int pair = 0; pair < 6; ++pair) {
+            const Real *tb = tabs[tsel(pair, 2)];
+            const Real *in = Mc + (c * 6 + pair) * SZ + off;
+            Real x[N];
+#pragma unroll
+            for (int t = 0; t < N; ++t) x[t] = in[t * R * N];
+#pragma unroll
+            for (int o = 0; o < N; ++o)
+#pragma unroll
+                for (int t = 0; t < N; ++t) acc[o] = fma(tb[t * N + o], x[t], acc[o]);
+        }
+#pragma unroll
+        for (int o = 0; o < N; ++o) U[c * SZ + off + o * R * N] = acc[o];
+    }
+    __syncthreads();
+    scatter_add(m, e0, EPB, U, diag, true);
+}
+
+// geometry at every quadrature point: J0 = dX/dxi from the degree-g map,
+// J0^-1 (row-major (J0^-1)_{ed}) and JxW = det J0 * w (FP64 and FP32 copies)
+__global__ void __launch_bounds__(256) k_geometry(const hx::MeshView m, const double *__restrict__ X, const int32_t *__restrict__ gconn,
+                           int g, double *__restrict__ geo64, float *__restrict__ geo32) {
+    const int ng = g + 1, ngg = ng * ng * ng;
+    const int64_t total = m.n_qp;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int e = (int)(idx / NQ);
+        const int q = (int)(idx - (int64_t)e * NQ);
+        const int qx = q % N, qy = (q / N) % N, qz = q / NN;
+        double J0[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int a = 0; a < ngg; ++a) {
+            const int ia = a % ng, ja = (a / ng) % ng, ka = a / (ng * ng);
+            const double vx = cGeoV[g - 1][ia * N + qx], vy = cGeoV[g - 1][ja * N + qy], vz = cGeoV[g - 1][ka * N + qz];
+            const double dx = cGeoD[g - 1][ia * N + qx], dy = cGeoD[g - 1][ja * N + qy], dz = cGeoD[g - 1][ka * N + qz];
+            const double d0 = dx * vy * vz, d1 = vx * dy * vz, d2 = vx * vy * dz;
+            const double *xp = X + 3 * (int64_t)gconn[(int64_t)e * ngg + a];
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                J0[r * 3 + 0] += xp[r] * d0;
+                J0[r * 3 + 1] += xp[r] * d1;
+                J0[r * 3 + 2] += xp[r] * d2;
+            }
+        }
+        const double det = J0[0] * (J0[4] * J0[8] - J0[5] * J0[7]) - J0[1] * (J0[3] * J0[8] - J0[5] * J0[6]) +
+                           J0[2] * (J0[3] * J0[7] - J0[4] * J0[6]);
+        if (!(det > 0.0)) atomicOr(m.err + 0, 2);
+        const double id = 1.0 / det;
+        double Ji[9];
+        Ji[0] = (J0[4] * J0[8] - J0[5] * J0[7]) * id;
+        Ji[1] = (J0[2] * J0[7] - J0[1] * J0[8]) * id;
+        Ji[2] = (J0[1] * J0[5] - J0[2] * J0[4]) * id;
+        Ji[3] = (J0[5] * J0[6] - J0[3] * J0[8]) * id;
+        Ji[4] = (J0[0] * J0[8] - J0[2] * J0[6]) * id;
+        Ji[5] = (J0[2] * J0[3] - J0[0] * J0[5]) * id;
+        Ji[6] = (J0[3] * J0[7] - J0[4] * J0[6]) * id;
+        Ji[7] = (J0[1] * J0[6] - J0[0] * J0[7]) * id;
+        Ji[8] = (J0[0] * J0[4] - J0[1] * J0[3]) * id;
+        const double jxw = det * cW[qx] * cW[qy] * cW[qz];
+        for (int k = 0; k < 9; ++k) {
+            geo64[(int64_t)k * total + idx] = Ji[k];
+            geo32[(int64_t)k * total + idx] = (float)Ji[k];
+        }
+        geo64[(int64_t)9 * total + idx] = jxw;
+        geo32[(int64_t)9 * total + idx] = (float)jxw;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_node_coords(const hx::MeshView m, const double *__restrict__ X, const int32_t *__restrict__ gconn,
+                              int g, double *__restrict__ out) {
+    const int ng = g + 1, ngg = ng * ng * ng;
+    const int64_t total = (int64_t)m.n_elem * NQ;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int e = (int)(idx / NQ);
+        const int a = (int)(idx - (int64_t)e * NQ);
+        const int i = a % N, j = (a / N) % N, k = a / NN;
+        double x[3] = {0, 0, 0};
+        for (int b = 0; b < ngg; ++b) {
+            const int ib = b % ng, jb = (b / ng) % ng, kb = b / (ng * ng);
+            const double w = cGeoVn[g - 1][ib * N + i] * cGeoVn[g - 1][jb * N + j] * cGeoVn[g - 1][kb * N + k];
+            const double *xp = X + 3 * (int64_t)gconn[(int64_t)e * ngg + b];
+            x[0] += w * xp[0];
+            x[1] += w * xp[1];
+            x[2] += w * xp[2];
+        }
+        const int64_t nd = node_of(m, e, i, j, k);
+        out[3 * nd + 0] = x[0];
+        out[3 * nd + 1] = x[1];
+        out[3 * nd + 2] = x[2];
+    }
+}
+
+__global__ void k_convert_uk(const double *__restrict__ u, Real *__restrict__ uk, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        uk[i] = (Real)u[i];
+}
+
+// copy the 1D tables of this degree into this unit's constant memory
+cudaError_t op_upload(const double *B, const double *D, const double *Gd, const double *w, const double *geoV,
+                      const double *geoD, const double *geoVn) {
+    Real t[3][NN];
+    for (int i = 0; i < NN; ++i) {
+        t[0][i] = (Real)B[i];
+        t[1][i] = (Real)D[i];
+        t[2][i] = (Real)Gd[i];
+    }
+    cudaError_t e = cudaMemcpyToSymbol(cTab, t, sizeof t);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cW, w, sizeof(double) * N);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cGeoV, geoV, sizeof(double) * 2 * 3 * N);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cGeoD, geoD, sizeof(double) * 2 * 3 * N);
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(cGeoVn, geoVn, sizeof(double) * 2 * 3 * N);
+    return e;
+}

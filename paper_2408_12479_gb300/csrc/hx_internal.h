@@ -84,6 +84,26 @@ struct PrecOps {
 
 const PrecOps *prec_ops(int p, int prec);
 
+// One mesh of a batch as the batch kernel sees it.
+struct BatchMesh {
+    MeshView m;
+    const void *du;
+    void *out;
+    int64_t n_dofs;
+};
+
+// Entry points of the batch unit of one precision (hx_batch.cu).
+struct BatchOps {
+    int prec;
+    cudaError_t (*upload_tables)(int p, const double *B, const double *D, const double *Gd, const double *w,
+                                 const double *geoV, const double *geoD, const double *geoVn);
+    int (*epb)(int p, int storage);  // elements per work item of degree p
+    cudaError_t (*apply)(int law, int storage, const BatchMesh *meshes, const int2 *items, int nitems,
+                         cudaStream_t s);
+    cudaError_t (*zero)(const BatchMesh *meshes, int nmesh, cudaStream_t s);
+};
+const BatchOps *batch_ops(int prec);
+
 }  // namespace hx
 
 struct hx_ctx {

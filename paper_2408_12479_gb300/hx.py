@@ -292,6 +292,25 @@ def hx_autotune(ctx, mesh, du, out, reps=10):
     return best.value, list(t)
 
 
+def hx_batch_create(ctx, meshes):
+    """Group Mesh objects (same context and law) for one-launch applies."""
+    arr = (C.c_void_p * len(meshes))(*[m.handle.value for m in meshes])
+    out = C.c_void_p()
+    _check(lib().hx_batch_create(ctx, arr, len(meshes), C.byref(out)), ctx)
+    return out
+
+
+def hx_batch_destroy(batch):
+    lib().hx_batch_destroy(batch)
+
+
+def hx_batch_tangent_apply(ctx, batch, dus, outs):
+    """out_i = K_i du_i for every mesh of the batch in one persistent launch."""
+    a = (C.c_void_p * len(dus))(*[d.data_ptr() for d in dus])
+    b = (C.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
+    _check(lib().hx_batch_tangent_apply(batch, a, b, _prec_of(dus[0])), ctx)
+
+
 def hx_measure_fma_peak(ctx, prec):
     f = C.c_double()
     _check(lib().hx_measure_fma_peak(ctx, int(prec), C.byref(f)), ctx)

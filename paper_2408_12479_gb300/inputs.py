@@ -300,3 +300,17 @@ def workload_jittered_cube(p, n=32, seed=SEED_BASE + 2):
     """n^3 cube with interior vertices jittered by +-10% of h, sines at 5% strain."""
     m = box_mesh(n, p, jitter=0.1, seed=seed, name=f"cube{n}_p{p}_jitter")
     return m, sine_field(seed + 17, strain=0.05), seed
+
+
+def workload_batch(n_meshes=64, seed=SEED_BASE + 5):
+    """Batch of independent cNH cubes: n^3 elements with n ~ U{8..24}, degree
+    p ~ U{2,3,4,5}, interior vertices jittered by +-10% of h, each with its own
+    seeded 5% sine state (about 30 M DoFs in total)."""
+    g = rng(seed)
+    out = []
+    for k in range(n_meshes):
+        n = int(g.integers(8, 25))
+        p = int(g.integers(2, 6))
+        m = box_mesh(n, p, jitter=0.1, seed=seed + 100 + k, name=f"batch{k}_cube{n}_p{p}")
+        out.append((m, sine_field(seed + 1000 + k, strain=0.05), seed + 2000 + k))
+    return out

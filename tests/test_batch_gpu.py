@@ -1,0 +1,91 @@
+"""Batched persistent launch: many meshes of mixed degree, size and Newton
+state applied in one launch, each checked against the oracle and against the
+single-mesh kernel."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O
+from paper_2408_12479_gb300 import hx
+from paper_2408_12479_gb300 import inputs as I
+from tests import cases
+from tests._util import rel_inf
+
+pytestmark = pytest.mark.gpu
+
+TOL = {hx.HX_FP64: 1e-12, hx.HX_FP32: 1e-5}
+DT = {hx.HX_FP64: torch.float64, hx.HX_FP32: torch.float32}
+
+
+def _meshes(law, specs, ctx):
+    out = []
+    for k, (n, p) in enumerate(specs):
+        m = cases.small_cube(n, p, law, seed=500 + k, clamp=(k == 1))
+        M, X, u = cases.state_for(m, law, seed=600 + k)
+        if k == 1:
+            u[M.dirichlet] = 0.0
+        G = hx.Mesh(m, cases.MATS[law], ctx=ctx)
+        out.append((m, M, u, G))
+    return out
+
+
+@pytest.mark.parametrize("law", cases.LAWS)
+@pytest.mark.parametrize("storage", [hx.HX_CACHE_F, hx.HX_CACHE_TENSORS])
+@pytest.mark.parametrize("prec", [hx.HX_FP64, hx.HX_FP32])
+def test_batch_matches_oracle_and_single_mesh(law, storage, prec):
+    ctx = hx.hx_create(0)
+    specs = [(3, 4), (2, 6), (4, 2), (3, 3), (2, 5), (5, 1), (3, 4)]
+    items = _meshes(law, specs, ctx)
+    batch = None
+    try:
+        dus, outs = [], []
+        for k, (m, M, u, G) in enumerate(items):
+            G.precompute(torch.tensor(u, dtype=torch.float64, device="cuda"), prec, storage)
+            dus.append(torch.tensor(I.random_direction(m.n_dofs, 700 + k), dtype=DT[prec], device="cuda"))
+            outs.append(torch.full_like(dus[-1], 7.0))  # stale values must be overwritten
+        batch = hx.hx_batch_create(ctx, [it[3] for it in items])
+        for rep in range(2):
+            hx.hx_batch_tangent_apply(ctx, batch, dus, outs)
+            hx.hx_sync(ctx, 60000)
+            mat = cases.oracle_material(law)
+            for k, (m, M, u, G) in enumerate(items):
+                du = dus[k].double().cpu().numpy()
+                ref = O.apply_constrained(M, mat, u, du) if k == 1 else O.apply(M, mat, u, du)
+                got = outs[k].double().cpu().numpy()
+                assert rel_inf(got, ref) < TOL[prec], (k, rel_inf(got, ref))
+                single = G.apply(dus[k]).double().cpu().numpy()
+                assert rel_inf(got, single) < (1e-14 if prec == hx.HX_FP64 else 1e-6)
+    finally:
+        if batch is not None:
+            hx.hx_batch_destroy(batch)
+        for it in items:
+            it[3].close()
+        hx.hx_destroy(ctx)
+
+
+def test_batch_statuses():
+    ctx = hx.hx_create(0)
+    items = _meshes("cNH", [(2, 2), (2, 3)], ctx)
+    other = hx.Mesh(cases.small_cube(2, 2, "iNH"), cases.MATS["iNH"], ctx=ctx)
+    try:
+        with pytest.raises(hx.HxError) as e:
+            hx.hx_batch_create(ctx, [items[0][3], other])
+        assert e.value.status == hx.HX_ERR_ARG
+        batch = hx.hx_batch_create(ctx, [it[3] for it in items])
+        dus = [it[3].zeros() for it in items]
+        outs = [torch.zeros_like(d) for d in dus]
+        with pytest.raises(hx.HxError) as e:
+            hx.hx_batch_tangent_apply(ctx, batch, dus, outs)
+        assert e.value.status == hx.HX_ERR_NOT_READY
+        for it in items:
+            it[3].precompute(torch.tensor(it[2], device="cuda"), hx.HX_FP64, hx.HX_RECOMPUTE)
+        with pytest.raises(hx.HxError) as e:
+            hx.hx_batch_tangent_apply(ctx, batch, dus, outs)
+        assert e.value.status == hx.HX_ERR_UNSUPPORTED
+        hx.hx_batch_destroy(batch)
+    finally:
+        other.close()
+        for it in items:
+            it[3].close()
+        hx.hx_destroy(ctx)
