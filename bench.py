@@ -166,6 +166,60 @@ def run_batch(device, steps=20):
     return res
 
 
+def run_solve(device, n=48, p=4, tol=1e-8, max_iter=20000, degree=5, smoothing_range=15.0, J_target=0.9999,
+              sine_amp=1e-5):
+    """Newton-step solve on the compressed iNH cube (kappa = 1e3 mu): FP64 CG on
+    K(u) du = -R(u) with a Chebyshev(degree)-Jacobi preconditioner applied in
+    FP32 and, for comparison, in FP64; both stop at the same FP64 true-residual
+    ratio. The state keeps the pressure below mu (J ~ 0.9999) so that K is
+    positive definite; at J ~ 0.9 the pressure (~95 mu) makes rotation-dominated
+    modes unstable and CG reports the non-positive curvature (recorded too)."""
+    import torch
+    from paper_2408_12479_gb300 import hx
+    from paper_2408_12479_gb300 import inputs as I
+    m, field, seed = I.workload_compressed_cube(n=n, p=p, J_target=J_target, sine_amp=sine_amp)
+    mat = dict(I.MAT_INH)
+    G = hx.Mesh(m, mat, device=device)
+    X = G.node_coords().cpu().numpy()
+    u = torch.tensor(field(X).ravel(), dtype=torch.float64, device=G.device)
+    G.precompute(u, hx.HX_FP64, hx.HX_CACHE_TENSORS)
+    G.precompute(u, hx.HX_FP32, hx.HX_CACHE_TENSORS)
+    r = G.residual(u)
+    rhs = -r
+    dinv = 1.0 / G.diagonal(hx.HX_FP64)
+    lam = hx.hx_estimate_lambda_max(G.ctx, G.handle, dinv, iters=40, seed=7)
+    G.sync(120000)
+    res = {"workload": f"iNH kappa=1e3 mu, {n}^3 jittered cube, p={p}, J~{J_target}, symmetry clamps",
+           "n_dofs": G.n_dofs, "lambda_max_est": lam, "lambda_max_used": 1.2 * lam, "degree": degree,
+           "smoothing_range": smoothing_range, "tol": tol}
+    for name, pp in (("fp32_precond", hx.HX_FP32), ("fp64_precond", hx.HX_FP64)):
+        x = torch.zeros_like(u)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        it, rel, st = hx.hx_cg_solve(G.ctx, G.handle, rhs, x, tol, max_iter, degree, 1.2 * lam, smoothing_range, pp)
+        torch.cuda.synchronize()
+        res[name] = {"iterations": it, "true_rel_residual": rel, "seconds": round(time.perf_counter() - t0, 3),
+                     "status": hx.STATUS_NAMES.get(st, st)}
+    res["speedup_fp32_precond"] = round(res["fp64_precond"]["seconds"] / res["fp32_precond"]["seconds"], 3)
+    G.close()
+    # the literal J ~ 0.9 state: CG must stop with a non-positive-curvature status
+    m9, f9, _ = I.workload_compressed_cube(n=n, p=p, J_target=0.9, sine_amp=0.005)
+    G9 = hx.Mesh(m9, mat, device=device)
+    u9 = torch.tensor(f9(G9.node_coords().cpu().numpy()).ravel(), dtype=torch.float64, device=G9.device)
+    G9.precompute(u9, hx.HX_FP64, hx.HX_CACHE_TENSORS)
+    G9.precompute(u9, hx.HX_FP32, hx.HX_CACHE_TENSORS)
+    d9 = 1.0 / G9.diagonal(hx.HX_FP64)
+    lam9 = hx.hx_estimate_lambda_max(G9.ctx, G9.handle, d9, iters=40, seed=7)
+    try:
+        it9, rel9, st9 = hx.hx_cg_solve(G9.ctx, G9.handle, -G9.residual(u9), torch.zeros_like(u9), tol, 200, degree,
+                                        1.2 * lam9, smoothing_range, hx.HX_FP32)
+        res["J0.9_state"] = {"status": hx.STATUS_NAMES.get(st9, st9), "iterations": it9}
+    except hx.HxError as e:
+        res["J0.9_state"] = {"status": str(e)[:120]}
+    G9.close()
+    return res
+
+
 def cpu_baseline(m, field, seed, p, mat_d, target_s=12.0):
     """The FP64 oracle's full-tensor apply on a bounded sample of the same mesh
     (leading elements), on all host cores; scaled to GDoF/s of the whole mesh."""
@@ -241,6 +295,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--storage", default="best", choices=["best", "recompute", "cache_F", "cache_tensors"])
     ap.add_argument("--prec", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--solve", type=int, default=16,
+                    help="also run the FP32- vs FP64-preconditioned CG solve on an n^3 compressed cube (n given)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -352,6 +408,9 @@ def main():
     batch = None
     if rank == 0 and not args.no_sweep:
         batch = run_batch(local)
+    solve = None
+    if rank == 0 and args.solve and not args.no_sweep:
+        solve = run_solve(local, n=args.solve)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -379,6 +438,7 @@ def main():
             "cpu_baseline": cpu,
             "sweep": sweep,
             "batch": batch,
+            "solve": solve,
         }
         print(json.dumps(line))
     if world > 1:

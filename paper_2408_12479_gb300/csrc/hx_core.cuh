@@ -818,6 +818,72 @@ struct ApplySmem {
     static constexpr size_t bytes = (size_t)arrays * EPB * CES * sizeof(Real);
 };
 
+// Test-gradient integration of the per-point coefficients Q (x, y, z parts in
+// GX, GY, GZ, overwritten) back to nodal values and the atomic scatter into
+// out: Dz^T and Dy^T in place, then Bx^T (Dx^T Qx + .), By^T, Bz^T and the
+// scatter from registers. Called after a CTA barrier.
+__device__ __forceinline__ void col_backward(const hx::MeshView &m, Real *U, Real *W, Real *GX, Real *GY, Real *GZ,
+                                             bool act, bool valid, int eoff, int a0, int a1, int e,
+                                             Real *__restrict__ out, uint64_t pol_keep) {
+    Real x[N], y[N], w[N];
+    if (act) {  // in place: z-lines (qx, qy) GZ = Dz^T GZ, y-lines (qx, qz) GY = Dy^T GY
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int oz = eoff + c * CCZ + line_off<2>(a0, a1);
+            ld_line<2>(GZ + oz, x);
+            mv<TD, true>(x, y);
+            st_line<2>(GZ + oz, y);
+            const int oy = eoff + c * CCZ + line_off<1>(a0, a1);
+            ld_line<1>(GY + oy, x);
+            mv<TD, true>(x, y);
+            st_line<1>(GY + oy, y);
+        }
+    }
+    __syncthreads();
+    if (act) {  // x-lines (qy, qz): U = Bx^T (Dx^T Qx + GY + GZ)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int o = eoff + c * CCZ + line_off<0>(a0, a1);
+            ld_line<0>(GX + o, x);
+            mv<TD, true>(x, y);
+            ld_line<0>(GY + o, w);
+#pragma unroll
+            for (int k = 0; k < N; ++k) y[k] += w[k];
+            ld_line<0>(GZ + o, w);
+#pragma unroll
+            for (int k = 0; k < N; ++k) w[k] += y[k];
+            mv<TB, true>(w, y);
+            st_line<0>(U + o, y);
+        }
+    }
+    __syncthreads();
+    if (act) {  // y-lines (i, qz): W = By^T U
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int o = eoff + c * CCZ + line_off<1>(a0, a1);
+            ld_line<1>(U + o, x);
+            mv<TB, true>(x, y);
+            st_line<1>(W + o, y);
+        }
+    }
+    __syncthreads();
+    if (valid) {  // z-lines (i, j): r = Bz^T W, scattered from registers
+        const int64_t base = elem_base(m, e);
+        const bool msk = m.dmask != nullptr;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int o = eoff + c * CCZ + line_off<2>(a0, a1);
+            ld_line<2>(W + o, x);
+            mv<TB, true>(x, y);
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                const int64_t d = 3 * node_at(m, base, a0, a1, k) + c;
+                if (!(msk && m.dmask[d])) red_add(out + d, y[k], pol_keep);
+            }
+        }
+    }
+}
+
 // One tile (EPB elements, starting at element tile*EPB) of the tangent apply
 // on NT threads: forward sum factorization from the x-rows of du (and u_k) that
 // each thread holds in cd (ck), the quadrature-point phase, the transposed
@@ -910,62 +976,113 @@ __device__ __forceinline__ void apply_tile(const hx::MeshView &m, int tile, Real
         for (int f = 0; f < NR; ++f) rc[f] = rn[f];
     }
     __syncthreads();
-    Real x[N], y[N], w[N];
-    if (act) {  // in place: z-lines (qx, qy) GZ = Dz^T GZ, y-lines (qx, qz) GY = Dy^T GY
+    col_backward(m, U, W, GX, GY, GZ, act, valid, eoff, a0, a1, e, out, pol_keep);
+}
+
+// One tile of the residual R(u) (same structure as apply_tile): the state is
+// rebuilt at every point from the forward gradient of u (Hk = Grad u), then
+// P = (I + Hk) S and Q = JxW P J0^-T. Geometry is read with a one-point-ahead
+// register prefetch.
+template <int EPB, int NT, int LAW>
+__device__ __forceinline__ void residual_tile(const hx::MeshView &m, int tile, Real *__restrict__ out,
+                                              const Real *cu, unsigned char *smem_raw, uint64_t pol_keep,
+                                              uint64_t pol_stream) {
+    Real *U = (Real *)smem_raw;
+    Real *W = U + EPB * CES;
+    Real *GX = W + EPB * CES;
+    Real *GY = GX + EPB * CES;
+    Real *GZ = GY + EPB * CES;
+    const int t = threadIdx.x;
+    const int el = t / NN;
+    const int a = t - el * NN;
+    const int a0 = a % N, a1 = a / N;
+    const bool act = el < EPB;
+    const int eoff = (act ? el : 0) * CES;
+    const int e0 = tile * EPB;
+    const int e = e0 + el;
+    const bool valid = act && e < m.n_elem;
+    const int nval = min(EPB, m.n_elem - e0) * NQ;
+    const int64_t g0 = (int64_t)e0 * NQ;
+    Real rc[10], rn[10];
+    auto load_geo_raw = [&](int q, Real *r) {
+        const Real *geo = (const Real *)m.geo + g0 + q;
+#pragma unroll
+        for (int f = 0; f < 10; ++f) r[f] = ld_stream(geo + (int64_t)f * m.n_qp, pol_stream);
+    };
+    if (t < nval) load_geo_raw(t, rc);
+    col_forward(cu, U, W, GX, GY, GZ, act, eoff, a0, a1);
+#pragma unroll 1
+    for (int q = t; q < nval; q += NT) {
+        if (q + NT < nval) load_geo_raw(q + NT, rn);
+        const int qel = q / NQ;
+        const int ql = q - qel * NQ;
+        const int pos = qel * CES + (ql % N) + ((ql / N) % N) * CRS + (ql / NN) * CPS;
+        Real Ji[9], Gr[9], P[9], Q[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Ji[k] = rc[k];
+        const Real JxW = rc[9];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const int oz = eoff + c * CCZ + line_off<2>(a0, a1);
-            ld_line<2>(GZ + oz, x);
-            mv<TD, true>(x, y);
-            st_line<2>(GZ + oz, y);
-            const int oy = eoff + c * CCZ + line_off<1>(a0, a1);
-            ld_line<1>(GY + oy, x);
-            mv<TD, true>(x, y);
-            st_line<1>(GY + oy, y);
+            Gr[c * 3 + 0] = GX[pos + c * CCZ];
+            Gr[c * 3 + 1] = GY[pos + c * CCZ];
+            Gr[c * 3 + 2] = GZ[pos + c * CCZ];
         }
-    }
-    __syncthreads();
-    if (act) {  // x-lines (qy, qz): U = Bx^T (Dx^T Qx + GY + GZ)
+        State<Real> st;
+        push_grad(Gr, Ji, st.Hk);
+        state_from_Hk<Real, LAW, (bool)HX_UNIT_F32>(m, e0 + qel, st);
+        flag_state(m, (double)st.Jm1);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const int o = eoff + c * CCZ + line_off<0>(a0, a1);
-            ld_line<0>(GX + o, x);
-            mv<TD, true>(x, y);
-            ld_line<0>(GY + o, w);
+        for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int k = 0; k < N; ++k) y[k] += w[k];
-            ld_line<0>(GZ + o, w);
+            for (int d = 0; d < 3; ++d) {
+                Real s = st.S[SI(c, d)];
 #pragma unroll
-            for (int k = 0; k < N; ++k) w[k] += y[k];
-            mv<TB, true>(w, y);
-            st_line<0>(U + o, y);
-        }
-    }
-    __syncthreads();
-    if (act) {  // y-lines (i, qz): W = By^T U
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const int o = eoff + c * CCZ + line_off<1>(a0, a1);
-            ld_line<1>(U + o, x);
-            mv<TB, true>(x, y);
-            st_line<1>(W + o, y);
-        }
-    }
-    __syncthreads();
-    if (valid) {  // z-lines (i, j): r = Bz^T W, scattered from registers
-        const int64_t base = elem_base(m, e);
-        const bool msk = m.dmask != nullptr;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const int o = eoff + c * CCZ + line_off<2>(a0, a1);
-            ld_line<2>(W + o, x);
-            mv<TB, true>(x, y);
-#pragma unroll
-            for (int k = 0; k < N; ++k) {
-                const int64_t d = 3 * node_at(m, base, a0, a1, k) + c;
-                if (!(msk && m.dmask[d])) red_add(out + d, y[k], pol_keep);
+                for (int k = 0; k < 3; ++k) s = fma(st.Hk[c * 3 + k], st.S[SI(k, d)], s);
+                P[c * 3 + d] = s;
             }
+        pull_flux(P, Ji, JxW, Q);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            GX[pos + c * CCZ] = Q[c * 3 + 0];
+            GY[pos + c * CCZ] = Q[c * 3 + 1];
+            GZ[pos + c * CCZ] = Q[c * 3 + 2];
         }
+#pragma unroll
+        for (int f = 0; f < 10; ++f) rc[f] = rn[f];
+    }
+    __syncthreads();
+    col_backward(m, U, W, GX, GY, GZ, act, valid, eoff, a0, a1, e, out, pol_keep);
+}
+
+// r += R(u) over all elements (r zeroed by the caller); persistent like
+// k_apply, with the rows of u (Dirichlet values included) one tile ahead.
+template <int EPB, int LAW>
+__global__ void __launch_bounds__(col_threads(EPB)) k_residual_col(const hx::MeshView m, const Real *__restrict__ u,
+                                                                   Real *__restrict__ r, int ntiles) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int t = threadIdx.x;
+    const int el = t / NN;
+    const int a = t - el * NN;
+    const int a0 = a % N, a1 = a / N;
+    const bool act = el < EPB;
+    const uint64_t pol_keep = policy_evict_last();
+    const uint64_t pol_stream = policy_evict_first();
+    Real row[3 * N];
+    if (act && (int)blockIdx.x < ntiles) {
+        const int e1 = blockIdx.x * EPB + el;
+        load_row(m, e1, elem_base(m, e1), a0, a1, u, false, row);
+    }
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int ntile = tile + gridDim.x;
+        Real cu[3 * N];
+#pragma unroll
+        for (int i = 0; i < 3 * N; ++i) cu[i] = row[i];
+        if (act && ntile < ntiles) {
+            const int e1 = ntile * EPB + el;
+            load_row(m, e1, elem_base(m, e1), a0, a1, u, false, row);
+        }
+        __syncthreads();
+        residual_tile<EPB, col_threads(EPB), LAW>(m, tile, r, cu, smem_raw, pol_keep, pol_stream);
     }
 }
 
@@ -1032,51 +1149,6 @@ __device__ __forceinline__ void batch_tile(const hx::MeshView &m, int tile, cons
         if constexpr (RC) load_row(m, e1, b1, a0, a1, (const Real *)m.uk, false, ck);
     }
     apply_tile<EPB, NT, LAW, STORAGE>(m, tile, out, cd, ck, smem_raw, policy_evict_last(), policy_evict_first());
-}
-
-// r += R(u): state recomputed from u at every point, P = (I + Hk) S
-template <int EPB, int LAW>
-__global__ void __launch_bounds__(threads_for(EPB)) k_residual(const hx::MeshView m, const Real *__restrict__ u, Real *__restrict__ r) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Real *U = (Real *)smem_raw;
-    Real *W = U + 3 * EPB * SZ;
-    Real *G = W + 3 * EPB * SZ;
-    const int e0 = blockIdx.x * EPB;
-    constexpr int nc = 3 * EPB;
-    gather(m, e0, EPB, u, U, false);
-    __syncthreads();
-    forward_grad(U, W, G, nc);
-    for (int it = threadIdx.x; it < EPB * NQ; it += blockDim.x) {
-        const int el = it / NQ;
-        const int q = it - el * NQ;
-        const int e = e0 + el;
-        if (e >= m.n_elem) continue;
-        const int ci = cidx(q % N, (q / N) % N, q / NN);
-        const int64_t g = (int64_t)e * NQ + q;
-        Real Ji[9], JxW, Gr[9], P[9], Q[9];
-        load_geo(m, g, Ji, JxW);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) Gr[k] = G[(el * 9 + k) * SZ + ci];
-        State<Real> st;
-        push_grad(Gr, Ji, st.Hk);
-        state_from_Hk<Real, LAW, (bool)HX_UNIT_F32>(m, e, st);
-        flag_state(m, (double)st.Jm1);
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                Real s = st.S[SI(c, d)];
-#pragma unroll
-                for (int k = 0; k < 3; ++k) s = fma(st.Hk[c * 3 + k], st.S[SI(k, d)], s);
-                P[c * 3 + d] = s;
-            }
-        pull_flux(P, Ji, JxW, Q);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) G[(el * 9 + k) * SZ + ci] = Q[k];
-    }
-    __syncthreads();
-    backward_int(G, W, U, nc);
-    scatter_add(m, e0, EPB, U, r, true);
 }
 
 // qp cache at state u: interpolation and state in FP64, stored as Real

@@ -115,14 +115,20 @@ cudaError_t op_apply(const hx::MeshView &m, int storage, const void *du, void *o
 
 template <int LAW>
 cudaError_t launch_residual_t(const hx::MeshView &m, const void *u, void *r, cudaStream_t s) {
-    constexpr int EPB = epb_default();
-    auto kern = k_residual<EPB, LAW>;
-    const size_t smem = (size_t)15 * EPB * SZ * sizeof(Real);
-    static cudaError_t attr = set_smem(kern, smem);
-    if (attr != cudaSuccess) return attr;
-    const int grid = (m.n_elem + EPB - 1) / EPB;
-    if (grid == 0) return cudaSuccess;
-    kern<<<grid, threads_for(EPB), smem, s>>>(m, (const Real *)u, (Real *)r);
+    constexpr int EPB = EPB_A;
+    auto kern = k_residual_col<EPB, LAW>;
+    constexpr size_t smem = (size_t)5 * EPB * CES * sizeof(Real);
+    static int per_sm = [&] {
+        if (set_smem(kern, smem) != cudaSuccess) return 0;
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, col_threads(EPB), smem) != cudaSuccess) return 0;
+        return b;
+    }();
+    if (per_sm <= 0) return cudaErrorInvalidConfiguration;
+    const int ntiles = (m.n_elem + EPB - 1) / EPB;
+    if (ntiles == 0) return cudaSuccess;
+    const int grid = ntiles < per_sm * sm_count() ? ntiles : per_sm * sm_count();
+    kern<<<grid, col_threads(EPB), smem, s>>>(m, (const Real *)u, (Real *)r, ntiles);
     return cudaGetLastError();
 }
 

@@ -314,3 +314,41 @@ def workload_batch(n_meshes=64, seed=SEED_BASE + 5):
         m = box_mesh(n, p, jitter=0.1, seed=seed + 100 + k, name=f"batch{k}_cube{n}_p{p}")
         out.append((m, sine_field(seed + 1000 + k, strain=0.05), seed + 2000 + k))
     return out
+
+
+def box_dirichlet_symmetry(nx, ny, nz, p):
+    """Symmetry clamps: component x on the face x = 0, y on y = 0, z on z = 0
+    (removes the rigid motions; a compression towards the origin satisfies
+    them)."""
+    Nx, Ny, Nz = nx * p + 1, ny * p + 1, nz * p + 1
+    idx = np.arange(Nx * Ny * Nz)
+    I_, J_, K_ = idx % Nx, (idx // Nx) % Ny, idx // (Nx * Ny)
+    m = np.zeros((idx.size, 3), np.uint8)
+    m[:, 0] = I_ == 0
+    m[:, 1] = J_ == 0
+    m[:, 2] = K_ == 0
+    return m.ravel()
+
+
+@dataclass
+class CompressionField:
+    """u_c = s X_c + a X_c sum_j sin(pi k_cj . X + phi_cj): uniform compression
+    towards the origin (J = (1+s)^3) plus sines that vanish on the symmetry
+    faces X_c = 0."""
+
+    s: float
+    sines: SineField
+
+    def __call__(self, X):
+        X = np.asarray(X, dtype=np.float64)
+        return self.s * X + X * self.sines(X)
+
+
+def workload_compressed_cube(n=48, p=4, J_target=0.9, sine_amp=0.005, seed=SEED_BASE + 3):
+    """n^3 jittered cube (iNH, kappa = 1e3 mu): compression to J ~ J_target plus a
+    small sine perturbation; symmetry clamps on the three faces through the
+    origin."""
+    m = box_mesh(n, p, jitter=0.1, seed=seed, name=f"cube{n}_p{p}_compressed")
+    m.dirichlet = box_dirichlet_symmetry(n, n, n, p)
+    f = CompressionField(J_target ** (1.0 / 3.0) - 1.0, sine_field(seed + 11, amp=sine_amp))
+    return m, f, seed

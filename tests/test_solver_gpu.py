@@ -119,3 +119,25 @@ def test_autograd_backward_is_tangent(prec):
             assert abs(fd - grad @ v) < 1e-6 * abs(grad @ v)
     finally:
         G.close()
+
+
+def test_cg_reports_indefinite_tangent_under_high_pressure():
+    """iNH with kappa = 1e3 mu compressed to J ~ 0.9: the pressure (~95 mu)
+    makes rotation-dominated modes unstable, so p.Kp <= 0 appears and CG must
+    stop with HX_ERR_NAN instead of returning a wrong solution."""
+    m, field, seed = I.workload_compressed_cube(n=4, p=3, J_target=0.9, sine_amp=0.005)
+    G = hx.Mesh(m, dict(I.MAT_INH))
+    try:
+        u = torch.tensor(field(G.node_coords().cpu().numpy()).ravel(), dtype=torch.float64, device="cuda")
+        G.precompute(u, hx.HX_FP64, hx.HX_CACHE_TENSORS)
+        # the constrained tangent has a negative eigenvalue (oracle, dense)
+        M = O.OracleMesh(m)
+        K = O.constrain_matrix(O.assemble_sparse(M, O.Material.from_dict(dict(I.MAT_INH)), u.cpu().numpy()),
+                               M.dirichlet).toarray()
+        assert np.linalg.eigvalsh(K).min() < 0
+        x = torch.zeros_like(u)
+        with pytest.raises(hx.HxError) as e:
+            hx.hx_cg_solve(G.ctx, G.handle, -G.residual(u), x, 1e-10, 500, 0, 1.0, 2.0, hx.HX_FP64)
+        assert e.value.status == hx.HX_ERR_NAN and "curvature" in str(e.value)
+    finally:
+        G.close()
