@@ -46,6 +46,7 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.skip = 0
 
     def __enter__(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -57,6 +58,10 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 5.0:  # first sample before timing starts
+                time.sleep(0.02)
+            self.skip = len(self.lines)
         except Exception:
             self.proc = None
         return self
@@ -76,7 +81,7 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self.lines[self.skip:]:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -90,6 +95,24 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def measured_traffic(p, prec, storage):
+    """DRAM bytes (read + write) per launch of the apply kernel from the
+    committed ncu summary of this (p, prec, storage) workload, if the summary
+    was taken on the current kernel sources; else None."""
+    from paper_2408_12479_gb300.build import kernel_digest
+    path = os.path.join(ROOT, "profiles", f"k_apply_cNH_p{p}_{prec}_{storage}.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for ln in open(path):
+        if ":" in ln and ln.strip().startswith(("traffic_bytes_per_launch", "source_digest")):
+            k, v = ln.strip().strip("`").split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("source_digest") != kernel_digest() or "traffic_bytes_per_launch" not in vals:
+        return None
+    return float(vals["traffic_bytes_per_launch"])
 
 
 def build_case(p, prec, storage, device, law="cNH", n=32):
@@ -263,7 +286,11 @@ def run_reference(args):
     u = field(X).ravel()
     du = I.random_direction(m.n_dofs, seed + 3)
     mat = O.Material.from_dict(mat_d)
-    k = 256
+    # elements per step: sized so that the whole run stays near two minutes
+    t0 = time.perf_counter()
+    O.apply(M, mat, u, du, elems=np.arange(64, dtype=np.int32))
+    per_elem = (time.perf_counter() - t0) / 64
+    k = int(min(1024, max(8, 120.0 / (args.steps + args.warmup) / per_elem)))
     elems = np.arange(k, dtype=np.int32)
     for _ in range(args.warmup):
         O.apply(M, mat, u, du, elems=elems)
@@ -275,8 +302,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": gdofs, "unit": "GDoF/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 * m.n_elem / k,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": f"cNH 32^3 jittered cube p={p}", "p": p,
-                                            "n_dofs": m.n_dofs},
+            "data": "synthetic", "config": {"workload": f"cNH tangent apply, 32^3 jittered cube, p={p}", "p": p,
+                                            "n_dofs": m.n_dofs, "law": "cNH", "prec": "f64",
+                                            "storage": "none (full-tensor oracle)"},
             "cpu_baseline": {"value": gdofs, "unit": "GDoF/s", "cores": O.num_threads(), "kind": "oracle",
                              "sample": f"first {k} of {m.n_elem} elements per step, scaled by the element fraction"},
             "e2e": {"value": gdofs, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -286,7 +314,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=5000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="hx")
     ap.add_argument("--p", type=int, default=4)
@@ -422,15 +450,15 @@ def main():
             "metric": METRIC, "value": round(value, 4), "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(t_max, 5), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
-            "config": {"workload": f"cNH tangent apply, 32^3 jittered cube, p={p}, {args.prec.upper()}, "
-                                   f"storage={hx.STORAGE_NAMES[storage]}",
+            "config": {"workload": f"cNH tangent apply, 32^3 jittered cube, p={p}",
                        "p": p, "n_dofs": n_dofs, "law": "cNH", "prec": args.prec,
                        "storage": hx.STORAGE_NAMES[storage],
                        "l2": "inputs larger than L2 (vectors + qp data %.0f MB > 129 MB)" % (bytes_alg / 1e6),
                        "per_storage_ms": {k: round(v, 4) for k, v in per_storage.items() if v},
                        "tile_variant": G.tune[0], "variant_ms": [round(x, 4) for x in G.tune[1]]},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-                         "frac": round(achieved / hbm_peak, 4), "traffic": None,
+                         "frac": round(achieved / hbm_peak, 4),
+                         "traffic": measured_traffic(p, args.prec, hx.STORAGE_NAMES[storage]),
                          "peak_kind": peak_kind, "bytes_per_launch": bytes_alg},
             "e2e": e2e,
             "gpu_launches": launches,

@@ -148,9 +148,10 @@ hx_status hx_apply_bytes(const hx_mesh *mesh, int32_t storage, int32_t prec, dou
  * keeps, computed in FP64 (J-1 from the components of Grad u, ln J as
  * ln_{+1}(J-1), J^-2/3 exactly) and stored in store_prec. This is Alg. 1's
  * "update quadrature point data" (Sec. 4). The first call per mesh allocates
- * the cache (call it before any stream capture). Returns a status of the
- * previous device-side error, if any; this call's own J <= 0 check is reported
- * by hx_sync. */
+ * the cache (call it before any stream capture). Returns HX_ERR_ARG for a bad
+ * argument, HX_ERR_CUDA if an allocation or launch fails, else HX_OK without
+ * waiting: a J <= 0 or non-finite value met at a quadrature point sets the
+ * mesh's device flag, which hx_sync reports. */
 hx_status hx_precompute_qp(hx_mesh *mesh, const double *u_dev, int32_t store_prec, int32_t storage);
 
 /* r = R(u) (Sec. 2), constrained rows zero. u_dev, r_dev in `prec`. The state

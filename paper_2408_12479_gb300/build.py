@@ -44,6 +44,12 @@ def _sources_digest(extra: str) -> str:
     return h.hexdigest()
 
 
+def kernel_digest() -> str:
+    """Digest of the kernel and C-ABI sources alone (no flags): profile
+    summaries record it so that their counters can be matched to the code."""
+    return _sources_digest("")
+
+
 def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:
     nvcc = _nvcc()
     os.makedirs(LIBDIR, exist_ok=True)
