@@ -321,7 +321,7 @@ def main():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--storage", default="best", choices=["best", "recompute", "cache_F", "cache_tensors"])
+    ap.add_argument("--storage", default="best", choices=["best", "recompute", "cache_F", "cache_tensors", "spatial_tensors"])
     ap.add_argument("--prec", default="f32", choices=["f32", "f64"])
     ap.add_argument("--solve", type=int, default=16,
                     help="also run the FP32- vs FP64-preconditioned CG solve on an n^3 compressed cube (n given)")
@@ -350,7 +350,7 @@ def main():
     best = None
     per_storage = {}
     names = {v: k for k, v in hx.STORAGE_NAMES.items()}
-    cands = (hx.HX_RECOMPUTE, hx.HX_CACHE_F, hx.HX_CACHE_TENSORS) if args.storage == "best" else (names[args.storage],)
+    cands = (hx.HX_RECOMPUTE, hx.HX_CACHE_F, hx.HX_CACHE_TENSORS, hx.HX_SPATIAL_TENSORS) if args.storage == "best" else (names[args.storage],)
     for storage in cands:
         if len(cands) == 1:
             best = (storage, None)
@@ -419,7 +419,7 @@ def main():
         torch.cuda.empty_cache()
         for pp in (2, 3, 4, 5, 6):
             for pr in (hx.HX_FP32, hx.HX_FP64):
-                for st in (hx.HX_RECOMPUTE, hx.HX_CACHE_F, hx.HX_CACHE_TENSORS):
+                for st in (hx.HX_RECOMPUTE, hx.HX_CACHE_F, hx.HX_CACHE_TENSORS, hx.HX_SPATIAL_TENSORS):
                     Gs, ms_, us, dus, outs = build_case(pp, pr, st, local)
                     reps = 30 if pr == hx.HX_FP32 else 5
                     t = time_steps(Gs, dus, outs, reps, 2)

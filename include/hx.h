@@ -72,8 +72,17 @@ typedef enum { HX_FP64 = 0, HX_FP32 = 1 } hx_prec;
  *                     iNH; plus the fibre factors for fiber) -- stage ii;
  *   HX_CACHE_TENSORS  F - I, F^-1, C^-1, S and the tangent scalars -- the
  *                     paper's stage iii "scalars and tensors".
- * Geometry (J0^-1 and JxW per qp) is stored once at mesh setup for all. */
-typedef enum { HX_RECOMPUTE = 0, HX_CACHE_F = 1, HX_CACHE_TENSORS = 2 } hx_storage;
+ * Geometry (J0^-1 and JxW per qp) is stored once at mesh setup for all three.
+ *   HX_SPATIAL_TENSORS integration over the spatial configuration (Sec. 2,
+ *                     Eq. stress_term_in_Ot_with_JC; Sec. 4 "spatial
+ *                     integration" paragraphs; Table 2, Omega_t, tensors):
+ *                     the tangent is (grad v, Jc:(grad du)^S + (grad du) tau)
+ *                     over Omega_0 with grad = Grad F^-1. Stored per qp: the
+ *                     inverse deformed mapping J_t^-1 = J0^-1 F^-1 and the
+ *                     symmetric tensors and scalars of tau and Jc, scaled by
+ *                     JxW (17 fields for cNH, 23 iNH, 35 fiber); the stored
+ *                     geometry is not read. */
+typedef enum { HX_RECOMPUTE = 0, HX_CACHE_F = 1, HX_CACHE_TENSORS = 2, HX_SPATIAL_TENSORS = 3 } hx_storage;
 
 /* Material parameters (Sec. 3, Table 1). lambda is used by cNH only (note
  * Psi_cNH = mu/2(I1 - 3 - 2 ln J) + lambda ln^2 J, so the small-strain Lame
@@ -247,8 +256,8 @@ void hx_batch_destroy(hx_batch *batch);
 /* out_i = K_i du_i for every mesh i in one launch (plus one launch that zeroes
  * the outputs); du/out are host arrays of n_meshes device pointers. Every mesh
  * needs a cache at `prec` from hx_precompute_qp, all with the same caching
- * strategy (HX_CACHE_F or HX_CACHE_TENSORS; HX_RECOMPUTE gives
- * HX_ERR_UNSUPPORTED). */
+ * strategy (HX_CACHE_F, HX_CACHE_TENSORS or HX_SPATIAL_TENSORS; HX_RECOMPUTE
+ * gives HX_ERR_UNSUPPORTED). */
 hx_status hx_batch_tangent_apply(hx_batch *batch, const void *const *du_dev, void *const *out_dev, int32_t prec);
 
 /* ---- measurement support ------------------------------------------------- */

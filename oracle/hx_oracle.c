@@ -15,6 +15,9 @@
  *   tangent   (K du)_{j,a} = sum_e sum_q JxW_q dN_j/dX_b [H S + F D_uS[H]]_ab
  *             with H = Grad du                                             Sec. 2, Eq. (DDu_residual_material)
  *   energy    Pi(u) = sum_e sum_q JxW_q Psi(F_q)                           Sec. 3
+ *   tangent, spatial form (integration over Omega_t, pulled to Omega_0):
+ *             (K du)_{j,a} = sum_e sum_q JxW_q dN_j/dx_b [Jc:(grad du)^S + (grad du) tau]_ab
+ *             with grad = Grad F^-1                                        Sec. 2, Eq. (stress_term_in_Ot_with_JC)
  *
  * Material laws (Sec. 3; derivatives from Appendix A) in their textbook form:
  *   cNH   Psi = mu/2 (I1 - 3 - 2 ln J) + lambda ln^2 J                     Eq. (NH_compressible)
@@ -268,6 +271,91 @@ static void law_dP(const orc_material *m, const orc_fibres *fb, const orc_state 
     for (int i = 0; i < 9; ++i) dP[i] = T1[i] + T2[i];
 }
 
+/* Spatial quantities of Sec. 4 ("spatial integration" paragraphs), from the
+ * definitions: b = F F^T, the Kirchhoff stress tau = F S F^T written per law,
+ * and the action of the pushed-forward moduli J c on a symmetric tensor e:
+ *   cNH   tau = mu b - (mu - 2 lambda ln J) I
+ *         Jc:e = 2 (mu - 2 lambda ln J) e + 2 lambda tr(e) I
+ *   iNH   tau = mu J^-2/3 b + c1 I
+ *         Jc:e = -2 c1 e + c2 tr(e) I - 2 mu/3 J^-2/3 [tr(e) b + (b:e) I]
+ *   fiber tau += sum_i c3 E_i F H_i F^T
+ *         Jc:e += sum_i 2 c3 (2 k2 E_i^2 + 1) [(F H_i F^T) : e] F H_i F^T
+ * with c1, c2 of Sec. 4 and c3 = 2 k1 exp(k2 E_i^2) for an active family.
+ * The iNH moduli are the push-forward of the material D_uS of App. A: its
+ * I (x) C^-1 part maps to tr(e) b + (b:e) I (the Sec. 4 restatement prints
+ * -4 mu/3 J^-2/3 tr(e) C instead; that form is not used). */
+static void law_tau(const orc_material *m, const orc_fibres *fb, const orc_state *s, double *b, double *tau) {
+    double Ft[9];
+    m_transpose(s->F, Ft);
+    m_mul(s->F, Ft, b);
+    if (m->law == 0) {
+        for (int i = 0; i < 9; ++i) tau[i] = m->mu * b[i];
+        double a = m->mu - 2.0 * m->lambda * s->lnJ;
+        tau[0] -= a;
+        tau[4] -= a;
+        tau[8] -= a;
+        return;
+    }
+    double c1 = 0.5 * m->kappa * (s->J * s->J - 1.0) - m->mu / 3.0 * s->j23 * s->I1;
+    for (int i = 0; i < 9; ++i) tau[i] = m->mu * s->j23 * b[i];
+    tau[0] += c1;
+    tau[4] += c1;
+    tau[8] += c1;
+    if (m->law == 2)
+        for (int f = 0; f < 2; ++f)
+            if (s->active[f]) {
+                double E = s->Ei[f], FH[9], h[9];
+                double c3 = 2.0 * m->k1 * exp(m->k2 * E * E);
+                m_mul(s->F, fb->Hs[f], FH);
+                m_mul(FH, Ft, h);
+                for (int i = 0; i < 9; ++i) tau[i] += c3 * E * h[i];
+            }
+}
+
+static void law_Jc(const orc_material *m, const orc_fibres *fb, const orc_state *s, const double *b,
+                   const double *e, double *out) {
+    double tr = m_trace(e);
+    if (m->law == 0) {
+        double a = m->mu - 2.0 * m->lambda * s->lnJ;
+        for (int i = 0; i < 9; ++i) out[i] = 2.0 * a * e[i];
+        out[0] += 2.0 * m->lambda * tr;
+        out[4] += 2.0 * m->lambda * tr;
+        out[8] += 2.0 * m->lambda * tr;
+        return;
+    }
+    double c1 = 0.5 * m->kappa * (s->J * s->J - 1.0) - m->mu / 3.0 * s->j23 * s->I1;
+    double c2 = 2.0 * m->mu / 9.0 * s->j23 * s->I1 + m->kappa * s->J * s->J;
+    double g = 2.0 * m->mu / 3.0 * s->j23;
+    double be = m_ddot(b, e);
+    for (int i = 0; i < 9; ++i) out[i] = -2.0 * c1 * e[i] - g * tr * b[i];
+    for (int d = 0; d < 3; ++d) out[d * 4] += c2 * tr - g * be;
+    if (m->law == 2) {
+        double Ft[9];
+        m_transpose(s->F, Ft);
+        for (int f = 0; f < 2; ++f)
+            if (s->active[f]) {
+                double E = s->Ei[f], FH[9], h[9];
+                double c3 = 2.0 * m->k1 * exp(m->k2 * E * E);
+                m_mul(s->F, fb->Hs[f], FH);
+                m_mul(FH, Ft, h);
+                double cf = 2.0 * c3 * (2.0 * m->k2 * E * E + 1.0) * m_ddot(h, e);
+                for (int i = 0; i < 9; ++i) out[i] += cf * h[i];
+            }
+    }
+}
+
+/* spatial tangent integrand sigma = Jc:(g)^S + g tau for g = grad du */
+static void law_spatial(const orc_material *m, const orc_fibres *fb, const orc_state *s, const double *g,
+                        double *sigma) {
+    double b[9], tau[9], e[9], gt[9];
+    law_tau(m, fb, s, b, tau);
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) e[r * 3 + c] = 0.5 * (g[r * 3 + c] + g[c * 3 + r]);
+    law_Jc(m, fb, s, b, e, sigma);
+    m_mul(g, tau, gt);
+    for (int i = 0; i < 9; ++i) sigma[i] += gt[i];
+}
+
 /* Pointwise evaluation for the material pins: given F (and H), return
  * Psi, S, P and dP. frame may be NULL for the isotropic laws. Returns J. */
 double orc_material_point(const orc_material *m, const double *frame, const double *F, const double *H,
@@ -418,7 +506,7 @@ static void elem_fibres(const orc_mesh *M, const orc_material *m, int e, orc_fib
 /* ------------------------------------------------------------------ */
 /* element kernels                                                      */
 /* ------------------------------------------------------------------ */
-enum { OP_RESIDUAL = 0, OP_APPLY = 1, OP_DIAG = 2 };
+enum { OP_RESIDUAL = 0, OP_APPLY = 1, OP_DIAG = 2, OP_APPLY_SPATIAL = 3 };
 
 /* Element vector of the chosen operator; returns 0, or 1 if J <= 0 or
  * det J0 <= 0 was met at some quadrature point. */
@@ -431,7 +519,7 @@ static int element_vector(const orc_mesh *M, const orc_material *m, const orc_ta
     orc_fibres fb;
     elem_fibres(M, m, e, &fb);
     gather(M, T, e, u, ue);
-    if (op == OP_APPLY) gather(M, T, e, du, due);
+    if (op == OP_APPLY || op == OP_APPLY_SPATIAL) gather(M, T, e, du, due);
     for (int i = 0; i < T->nn * 3; ++i) ve[i] = 0.0;
     for (int q = 0; q < T->qq; ++q) {
         double J0[9];
@@ -459,6 +547,20 @@ static int element_vector(const orc_mesh *M, const orc_material *m, const orc_ta
                 for (int r = 0; r < 3; ++r)
                     ve[a * 3 + r] += JxW * (P[r * 3 + 0] * gX[a * 3 + 0] + P[r * 3 + 1] * gX[a * 3 + 1] +
                                             P[r * 3 + 2] * gX[a * 3 + 2]);
+        } else if (op == OP_APPLY_SPATIAL) {
+            /* g = grad du = (Grad du) F^-1; test gradients dN_j/dx = F^-T dN_j/dX */
+            double H[9], g[9], sig[9];
+            grad_local(T, gX, due, H);
+            m_mul(H, s.Finv, g);
+            law_spatial(m, &fb, &s, g, sig);
+            for (int a = 0; a < T->nn; ++a) {
+                double gx[3];
+                for (int d = 0; d < 3; ++d)
+                    gx[d] = gX[a * 3 + 0] * s.Finv[0 * 3 + d] + gX[a * 3 + 1] * s.Finv[1 * 3 + d] +
+                            gX[a * 3 + 2] * s.Finv[2 * 3 + d];
+                for (int r = 0; r < 3; ++r)
+                    ve[a * 3 + r] += JxW * (sig[r * 3 + 0] * gx[0] + sig[r * 3 + 1] * gx[1] + sig[r * 3 + 2] * gx[2]);
+            }
         } else { /* OP_DIAG: K_e[(a,r),(a,r)] with H = e_r (x) dN_a/dX */
             for (int a = 0; a < T->nn; ++a)
                 for (int r = 0; r < 3; ++r) {
@@ -518,6 +620,11 @@ int orc_residual(const orc_mesh *M, const orc_material *m, const double *u, doub
 int orc_apply(const orc_mesh *M, const orc_material *m, const double *u, const double *du, double *out,
               const int32_t *elems, int n_list) {
     return run_vector_op(M, m, OP_APPLY, u, du, out, elems, n_list);
+}
+
+int orc_apply_spatial(const orc_mesh *M, const orc_material *m, const double *u, const double *du, double *out,
+                      const int32_t *elems, int n_list) {
+    return run_vector_op(M, m, OP_APPLY_SPATIAL, u, du, out, elems, n_list);
 }
 
 int orc_diagonal(const orc_mesh *M, const orc_material *m, const double *u, double *diag, const int32_t *elems,

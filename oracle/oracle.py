@@ -69,11 +69,12 @@ def lib():
             build()
             L = C.CDLL(_LIB)
             P = C.c_void_p
-            for name in ("orc_residual", "orc_apply", "orc_diagonal", "orc_assemble"):
+            for name in ("orc_residual", "orc_apply", "orc_apply_spatial", "orc_diagonal", "orc_assemble"):
                 f = getattr(L, name)
                 f.restype = C.c_int
             L.orc_residual.argtypes = [P, P, P, P, P, C.c_int]
             L.orc_apply.argtypes = [P, P, P, P, P, P, C.c_int]
+            L.orc_apply_spatial.argtypes = [P, P, P, P, P, P, C.c_int]
             L.orc_diagonal.argtypes = [P, P, P, P, P, C.c_int]
             L.orc_assemble.argtypes = [P, P, P, P, P, C.c_int]
             L.orc_energy.restype = C.c_double
@@ -239,6 +240,21 @@ def apply(M: OracleMesh, mat: Material, u, du, elems=None) -> np.ndarray:
     mc = mat.c()
     _check(lib().orc_apply(M.cref(), C.byref(mc), u.ctypes.data, du.ctypes.data, out.ctypes.data, _ptr(e), ne),
            "apply")
+    return out
+
+
+def apply_spatial(M: OracleMesh, mat: Material, u, du, elems=None) -> np.ndarray:
+    """K(u) du in the spatial form of Sec. 2, Eq. (stress_term_in_Ot_with_JC):
+    (grad v, Jc:(grad du)^S + (grad du) tau) with the Sec. 4 spatial tau and
+    Jc per law (iNH moduli pushed forward from App. A). Equal to apply() in
+    exact arithmetic."""
+    u = _vec(u, M.n_dofs)
+    du = _vec(du, M.n_dofs)
+    out = np.zeros(M.n_dofs)
+    e, ne = _elems(elems)
+    mc = mat.c()
+    _check(lib().orc_apply_spatial(M.cref(), C.byref(mc), u.ctypes.data, du.ctypes.data, out.ctypes.data, _ptr(e),
+                                   ne), "apply_spatial")
     return out
 
 

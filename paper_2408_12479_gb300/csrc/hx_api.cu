@@ -221,7 +221,7 @@ struct hx_mesh {
     float *d_fibH32 = nullptr;
     double *d_fibM = nullptr;
     QpCache cache[2];
-    int variant[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    int variant[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};  // autotuned apply variant per (prec, storage)
     // workspace (allocated on first use)
     std::vector<void *> ws;
     void *w_cheb_d[2] = {nullptr, nullptr}, *w_cheb_Kx[2] = {nullptr, nullptr};
@@ -551,10 +551,11 @@ hx_status hx_node_coords(hx_mesh *m, double *X_dev) {
 }
 
 hx_status hx_apply_bytes(const hx_mesh *m, int32_t storage, int32_t prec, double *bytes) {
-    if (!m || !bytes || bad_prec(prec) || storage < 0 || storage > 2) return HX_ERR_ARG;
+    if (!m || !bytes || bad_prec(prec) || storage < HX_RECOMPUTE || storage > HX_SPATIAL_TENSORS) return HX_ERR_ARG;
     const double s = (double)prec_size(prec);
     double b = 2.0 * 3.0 * m->n_nodes * s;    // read du, write out
-    b += 10.0 * m->n_qp * s;                  // J0^-1, JxW
+    if (storage != HX_SPATIAL_TENSORS)
+        b += 10.0 * m->n_qp * s;              // J0^-1, JxW (the spatial fields carry J_t^-1)
     if (storage == HX_RECOMPUTE)
         b += 3.0 * m->n_nodes * s;            // u_k
     else
@@ -568,7 +569,7 @@ hx_status hx_apply_bytes(const hx_mesh *m, int32_t storage, int32_t prec, double
 // hot path
 // ---------------------------------------------------------------------------
 hx_status hx_precompute_qp(hx_mesh *m, const double *u_dev, int32_t store_prec, int32_t storage) {
-    if (!m || !u_dev || bad_prec(store_prec) || storage < HX_RECOMPUTE || storage > HX_CACHE_TENSORS)
+    if (!m || !u_dev || bad_prec(store_prec) || storage < HX_RECOMPUTE || storage > HX_SPATIAL_TENSORS)
         return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_precompute_qp: bad argument");
     hx_ctx *ctx = m->ctx;
     QpCache &c = m->cache[store_prec];
@@ -612,7 +613,7 @@ hx_status hx_tangent_apply(hx_mesh *m, const void *du_dev, void *out_dev, int32_
 }
 
 hx_status hx_autotune(hx_mesh *m, int32_t prec, const void *du_dev, void *out_dev, int32_t reps, int32_t *best_variant,
-                      double times_ms[3]) {
+                      double times_ms[6]) {
     if (!m || bad_prec(prec) || !du_dev || !out_dev || du_dev == out_dev || reps < 1)
         return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_autotune: bad argument");
     hx_ctx *ctx = m->ctx;
@@ -1063,8 +1064,8 @@ struct hx_batch {
     int law = 0;
     hx::BatchMesh *d_meshes = nullptr;
     std::vector<hx::BatchMesh> h;
-    int2 *d_items[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
-    int nitems[2][3] = {{-1, -1, -1}, {-1, -1, -1}};
+    int2 *d_items[2][4] = {{nullptr, nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr, nullptr}};
+    int nitems[2][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}};
 };
 
 extern "C" {

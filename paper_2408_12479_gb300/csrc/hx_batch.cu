@@ -7,7 +7,7 @@
 // CTA mostly stays on one code path -- and dispatches each item to the tile
 // function of its mesh's degree. All items share one block shape (BT threads);
 // the tile size of a degree is the largest that fits BT threads and the
-// shared-memory budget. Batches run the two caching strategies (the
+// shared-memory budget. Batches run the caching strategies (the
 // quadrature-point data of every mesh is refreshed by hx_precompute_qp).
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -31,171 +31,39 @@ constexpr size_t BATCH_SMEM = 160 * 1024;  // shared arrays per CTA at most
 }  // namespace hx_batch_unit
 
 #define HX_P 1
-namespace hxb1 {
-using Real = hx_batch_unit::Real;
-namespace {
-#include "hx_core.cuh"
-
-// elements per work item: at most BT threads (n^2 per element) and at most
-// BATCH_SMEM bytes of shared arrays
-template <int STORAGE>
-constexpr int batch_epb() {
-    constexpr int arrays = STORAGE == HX_RECOMPUTE ? 8 : 5;
-    constexpr int by_threads = hx_batch_unit::BT / NN;
-    constexpr int by_smem = (int)(hx_batch_unit::BATCH_SMEM / ((size_t)arrays * CES * sizeof(Real)));
-    constexpr int e = by_threads < by_smem ? by_threads : by_smem;
-    return e < 1 ? 1 : e;
-}
-template <int STORAGE>
-constexpr size_t batch_smem() {
-    return ApplySmem<batch_epb<STORAGE>(), STORAGE>::bytes;
-}
-template <int LAW, int STORAGE>
-__device__ __noinline__ void tile(const hx::MeshView &m, int t, const void *du, void *out, unsigned char *smem) {
-    batch_tile<batch_epb<STORAGE>(), hx_batch_unit::BT, LAW, STORAGE>(m, t, (const Real *)du, (Real *)out, smem);
-}
-}  // namespace
-}  // namespace hxb1
+#define HXB_NS hxb1
+#include "hx_batch_degree.cuh"
+#undef HXB_NS
 #undef HX_P
 
 #define HX_P 2
-namespace hxb2 {
-using Real = hx_batch_unit::Real;
-namespace {
-#include "hx_core.cuh"
-
-// elements per work item: at most BT threads (n^2 per element) and at most
-// BATCH_SMEM bytes of shared arrays
-template <int STORAGE>
-constexpr int batch_epb() {
-    constexpr int arrays = STORAGE == HX_RECOMPUTE ? 8 : 5;
-    constexpr int by_threads = hx_batch_unit::BT / NN;
-    constexpr int by_smem = (int)(hx_batch_unit::BATCH_SMEM / ((size_t)arrays * CES * sizeof(Real)));
-    constexpr int e = by_threads < by_smem ? by_threads : by_smem;
-    return e < 1 ? 1 : e;
-}
-template <int STORAGE>
-constexpr size_t batch_smem() {
-    return ApplySmem<batch_epb<STORAGE>(), STORAGE>::bytes;
-}
-template <int LAW, int STORAGE>
-__device__ __noinline__ void tile(const hx::MeshView &m, int t, const void *du, void *out, unsigned char *smem) {
-    batch_tile<batch_epb<STORAGE>(), hx_batch_unit::BT, LAW, STORAGE>(m, t, (const Real *)du, (Real *)out, smem);
-}
-}  // namespace
-}  // namespace hxb2
+#define HXB_NS hxb2
+#include "hx_batch_degree.cuh"
+#undef HXB_NS
 #undef HX_P
 
 #define HX_P 3
-namespace hxb3 {
-using Real = hx_batch_unit::Real;
-namespace {
-#include "hx_core.cuh"
-
-// elements per work item: at most BT threads (n^2 per element) and at most
-// BATCH_SMEM bytes of shared arrays
-template <int STORAGE>
-constexpr int batch_epb() {
-    constexpr int arrays = STORAGE == HX_RECOMPUTE ? 8 : 5;
-    constexpr int by_threads = hx_batch_unit::BT / NN;
-    constexpr int by_smem = (int)(hx_batch_unit::BATCH_SMEM / ((size_t)arrays * CES * sizeof(Real)));
-    constexpr int e = by_threads < by_smem ? by_threads : by_smem;
-    return e < 1 ? 1 : e;
-}
-template <int STORAGE>
-constexpr size_t batch_smem() {
-    return ApplySmem<batch_epb<STORAGE>(), STORAGE>::bytes;
-}
-template <int LAW, int STORAGE>
-__device__ __noinline__ void tile(const hx::MeshView &m, int t, const void *du, void *out, unsigned char *smem) {
-    batch_tile<batch_epb<STORAGE>(), hx_batch_unit::BT, LAW, STORAGE>(m, t, (const Real *)du, (Real *)out, smem);
-}
-}  // namespace
-}  // namespace hxb3
+#define HXB_NS hxb3
+#include "hx_batch_degree.cuh"
+#undef HXB_NS
 #undef HX_P
 
 #define HX_P 4
-namespace hxb4 {
-using Real = hx_batch_unit::Real;
-namespace {
-#include "hx_core.cuh"
-
-// elements per work item: at most BT threads (n^2 per element) and at most
-// BATCH_SMEM bytes of shared arrays
-template <int STORAGE>
-constexpr int batch_epb() {
-    constexpr int arrays = STORAGE == HX_RECOMPUTE ? 8 : 5;
-    constexpr int by_threads = hx_batch_unit::BT / NN;
-    constexpr int by_smem = (int)(hx_batch_unit::BATCH_SMEM / ((size_t)arrays * CES * sizeof(Real)));
-    constexpr int e = by_threads < by_smem ? by_threads : by_smem;
-    return e < 1 ? 1 : e;
-}
-template <int STORAGE>
-constexpr size_t batch_smem() {
-    return ApplySmem<batch_epb<STORAGE>(), STORAGE>::bytes;
-}
-template <int LAW, int STORAGE>
-__device__ __noinline__ void tile(const hx::MeshView &m, int t, const void *du, void *out, unsigned char *smem) {
-    batch_tile<batch_epb<STORAGE>(), hx_batch_unit::BT, LAW, STORAGE>(m, t, (const Real *)du, (Real *)out, smem);
-}
-}  // namespace
-}  // namespace hxb4
+#define HXB_NS hxb4
+#include "hx_batch_degree.cuh"
+#undef HXB_NS
 #undef HX_P
 
 #define HX_P 5
-namespace hxb5 {
-using Real = hx_batch_unit::Real;
-namespace {
-#include "hx_core.cuh"
-
-// elements per work item: at most BT threads (n^2 per element) and at most
-// BATCH_SMEM bytes of shared arrays
-template <int STORAGE>
-constexpr int batch_epb() {
-    constexpr int arrays = STORAGE == HX_RECOMPUTE ? 8 : 5;
-    constexpr int by_threads = hx_batch_unit::BT / NN;
-    constexpr int by_smem = (int)(hx_batch_unit::BATCH_SMEM / ((size_t)arrays * CES * sizeof(Real)));
-    constexpr int e = by_threads < by_smem ? by_threads : by_smem;
-    return e < 1 ? 1 : e;
-}
-template <int STORAGE>
-constexpr size_t batch_smem() {
-    return ApplySmem<batch_epb<STORAGE>(), STORAGE>::bytes;
-}
-template <int LAW, int STORAGE>
-__device__ __noinline__ void tile(const hx::MeshView &m, int t, const void *du, void *out, unsigned char *smem) {
-    batch_tile<batch_epb<STORAGE>(), hx_batch_unit::BT, LAW, STORAGE>(m, t, (const Real *)du, (Real *)out, smem);
-}
-}  // namespace
-}  // namespace hxb5
+#define HXB_NS hxb5
+#include "hx_batch_degree.cuh"
+#undef HXB_NS
 #undef HX_P
 
 #define HX_P 6
-namespace hxb6 {
-using Real = hx_batch_unit::Real;
-namespace {
-#include "hx_core.cuh"
-
-// elements per work item: at most BT threads (n^2 per element) and at most
-// BATCH_SMEM bytes of shared arrays
-template <int STORAGE>
-constexpr int batch_epb() {
-    constexpr int arrays = STORAGE == HX_RECOMPUTE ? 8 : 5;
-    constexpr int by_threads = hx_batch_unit::BT / NN;
-    constexpr int by_smem = (int)(hx_batch_unit::BATCH_SMEM / ((size_t)arrays * CES * sizeof(Real)));
-    constexpr int e = by_threads < by_smem ? by_threads : by_smem;
-    return e < 1 ? 1 : e;
-}
-template <int STORAGE>
-constexpr size_t batch_smem() {
-    return ApplySmem<batch_epb<STORAGE>(), STORAGE>::bytes;
-}
-template <int LAW, int STORAGE>
-__device__ __noinline__ void tile(const hx::MeshView &m, int t, const void *du, void *out, unsigned char *smem) {
-    batch_tile<batch_epb<STORAGE>(), hx_batch_unit::BT, LAW, STORAGE>(m, t, (const Real *)du, (Real *)out, smem);
-}
-}  // namespace
-}  // namespace hxb6
+#define HXB_NS hxb6
+#include "hx_batch_degree.cuh"
+#undef HXB_NS
 #undef HX_P
 
 namespace hx_batch_unit {
@@ -288,6 +156,9 @@ cudaError_t op_apply(int law, int storage, const hx::BatchMesh *meshes, const in
     HX_B_CASE(HX_INH, HX_CACHE_TENSORS)
     HX_B_CASE(HX_FIBER, HX_CACHE_F)
     HX_B_CASE(HX_FIBER, HX_CACHE_TENSORS)
+    HX_B_CASE(HX_CNH, HX_SPATIAL_TENSORS)
+    HX_B_CASE(HX_INH, HX_SPATIAL_TENSORS)
+    HX_B_CASE(HX_FIBER, HX_SPATIAL_TENSORS)
 #undef HX_B_CASE
     return cudaErrorInvalidValue;
 }
@@ -301,9 +172,10 @@ cudaError_t op_zero(const hx::BatchMesh *meshes, int nmesh, cudaStream_t s) {
 int op_epb(int p, int storage) {
 #define HX_B_EPB(P)                                                                     \
     case P:                                                                             \
-        return storage == HX_RECOMPUTE ? hxb##P::batch_epb<HX_RECOMPUTE>()              \
-                                       : (storage == HX_CACHE_F ? hxb##P::batch_epb<HX_CACHE_F>() \
-                                                                : hxb##P::batch_epb<HX_CACHE_TENSORS>());
+        return storage == HX_RECOMPUTE   ? hxb##P::batch_epb<HX_RECOMPUTE>()    \
+               : storage == HX_CACHE_F   ? hxb##P::batch_epb<HX_CACHE_F>()      \
+               : storage == HX_CACHE_TENSORS ? hxb##P::batch_epb<HX_CACHE_TENSORS>() \
+                                             : hxb##P::batch_epb<HX_SPATIAL_TENSORS>();
     switch (p) {
         HX_B_EPB(1)
         HX_B_EPB(2)

@@ -600,6 +600,164 @@ __device__ __forceinline__ void pull_flux(const T *P, const T *Ji, T JxW, T *Q) 
         for (int e = 0; e < 3; ++e) Q[c * 3 + e] = JxW * fma(P[c * 3 + 0], Ji[e * 3 + 0], fma(P[c * 3 + 1], Ji[e * 3 + 1], P[c * 3 + 2] * Ji[e * 3 + 2]));
 }
 
+// ---------------------------------------------------------------------------
+// Integration over the spatial configuration (Sec. 2, Eq.
+// stress_term_in_Ot_with_JC; Sec. 4 "spatial integration" paragraphs). With
+// g = grad du = (Grad du) F^-1 = G J_t^-1 (J_t = F J0, the deformed mapping)
+// the tangent integrand is (grad v) : [Jc:g^S + g tau] over Omega_0, i.e.
+//   Q = JxW (Jc:g^S + g tau) J_t^-T.
+// Per law (c1, c2 of Sec. 4; b = F F^T; h_i = F H_i F^T; j = J^-2/3; the iNH
+// moduli pushed forward from the material D_uS, whose I (x) C^-1 part gives
+// tr(e) b + (b:e) I):
+//   cNH:   tau = mu b - c I,  Jc:e = 2c e + 2 lambda tr(e) I,  c = mu - 2 lambda ln J
+//   iNH:   tau = mu j b + c1 I,
+//          Jc:e = -2 c1 e + c2 tr(e) I - (2 mu/3) j [tr(e) b + (b:e) I]
+//   fiber: tau += sum_i c3 E_i h_i,  Jc:e += sum_i 2 c3 (2 k2 E_i^2 + 1) (h_i:e) h_i
+// The multiples of g from the I-part of tau cancel against those of Jc:g^S,
+// which leaves
+//   sigma = g T + a g^T + (b tr g + B:g) I + tr(g) B + sum_i (h^_i:g) h^_i
+// with T = mu b (cNH) or mu j b + sum_i c3 E_i h_i, a = c (cNH) or -c1,
+// b = 2 lambda (cNH) or c2, B = -(2 mu/3) j b (iNH, fiber) and
+// h^_i = sqrt(2 c3 (2 k2 E_i^2 + 1)) h_i. Every stored tensor and scalar is
+// multiplied by JxW (h^_i by its square root), so that Q = sigma J_t^-T.
+// Field layout (SoA [field][n_qp]): 0-8 J_t^-1 (row-major, g = G J_t^-1),
+// 9-14 T (sym6), 15 a, 16 b; iNH/fiber 17-22 B (sym6); fiber 23-28 h^_4,
+// 29-34 h^_6.
+// ---------------------------------------------------------------------------
+template <int LAW>
+__device__ __forceinline__ void spatial_fields(const State<double> &st, const double *Ji, double JxW,
+                                               const hx::MeshView &m, double *f) {
+    const double mu = m.mat.mu;
+    // J_t^-1 = J0^-1 F^-1
+#pragma unroll
+    for (int e = 0; e < 3; ++e)
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+            f[e * 3 + d] = Ji[e * 3 + 0] * st.Fi[0 * 3 + d] + Ji[e * 3 + 1] * st.Fi[1 * 3 + d] + Ji[e * 3 + 2] * st.Fi[2 * 3 + d];
+    // b = F F^T = I + Hk + Hk^T + Hk Hk^T (no I - I cancellation in the strain part)
+    double b[6];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i; j < 3; ++j) {
+            double v = st.Hk[i * 3 + j] + st.Hk[j * 3 + i];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) v += st.Hk[i * 3 + k] * st.Hk[j * 3 + k];
+            b[SI(i, j)] = v + (i == j ? 1.0 : 0.0);
+        }
+    double T[6], a, bb;
+    if constexpr (LAW == HX_CNH) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) T[k] = mu * b[k];
+        a = mu - 2.0 * m.mat.lambda * st.lnJ;
+        bb = 2.0 * m.mat.lambda;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) T[k] = mu * st.j23 * b[k];
+        a = -st.c1;
+        bb = st.c2;
+        const double ga = -(2.0 / 3.0) * mu * st.j23;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) f[17 + k] = JxW * ga * b[k];
+        if constexpr (LAW == HX_FIBER) {
+            double F[9];
+#pragma unroll
+            for (int k = 0; k < 9; ++k) F[k] = st.Hk[k] + ((k % 4) == 0 ? 1.0 : 0.0);
+#pragma unroll
+            for (int fam = 0; fam < 2; ++fam) {
+                const double *Hs = fam ? st.H6 : st.H4;
+                // h = F H_i F^T
+                double FH[9];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+                        FH[i * 3 + j] = F[i * 3 + 0] * Hs[SI(0, j)] + F[i * 3 + 1] * Hs[SI(1, j)] + F[i * 3 + 2] * Hs[SI(2, j)];
+                double h[6];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = i; j < 3; ++j)
+                        h[SI(i, j)] = FH[i * 3 + 0] * F[j * 3 + 0] + FH[i * 3 + 1] * F[j * 3 + 1] + FH[i * 3 + 2] * F[j * 3 + 2];
+                const double sg = fam ? st.sg6 : st.sg4;   // c3 E_i
+                const double ph = fam ? st.ph6 : st.ph4;   // c3 (2 k2 E_i^2 + 1) >= 0
+                const double sc = sqrt(JxW * 2.0 * ph);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    T[k] += sg * h[k];
+                    f[23 + 6 * fam + k] = sc * h[k];
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) f[9 + k] = JxW * T[k];
+    f[15] = JxW * a;
+    f[16] = JxW * bb;
+}
+
+// Q = sigma(g) J_t^-T from the reference gradient G and the stored fields
+// (get(f) returns field f)
+template <typename T, int LAW, typename Get>
+__device__ __forceinline__ void spatial_Q(const T *G, Get get, T *Q) {
+    T Jt[9], g[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Jt[k] = get(k);
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) g[c * 3 + d] = fma(G[c * 3 + 0], Jt[0 * 3 + d], fma(G[c * 3 + 1], Jt[1 * 3 + d], G[c * 3 + 2] * Jt[2 * 3 + d]));
+    const T tr = g[0] + g[4] + g[8];
+    T Ts[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) Ts[k] = get(9 + k);
+    const T a = get(15);
+    T diag = get(16) * tr;
+    T sig[9];
+    if constexpr (LAW != HX_CNH) {
+        T Bs[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) Bs[k] = get(17 + k);
+        diag = fma(Bs[0], g[0], fma(Bs[1], g[4], fma(Bs[2], g[8], diag)));
+        diag = fma(Bs[3], g[1] + g[3], fma(Bs[4], g[2] + g[6], fma(Bs[5], g[5] + g[7], diag)));
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) sig[c * 3 + d] = tr * Bs[SI(c, d)];
+    } else {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) sig[k] = T(0);
+    }
+    if constexpr (LAW == HX_FIBER) {
+#pragma unroll
+        for (int fam = 0; fam < 2; ++fam) {
+            T h[6];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) h[k] = get(23 + 6 * fam + k);
+            T hg = h[0] * g[0];
+            hg = fma(h[1], g[4], fma(h[2], g[8], hg));
+            hg = fma(h[3], g[1] + g[3], fma(h[4], g[2] + g[6], fma(h[5], g[5] + g[7], hg)));
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) sig[c * 3 + d] = fma(hg, h[SI(c, d)], sig[c * 3 + d]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            T s = fma(a, g[d * 3 + c], sig[c * 3 + d]);
+            if (c == d) s += diag;
+            s = fma(g[c * 3 + 0], Ts[SI(0, d)], fma(g[c * 3 + 1], Ts[SI(1, d)], fma(g[c * 3 + 2], Ts[SI(2, d)], s)));
+            sig[c * 3 + d] = s;
+        }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int e = 0; e < 3; ++e) Q[c * 3 + e] = fma(sig[c * 3 + 0], Jt[e * 3 + 0], fma(sig[c * 3 + 1], Jt[e * 3 + 1], sig[c * 3 + 2] * Jt[e * 3 + 2]));
+}
+
 __device__ __forceinline__ void flag_state(const hx::MeshView &m, double Jm1) {
     if (!(Jm1 > -1.0)) {
         if (Jm1 != Jm1)
@@ -804,10 +962,11 @@ __device__ __forceinline__ void prefetch_tile(const hx::MeshView &m, int tile) {
     const int cnt = min(EPB, m.n_elem - e0);
     const unsigned bytes = (unsigned)(cnt * NQ * sizeof(Real));
     const int nfc = STORAGE == HX_RECOMPUTE ? 0 : m.nf;
+    constexpr int ng = STORAGE == HX_SPATIAL_TENSORS ? 0 : 10;
     const int f = threadIdx.x;
-    if (f >= 10 + nfc || (bytes & 15u)) return;
-    const Real *p = f < 10 ? (const Real *)m.geo + (int64_t)f * m.n_qp + (int64_t)e0 * NQ
-                           : (const Real *)m.qp + (int64_t)(f - 10) * m.n_qp + (int64_t)e0 * NQ;
+    if (f >= ng + nfc || (bytes & 15u)) return;
+    const Real *p = f < ng ? (const Real *)m.geo + (int64_t)f * m.n_qp + (int64_t)e0 * NQ
+                           : (const Real *)m.qp + (int64_t)(f - ng) * m.n_qp + (int64_t)e0 * NQ;
     if (((uintptr_t)p & 15u) == 0) prefetch_l2(p, bytes, policy_evict_first());
 }
 
@@ -915,19 +1074,24 @@ __device__ __forceinline__ void apply_tile(const hx::MeshView &m, int tile, Real
     // threads read consecutive points of every field: coalesced, no sector
     // shared between iterations); the data of a thread's next point is
     // requested one iteration ahead, the first before the forward sweeps
+    // (the spatial strategy's fields include the deformed mapping: no geometry)
+    constexpr bool SP = STORAGE == HX_SPATIAL_TENSORS;
     constexpr int NFC = STORAGE == HX_RECOMPUTE ? 0 : hx::qp_fields(LAW, STORAGE);
-    constexpr int NR = 10 + NFC;
-        const int nval = min(EPB, m.n_elem - e0) * NQ;  // valid points of this tile
+    constexpr int NG = SP ? 0 : 10;
+    constexpr int NR = NG + NFC;
+    const int nval = min(EPB, m.n_elem - e0) * NQ;  // valid points of this tile
     const int64_t g0 = (int64_t)e0 * NQ;
     Real rc[NR], rn[NR];
     auto load_raw = [&](int q, Real *r) {
-        const Real *geo = (const Real *)m.geo + g0 + q;
+        if constexpr (NG > 0) {
+            const Real *geo = (const Real *)m.geo + g0 + q;
 #pragma unroll
-        for (int f = 0; f < 10; ++f) r[f] = ld_stream(geo + (int64_t)f * m.n_qp, pol_stream);
+            for (int f = 0; f < NG; ++f) r[f] = ld_stream(geo + (int64_t)f * m.n_qp, pol_stream);
+        }
         if constexpr (NFC > 0) {
             const Real *qp = (const Real *)m.qp + g0 + q;
 #pragma unroll
-            for (int f = 0; f < NFC; ++f) r[10 + f] = ld_stream(qp + (int64_t)f * m.n_qp, pol_stream);
+            for (int f = 0; f < NFC; ++f) r[NG + f] = ld_stream(qp + (int64_t)f * m.n_qp, pol_stream);
         }
     };
     if (t < nval) load_raw(t, rc);
@@ -939,16 +1103,20 @@ __device__ __forceinline__ void apply_tile(const hx::MeshView &m, int tile, Real
         const int qel = q / NQ;
         const int ql = q - qel * NQ;
         const int pos = qel * CES + (ql % N) + ((ql / N) % N) * CRS + (ql / NN) * CPS;
-        Real Ji[9], Gr[9], H[9], dP[9], Q[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) Ji[k] = rc[k];
-        const Real JxW = rc[9];
+        Real Gr[9], Q[9];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             Gr[c * 3 + 0] = GX[pos + c * CCZ];
             Gr[c * 3 + 1] = GY[pos + c * CCZ];
             Gr[c * 3 + 2] = GZ[pos + c * CCZ];
         }
+        if constexpr (SP) {
+            spatial_Q<Real, LAW>(Gr, [&](int f) { return rc[f]; }, Q);
+        } else {
+        Real Ji[9], H[9], dP[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Ji[k] = rc[k];
+        const Real JxW = rc[9];
         State<Real> st;
         if constexpr (STORAGE == HX_RECOMPUTE) {
             Real Gu[9];
@@ -966,6 +1134,7 @@ __device__ __forceinline__ void apply_tile(const hx::MeshView &m, int tile, Real
         push_grad(Gr, Ji, H);
         tangent_dP<Real, LAW>(st, H, dP);
         pull_flux(dP, Ji, JxW, Q);
+        }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             GX[pos + c * CCZ] = Q[c * 3 + 0];
@@ -1180,7 +1349,14 @@ __global__ void __launch_bounds__(threads_for(EPB)) k_precompute(const hx::MeshV
         push_grad(Gr, Ji, st.Hk);
         state_from_Hk<double, LAW, false>(m, e, st);
         flag_state(m, st.Jm1);
-        if constexpr (STORAGE != HX_RECOMPUTE) store_state<Real, LAW, STORAGE>(qp, m.n_qp, g, st);
+        if constexpr (STORAGE == HX_SPATIAL_TENSORS) {
+            double f[hx::qp_fields(LAW, STORAGE)];
+            spatial_fields<LAW>(st, Ji, geo[(int64_t)9 * m.n_qp + g], m, f);
+#pragma unroll
+            for (int k = 0; k < hx::qp_fields(LAW, STORAGE); ++k) qp[(int64_t)k * m.n_qp + g] = (Real)f[k];
+        } else if constexpr (STORAGE != HX_RECOMPUTE) {
+            store_state<Real, LAW, STORAGE>(qp, m.n_qp, g, st);
+        }
     }
 }
 
@@ -1215,6 +1391,28 @@ __global__ void __launch_bounds__(threads_for(2)) k_diagonal(const hx::MeshView 
         const int e = e0;
         const int ci = cidx(q % N, (q / N) % N, q / NN);
         const int64_t g = (int64_t)e * NQ + q;
+        if constexpr (STORAGE == HX_SPATIAL_TENSORS) {
+            // M_c[e1][e2] = dQ_{c e1} / dG_{c e2}: Q for G = e_c (x) e_e2
+            Real fl[hx::qp_fields(LAW, STORAGE)];
+            const Real *qpd = (const Real *)m.qp;
+#pragma unroll
+            for (int k = 0; k < hx::qp_fields(LAW, STORAGE); ++k) fl[k] = __ldcs(qpd + (int64_t)k * m.n_qp + g);
+#pragma unroll 1
+            for (int c = 0; c < 3; ++c) {
+#pragma unroll 1
+                for (int e2 = 0; e2 < 3; ++e2) {
+                    Real Gu[9], Q[9];
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) Gu[k] = Real(0);
+                    Gu[c * 3 + e2] = Real(1);
+                    spatial_Q<Real, LAW>(Gu, [&](int f) { return fl[f]; }, Q);
+#pragma unroll
+                    for (int e1 = 0; e1 < 3; ++e1)
+                        if (e1 <= e2) Mc[(c * 6 + SI(e1, e2)) * SZ + ci] = (e1 == e2) ? Q[c * 3 + e1] : Real(2) * Q[c * 3 + e1];
+                }
+            }
+            continue;
+        }
         Real Ji[9], JxW;
         load_geo(m, g, Ji, JxW);
         State<Real> st;

@@ -24,6 +24,7 @@ enum Op { OP_APPLY = 0, OP_RESIDUAL = 1, OP_PRECOMPUTE = 2, OP_DIAG = 3 };
 __host__ __device__ constexpr int qp_fields(int law, int storage) {
     if (storage == HX_RECOMPUTE) return 0;
     if (storage == HX_CACHE_F) return law == HX_CNH ? 11 : (law == HX_INH ? 14 : 18);
+    if (storage == HX_SPATIAL_TENSORS) return law == HX_CNH ? 17 : (law == HX_INH ? 23 : 35);
     return law == HX_CNH ? 31 : (law == HX_INH ? 33 : 35);
 }
 

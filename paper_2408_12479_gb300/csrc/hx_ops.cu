@@ -103,12 +103,15 @@ cudaError_t op_apply(const hx::MeshView &m, int storage, const void *du, void *o
     HX_APPLY_CASE(HX_CNH, HX_RECOMPUTE)
     HX_APPLY_CASE(HX_CNH, HX_CACHE_F)
     HX_APPLY_CASE(HX_CNH, HX_CACHE_TENSORS)
+    HX_APPLY_CASE(HX_CNH, HX_SPATIAL_TENSORS)
     HX_APPLY_CASE(HX_INH, HX_RECOMPUTE)
     HX_APPLY_CASE(HX_INH, HX_CACHE_F)
     HX_APPLY_CASE(HX_INH, HX_CACHE_TENSORS)
+    HX_APPLY_CASE(HX_INH, HX_SPATIAL_TENSORS)
     HX_APPLY_CASE(HX_FIBER, HX_RECOMPUTE)
     HX_APPLY_CASE(HX_FIBER, HX_CACHE_F)
     HX_APPLY_CASE(HX_FIBER, HX_CACHE_TENSORS)
+    HX_APPLY_CASE(HX_FIBER, HX_SPATIAL_TENSORS)
 #undef HX_APPLY_CASE
     return cudaErrorInvalidValue;
 }
@@ -164,12 +167,15 @@ cudaError_t op_precompute(const hx::MeshView &m, int storage, const double *u, v
     HX_PRE_CASE(HX_CNH, HX_RECOMPUTE)
     HX_PRE_CASE(HX_CNH, HX_CACHE_F)
     HX_PRE_CASE(HX_CNH, HX_CACHE_TENSORS)
+    HX_PRE_CASE(HX_CNH, HX_SPATIAL_TENSORS)
     HX_PRE_CASE(HX_INH, HX_RECOMPUTE)
     HX_PRE_CASE(HX_INH, HX_CACHE_F)
     HX_PRE_CASE(HX_INH, HX_CACHE_TENSORS)
+    HX_PRE_CASE(HX_INH, HX_SPATIAL_TENSORS)
     HX_PRE_CASE(HX_FIBER, HX_RECOMPUTE)
     HX_PRE_CASE(HX_FIBER, HX_CACHE_F)
     HX_PRE_CASE(HX_FIBER, HX_CACHE_TENSORS)
+    HX_PRE_CASE(HX_FIBER, HX_SPATIAL_TENSORS)
 #undef HX_PRE_CASE
     return cudaErrorInvalidValue;
 }
@@ -191,12 +197,15 @@ cudaError_t op_diagonal(const hx::MeshView &m, int storage, void *diag, cudaStre
     HX_DIAG_CASE(HX_CNH, HX_RECOMPUTE)
     HX_DIAG_CASE(HX_CNH, HX_CACHE_F)
     HX_DIAG_CASE(HX_CNH, HX_CACHE_TENSORS)
+    HX_DIAG_CASE(HX_CNH, HX_SPATIAL_TENSORS)
     HX_DIAG_CASE(HX_INH, HX_RECOMPUTE)
     HX_DIAG_CASE(HX_INH, HX_CACHE_F)
     HX_DIAG_CASE(HX_INH, HX_CACHE_TENSORS)
+    HX_DIAG_CASE(HX_INH, HX_SPATIAL_TENSORS)
     HX_DIAG_CASE(HX_FIBER, HX_RECOMPUTE)
     HX_DIAG_CASE(HX_FIBER, HX_CACHE_F)
     HX_DIAG_CASE(HX_FIBER, HX_CACHE_TENSORS)
+    HX_DIAG_CASE(HX_FIBER, HX_SPATIAL_TENSORS)
 #undef HX_DIAG_CASE
     return cudaErrorInvalidValue;
 }

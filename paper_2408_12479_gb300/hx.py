@@ -23,10 +23,11 @@ HX_OK, HX_ERR_ARG, HX_ERR_CUDA, HX_ERR_NONINVERTIBLE, HX_ERR_NOT_READY = 0, 1, 2
 HX_ERR_TIMEOUT, HX_ERR_NOT_CONVERGED, HX_ERR_NAN, HX_ERR_UNSUPPORTED = 5, 6, 7, 8
 HX_CNH, HX_INH, HX_FIBER = 0, 1, 2
 HX_FP64, HX_FP32 = 0, 1
-HX_RECOMPUTE, HX_CACHE_F, HX_CACHE_TENSORS = 0, 1, 2
+HX_RECOMPUTE, HX_CACHE_F, HX_CACHE_TENSORS, HX_SPATIAL_TENSORS = 0, 1, 2, 3
 STATUS_NAMES = {0: "HX_OK", 1: "HX_ERR_ARG", 2: "HX_ERR_CUDA", 3: "HX_ERR_NONINVERTIBLE", 4: "HX_ERR_NOT_READY",
                 5: "HX_ERR_TIMEOUT", 6: "HX_ERR_NOT_CONVERGED", 7: "HX_ERR_NAN", 8: "HX_ERR_UNSUPPORTED"}
-STORAGE_NAMES = {HX_RECOMPUTE: "recompute", HX_CACHE_F: "cache_F", HX_CACHE_TENSORS: "cache_tensors"}
+STORAGE_NAMES = {HX_RECOMPUTE: "recompute", HX_CACHE_F: "cache_F", HX_CACHE_TENSORS: "cache_tensors",
+                 HX_SPATIAL_TENSORS: "spatial_tensors"}
 
 # every symbol the header declares
 EXPORTS = ["hx_create", "hx_destroy", "hx_set_stream", "hx_last_error", "hx_sync", "hx_setup_mesh",

@@ -31,7 +31,7 @@ def _meshes(law, specs, ctx):
 
 
 @pytest.mark.parametrize("law", cases.LAWS)
-@pytest.mark.parametrize("storage", [hx.HX_CACHE_F, hx.HX_CACHE_TENSORS])
+@pytest.mark.parametrize("storage", [hx.HX_CACHE_F, hx.HX_CACHE_TENSORS, hx.HX_SPATIAL_TENSORS])
 @pytest.mark.parametrize("prec", [hx.HX_FP64, hx.HX_FP32])
 def test_batch_matches_oracle_and_single_mesh(law, storage, prec):
     ctx = hx.hx_create(0)

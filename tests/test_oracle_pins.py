@@ -310,6 +310,23 @@ def test_tangent_is_residual_derivative_and_symmetric(law):
     assert abs(a - b) < 1e-12 * abs(a)
 
 
+@pytest.mark.parametrize("law", ["cNH", "iNH", "fiber"])
+def test_spatial_form_tangent_is_residual_derivative(law):
+    """The spatial-configuration tangent (Sec. 2 Eq. stress_term_in_Ot_with_JC
+    with the Sec. 4 tau and Jc, iNH moduli pushed forward from App. A) is the
+    derivative of the material residual and equals the material-form tangent."""
+    m, mat = _small(law)
+    M = O.OracleMesh(m)
+    u = _state(M, 43, fibre=law == "fiber")
+    g = np.random.Generator(np.random.PCG64(44))
+    du = g.uniform(-1, 1, size=m.n_dofs)
+    h = 1e-6
+    fd = (O.residual(M, mat, u + h * du) - O.residual(M, mat, u - h * du)) / (2 * h)
+    Ks = O.apply_spatial(M, mat, u, du)
+    assert rel_inf(Ks, fd) < 1e-7
+    assert rel_inf(Ks, O.apply(M, mat, u, du)) < 1e-12
+
+
 @pytest.mark.parametrize("p", [1, 2, 3])
 @pytest.mark.parametrize("name,mat,lam_lin", [("cNH", CNH, 20.0), ("iNH", INH, 50.0 - 2.0 / 3.0)])
 def test_tangent_at_rest_is_linear_elastic_stiffness(p, name, mat, lam_lin):

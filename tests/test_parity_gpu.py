@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 
 TOL = {hx.HX_FP64: 1e-12, hx.HX_FP32: 1e-5}
 DT = {hx.HX_FP64: torch.float64, hx.HX_FP32: torch.float32}
-STORAGES = [hx.HX_RECOMPUTE, hx.HX_CACHE_F, hx.HX_CACHE_TENSORS]
+STORAGES = [hx.HX_RECOMPUTE, hx.HX_CACHE_F, hx.HX_CACHE_TENSORS, hx.HX_SPATIAL_TENSORS]
 
 
 def cuda(x, prec=hx.HX_FP64):
