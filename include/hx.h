@@ -179,13 +179,21 @@ hx_status hx_tangent_apply_host(hx_mesh *mesh, const void *du_host, void *out_ho
 
 /* Autotuner: time every compiled variant of the tangent apply for the mesh's
  * current cache at `prec` -- tile shape (elements per CTA: default, half,
- * double) times L2 prefetch of the next tile's quadrature-point data (on for
- * variants 0-2, off for 3-5) -- keep the fastest for later hx_tangent_apply
- * calls, and return its index and the six mean times in ms (a variant that
- * cannot launch reports a negative time). Uses du_dev/out_dev as scratch
- * vectors of the mesh's size; synchronous. */
+ * double) times how the quadrature-point data arrives (0-2: per-thread loads
+ * one point ahead plus an L2 prefetch of the next tile; 3-5: bulk copies into
+ * shared memory one tile ahead, quadrature points taken in column order) --
+ * keep the fastest for later hx_tangent_apply calls, and return its index and
+ * the six mean times in ms (a variant that cannot launch, e.g. a staged tile
+ * whose chunks would not be 16-byte aligned or would not fit in shared
+ * memory, reports a negative time). Uses du_dev/out_dev as scratch vectors of
+ * the mesh's size; synchronous. */
 hx_status hx_autotune(hx_mesh *mesh, int32_t prec, const void *du_dev, void *out_dev, int32_t reps,
                       int32_t *best_variant, double times_ms[6]);
+/* Pin the tangent-apply variant (0-5, as numbered by hx_autotune) used for the
+ * mesh's `storage` cache at `prec`. HX_ERR_ARG for an unknown variant; a
+ * variant that cannot launch on this mesh makes hx_tangent_apply return
+ * HX_ERR_CUDA. */
+hx_status hx_set_apply_variant(hx_mesh *mesh, int32_t prec, int32_t storage, int32_t variant);
 
 /* diag(K(u_k)), constrained entries 1 (needed by the Jacobi smoother,
  * Sec. 5); sum-factorized from the per-qp tangent blocks. */

@@ -206,6 +206,7 @@ struct hx_mesh {
     hx_ctx *ctx = nullptr;
     int p = 0, g = 1, n_elem = 0;
     int64_t n_nodes = 0, n_qp = 0, n_geo = 0;
+    int64_t qs = 0;  // field stride of the SoA point arrays (n_qp rounded up to 32)
     int structured = 0, nx = 0, ny = 0, nz = 0;
     int law = 0;
     hx::MatParams mat{};
@@ -257,6 +258,7 @@ hx::MeshView view(const hx_mesh *m, int prec) {
     v.n_elem = m->n_elem;
     v.n_nodes = m->n_nodes;
     v.n_qp = m->n_qp;
+    v.qs = m->qs;
     v.structured = m->structured;
     v.nx = m->nx;
     v.ny = m->ny;
@@ -285,7 +287,7 @@ size_t prec_size(int prec) { return prec == HX_FP64 ? 8 : 4; }
 
 template <typename T>
 cudaError_t dalloc(T **p, size_t n) {
-    return cudaMalloc((void **)p, n * sizeof(T) + 16);
+    return cudaMalloc((void **)p, n * sizeof(T) + 64);  // slack: bulk copies round up to 16 bytes
 }
 
 void dfree(void *p) {
@@ -313,8 +315,8 @@ hx_status hx_create(hx_ctx **ctx, int device, void *cuda_stream) {
     c->device = device;
     c->stream = (cudaStream_t)cuda_stream;
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
-    e = cudaMalloc((void **)&c->d_flags, 2 * sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(c->d_flags, 0, 2 * sizeof(int));
+    e = cudaMalloc((void **)&c->d_flags, 3 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_flags, 0, 3 * sizeof(int));
     if (e != cudaSuccess) {
         delete c;
         return HX_ERR_CUDA;
@@ -357,10 +359,11 @@ hx_status hx_sync(hx_ctx *ctx, int timeout_ms) {
         }
         std::this_thread::sleep_for(std::chrono::microseconds(50));
     }
-    int flags[2] = {0, 0};
+    int flags[3] = {0, 0, 0};
     HX_CUDA(ctx, cudaMemcpy(flags, ctx->d_flags, sizeof flags, cudaMemcpyDeviceToHost));
-    if (flags[0] || flags[1]) {
-        HX_CUDA(ctx, cudaMemset(ctx->d_flags, 0, 2 * sizeof(int)));
+    if (flags[0] || flags[1] || flags[2]) {
+        HX_CUDA(ctx, cudaMemset(ctx->d_flags, 0, 3 * sizeof(int)));
+        if (flags[2]) return fail(ctx, HX_ERR_TIMEOUT, "a kernel gave up waiting for staged quadrature-point data");
         if (flags[1]) return fail(ctx, HX_ERR_NAN, "NaN met in a quadrature-point state");
         return fail(ctx, HX_ERR_NONINVERTIBLE, "J <= 0 or det J0 <= 0 at a quadrature point");
     }
@@ -432,6 +435,7 @@ hx_status hx_setup_mesh(hx_ctx *ctx, const hx_mesh_desc *d, const hx_material *m
     m->n_elem = d->n_elem;
     m->n_nodes = d->n_nodes;
     m->n_qp = (int64_t)d->n_elem * nq;
+    m->qs = (m->n_qp + 31) / 32 * 32;
     m->n_geo = d->n_geo_nodes;
     m->structured = structured;
     m->nx = d->nx;
@@ -513,19 +517,19 @@ hx_status hx_setup_mesh(hx_ctx *ctx, const hx_mesh_desc *d, const hx_material *m
         HX_MCUDA(cudaMemcpy(m->d_fibM, fm.data(), sizeof(double) * fm.size(), cudaMemcpyHostToDevice));
     }
     // geometry at the quadrature points
-    HX_MCUDA(dalloc(&m->d_geo64, 10 * (size_t)m->n_qp));
-    HX_MCUDA(dalloc(&m->d_geo32, 10 * (size_t)m->n_qp));
-    HX_MCUDA(cudaMemsetAsync(ctx->d_flags, 0, 2 * sizeof(int), s));
+    HX_MCUDA(dalloc(&m->d_geo64, 10 * (size_t)m->qs));
+    HX_MCUDA(dalloc(&m->d_geo32, 10 * (size_t)m->qs));
+    HX_MCUDA(cudaMemsetAsync(ctx->d_flags, 0, 3 * sizeof(int), s));
     {
         const hx::MeshView v = view(m, HX_FP64);
         HX_MCUDA(hx::prec_ops(p, HX_FP64)->geometry(v, m->d_geo_nodes, m->d_geo_conn, g, m->d_geo64, m->d_geo32, s));
         ctx->launches++;
     }
     HX_MCUDA(cudaStreamSynchronize(s));
-    int flags[2];
+    int flags[3];
     HX_MCUDA(cudaMemcpy(flags, ctx->d_flags, sizeof flags, cudaMemcpyDeviceToHost));
     if (flags[0]) {
-        HX_MCUDA(cudaMemset(ctx->d_flags, 0, 2 * sizeof(int)));
+        HX_MCUDA(cudaMemset(ctx->d_flags, 0, 3 * sizeof(int)));
         return bail(fail(ctx, HX_ERR_NONINVERTIBLE, "hx_setup_mesh: det J0 <= 0 at a quadrature point"));
     }
 #undef HX_MCUDA
@@ -574,12 +578,12 @@ hx_status hx_precompute_qp(hx_mesh *m, const double *u_dev, int32_t store_prec, 
     hx_ctx *ctx = m->ctx;
     QpCache &c = m->cache[store_prec];
     const size_t bytes = storage == HX_RECOMPUTE ? 3 * (size_t)m->n_nodes * prec_size(store_prec)
-                                                 : (size_t)hx::qp_fields(m->law, storage) * m->n_qp * prec_size(store_prec);
+                                                 : (size_t)hx::qp_fields(m->law, storage) * m->qs * prec_size(store_prec);
     if (c.bytes != bytes) {
         dfree(c.buf);
         c.buf = nullptr;
         c.bytes = 0;
-        HX_CUDA(ctx, cudaMalloc(&c.buf, bytes + 16));
+        HX_CUDA(ctx, cudaMalloc(&c.buf, bytes + 64));  // slack: bulk copies round up to 16 bytes
         c.bytes = bytes;
     }
     c.storage = storage;
@@ -610,6 +614,14 @@ hx_status hx_tangent_apply(hx_mesh *m, const void *du_dev, void *out_dev, int32_
     if (!m || !du_dev || !out_dev || bad_prec(prec) || du_dev == out_dev)
         return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_tangent_apply: bad argument");
     return apply_dev(m, du_dev, out_dev, prec);
+}
+
+hx_status hx_set_apply_variant(hx_mesh *m, int32_t prec, int32_t storage, int32_t variant) {
+    if (!m || bad_prec(prec) || storage < HX_RECOMPUTE || storage > HX_SPATIAL_TENSORS || variant < 0 ||
+        variant >= hx::prec_ops(m->p, prec)->n_variants)
+        return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_set_apply_variant: bad argument");
+    m->variant[prec][storage] = variant;
+    return HX_OK;
 }
 
 hx_status hx_autotune(hx_mesh *m, int32_t prec, const void *du_dev, void *out_dev, int32_t reps, int32_t *best_variant,

@@ -10,7 +10,7 @@ namespace {
 // BATCH_SMEM bytes of shared arrays
 template <int STORAGE>
 constexpr int batch_epb() {
-    constexpr int arrays = ApplySmem<1, STORAGE>::arrays;
+    constexpr int arrays = ApplySmem<1, HX_CNH, STORAGE, false>::arrays;
     constexpr int by_threads = hx_batch_unit::BT / NN;
     constexpr int by_smem = (int)(hx_batch_unit::BATCH_SMEM / ((size_t)arrays * CES * sizeof(Real)));
     constexpr int e = by_threads < by_smem ? by_threads : by_smem;
@@ -18,7 +18,7 @@ constexpr int batch_epb() {
 }
 template <int STORAGE>
 constexpr size_t batch_smem() {
-    return ApplySmem<batch_epb<STORAGE>(), STORAGE>::bytes;
+    return ApplySmem<batch_epb<STORAGE>(), HX_CNH, STORAGE, false>::bytes;
 }
 template <int LAW, int STORAGE>
 __device__ __noinline__ void tile(const hx::MeshView &m, int t, const void *du, void *out, unsigned char *smem) {

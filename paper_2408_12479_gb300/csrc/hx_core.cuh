@@ -510,7 +510,7 @@ __device__ __forceinline__ void build_state(const hx::MeshView &m, int e, Get ge
 template <typename T, int LAW, int STORAGE>
 __device__ __forceinline__ void load_state(const hx::MeshView &m, int e, int64_t g, State<T> &st) {
     const T *qp = (const T *)m.qp;
-    const int64_t nq = m.n_qp;
+    const int64_t nq = m.qs;
     build_state<T, LAW, STORAGE>(m, e, [&](int f) { return __ldcs(qp + (int64_t)f * nq + g); }, st);
 }
 
@@ -578,8 +578,8 @@ template <typename T>
 __device__ __forceinline__ void load_geo(const hx::MeshView &m, int64_t g, T *Ji, T &JxW) {
     const T *geo = (const T *)m.geo;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) Ji[k] = __ldcs(geo + (int64_t)k * m.n_qp + g);
-    JxW = __ldcs(geo + (int64_t)9 * m.n_qp + g);
+    for (int k = 0; k < 9; ++k) Ji[k] = __ldcs(geo + (int64_t)k * m.qs + g);
+    JxW = __ldcs(geo + (int64_t)9 * m.qs + g);
 }
 
 // physical gradient H = G J0^-1 from the reference gradient G (G_{cd} = du_c/dxi_d)
@@ -897,61 +897,113 @@ __device__ __forceinline__ void load_row(const hx::MeshView &m, int e, int64_t b
 }
 
 // forward sum factorization of an element whose x-rows are in the threads'
-// registers (row[3*i + c], x-line (a0, a1)): writes the x-, y- and
-// z-reference derivatives at the Gauss points to GXo, GYo, GZo. A and W are
-// scratch. The caller synchronises before the first call of a tile.
-__device__ __forceinline__ void col_forward(const Real *row, Real *A, Real *W, Real *GXo, Real *GYo, Real *GZo,
-                                            bool act, int eoff, int a0, int a1) {
-    Real x[N], y[N], z[N];
-    if (act) {
+// registers (row[3*i + c], x-line (a0, a1)): leaves the x-, y- and
+// z-reference derivatives at the Gauss points in X0, X1 and X2, which also
+// serve as scratch. X0 must not be read by other threads when the call starts
+// (the last phase of the previous tile reads X1 only); the caller places a
+// CTA barrier after the call before the derivatives are read.
+__device__ __forceinline__ void col_forward(const Real *row, Real *X0, Real *X1, Real *X2, bool act, int eoff, int a0,
+                                            int a1) {
+    Real x[N], y[N];
+    const int o0 = eoff + line_off<0>(a0, a1), o1 = eoff + line_off<1>(a0, a1), o2 = eoff + line_off<2>(a0, a1);
+    if (act) {  // x-lines: X0 = Bx u
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
 #pragma unroll
             for (int i = 0; i < N; ++i) x[i] = row[3 * i + c];
             mv<TB, false>(x, y);
-            st_line<0>(W + eoff + c * CCZ + line_off<0>(a0, a1), y);
+            st_line<0>(X0 + c * CCZ + o0, y);
         }
     }
     __syncthreads();
-    if (act) {
+    if (act) {  // y-lines: X1 = By X0
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const int o = eoff + c * CCZ + line_off<1>(a0, a1);
-            ld_line<1>(W + o, x);
+            ld_line<1>(X0 + c * CCZ + o1, x);
             mv<TB, false>(x, y);
-            st_line<1>(A + o, y);
+            st_line<1>(X1 + c * CCZ + o1, y);
         }
     }
     __syncthreads();
-    if (act) {
+    if (act) {  // z-lines: values V = Bz X1 (in place, per line) and X2 = Dz V
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const int o = eoff + c * CCZ + line_off<2>(a0, a1);
-            ld_line<2>(A + o, x);
-            mv<TB, false>(x, y);   // values at the Gauss points of this column
-            st_line<2>(W + o, y);
-            mv<TD, false>(y, z);
-            st_line<2>(GZo + o, z);
+            ld_line<2>(X1 + c * CCZ + o2, x);
+            mv<TB, false>(x, y);
+            st_line<2>(X1 + c * CCZ + o2, y);
+            mv<TD, false>(y, x);
+            st_line<2>(X2 + c * CCZ + o2, x);
         }
     }
     __syncthreads();
-    if (act) {
+    Real dy[3][N];
+    if (act) {  // x-lines: X0 = Dx V (X0 is free); y-lines: Dy V held until V is read
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const int o0 = eoff + c * CCZ + line_off<0>(a0, a1);
-            ld_line<0>(W + o0, x);
+            ld_line<0>(X1 + c * CCZ + o0, x);
             mv<TD, false>(x, y);
-            st_line<0>(GXo + o0, y);
-            const int o1 = eoff + c * CCZ + line_off<1>(a0, a1);
-            ld_line<1>(W + o1, x);
-            mv<TD, false>(x, y);
-            st_line<1>(GYo + o1, y);
+            st_line<0>(X0 + c * CCZ + o0, y);
+            ld_line<1>(X1 + c * CCZ + o1, x);
+            mv<TD, false>(x, dy[c]);
         }
     }
-    __syncthreads();
+    __syncthreads();  // every y-line of V has been read
+    if (act) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) st_line<1>(X1 + c * CCZ + o1, dy[c]);
+    }
 }
 
-
+// Forward sweeps for the column-ordered quadrature-point phase: as
+// col_forward, but the z-derivative of each thread's z-line (its column of
+// quadrature points, (qx, qy) = (a0, a1)) stays in registers gz[c][k], the
+// x-derivative goes to X0 and the y-derivative to X2 (X1 keeps the values).
+// No final barrier (the caller's barrier completes the sweeps).
+__device__ __forceinline__ void col_forward_c(const Real *row, Real *X0, Real *X1, Real *X2, Real (*gz)[N], bool act,
+                                              int eoff, int a0, int a1) {
+    Real x[N], y[N];
+    const int o0 = eoff + line_off<0>(a0, a1), o1 = eoff + line_off<1>(a0, a1), o2 = eoff + line_off<2>(a0, a1);
+    if (act) {  // x-lines: X0 = Bx u
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+#pragma unroll
+            for (int i = 0; i < N; ++i) x[i] = row[3 * i + c];
+            mv<TB, false>(x, y);
+            st_line<0>(X0 + c * CCZ + o0, y);
+        }
+    }
+    __syncthreads();
+    if (act) {  // y-lines: X1 = By X0
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            ld_line<1>(X0 + c * CCZ + o1, x);
+            mv<TB, false>(x, y);
+            st_line<1>(X1 + c * CCZ + o1, y);
+        }
+    }
+    __syncthreads();
+    if (act) {  // z-lines: values V = Bz X1 (in place, per line), Dz V kept
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            ld_line<2>(X1 + c * CCZ + o2, x);
+            mv<TB, false>(x, y);
+            st_line<2>(X1 + c * CCZ + o2, y);
+            mv<TD, false>(y, gz[c]);
+        }
+    }
+    __syncthreads();
+    if (act) {  // x-lines: X0 = Dx V; y-lines: X2 = Dy V
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            ld_line<0>(X1 + c * CCZ + o0, x);
+            mv<TD, false>(x, y);
+            st_line<0>(X0 + c * CCZ + o0, y);
+            ld_line<1>(X1 + c * CCZ + o1, x);
+            mv<TD, false>(x, y);
+            st_line<1>(X2 + c * CCZ + o1, y);
+        }
+    }
+}
 
 // L2 prefetch of a tile's quadrature-point data (geometry + cache), one
 // contiguous chunk per field; skipped where a chunk is not 16-byte aligned
@@ -965,74 +1017,140 @@ __device__ __forceinline__ void prefetch_tile(const hx::MeshView &m, int tile) {
     constexpr int ng = STORAGE == HX_SPATIAL_TENSORS ? 0 : 10;
     const int f = threadIdx.x;
     if (f >= ng + nfc || (bytes & 15u)) return;
-    const Real *p = f < ng ? (const Real *)m.geo + (int64_t)f * m.n_qp + (int64_t)e0 * NQ
-                           : (const Real *)m.qp + (int64_t)(f - ng) * m.n_qp + (int64_t)e0 * NQ;
+    const Real *p = f < ng ? (const Real *)m.geo + (int64_t)f * m.qs + (int64_t)e0 * NQ
+                           : (const Real *)m.qp + (int64_t)(f - ng) * m.qs + (int64_t)e0 * NQ;
     if (((uintptr_t)p & 15u) == 0) prefetch_l2(p, bytes, policy_evict_first());
 }
 
-template <int EPB, int STORAGE>
-struct ApplySmem {
-    // U, W, GX, GY, GZ; recompute adds KX, KY, KZ
-    static constexpr int arrays = STORAGE == HX_RECOMPUTE ? 8 : 5;
-    static constexpr size_t bytes = (size_t)arrays * EPB * CES * sizeof(Real);
+// quadrature-point fields a strategy reads per point: geometry (J0^-1, JxW;
+// not for the spatial strategy, whose fields carry J_t^-1) and the cache
+template <int LAW, int STORAGE>
+struct QpFields {
+    static constexpr int ng = STORAGE == HX_SPATIAL_TENSORS ? 0 : 10;
+    static constexpr int nc = STORAGE == HX_RECOMPUTE ? 0 : hx::qp_fields(LAW, STORAGE);
+    static constexpr int n = ng + nc;
 };
 
+// Shared memory of an apply CTA: three cubes per element (six for the
+// recompute strategy, which also interpolates Grad u_k), then, for the staged
+// variant, the tile's quadrature-point fields (one EPB*NQ chunk per field).
+template <int EPB, int LAW, int STORAGE, bool STAGED>
+struct ApplySmem {
+    static constexpr int arrays = STORAGE == HX_RECOMPUTE ? 6 : 3;
+    static constexpr size_t cube_bytes = (size_t)arrays * EPB * CES * sizeof(Real);
+    static constexpr size_t field_bytes = (size_t)EPB * NQ * sizeof(Real);
+    // bulk copies need 16-byte aligned starts: every tile offset is a
+    // multiple of field_bytes, and the field strides are padded to 32 points
+    static constexpr bool stageable = field_bytes % 16 == 0;
+    static constexpr size_t bytes =
+        (cube_bytes + 15) / 16 * 16 + (STAGED ? (size_t)QpFields<LAW, STORAGE>::n * field_bytes : 0);
+};
+
+// ---- mbarrier + bulk-copy staging (Hopper/Blackwell async proxy) ------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// Wait for the phase of the given parity; gives up after 2^20 polls or about
+// 2^32 clock cycles and returns false.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    const long long t0 = clock64();
+    for (int it = 0;; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if (it >= (1 << 20) || clock64() - t0 > (1ll << 32)) return false;
+    }
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
+// Issue (one thread) the bulk copies of a tile's quadrature-point fields into
+// the stage; the stage's previous contents must have been consumed (CTA
+// barrier) -- the proxy fence orders those generic reads before the copies.
+template <int EPB, int LAW, int STORAGE>
+__device__ __forceinline__ void stage_issue(const hx::MeshView &m, int tile, Real *stg, uint64_t *bar) {
+    using QF = QpFields<LAW, STORAGE>;
+    constexpr int FE = EPB * NQ;  // stage points per field
+    const int e0 = tile * EPB;
+    const int cnt = min(EPB, m.n_elem - e0);
+    const uint32_t bytes = (uint32_t)((cnt * NQ * (int)sizeof(Real) + 15) / 16 * 16);
+    const uint64_t pol = policy_evict_first();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bar, QF::n * bytes);
+#pragma unroll 1
+    for (int f = 0; f < QF::n; ++f) {
+        const Real *src = f < QF::ng ? (const Real *)m.geo + (int64_t)f * m.qs + (int64_t)e0 * NQ
+                                     : (const Real *)m.qp + (int64_t)(f - QF::ng) * m.qs + (int64_t)e0 * NQ;
+        bulk_g2s(stg + f * FE, src, bytes, bar, pol);
+    }
+}
+
 // Test-gradient integration of the per-point coefficients Q (x, y, z parts in
-// GX, GY, GZ, overwritten) back to nodal values and the atomic scatter into
-// out: Dz^T and Dy^T in place, then Bx^T (Dx^T Qx + .), By^T, Bz^T and the
-// scatter from registers. Called after a CTA barrier.
-__device__ __forceinline__ void col_backward(const hx::MeshView &m, Real *U, Real *W, Real *GX, Real *GY, Real *GZ,
-                                             bool act, bool valid, int eoff, int a0, int a1, int e,
-                                             Real *__restrict__ out, uint64_t pol_keep) {
+// X0, X1, X2, overwritten) back to nodal values and the atomic scatter into
+// out: Dz^T and Dy^T in place, then Bx^T (Dx^T Qx + .) in place, By^T, Bz^T
+// and the scatter from registers. Called after a CTA barrier.
+__device__ __forceinline__ void col_backward(const hx::MeshView &m, Real *X0, Real *X1, Real *X2, bool act, bool valid,
+                                             int eoff, int a0, int a1, int e, Real *__restrict__ out,
+                                             uint64_t pol_keep) {
     Real x[N], y[N], w[N];
-    if (act) {  // in place: z-lines (qx, qy) GZ = Dz^T GZ, y-lines (qx, qz) GY = Dy^T GY
+    const int o0 = eoff + line_off<0>(a0, a1), o1 = eoff + line_off<1>(a0, a1), o2 = eoff + line_off<2>(a0, a1);
+    if (act) {  // in place: z-lines X2 = Dz^T X2, y-lines X1 = Dy^T X1
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const int oz = eoff + c * CCZ + line_off<2>(a0, a1);
-            ld_line<2>(GZ + oz, x);
+            ld_line<2>(X2 + c * CCZ + o2, x);
             mv<TD, true>(x, y);
-            st_line<2>(GZ + oz, y);
-            const int oy = eoff + c * CCZ + line_off<1>(a0, a1);
-            ld_line<1>(GY + oy, x);
+            st_line<2>(X2 + c * CCZ + o2, y);
+            ld_line<1>(X1 + c * CCZ + o1, x);
             mv<TD, true>(x, y);
-            st_line<1>(GY + oy, y);
+            st_line<1>(X1 + c * CCZ + o1, y);
         }
     }
     __syncthreads();
-    if (act) {  // x-lines (qy, qz): U = Bx^T (Dx^T Qx + GY + GZ)
+    if (act) {  // x-lines, in place: X0 = Bx^T (Dx^T X0 + X1 + X2)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const int o = eoff + c * CCZ + line_off<0>(a0, a1);
-            ld_line<0>(GX + o, x);
+            ld_line<0>(X0 + c * CCZ + o0, x);
             mv<TD, true>(x, y);
-            ld_line<0>(GY + o, w);
+            ld_line<0>(X1 + c * CCZ + o0, w);
 #pragma unroll
             for (int k = 0; k < N; ++k) y[k] += w[k];
-            ld_line<0>(GZ + o, w);
+            ld_line<0>(X2 + c * CCZ + o0, w);
 #pragma unroll
             for (int k = 0; k < N; ++k) w[k] += y[k];
             mv<TB, true>(w, y);
-            st_line<0>(U + o, y);
+            st_line<0>(X0 + c * CCZ + o0, y);
         }
     }
     __syncthreads();
-    if (act) {  // y-lines (i, qz): W = By^T U
+    if (act) {  // y-lines: X1 = By^T X0
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const int o = eoff + c * CCZ + line_off<1>(a0, a1);
-            ld_line<1>(U + o, x);
+            ld_line<1>(X0 + c * CCZ + o1, x);
             mv<TB, true>(x, y);
-            st_line<1>(W + o, y);
+            st_line<1>(X1 + c * CCZ + o1, y);
         }
     }
     __syncthreads();
-    if (valid) {  // z-lines (i, j): r = Bz^T W, scattered from registers
+    if (valid) {  // z-lines: r = Bz^T X1, scattered from registers
         const int64_t base = elem_base(m, e);
         const bool msk = m.dmask != nullptr;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const int o = eoff + c * CCZ + line_off<2>(a0, a1);
-            ld_line<2>(W + o, x);
+            ld_line<2>(X1 + c * CCZ + o2, x);
             mv<TB, true>(x, y);
 #pragma unroll
             for (int k = 0; k < N; ++k) {
@@ -1043,23 +1161,113 @@ __device__ __forceinline__ void col_backward(const hx::MeshView &m, Real *U, Rea
     }
 }
 
+// Backward sweeps after the column-ordered quadrature-point phase: X0 holds
+// Qx, X2 holds Qy and rz[c] = Dz^T Qz of each thread's z-line (registers).
+// Dy^T in place on X2 and rz into X1, then X0 = Bx^T (Dx^T X0 + X1 + X2)
+// in place, X1 = By^T X0 and the scatter of Bz^T X1. Called after a barrier.
+__device__ __forceinline__ void col_backward_c(const hx::MeshView &m, Real *X0, Real *X1, Real *X2, Real (*rz)[N],
+                                               bool act, bool valid, int eoff, int a0, int a1, int e,
+                                               Real *__restrict__ out, uint64_t pol_keep) {
+    Real x[N], y[N], w[N];
+    const int o0 = eoff + line_off<0>(a0, a1), o1 = eoff + line_off<1>(a0, a1), o2 = eoff + line_off<2>(a0, a1);
+    if (act) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            st_line<2>(X1 + c * CCZ + o2, rz[c]);
+            ld_line<1>(X2 + c * CCZ + o1, x);
+            mv<TD, true>(x, y);
+            st_line<1>(X2 + c * CCZ + o1, y);
+        }
+    }
+    __syncthreads();
+    if (act) {  // x-lines, in place: X0 = Bx^T (Dx^T X0 + X1 + X2)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            ld_line<0>(X0 + c * CCZ + o0, x);
+            mv<TD, true>(x, y);
+            ld_line<0>(X1 + c * CCZ + o0, w);
+#pragma unroll
+            for (int k = 0; k < N; ++k) y[k] += w[k];
+            ld_line<0>(X2 + c * CCZ + o0, w);
+#pragma unroll
+            for (int k = 0; k < N; ++k) w[k] += y[k];
+            mv<TB, true>(w, y);
+            st_line<0>(X0 + c * CCZ + o0, y);
+        }
+    }
+    __syncthreads();
+    if (act) {  // y-lines: X1 = By^T X0
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            ld_line<1>(X0 + c * CCZ + o1, x);
+            mv<TB, true>(x, y);
+            st_line<1>(X1 + c * CCZ + o1, y);
+        }
+    }
+    __syncthreads();
+    if (valid) {  // z-lines: r = Bz^T X1, scattered from registers
+        const int64_t base = elem_base(m, e);
+        const bool msk = m.dmask != nullptr;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            ld_line<2>(X1 + c * CCZ + o2, x);
+            mv<TB, true>(x, y);
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                const int64_t d = 3 * node_at(m, base, a0, a1, k) + c;
+                if (!(msk && m.dmask[d])) red_add(out + d, y[k], pol_keep);
+            }
+        }
+    }
+}
+
+// Per-point tangent flux Q from the reference gradient Gr and the point's
+// fields r (geometry first unless spatial, then the cache; for the recompute
+// strategy Gu is the reference gradient of u_k).
+template <int LAW, int STORAGE>
+__device__ __forceinline__ void qp_tangent(const hx::MeshView &m, int e, const Real *Gr, const Real *Gu, const Real *r,
+                                           Real *Q) {
+    if constexpr (STORAGE == HX_SPATIAL_TENSORS) {
+        spatial_Q<Real, LAW>(Gr, [&](int f) { return r[f]; }, Q);
+    } else {
+        Real Ji[9], H[9], dP[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Ji[k] = r[k];
+        const Real JxW = r[9];
+        State<Real> st;
+        if constexpr (STORAGE == HX_RECOMPUTE) {
+            push_grad(Gu, Ji, st.Hk);
+            state_from_Hk<Real, LAW, (bool)HX_UNIT_F32>(m, e, st);
+        } else {
+            build_state<Real, LAW, STORAGE>(m, e, [&](int f) { return r[10 + f]; }, st);
+        }
+        push_grad(Gr, Ji, H);
+        tangent_dP<Real, LAW>(st, H, dP);
+        pull_flux(dP, Ji, JxW, Q);
+    }
+}
+
 // One tile (EPB elements, starting at element tile*EPB) of the tangent apply
 // on NT threads: forward sum factorization from the x-rows of du (and u_k) that
 // each thread holds in cd (ck), the quadrature-point phase, the transposed
-// sweeps and the atomic scatter into out. The caller synchronises the CTA
-// before each call (the shared arrays of the previous tile are reused).
-template <int EPB, int NT, int LAW, int STORAGE>
-__device__ __forceinline__ void apply_tile(const hx::MeshView &m, int tile, Real *__restrict__ out, const Real *cd,
-                                           const Real *ck, unsigned char *smem_raw, uint64_t pol_keep,
-                                           uint64_t pol_stream) {
-    Real *U = (Real *)smem_raw;
-    Real *W = U + EPB * CES;
-    Real *GX = W + EPB * CES;
-    Real *GY = GX + EPB * CES;
-    Real *GZ = GY + EPB * CES;
-    Real *KX = GZ + EPB * CES;  // recompute strategy: gradients of u_k
-    Real *KY = KX + EPB * CES;
-    Real *KZ = KY + EPB * CES;
+// sweeps and the atomic scatter into out. Consecutive calls need no barrier
+// between them (see col_forward).
+// Quadrature-point phase: flat over the tile's EPB*NQ points (consecutive
+// threads take consecutive points). STAGED: the fields were copied into the
+// shared stage by bulk copies on `bar` (issued a tile earlier); the copies of
+// tile `ntile` (< 0: none) are issued once the stage is consumed. Otherwise
+// each thread requests its next point's fields one point ahead. Returns false
+// (on every thread) if the staged data never arrived.
+template <int EPB, int NT, int LAW, int STORAGE, bool STAGED>
+__device__ __forceinline__ bool apply_tile(const hx::MeshView &m, int tile, int ntile, Real *__restrict__ out,
+                                           const Real *cd, const Real *ck, unsigned char *smem_raw, Real *stg,
+                                           uint64_t *bar, uint32_t &phase, uint64_t pol_keep, uint64_t pol_stream) {
+    Real *X0 = (Real *)smem_raw;
+    Real *X1 = X0 + EPB * CES;
+    Real *X2 = X1 + EPB * CES;
+    Real *K0 = X2 + EPB * CES;  // recompute strategy: reference gradient of u_k
+    Real *K1 = K0 + EPB * CES;
+    Real *K2 = K1 + EPB * CES;
     const int t = threadIdx.x;
     const int el = t / NN;
     const int a = t - el * NN;
@@ -1067,85 +1275,114 @@ __device__ __forceinline__ void apply_tile(const hx::MeshView &m, int tile, Real
     const bool act = el < EPB;
     const int eoff = (act ? el : 0) * CES;
     constexpr bool RC = STORAGE == HX_RECOMPUTE;
+    using QF = QpFields<LAW, STORAGE>;
+    constexpr int NR = QF::n;
     const int e0 = tile * EPB;
     const int e = e0 + el;
     const bool valid = act && e < m.n_elem;
-    // quadrature-point phase: flat over the tile's EPB*NQ points (consecutive
-    // threads read consecutive points of every field: coalesced, no sector
-    // shared between iterations); the data of a thread's next point is
-    // requested one iteration ahead, the first before the forward sweeps
-    // (the spatial strategy's fields include the deformed mapping: no geometry)
-    constexpr bool SP = STORAGE == HX_SPATIAL_TENSORS;
-    constexpr int NFC = STORAGE == HX_RECOMPUTE ? 0 : hx::qp_fields(LAW, STORAGE);
-    constexpr int NG = SP ? 0 : 10;
-    constexpr int NR = NG + NFC;
     const int nval = min(EPB, m.n_elem - e0) * NQ;  // valid points of this tile
     const int64_t g0 = (int64_t)e0 * NQ;
-    Real rc[NR], rn[NR];
     auto load_raw = [&](int q, Real *r) {
-        if constexpr (NG > 0) {
-            const Real *geo = (const Real *)m.geo + g0 + q;
+        const Real *geo = (const Real *)m.geo + g0 + q;
 #pragma unroll
-            for (int f = 0; f < NG; ++f) r[f] = ld_stream(geo + (int64_t)f * m.n_qp, pol_stream);
-        }
-        if constexpr (NFC > 0) {
-            const Real *qp = (const Real *)m.qp + g0 + q;
+        for (int f = 0; f < QF::ng; ++f) r[f] = ld_stream(geo + (int64_t)f * m.qs, pol_stream);
+        const Real *qp = (const Real *)m.qp + g0 + q;
 #pragma unroll
-            for (int f = 0; f < NFC; ++f) r[NG + f] = ld_stream(qp + (int64_t)f * m.n_qp, pol_stream);
-        }
+        for (int f = 0; f < QF::nc; ++f) r[QF::ng + f] = ld_stream(qp + (int64_t)f * m.qs, pol_stream);
     };
-    if (t < nval) load_raw(t, rc);
-    if constexpr (RC) col_forward(ck, U, W, KX, KY, KZ, act, eoff, a0, a1);
-    col_forward(cd, U, W, GX, GY, GZ, act, eoff, a0, a1);
-#pragma unroll 1
-    for (int q = t; q < nval; q += NT) {
-        if (q + NT < nval) load_raw(q + NT, rn);
+    auto point = [&](int q, const Real *r) {
         const int qel = q / NQ;
         const int ql = q - qel * NQ;
         const int pos = qel * CES + (ql % N) + ((ql / N) % N) * CRS + (ql / NN) * CPS;
-        Real Gr[9], Q[9];
+        Real Gr[9], Gu[9], Q[9];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            Gr[c * 3 + 0] = GX[pos + c * CCZ];
-            Gr[c * 3 + 1] = GY[pos + c * CCZ];
-            Gr[c * 3 + 2] = GZ[pos + c * CCZ];
-        }
-        if constexpr (SP) {
-            spatial_Q<Real, LAW>(Gr, [&](int f) { return rc[f]; }, Q);
-        } else {
-        Real Ji[9], H[9], dP[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) Ji[k] = rc[k];
-        const Real JxW = rc[9];
-        State<Real> st;
-        if constexpr (STORAGE == HX_RECOMPUTE) {
-            Real Gu[9];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                Gu[c * 3 + 0] = KX[pos + c * CCZ];
-                Gu[c * 3 + 1] = KY[pos + c * CCZ];
-                Gu[c * 3 + 2] = KZ[pos + c * CCZ];
+            Gr[c * 3 + 0] = X0[pos + c * CCZ];
+            Gr[c * 3 + 1] = X1[pos + c * CCZ];
+            Gr[c * 3 + 2] = X2[pos + c * CCZ];
+            if constexpr (RC) {
+                Gu[c * 3 + 0] = K0[pos + c * CCZ];
+                Gu[c * 3 + 1] = K1[pos + c * CCZ];
+                Gu[c * 3 + 2] = K2[pos + c * CCZ];
             }
-            push_grad(Gu, Ji, st.Hk);
-            state_from_Hk<Real, LAW, (bool)HX_UNIT_F32>(m, e0 + qel, st);
-        } else {
-            build_state<Real, LAW, STORAGE>(m, e0 + qel, [&](int f) { return rc[10 + f]; }, st);
         }
-        push_grad(Gr, Ji, H);
-        tangent_dP<Real, LAW>(st, H, dP);
-        pull_flux(dP, Ji, JxW, Q);
-        }
+        qp_tangent<LAW, STORAGE>(m, e0 + qel, Gr, Gu, r, Q);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            GX[pos + c * CCZ] = Q[c * 3 + 0];
-            GY[pos + c * CCZ] = Q[c * 3 + 1];
-            GZ[pos + c * CCZ] = Q[c * 3 + 2];
+            X0[pos + c * CCZ] = Q[c * 3 + 0];
+            X1[pos + c * CCZ] = Q[c * 3 + 1];
+            X2[pos + c * CCZ] = Q[c * 3 + 2];
         }
+    };
+    if constexpr (STAGED) {
+        // column order: thread (a0, a1) of element el handles the points
+        // (a0, a1, k) of its z-line; the stage holds them at el*NQ + a0 +
+        // N*a1 + NN*k (consecutive threads, consecutive words)
+        Real gz[3][N], gk[RC ? 3 : 1][N];
+        if constexpr (RC) col_forward_c(ck, K0, K1, K2, gk, act, eoff, a0, a1);
+        col_forward_c(cd, X0, X1, X2, gz, act, eoff, a0, a1);
+        const bool ok = mbar_wait(bar, phase);
+        if (__syncthreads_or(!ok)) {  // also the barrier that completes the forward sweeps
+            if (t == 0) {
+                atomicOr(m.err + 2, 1);
+                mbar_wait(bar, phase);  // let a copy still in flight land before the CTA exits
+            }
+            return false;
+        }
+        phase ^= 1u;
+        if (valid) {
+            const Real *sp = stg + el * NQ + a0 + N * a1;
+            const int p0 = eoff + line_off<2>(a0, a1);
 #pragma unroll
-        for (int f = 0; f < NR; ++f) rc[f] = rn[f];
+            for (int k = 0; k < N; ++k) {
+                Real r[NR], Gr[9], Gu[9], Q[9];
+#pragma unroll
+                for (int f = 0; f < NR; ++f) r[f] = sp[f * (EPB * NQ) + NN * k];
+                const int pk = p0 + k * CPS;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    Gr[c * 3 + 0] = X0[pk + c * CCZ];
+                    Gr[c * 3 + 1] = X2[pk + c * CCZ];
+                    Gr[c * 3 + 2] = gz[c][k];
+                    if constexpr (RC) {
+                        Gu[c * 3 + 0] = K0[pk + c * CCZ];
+                        Gu[c * 3 + 1] = K2[pk + c * CCZ];
+                        Gu[c * 3 + 2] = gk[c][k];
+                    }
+                }
+                qp_tangent<LAW, STORAGE>(m, e, Gr, Gu, r, Q);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    X0[pk + c * CCZ] = Q[c * 3 + 0];
+                    X2[pk + c * CCZ] = Q[c * 3 + 1];
+                    gz[c][k] = Q[c * 3 + 2];
+                }
+            }
+        }
+        Real rz[3][N];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) mv<TD, true>(gz[c], rz[c]);
+        __syncthreads();
+        if (t == 0 && ntile >= 0) stage_issue<EPB, LAW, STORAGE>(m, ntile, stg, bar);
+        col_backward_c(m, X0, X1, X2, rz, act, valid, eoff, a0, a1, e, out, pol_keep);
+        return true;
+    } else {
+        Real rc[NR], rn[NR];
+        if (t < nval) load_raw(t, rc);
+        if constexpr (RC) col_forward(ck, K0, K1, K2, act, eoff, a0, a1);
+        col_forward(cd, X0, X1, X2, act, eoff, a0, a1);
+        __syncthreads();
+#pragma unroll 1
+        for (int q = t; q < nval; q += NT) {
+            if (q + NT < nval) load_raw(q + NT, rn);
+            point(q, rc);
+#pragma unroll
+            for (int f = 0; f < NR; ++f) rc[f] = rn[f];
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    col_backward(m, U, W, GX, GY, GZ, act, valid, eoff, a0, a1, e, out, pol_keep);
+    col_backward(m, X0, X1, X2, act, valid, eoff, a0, a1, e, out, pol_keep);
+    return true;
 }
 
 // One tile of the residual R(u) (same structure as apply_tile): the state is
@@ -1156,11 +1393,9 @@ template <int EPB, int NT, int LAW>
 __device__ __forceinline__ void residual_tile(const hx::MeshView &m, int tile, Real *__restrict__ out,
                                               const Real *cu, unsigned char *smem_raw, uint64_t pol_keep,
                                               uint64_t pol_stream) {
-    Real *U = (Real *)smem_raw;
-    Real *W = U + EPB * CES;
-    Real *GX = W + EPB * CES;
-    Real *GY = GX + EPB * CES;
-    Real *GZ = GY + EPB * CES;
+    Real *X0 = (Real *)smem_raw;
+    Real *X1 = X0 + EPB * CES;
+    Real *X2 = X1 + EPB * CES;
     const int t = threadIdx.x;
     const int el = t / NN;
     const int a = t - el * NN;
@@ -1176,10 +1411,11 @@ __device__ __forceinline__ void residual_tile(const hx::MeshView &m, int tile, R
     auto load_geo_raw = [&](int q, Real *r) {
         const Real *geo = (const Real *)m.geo + g0 + q;
 #pragma unroll
-        for (int f = 0; f < 10; ++f) r[f] = ld_stream(geo + (int64_t)f * m.n_qp, pol_stream);
+        for (int f = 0; f < 10; ++f) r[f] = ld_stream(geo + (int64_t)f * m.qs, pol_stream);
     };
     if (t < nval) load_geo_raw(t, rc);
-    col_forward(cu, U, W, GX, GY, GZ, act, eoff, a0, a1);
+    col_forward(cu, X0, X1, X2, act, eoff, a0, a1);
+    __syncthreads();
 #pragma unroll 1
     for (int q = t; q < nval; q += NT) {
         if (q + NT < nval) load_geo_raw(q + NT, rn);
@@ -1192,9 +1428,9 @@ __device__ __forceinline__ void residual_tile(const hx::MeshView &m, int tile, R
         const Real JxW = rc[9];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            Gr[c * 3 + 0] = GX[pos + c * CCZ];
-            Gr[c * 3 + 1] = GY[pos + c * CCZ];
-            Gr[c * 3 + 2] = GZ[pos + c * CCZ];
+            Gr[c * 3 + 0] = X0[pos + c * CCZ];
+            Gr[c * 3 + 1] = X1[pos + c * CCZ];
+            Gr[c * 3 + 2] = X2[pos + c * CCZ];
         }
         State<Real> st;
         push_grad(Gr, Ji, st.Hk);
@@ -1212,15 +1448,15 @@ __device__ __forceinline__ void residual_tile(const hx::MeshView &m, int tile, R
         pull_flux(P, Ji, JxW, Q);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            GX[pos + c * CCZ] = Q[c * 3 + 0];
-            GY[pos + c * CCZ] = Q[c * 3 + 1];
-            GZ[pos + c * CCZ] = Q[c * 3 + 2];
+            X0[pos + c * CCZ] = Q[c * 3 + 0];
+            X1[pos + c * CCZ] = Q[c * 3 + 1];
+            X2[pos + c * CCZ] = Q[c * 3 + 2];
         }
 #pragma unroll
         for (int f = 0; f < 10; ++f) rc[f] = rn[f];
     }
     __syncthreads();
-    col_backward(m, U, W, GX, GY, GZ, act, valid, eoff, a0, a1, e, out, pol_keep);
+    col_backward(m, X0, X1, X2, act, valid, eoff, a0, a1, e, out, pol_keep);
 }
 
 // r += R(u) over all elements (r zeroed by the caller); persistent like
@@ -1250,7 +1486,8 @@ __global__ void __launch_bounds__(col_threads(EPB)) k_residual_col(const hx::Mes
             const int e1 = ntile * EPB + el;
             load_row(m, e1, elem_base(m, e1), a0, a1, u, false, row);
         }
-        __syncthreads();
+        // no barrier: the previous tile's last phase reads X1 only, the first
+        // phase of this one writes X0 only
         residual_tile<EPB, col_threads(EPB), LAW>(m, tile, r, cu, smem_raw, pol_keep, pol_stream);
     }
 }
@@ -1258,10 +1495,15 @@ __global__ void __launch_bounds__(col_threads(EPB)) k_residual_col(const hx::Mes
 // out += K(u_k) du over all elements (out zeroed by the caller). Persistent:
 // CTAs walk tiles of EPB elements with stride gridDim.x. Each thread loads
 // its element x-row of du (and u_k) straight into registers, one tile ahead.
-template <int EPB, int LAW, int STORAGE>
+// STAGED: the tile's quadrature-point fields arrive in shared memory by bulk
+// copies issued one tile ahead (a single stage, refilled after each
+// quadrature-point phase); a copy that never completes sets the device
+// timeout flag and ends the CTA.
+template <int EPB, int LAW, int STORAGE, bool STAGED>
 __global__ void __launch_bounds__(col_threads(EPB)) k_apply(const hx::MeshView m, const Real *__restrict__ du,
                                                             Real *__restrict__ out, int ntiles) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
     const int t = threadIdx.x;
     const int el = t / NN;
     const int a = t - el * NN;
@@ -1270,6 +1512,14 @@ __global__ void __launch_bounds__(col_threads(EPB)) k_apply(const hx::MeshView m
     const uint64_t pol_keep = policy_evict_last();
     const uint64_t pol_stream = policy_evict_first();
     constexpr bool RC = STORAGE == HX_RECOMPUTE;
+    using SM = ApplySmem<EPB, LAW, STORAGE, STAGED>;
+    Real *stg = (Real *)(smem_raw + (SM::cube_bytes + 15) / 16 * 16);
+    uint32_t phase = 0;
+    if constexpr (STAGED) {
+        if (t == 0) mbar_init(&bar, 1);
+        __syncthreads();
+        if (t == 0 && (int)blockIdx.x < ntiles) stage_issue<EPB, LAW, STORAGE>(m, blockIdx.x, stg, &bar);
+    }
     Real rowd[3 * N], rowk[RC ? 3 * N : 1];
     if (act && (int)blockIdx.x < ntiles) {
         const int e1 = blockIdx.x * EPB + el;
@@ -1279,7 +1529,7 @@ __global__ void __launch_bounds__(col_threads(EPB)) k_apply(const hx::MeshView m
     }
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int ntile = tile + gridDim.x;
-        if (m.l2pf) prefetch_tile<EPB, STORAGE>(m, ntile);
+        if (!STAGED && m.l2pf) prefetch_tile<EPB, STORAGE>(m, ntile);
         // this tile's rows; the next tile's rows are requested now
         Real cd[3 * N], ck[RC ? 3 * N : 1];
 #pragma unroll
@@ -1294,8 +1544,12 @@ __global__ void __launch_bounds__(col_threads(EPB)) k_apply(const hx::MeshView m
             load_row(m, e1, b1, a0, a1, du, true, rowd);
             if constexpr (RC) load_row(m, e1, b1, a0, a1, (const Real *)m.uk, false, rowk);
         }
-        __syncthreads();  // the previous tile is done with the shared arrays
-        apply_tile<EPB, col_threads(EPB), LAW, STORAGE>(m, tile, out, cd, ck, smem_raw, pol_keep, pol_stream);
+        // no barrier: the previous tile's last phase reads X1 only, the first
+        // phase of this one writes X0 (and K0) only
+        if (!apply_tile<EPB, col_threads(EPB), LAW, STORAGE, STAGED>(m, tile, ntile < ntiles ? ntile : -1, out, cd,
+                                                                    ck, smem_raw, stg, &bar, phase, pol_keep,
+                                                                    pol_stream))
+            return;
     }
 }
 
@@ -1317,7 +1571,9 @@ __device__ __forceinline__ void batch_tile(const hx::MeshView &m, int tile, cons
         load_row(m, e1, b1, a0, a1, du, true, cd);
         if constexpr (RC) load_row(m, e1, b1, a0, a1, (const Real *)m.uk, false, ck);
     }
-    apply_tile<EPB, NT, LAW, STORAGE>(m, tile, out, cd, ck, smem_raw, policy_evict_last(), policy_evict_first());
+    uint32_t phase = 0;
+    apply_tile<EPB, NT, LAW, STORAGE, false>(m, tile, -1, out, cd, ck, smem_raw, nullptr, nullptr, phase,
+                                             policy_evict_last(), policy_evict_first());
 }
 
 // qp cache at state u: interpolation and state in FP64, stored as Real
@@ -1342,7 +1598,7 @@ __global__ void __launch_bounds__(threads_for(EPB)) k_precompute(const hx::MeshV
         const int64_t g = (int64_t)e * NQ + q;
         double Ji[9], Gr[9];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) Ji[k] = geo[(int64_t)k * m.n_qp + g];
+        for (int k = 0; k < 9; ++k) Ji[k] = geo[(int64_t)k * m.qs + g];
 #pragma unroll
         for (int k = 0; k < 9; ++k) Gr[k] = G[(el * 9 + k) * SZ + ci];
         State<double> st;
@@ -1351,11 +1607,11 @@ __global__ void __launch_bounds__(threads_for(EPB)) k_precompute(const hx::MeshV
         flag_state(m, st.Jm1);
         if constexpr (STORAGE == HX_SPATIAL_TENSORS) {
             double f[hx::qp_fields(LAW, STORAGE)];
-            spatial_fields<LAW>(st, Ji, geo[(int64_t)9 * m.n_qp + g], m, f);
+            spatial_fields<LAW>(st, Ji, geo[(int64_t)9 * m.qs + g], m, f);
 #pragma unroll
-            for (int k = 0; k < hx::qp_fields(LAW, STORAGE); ++k) qp[(int64_t)k * m.n_qp + g] = (Real)f[k];
+            for (int k = 0; k < hx::qp_fields(LAW, STORAGE); ++k) qp[(int64_t)k * m.qs + g] = (Real)f[k];
         } else if constexpr (STORAGE != HX_RECOMPUTE) {
-            store_state<Real, LAW, STORAGE>(qp, m.n_qp, g, st);
+            store_state<Real, LAW, STORAGE>(qp, m.qs, g, st);
         }
     }
 }
@@ -1396,7 +1652,7 @@ __global__ void __launch_bounds__(threads_for(2)) k_diagonal(const hx::MeshView 
             Real fl[hx::qp_fields(LAW, STORAGE)];
             const Real *qpd = (const Real *)m.qp;
 #pragma unroll
-            for (int k = 0; k < hx::qp_fields(LAW, STORAGE); ++k) fl[k] = __ldcs(qpd + (int64_t)k * m.n_qp + g);
+            for (int k = 0; k < hx::qp_fields(LAW, STORAGE); ++k) fl[k] = __ldcs(qpd + (int64_t)k * m.qs + g);
 #pragma unroll 1
             for (int c = 0; c < 3; ++c) {
 #pragma unroll 1
@@ -1554,11 +1810,11 @@ __global__ void __launch_bounds__(256) k_geometry(const hx::MeshView m, const do
         Ji[8] = (J0[0] * J0[4] - J0[1] * J0[3]) * id;
         const double jxw = det * cW[qx] * cW[qy] * cW[qz];
         for (int k = 0; k < 9; ++k) {
-            geo64[(int64_t)k * total + idx] = Ji[k];
-            geo32[(int64_t)k * total + idx] = (float)Ji[k];
+            geo64[(int64_t)k * m.qs + idx] = Ji[k];
+            geo32[(int64_t)k * m.qs + idx] = (float)Ji[k];
         }
-        geo64[(int64_t)9 * total + idx] = jxw;
-        geo32[(int64_t)9 * total + idx] = (float)jxw;
+        geo64[(int64_t)9 * m.qs + idx] = jxw;
+        geo32[(int64_t)9 * m.qs + idx] = (float)jxw;
     }
 }
 

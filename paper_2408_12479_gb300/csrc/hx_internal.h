@@ -39,23 +39,24 @@ struct MatParamsF {
 struct MeshView {
     int p, n_elem;
     int64_t n_nodes, n_qp;
+    int64_t qs;                  // field stride of the SoA point arrays: n_qp rounded up to 32
     int structured, nx, ny, nz;
     int64_t Nx, Ny;              // node lattice extents of a structured box
     const int32_t *dof_conn;     // [n_elem][(p+1)^3] or null (structured)
-    const void *geo;             // [10][n_qp] of T: (J0^-1)_{ed} at field 3e+d, JxW at field 9
+    const void *geo;             // [10][qs] of T: (J0^-1)_{ed} at field 3e+d, JxW at field 9
     const double *geo64;         // the same in FP64 (precompute)
-    const void *qp;              // [nf][n_qp] of T (strategy cache)
+    const void *qp;              // [nf][qs] of T (strategy cache)
     const void *uk;              // u_k in T (recompute strategy)
     int nf;
     const uint8_t *dmask;        // [3 n_nodes] or null
     const void *fibH;            // [12][n_elem] of T: H_4 (sym 6), H_6 (sym 6)
     const double *fibH64;        // the same in FP64
     const double *fibM;          // [6][n_elem] mean fibre directions M1 of families 4, 6
-    int *err;                    // device error flags: [0] non-invertible, [1] NaN
+    int *err;                    // device error flags: [0] non-invertible, [1] NaN, [2] wait gave up
     MatParams mat;
     MatParamsF matf;  // the same constants rounded once to FP32
     int law;
-    int l2pf;         // apply kernel: prefetch the next tile's qp data into L2
+    int l2pf;         // apply kernel (register-prefetch variants): prefetch the next tile's qp data into L2
 };
 
 // Kernel entry points provided by each (degree, precision) translation unit
@@ -111,7 +112,7 @@ struct hx_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     std::string err;
-    int *d_flags = nullptr;  // [2] device error flags
+    int *d_flags = nullptr;  // [3] device error flags
     int sm_count = 0;
     uint64_t launches = 0;
 };

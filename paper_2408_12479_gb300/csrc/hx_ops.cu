@@ -61,39 +61,48 @@ int sm_count() {
     return n;
 }
 
-template <int EPB, int LAW, int STORAGE>
+template <int EPB, int LAW, int STORAGE, bool STAGED>
 cudaError_t launch_apply_t(const hx::MeshView &m, const void *du, void *out, cudaStream_t s) {
-    auto kern = k_apply<EPB, LAW, STORAGE>;
-    constexpr size_t smem = ApplySmem<EPB, STORAGE>::bytes;
-    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-    static int per_sm = [&] {
-        if (set_smem(kern, smem) != cudaSuccess) return 0;
-        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-        int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, col_threads(EPB), smem) != cudaSuccess) return 0;
-        return b;
-    }();
-    if (per_sm <= 0) return cudaErrorInvalidConfiguration;
-    const int ntiles = (m.n_elem + EPB - 1) / EPB;
-    if (ntiles == 0) return cudaSuccess;
-    const int grid = ntiles < per_sm * sm_count() ? ntiles : per_sm * sm_count();
-    kern<<<grid, col_threads(EPB), smem, s>>>(m, (const Real *)du, (Real *)out, ntiles);
-    return cudaGetLastError();
+    using SM = ApplySmem<EPB, LAW, STORAGE, STAGED>;
+    if constexpr (STAGED && !SM::stageable) {
+        return cudaErrorInvalidConfiguration;  // tile chunks would not start on 16-byte boundaries
+    } else {
+        auto kern = k_apply<EPB, LAW, STORAGE, STAGED>;
+        constexpr size_t smem = SM::bytes;
+        if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+        static int per_sm = [&] {
+            if (set_smem(kern, smem) != cudaSuccess) return 0;
+            cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+            int b = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, col_threads(EPB), smem) != cudaSuccess) return 0;
+            return b;
+        }();
+        if (per_sm <= 0) return cudaErrorInvalidConfiguration;
+        const int ntiles = (m.n_elem + EPB - 1) / EPB;
+        if (ntiles == 0) return cudaSuccess;
+        const int grid = ntiles < per_sm * sm_count() ? ntiles : per_sm * sm_count();
+        kern<<<grid, col_threads(EPB), smem, s>>>(m, (const Real *)du, (Real *)out, ntiles);
+        return cudaGetLastError();
+    }
 }
 
-// variants: tile shape (default, half, double elements per CTA) x L2
-// prefetch of the next tile's qp data (on for 0-2, off for 3-5)
+// variants: tile shape (default, half, double elements per CTA) x how the
+// quadrature-point fields arrive: register prefetch one point ahead with an
+// L2 bulk prefetch of the next tile (0-2), or bulk copies into a shared stage
+// one tile ahead (3-5; not built where a tile's chunk is not a multiple of 16
+// bytes)
 template <int LAW, int STORAGE>
 cudaError_t apply_variant(const hx::MeshView &m0, const void *du, void *out, cudaStream_t s, int variant) {
     hx::MeshView m = m0;
-    m.l2pf = variant < 3;
-    switch (variant % 3) {
-        case 1:
-            return launch_apply_t<(EPB_A > 1 ? EPB_A / 2 : 1), LAW, STORAGE>(m, du, out, s);
-        case 2:
-            return launch_apply_t<2 * EPB_A, LAW, STORAGE>(m, du, out, s);
-        default:
-            return launch_apply_t<EPB_A, LAW, STORAGE>(m, du, out, s);
+    m.l2pf = 1;
+    constexpr int EH = EPB_A > 1 ? EPB_A / 2 : 1;
+    switch (variant) {
+        case 1: return launch_apply_t<EH, LAW, STORAGE, false>(m, du, out, s);
+        case 2: return launch_apply_t<2 * EPB_A, LAW, STORAGE, false>(m, du, out, s);
+        case 3: return launch_apply_t<EPB_A, LAW, STORAGE, true>(m, du, out, s);
+        case 4: return launch_apply_t<EH, LAW, STORAGE, true>(m, du, out, s);
+        case 5: return launch_apply_t<2 * EPB_A, LAW, STORAGE, true>(m, du, out, s);
+        default: return launch_apply_t<EPB_A, LAW, STORAGE, false>(m, du, out, s);
     }
 }
 
@@ -120,7 +129,7 @@ template <int LAW>
 cudaError_t launch_residual_t(const hx::MeshView &m, const void *u, void *r, cudaStream_t s) {
     constexpr int EPB = EPB_A;
     auto kern = k_residual_col<EPB, LAW>;
-    constexpr size_t smem = (size_t)5 * EPB * CES * sizeof(Real);
+    constexpr size_t smem = (size_t)3 * EPB * CES * sizeof(Real);
     static int per_sm = [&] {
         if (set_smem(kern, smem) != cudaSuccess) return 0;
         int b = 0;

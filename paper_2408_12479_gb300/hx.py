@@ -35,7 +35,7 @@ EXPORTS = ["hx_create", "hx_destroy", "hx_set_stream", "hx_last_error", "hx_sync
            "hx_residual", "hx_tangent_apply", "hx_tangent_apply_host", "hx_diagonal", "hx_chebyshev_smooth",
            "hx_estimate_lambda_max", "hx_cg_solve", "hx_fibre_dispersion", "hx_batch_create",
            "hx_batch_destroy", "hx_batch_tangent_apply", "hx_measure_fma_peak", "hx_launch_count",
-           "hx_autotune", "hx_chebyshev_smooth_noalloc"]
+           "hx_autotune", "hx_set_apply_variant", "hx_chebyshev_smooth_noalloc"]
 
 
 class HxError(RuntimeError):
@@ -101,6 +101,7 @@ def lib():
             "hx_measure_fma_peak": (I32, [P, I32, C.POINTER(D)]),
             "hx_launch_count": (U64, [P, I32]),
             "hx_autotune": (I32, [P, I32, P, P, I32, C.POINTER(I32), C.POINTER(D)]),
+            "hx_set_apply_variant": (I32, [P, I32, I32, I32]),
             "hx_chebyshev_smooth_noalloc": (I32, [P, P, P, P, I32, D, D, I32, I32]),
         }
         for name, (res, args) in sig.items():
@@ -283,6 +284,10 @@ def hx_cg_solve(ctx, mesh, rhs, x, tol, max_iter, degree, lambda_max, smoothing_
     if st not in (HX_OK, HX_ERR_NOT_CONVERGED):
         _check(st, ctx)
     return it.value, rel.value, st
+
+
+def hx_set_apply_variant(ctx, mesh, prec, storage, variant):
+    _check(lib().hx_set_apply_variant(mesh, int(prec), int(storage), int(variant)), ctx)
 
 
 def hx_autotune(ctx, mesh, du, out, reps=10):

@@ -44,6 +44,9 @@ def _lib():
 @pytest.mark.parametrize("storage", STORAGES)
 @pytest.mark.parametrize("prec", [hx.HX_FP64, hx.HX_FP32])
 def test_tangent_apply_matches_oracle(p, law, storage, prec):
+    """Every apply variant: three tile shapes, with per-thread loads or with
+    the tile's fields staged in shared memory by bulk copies (a staged variant
+    may be unavailable where its chunks would be misaligned or too large)."""
     n = 3 if p >= 4 else 4   # 27 or 64 elements: several CTA tiles plus a ragged tail
     m = cases.small_cube(n, p, law, seed=10 + p)
     M, X, u = cases.state_for(m, law, seed=20 + p)
@@ -55,11 +58,22 @@ def test_tangent_apply_matches_oracle(p, law, storage, prec):
     try:
         G.precompute(cuda(u), prec, storage)
         du_t = cuda(du, prec)
-        out = G.apply(du_t)
-        G.sync(60000)
         ref = O.apply(M, mat, u, host(du_t))
-        err = rel_inf(host(out), ref)
-        assert err < TOL[prec], err
+        ran = []
+        for variant in range(6):
+            hx.hx_set_apply_variant(G.ctx, G.handle, prec, storage, variant)
+            try:
+                out = G.apply(du_t)
+            except hx.HxError as e:
+                assert variant >= 2 and e.status == hx.HX_ERR_CUDA, (variant, str(e))
+                continue
+            G.sync(60000)
+            err = rel_inf(host(out), ref)
+            assert err < TOL[prec], (variant, err)
+            ran.append(variant)
+        assert 0 in ran and 1 in ran
+        if prec == hx.HX_FP32 and p <= 4:
+            assert any(v >= 3 for v in ran), ran
     finally:
         G.close()
 
