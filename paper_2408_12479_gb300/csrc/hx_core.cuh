@@ -961,46 +961,59 @@ __device__ __forceinline__ void col_forward(const Real *row, Real *X0, Real *X1,
 // No final barrier (the caller's barrier completes the sweeps).
 __device__ __forceinline__ void col_forward_c(const Real *row, Real *X0, Real *X1, Real *X2, Real (*gz)[N], bool act,
                                               int eoff, int a0, int a1) {
-    Real x[N], y[N];
+    // each phase loads all three components' lines before any store: the
+    // cubes share one allocation, so the compiler may not move a load above
+    // a store itself
+    Real x[3][N], y[3][N];
     const int o0 = eoff + line_off<0>(a0, a1), o1 = eoff + line_off<1>(a0, a1), o2 = eoff + line_off<2>(a0, a1);
     if (act) {  // x-lines: X0 = Bx u
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
 #pragma unroll
-            for (int i = 0; i < N; ++i) x[i] = row[3 * i + c];
-            mv<TB, false>(x, y);
-            st_line<0>(X0 + c * CCZ + o0, y);
+            for (int i = 0; i < N; ++i) x[c][i] = row[3 * i + c];
+            mv<TB, false>(x[c], y[c]);
         }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) st_line<0>(X0 + c * CCZ + o0, y[c]);
     }
     __syncthreads();
     if (act) {  // y-lines: X1 = By X0
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            ld_line<1>(X0 + c * CCZ + o1, x);
-            mv<TB, false>(x, y);
-            st_line<1>(X1 + c * CCZ + o1, y);
-        }
+        for (int c = 0; c < 3; ++c) ld_line<1>(X0 + c * CCZ + o1, x[c]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) mv<TB, false>(x[c], y[c]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) st_line<1>(X1 + c * CCZ + o1, y[c]);
     }
     __syncthreads();
     if (act) {  // z-lines: values V = Bz X1 (in place, per line), Dz V kept
 #pragma unroll
+        for (int c = 0; c < 3; ++c) ld_line<2>(X1 + c * CCZ + o2, x[c]);
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
-            ld_line<2>(X1 + c * CCZ + o2, x);
-            mv<TB, false>(x, y);
-            st_line<2>(X1 + c * CCZ + o2, y);
-            mv<TD, false>(y, gz[c]);
+            mv<TB, false>(x[c], y[c]);
+            mv<TD, false>(y[c], gz[c]);
         }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) st_line<2>(X1 + c * CCZ + o2, y[c]);
     }
     __syncthreads();
     if (act) {  // x-lines: X0 = Dx V; y-lines: X2 = Dy V
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            ld_line<0>(X1 + c * CCZ + o0, x);
-            mv<TD, false>(x, y);
-            st_line<0>(X0 + c * CCZ + o0, y);
-            ld_line<1>(X1 + c * CCZ + o1, x);
-            mv<TD, false>(x, y);
-            st_line<1>(X2 + c * CCZ + o1, y);
+            ld_line<0>(X1 + c * CCZ + o0, x[c]);
+            ld_line<1>(X1 + c * CCZ + o1, y[c]);
+        }
+        Real dx[3][N], dy[3][N];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            mv<TD, false>(x[c], dx[c]);
+            mv<TD, false>(y[c], dy[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            st_line<0>(X0 + c * CCZ + o0, dx[c]);
+            st_line<1>(X2 + c * CCZ + o1, dy[c]);
         }
     }
 }
@@ -1168,55 +1181,61 @@ __device__ __forceinline__ void col_backward(const hx::MeshView &m, Real *X0, Re
 __device__ __forceinline__ void col_backward_c(const hx::MeshView &m, Real *X0, Real *X1, Real *X2, Real (*rz)[N],
                                                bool act, bool valid, int eoff, int a0, int a1, int e,
                                                Real *__restrict__ out, uint64_t pol_keep) {
-    Real x[N], y[N], w[N];
+    Real x[3][N], y[3][N], w[N];
     const int o0 = eoff + line_off<0>(a0, a1), o1 = eoff + line_off<1>(a0, a1), o2 = eoff + line_off<2>(a0, a1);
     if (act) {
 #pragma unroll
+        for (int c = 0; c < 3; ++c) ld_line<1>(X2 + c * CCZ + o1, x[c]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) mv<TD, true>(x[c], y[c]);
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
             st_line<2>(X1 + c * CCZ + o2, rz[c]);
-            ld_line<1>(X2 + c * CCZ + o1, x);
-            mv<TD, true>(x, y);
-            st_line<1>(X2 + c * CCZ + o1, y);
+            st_line<1>(X2 + c * CCZ + o1, y[c]);
         }
     }
     __syncthreads();
     if (act) {  // x-lines, in place: X0 = Bx^T (Dx^T X0 + X1 + X2)
+        Real s1[3][N], s2[3][N];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            ld_line<0>(X0 + c * CCZ + o0, x);
-            mv<TD, true>(x, y);
-            ld_line<0>(X1 + c * CCZ + o0, w);
-#pragma unroll
-            for (int k = 0; k < N; ++k) y[k] += w[k];
-            ld_line<0>(X2 + c * CCZ + o0, w);
-#pragma unroll
-            for (int k = 0; k < N; ++k) w[k] += y[k];
-            mv<TB, true>(w, y);
-            st_line<0>(X0 + c * CCZ + o0, y);
+            ld_line<0>(X0 + c * CCZ + o0, x[c]);
+            ld_line<0>(X1 + c * CCZ + o0, s1[c]);
+            ld_line<0>(X2 + c * CCZ + o0, s2[c]);
         }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            mv<TD, true>(x[c], y[c]);
+#pragma unroll
+            for (int k = 0; k < N; ++k) w[k] = y[c][k] + s1[c][k] + s2[c][k];
+            mv<TB, true>(w, y[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) st_line<0>(X0 + c * CCZ + o0, y[c]);
     }
     __syncthreads();
     if (act) {  // y-lines: X1 = By^T X0
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            ld_line<1>(X0 + c * CCZ + o1, x);
-            mv<TB, true>(x, y);
-            st_line<1>(X1 + c * CCZ + o1, y);
-        }
+        for (int c = 0; c < 3; ++c) ld_line<1>(X0 + c * CCZ + o1, x[c]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) mv<TB, true>(x[c], y[c]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) st_line<1>(X1 + c * CCZ + o1, y[c]);
     }
     __syncthreads();
     if (valid) {  // z-lines: r = Bz^T X1, scattered from registers
+#pragma unroll
+        for (int c = 0; c < 3; ++c) ld_line<2>(X1 + c * CCZ + o2, x[c]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) mv<TB, true>(x[c], y[c]);
         const int64_t base = elem_base(m, e);
         const bool msk = m.dmask != nullptr;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            ld_line<2>(X1 + c * CCZ + o2, x);
-            mv<TB, true>(x, y);
+        for (int k = 0; k < N; ++k) {
+            const int64_t d = 3 * node_at(m, base, a0, a1, k);
 #pragma unroll
-            for (int k = 0; k < N; ++k) {
-                const int64_t d = 3 * node_at(m, base, a0, a1, k) + c;
-                if (!(msk && m.dmask[d])) red_add(out + d, y[k], pol_keep);
-            }
+            for (int c = 0; c < 3; ++c)
+                if (!(msk && m.dmask[d + c])) red_add(out + d + c, y[c][k], pol_keep);
         }
     }
 }
@@ -1333,24 +1352,39 @@ __device__ __forceinline__ bool apply_tile(const hx::MeshView &m, int tile, int 
         if (valid) {
             const Real *sp = stg + el * NQ + a0 + N * a1;
             const int p0 = eoff + line_off<2>(a0, a1);
-#pragma unroll
-            for (int k = 0; k < N; ++k) {
-                Real r[NR], Gr[9], Gu[9], Q[9];
+            // point k+1's shared loads are issued before point k's stores
+            Real r[NR], Gx[3], Gy[3], Ux[3], Uy[3];
+            auto fetch = [&](int k) {
 #pragma unroll
                 for (int f = 0; f < NR; ++f) r[f] = sp[f * (EPB * NQ) + NN * k];
-                const int pk = p0 + k * CPS;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    Gr[c * 3 + 0] = X0[pk + c * CCZ];
-                    Gr[c * 3 + 1] = X2[pk + c * CCZ];
+                    Gx[c] = X0[p0 + k * CPS + c * CCZ];
+                    Gy[c] = X2[p0 + k * CPS + c * CCZ];
+                    if constexpr (RC) {
+                        Ux[c] = K0[p0 + k * CPS + c * CCZ];
+                        Uy[c] = K2[p0 + k * CPS + c * CCZ];
+                    }
+                }
+            };
+            fetch(0);
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                Real Gr[9], Gu[9], Q[9];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    Gr[c * 3 + 0] = Gx[c];
+                    Gr[c * 3 + 1] = Gy[c];
                     Gr[c * 3 + 2] = gz[c][k];
                     if constexpr (RC) {
-                        Gu[c * 3 + 0] = K0[pk + c * CCZ];
-                        Gu[c * 3 + 1] = K2[pk + c * CCZ];
+                        Gu[c * 3 + 0] = Ux[c];
+                        Gu[c * 3 + 1] = Uy[c];
                         Gu[c * 3 + 2] = gk[c][k];
                     }
                 }
                 qp_tangent<LAW, STORAGE>(m, e, Gr, Gu, r, Q);
+                if (k + 1 < N) fetch(k + 1);
+                const int pk = p0 + k * CPS;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     X0[pk + c * CCZ] = Q[c * 3 + 0];
