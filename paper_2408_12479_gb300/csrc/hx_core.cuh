@@ -55,6 +55,12 @@ __host__ __device__ constexpr int threads_for(int epb) {
 }
 
 __constant__ Real cTab[3][NN];       // B[q][a], D[q][r], Gd[q][a]
+// Even-odd halves of the 1D matrices. On points symmetric about 1/2, B is
+// symmetric and D, Gd antisymmetric under (o, t) -> (N-1-o, N-1-t); for
+// o, t < N/2, P = (M[o][t] + M[o][N-1-t]) / 2 and Q = (M[o][t] - M[o][N-1-t]) / 2
+// of M and of M^T: [table][transposed][P, Q][o * (N/2) + t]
+constexpr int EOH = N / 2;
+__constant__ Real cEO[3][2][2][(EOH > 0 ? EOH : 1) * (EOH > 0 ? EOH : 1)];
 __constant__ double cW[N];           // Gauss weights on [0,1]
 __constant__ double cGeoV[2][3 * N]; // geometry bases at Gauss points [g-1][a*N+q]
 __constant__ double cGeoD[2][3 * N];
@@ -796,15 +802,49 @@ __device__ __forceinline__ void st_line(Real *p, const Real *y) {
 #pragma unroll
     for (int t = 0; t < N; ++t) p[t * line_str<DIR>()] = y[t];
 }
-// y = M x (TR: y = M^T x) with a 1D table from constant memory
+// y = M x (TR: y = M^T x) with a 1D table from constant memory. From five
+// points on, the even-odd decomposition: with e_t = x_t + x_{N-1-t} and
+// d_t = x_t - x_{N-1-t}, a_o = P e (+ M[o][h] x_h), b_o = Q d, and
+// y_o = a_o + b_o, y_{N-1-o} = +-(a_o - b_o) (N^2 FMAs become about N^2/2 + 2N).
 template <int TAB, bool TR>
 __device__ __forceinline__ void mv(const Real *x, Real *y) {
+    if constexpr (N >= 5) {
+        constexpr int H = EOH;
+        constexpr bool SYM = TAB == TB;
+        auto M = [](int o, int t) { return tab<TAB>(TR ? t * N + o : o * N + t); };
+        Real ev[H], od[H];
 #pragma unroll
-    for (int o = 0; o < N; ++o) {
-        Real s = Real(0);
+        for (int t = 0; t < H; ++t) {
+            ev[t] = x[t] + x[N - 1 - t];
+            od[t] = x[t] - x[N - 1 - t];
+        }
 #pragma unroll
-        for (int t = 0; t < N; ++t) s = fma(tab<TAB>(TR ? t * N + o : o * N + t), x[t], s);
-        y[o] = s;
+        for (int o = 0; o < H; ++o) {
+            Real a = Real(0), b = Real(0);
+#pragma unroll
+            for (int t = 0; t < H; ++t) {
+                a = fma(cEO[TAB][TR][0][o * H + t], ev[t], a);
+                b = fma(cEO[TAB][TR][1][o * H + t], od[t], b);
+            }
+            if constexpr (N % 2 == 1) a = fma(M(o, H), x[H], a);
+            y[o] = a + b;
+            y[N - 1 - o] = SYM ? a - b : b - a;
+        }
+        if constexpr (N % 2 == 1) {
+            Real c = Real(0);
+#pragma unroll
+            for (int t = 0; t < H; ++t) c = fma(M(H, t), SYM ? ev[t] : od[t], c);
+            if constexpr (SYM) c = fma(M(H, H), x[H], c);
+            y[H] = c;
+        }
+    } else {
+#pragma unroll
+        for (int o = 0; o < N; ++o) {
+            Real s = Real(0);
+#pragma unroll
+            for (int t = 0; t < N; ++t) s = fma(tab<TAB>(TR ? t * N + o : o * N + t), x[t], s);
+            y[o] = s;
+        }
     }
 }
 
@@ -1892,6 +1932,19 @@ cudaError_t op_upload(const double *B, const double *D, const double *Gd, const 
         t[2][i] = (Real)Gd[i];
     }
     cudaError_t e = cudaMemcpyToSymbol(cTab, t, sizeof t);
+    if (EOH > 0) {
+        Real eo[3][2][2][(EOH > 0 ? EOH : 1) * (EOH > 0 ? EOH : 1)];
+        const double *src[3] = {B, D, Gd};
+        for (int k = 0; k < 3; ++k)
+            for (int tr = 0; tr < 2; ++tr)
+                for (int o = 0; o < EOH; ++o)
+                    for (int c = 0; c < EOH; ++c) {
+                        auto Mx = [&](int r, int q) { return tr ? src[k][q * N + r] : src[k][r * N + q]; };
+                        eo[k][tr][0][o * EOH + c] = (Real)(0.5 * (Mx(o, c) + Mx(o, N - 1 - c)));
+                        eo[k][tr][1][o * EOH + c] = (Real)(0.5 * (Mx(o, c) - Mx(o, N - 1 - c)));
+                    }
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(cEO, eo, sizeof eo);
+    }
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(cW, w, sizeof(double) * N);
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(cGeoV, geoV, sizeof(double) * 2 * 3 * N);
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(cGeoD, geoD, sizeof(double) * 2 * 3 * N);
