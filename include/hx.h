@@ -250,6 +250,44 @@ typedef struct {
 hx_status hx_cg_solve(hx_mesh *mesh, const double *rhs_dev, double *x_dev, double tol, int32_t max_iter,
                       const hx_cg_options *opt, int32_t *iters, double *rel_residual);
 
+/* Load vector of a constant body force b[3] (Sec. 2, the (v, B) term of the
+ * residual): f_i = sum_e sum_q JxW_q N_i(x_q) b, FP64, f_dev[n_nodes][3]
+ * overwritten; constrained rows are zero. */
+hx_status hx_body_force(hx_mesh *mesh, const double b[3], double *f_dev);
+
+/* Newton's method of Alg. 1 on R(u) - f_ext = 0 over the free DoFs: while
+ * ||r|| > eps_abs and ||r|| > eps_rel ||r_0|| and k < max_newton, update the
+ * quadrature-point data at u_k (strategy `storage`, FP64 and the
+ * preconditioner's precision), solve K du = -r with hx_cg_solve (Chebyshev
+ * (cg_degree)-Jacobi, lambda_max = 1.2 x a power-iteration estimate with
+ * lambda_iters steps) and set u_k += du. u_dev (FP64, [n_nodes][3]) holds u_0
+ * with the Dirichlet values already in its constrained entries (Alg. 1's
+ * u_0 <- g_D), which the updates leave unchanged; it receives the last
+ * iterate. f_ext_dev (FP64, may be NULL) is the external load vector, e.g.
+ * from hx_body_force. A linear solve that stops at cg_max_iter still updates
+ * u (inexact Newton); a CG breakdown returns its status. Returns
+ * HX_ERR_NOT_CONVERGED if the tolerances are not met within max_newton steps.
+ * Synchronous. */
+typedef struct {
+    double eps_abs, eps_rel;
+    int32_t max_newton;
+    int32_t storage;         /* hx_storage refreshed at every Newton step */
+    int32_t cg_degree;       /* Chebyshev degree of the preconditioner */
+    double smoothing_range;  /* lambda_min = lambda_max / range */
+    int32_t precond_prec;    /* hx_prec of the preconditioner */
+    double cg_tol;           /* relative tolerance of each linear solve */
+    int32_t cg_max_iter;
+    int32_t lambda_iters;
+} hx_newton_options;
+typedef struct {
+    int32_t newton_iters;    /* Newton updates performed */
+    int32_t cg_iters;        /* CG iterations over all steps */
+    double res0, res;        /* ||r(u_0)||_2 and ||r(u_k)||_2 */
+    int32_t converged;
+} hx_newton_report;
+hx_status hx_newton_solve(hx_mesh *mesh, double *u_dev, const double *f_ext_dev, const hx_newton_options *opt,
+                          hx_newton_report *report);
+
 /* Fibre dispersion constants H11, H22, H33 from (a, b) (Sec. 3). Host only. */
 hx_status hx_fibre_dispersion(double a, double b, double H[3]);
 

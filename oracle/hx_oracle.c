@@ -15,6 +15,7 @@
  *   tangent   (K du)_{j,a} = sum_e sum_q JxW_q dN_j/dX_b [H S + F D_uS[H]]_ab
  *             with H = Grad du                                             Sec. 2, Eq. (DDu_residual_material)
  *   energy    Pi(u) = sum_e sum_q JxW_q Psi(F_q)                           Sec. 3
+ *   load      f_{j,a} = sum_e sum_q JxW_q N_j(q) b_a, constant body force b  Sec. 2, (v, B)
  *   tangent, spatial form (integration over Omega_t, pulled to Omega_0):
  *             (K du)_{j,a} = sum_e sum_q JxW_q dN_j/dx_b [Jc:(grad du)^S + (grad du) tau]_ab
  *             with grad = Grad F^-1                                        Sec. 2, Eq. (stress_term_in_Ot_with_JC)
@@ -434,6 +435,7 @@ typedef struct {
     double *dN;   /* [qq][nn][3] FE basis reference gradients */
     double *dNg;  /* [qq][ngg][3] geometry basis reference gradients */
     double *W;    /* [qq] tensor weights */
+    double *Nv;   /* [qq][nn] FE basis values */
 } orc_tables;
 
 static int tables_init(const orc_mesh *M, orc_tables *T) {
@@ -446,8 +448,9 @@ static int tables_init(const orc_mesh *M, orc_tables *T) {
     T->dN = (double *)malloc(sizeof(double) * (size_t)T->qq * T->nn * 3);
     T->dNg = (double *)malloc(sizeof(double) * (size_t)T->qq * T->ngg * 3);
     T->W = (double *)malloc(sizeof(double) * (size_t)T->qq);
-    if (!T->dN || !T->dNg || !T->W) return -1;
-    tabulate(M->xi_node, T->n, M->xi_q, T->nq, NULL, T->dN);
+    T->Nv = (double *)malloc(sizeof(double) * (size_t)T->qq * T->nn);
+    if (!T->dN || !T->dNg || !T->W || !T->Nv) return -1;
+    tabulate(M->xi_node, T->n, M->xi_q, T->nq, T->Nv, T->dN);
     tabulate(M->xi_geo, T->ng, M->xi_q, T->nq, NULL, T->dNg);
     for (int qz = 0; qz < T->nq; ++qz)
         for (int qy = 0; qy < T->nq; ++qy)
@@ -459,6 +462,7 @@ static void tables_free(orc_tables *T) {
     free(T->dN);
     free(T->dNg);
     free(T->W);
+    free(T->Nv);
 }
 
 /* Geometry at quadrature point q of element e: J0 = dX/dxi, returns
@@ -814,4 +818,27 @@ void orc_set_num_threads(int n) {
 #else
     (void)n;
 #endif
+}
+
+/* Load vector of a constant body force b: f_{j,a} = sum_e sum_q JxW_q N_j(q) b_a
+ * (the (v, B) term of the residual, Sec. 2), summed in element order. */
+int orc_body_force(const orc_mesh *M, const double *b, double *f) {
+    orc_tables T;
+    if (tables_init(M, &T)) return -1;
+    memset(f, 0, sizeof(double) * (size_t)M->n_nodes * 3);
+    int nbad = 0;
+    for (int e = 0; e < M->n_elem; ++e) {
+        const int32_t *dc = M->dof_conn + (size_t)e * T.nn;
+        for (int q = 0; q < T.qq; ++q) {
+            double J0[9];
+            double JxW = geometry_qp(M, &T, e, q, NULL, J0);
+            if (m_det(J0) <= 0.0) nbad = 1;
+            for (int a = 0; a < T.nn; ++a) {
+                double w = JxW * T.Nv[(size_t)q * T.nn + a];
+                for (int c = 0; c < 3; ++c) f[(size_t)dc[a] * 3 + c] += w * b[c];
+            }
+        }
+    }
+    tables_free(&T);
+    return nbad;
 }

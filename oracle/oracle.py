@@ -77,6 +77,8 @@ def lib():
             L.orc_apply_spatial.argtypes = [P, P, P, P, P, P, C.c_int]
             L.orc_diagonal.argtypes = [P, P, P, P, P, C.c_int]
             L.orc_assemble.argtypes = [P, P, P, P, P, C.c_int]
+            L.orc_body_force.restype = C.c_int
+            L.orc_body_force.argtypes = [P, P, P]
             L.orc_energy.restype = C.c_double
             L.orc_energy.argtypes = [P, P, P]
             L.orc_node_coords.restype = C.c_int
@@ -258,6 +260,14 @@ def apply_spatial(M: OracleMesh, mat: Material, u, du, elems=None) -> np.ndarray
     return out
 
 
+def body_force(M: OracleMesh, b) -> np.ndarray:
+    """Load vector of a constant body force b (Sec. 2, the (v, B) term)."""
+    bb = np.ascontiguousarray(np.asarray(b, dtype=np.float64).reshape(3))
+    f = np.zeros(M.n_dofs)
+    _check(lib().orc_body_force(M.cref(), bb.ctypes.data, f.ctypes.data), "body_force")
+    return f
+
+
 def diagonal(M: OracleMesh, mat: Material, u, elems=None) -> np.ndarray:
     u = _vec(u, M.n_dofs)
     d = np.zeros(M.n_dofs)
@@ -429,3 +439,31 @@ def pcg(Kop, b, Mop, tol=1e-8, maxit=10000, x0=None):
         hist.append(np.linalg.norm(r) / bn)
     true_rel = np.linalg.norm(b - Kop(x)) / bn
     return x, it, true_rel, hist
+
+
+def newton(M: OracleMesh, mat: Material, u0, f_ext=None, eps_abs=1e-10, eps_rel=1e-12, max_it=25):
+    """Newton's method of Alg. 1 on R(u) - f_ext = 0 over the free DoFs, each
+    update from a direct solve with the assembled constrained tangent. u0
+    carries the Dirichlet values (Alg. 1: u_0 <- g_D on Gamma_D). Returns
+    (u, residual norms per iterate)."""
+    import scipy.sparse.linalg as spla
+    mask = M.dirichlet
+    u = _vec(u0, M.n_dofs).copy()
+    f = np.zeros(M.n_dofs) if f_ext is None else _vec(f_ext, M.n_dofs)
+
+    def res(v):
+        r = residual(M, mat, v) - f
+        r[mask] = 0.0
+        return r
+    r = res(u)
+    norms = [float(np.linalg.norm(r))]
+    k = 0
+    while norms[-1] > eps_abs and norms[-1] > eps_rel * norms[0] and k < max_it:
+        K = constrain_matrix(assemble_sparse(M, mat, u), mask)
+        du = spla.spsolve(K.tocsc(), -r)
+        du[mask] = 0.0
+        u = u + du
+        k += 1
+        r = res(u)
+        norms.append(float(np.linalg.norm(r)))
+    return u, norms

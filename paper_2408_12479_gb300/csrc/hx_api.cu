@@ -228,6 +228,7 @@ struct hx_mesh {
     void *w_cheb_d[2] = {nullptr, nullptr}, *w_cheb_Kx[2] = {nullptr, nullptr};
     void *w_stage_in = nullptr, *w_stage_out = nullptr;
     double *w_cg = nullptr;   // r z zold p Ap dinv (FP64)
+    double *w_newton = nullptr;  // Newton: residual, update, inverse diagonal (FP64)
     float *w_cg32 = nullptr;  // r32 z32 dinv32
     cudaStream_t solve_stream = nullptr;
     hx::CgScalars *d_sc = nullptr;
@@ -388,7 +389,7 @@ void hx_destroy_mesh(hx_mesh *m) {
     cudaStreamSynchronize(m->ctx ? m->ctx->stream : nullptr);
     void *ptrs[] = {m->d_dof_conn, m->d_dmask, m->d_cidx, m->d_geo_nodes, m->d_geo_conn, m->d_geo64, m->d_geo32,
                     m->d_fibH64, m->d_fibH32, m->d_fibM, m->cache[0].buf, m->cache[1].buf, m->w_cheb_d[0],
-                    m->w_cheb_d[1], m->w_cheb_Kx[0], m->w_cheb_Kx[1], m->w_stage_in, m->w_stage_out, m->w_cg,
+                    m->w_cheb_d[1], m->w_cheb_Kx[0], m->w_cheb_Kx[1], m->w_stage_in, m->w_stage_out, m->w_cg, m->w_newton,
                     m->w_cg32, m->d_sc, m->d_dots, m->d_partial};
     for (void *p : ptrs) dfree(p);
     if (m->h_pinned) cudaFreeHost(m->h_pinned);
@@ -1168,3 +1169,95 @@ hx_status hx_batch_tangent_apply(hx_batch *b, const void *const *du_dev, void *c
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// external loads and Newton's method (Alg. 1)
+// ---------------------------------------------------------------------------
+hx_status hx_body_force(hx_mesh *m, const double b[3], double *f_dev) {
+    if (!m || !b || !f_dev) return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_body_force: bad argument");
+    hx_ctx *ctx = m->ctx;
+    const hx::PrecOps *ops = hx::prec_ops(m->p, HX_FP64);
+    const hx::MeshView v = view(m, HX_FP64);
+    HX_CUDA(ctx, cudaMemsetAsync(f_dev, 0, 3 * (size_t)m->n_nodes * sizeof(double), ctx->stream));
+    HX_CUDA(ctx, ops->body_force(v, b, f_dev, ctx->stream));
+    ctx->launches += 1;
+    return HX_OK;
+}
+
+hx_status hx_newton_solve(hx_mesh *m, double *u, const double *f_ext, const hx_newton_options *o,
+                          hx_newton_report *rep) {
+    if (!m || !u || !o || !(o->eps_abs >= 0.0) || !(o->eps_rel >= 0.0) || o->max_newton < 0 ||
+        o->storage < HX_RECOMPUTE || o->storage > HX_SPATIAL_TENSORS || bad_prec(o->precond_prec) ||
+        o->cg_degree < 0 || !(o->cg_tol > 0.0) || o->cg_max_iter < 1 || o->lambda_iters < 1 ||
+        !(o->smoothing_range > 1.0))
+        return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_newton_solve: bad argument");
+    hx_ctx *ctx = m->ctx;
+    const int64_t n = 3 * m->n_nodes;
+    if (!m->w_newton) HX_CUDA(ctx, cudaMalloc((void **)&m->w_newton, 3 * (size_t)n * sizeof(double) + 64));
+    hx_status st = ensure_cg_ws(m);
+    if (st != HX_OK) return st;
+    double *r = m->w_newton, *du = r + n, *dinv = r + 2 * n;
+    const int pp = o->precond_prec;
+    // r = R(u) - f_ext on the free DoFs, returns ||r||_2
+    auto residual_norm = [&](double *nrm) -> hx_status {
+        hx_status s2 = hx_residual(m, u, r, HX_FP64);
+        if (s2 != HX_OK) return s2;
+        cudaStream_t s = ctx->stream;
+        if (f_ext) {
+            HX_CUDA(ctx, hx::axpby(n, -1.0, f_ext, 1.0, r, s));
+            if (m->n_constrained) HX_CUDA(ctx, hx::set_idx(m->d_cidx, m->n_constrained, 0.0, r, HX_FP64, s));
+        }
+        HX_CUDA(ctx, hx::dots(n, 1, r, r, nullptr, nullptr, nullptr, nullptr, m->d_partial, m->d_dots, s));
+        double h = 0.0;
+        HX_CUDA(ctx, cudaMemcpyAsync(&h, m->d_dots, sizeof h, cudaMemcpyDeviceToHost, s));
+        HX_CUDA(ctx, cudaStreamSynchronize(s));
+        ctx->launches += 3;
+        if (!(h == h)) return fail(ctx, HX_ERR_NAN, "hx_newton_solve: NaN in the residual");
+        *nrm = std::sqrt(h);
+        return HX_OK;
+    };
+    double res0 = 0.0, res = 0.0;
+    st = residual_norm(&res0);
+    if (st != HX_OK) return st;
+    res = res0;
+    int k = 0, cg_total = 0;
+    hx_status lin = HX_OK;
+    while (res > o->eps_abs && res > o->eps_rel * res0 && k < o->max_newton) {
+        // update quadrature point data at u_k (both precisions the solve uses)
+        st = hx_precompute_qp(m, u, HX_FP64, o->storage);
+        if (st == HX_OK && pp != HX_FP64) st = hx_precompute_qp(m, u, pp, o->storage);
+        if (st == HX_OK) st = hx_sync(ctx, -1);  // reports J <= 0 met at the new state
+        if (st != HX_OK) return st;
+        // eigenvalue bound of D^-1 K for the Chebyshev preconditioner
+        double lam = 0.0;
+        st = hx_diagonal(m, dinv, HX_FP64);
+        if (st != HX_OK) return st;
+        HX_CUDA(ctx, hx::invert(n, dinv, dinv, HX_FP64, ctx->stream));
+        st = hx_estimate_lambda_max(m, dinv, o->lambda_iters, 7 + (uint64_t)k, &lam);
+        if (st != HX_OK) return st;
+        // K du = -r
+        HX_CUDA(ctx, hx::axpby(n, -1.0, r, 0.0, r, ctx->stream));
+        HX_CUDA(ctx, cudaMemsetAsync(du, 0, n * sizeof(double), ctx->stream));
+        hx_cg_options cg{o->cg_degree, 1.2 * lam, o->smoothing_range, pp, 1};
+        int32_t it = 0;
+        double rel = 0.0;
+        lin = hx_cg_solve(m, r, du, o->cg_tol, o->cg_max_iter, &cg, &it, &rel);
+        if (lin != HX_OK && lin != HX_ERR_NOT_CONVERGED) return lin;  // breakdown: no usable update
+        cg_total += it;
+        HX_CUDA(ctx, hx::axpby(n, 1.0, du, 1.0, u, ctx->stream));
+        ctx->launches += 3;
+        ++k;
+        st = residual_norm(&res);
+        if (st != HX_OK) return st;
+    }
+    const bool ok = res <= o->eps_abs || res <= o->eps_rel * res0;
+    if (rep) {
+        rep->newton_iters = k;
+        rep->cg_iters = cg_total;
+        rep->res0 = res0;
+        rep->res = res;
+        rep->converged = ok ? 1 : 0;
+    }
+    if (!ok) return fail(ctx, HX_ERR_NOT_CONVERGED, "hx_newton_solve: Newton iteration limit reached");
+    return HX_OK;
+}

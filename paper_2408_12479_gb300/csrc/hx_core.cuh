@@ -802,13 +802,16 @@ __device__ __forceinline__ void st_line(Real *p, const Real *y) {
 #pragma unroll
     for (int t = 0; t < N; ++t) p[t * line_str<DIR>()] = y[t];
 }
-// y = M x (TR: y = M^T x) with a 1D table from constant memory. From five
-// points on, the even-odd decomposition: with e_t = x_t + x_{N-1-t} and
-// d_t = x_t - x_{N-1-t}, a_o = P e (+ M[o][h] x_h), b_o = Q d, and
-// y_o = a_o + b_o, y_{N-1-o} = +-(a_o - b_o) (N^2 FMAs become about N^2/2 + 2N).
+// y = M x (TR: y = M^T x) with a 1D table from constant memory. FP64 units
+// from five points on use the even-odd decomposition: with e_t = x_t +
+// x_{N-1-t} and d_t = x_t - x_{N-1-t}, a_o = P e (+ M[o][h] x_h), b_o = Q d,
+// y_o = a_o + b_o and y_{N-1-o} = +-(a_o - b_o) (N^2 FMAs become about
+// N^2/2 + 2N; the FP64 apply is bound by the FP64 pipe). FP32 units keep the
+// plain products: a_o - b_o loses relative accuracy where the two nearly
+// cancel, and the FP32 apply is not bound by its FMA count.
 template <int TAB, bool TR>
 __device__ __forceinline__ void mv(const Real *x, Real *y) {
-    if constexpr (N >= 5) {
+    if constexpr (N >= 5 && sizeof(Real) == 8) {
         constexpr int H = EOH;
         constexpr bool SYM = TAB == TB;
         auto M = [](int o, int t) { return tab<TAB>(TR ? t * N + o : o * N + t); };
@@ -1841,6 +1844,37 @@ __global__ void __launch_bounds__(threads_for(2)) k_diagonal(const hx::MeshView 
     }
     __syncthreads();
     scatter_add(m, e0, EPB, U, diag, true);
+}
+
+// External load vector of a constant body force b (Sec. 2, the (v, B) term
+// of the residual): f_i += sum_q JxW_q N_i(x_q) b, by the transposed value
+// sweeps Bz^T, By^T, Bx^T of JxW b and a scatter (constrained rows skipped).
+// FP64 throughout (the geometry's FP64 copy).
+template <int EPB>
+__global__ void __launch_bounds__(threads_for(EPB)) k_body_force(const hx::MeshView m, double b0, double b1, double b2,
+                                                                double *__restrict__ f) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Real *U = (Real *)smem_raw;
+    Real *W = U + 3 * EPB * SZ;
+    const int e0 = blockIdx.x * EPB;
+    for (int it = threadIdx.x; it < EPB * NQ; it += blockDim.x) {
+        const int el = it / NQ;
+        const int q = it - el * NQ;
+        const int e = e0 + el;
+        const int ci = cidx(q % N, (q / N) % N, q / NN);
+        const double jxw = e < m.n_elem ? m.geo64[(int64_t)9 * m.qs + (int64_t)e * NQ + q] : 0.0;
+        W[(el * 3 + 0) * SZ + ci] = (Real)(jxw * b0);
+        W[(el * 3 + 1) * SZ + ci] = (Real)(jxw * b1);
+        W[(el * 3 + 2) * SZ + ci] = (Real)(jxw * b2);
+    }
+    __syncthreads();
+    sweep<Real, 2, TB, true, false, 1, 0, 1, 0>(W, U, 3 * EPB);
+    __syncthreads();
+    sweep<Real, 1, TB, true, false, 1, 0, 1, 0>(U, W, 3 * EPB);
+    __syncthreads();
+    sweep<Real, 0, TB, true, false, 1, 0, 1, 0>(W, U, 3 * EPB);
+    __syncthreads();
+    scatter_add(m, e0, EPB, U, f, true);
 }
 
 // geometry at every quadrature point: J0 = dX/dxi from the degree-g map,

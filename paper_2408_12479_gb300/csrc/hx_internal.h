@@ -81,6 +81,8 @@ struct PrecOps {
     cudaError_t (*apply)(const MeshView &m, int storage, const void *du, void *out, cudaStream_t s, int variant);
     cudaError_t (*residual)(const MeshView &m, const void *u, void *r, cudaStream_t s);
     cudaError_t (*diagonal)(const MeshView &m, int storage, void *diag, cudaStream_t s);
+    // f += load vector of a constant body force (FP64 unit only)
+    cudaError_t (*body_force)(const MeshView &m, const double *b, double *f, cudaStream_t s);
     int n_variants;  // tile variants of apply available to the autotuner
 };
 

@@ -233,6 +233,18 @@ cudaError_t op_node_coords(const hx::MeshView &m, const double *X, const int32_t
     return cudaGetLastError();
 }
 
+#if !HX_UNIT_F32
+cudaError_t op_body_force(const hx::MeshView &m, const double *b, double *f, cudaStream_t s) {
+    constexpr int EPB = 2;
+    constexpr size_t smem = (size_t)6 * EPB * SZ * sizeof(Real);
+    if (m.n_elem == 0) return cudaSuccess;
+    cudaError_t e = set_smem(k_body_force<EPB>, smem);
+    if (e != cudaSuccess) return e;
+    k_body_force<EPB><<<(m.n_elem + EPB - 1) / EPB, threads_for(EPB), smem, s>>>(m, b[0], b[1], b[2], f);
+    return cudaGetLastError();
+}
+#endif
+
 }  // namespace
 }  // namespace hx_unit
 
@@ -254,6 +266,11 @@ extern "C++" const hx::PrecOps *HX_OPS_NAME() {
         op_apply,
         op_residual,
         op_diagonal,
+#if HX_UNIT_F32
+        nullptr,
+#else
+        op_body_force,
+#endif
         6,
     };
     return &ops;

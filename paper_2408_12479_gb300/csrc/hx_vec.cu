@@ -125,6 +125,12 @@ __global__ void k_convert(int64_t n, const TI *__restrict__ a, TO *__restrict__ 
 }
 
 // y = a - b
+// y = a x + b y
+__global__ void k_axpby(int64_t n, double a, const double *__restrict__ x, double b, double *__restrict__ y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = b == 0.0 ? a * x[i] : fma(a, x[i], b * y[i]);
+}
+
 __global__ void k_sub(int64_t n, const double *__restrict__ a, const double *__restrict__ b, double *__restrict__ y) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = a[i] - b[i];
@@ -245,6 +251,10 @@ cudaError_t to_f32(int64_t n, const double *a, float *b, cudaStream_t s) {
 }
 cudaError_t to_f64(int64_t n, const float *a, double *b, cudaStream_t s) {
     k_convert<float, double><<<grid_for(n), VB, 0, s>>>(n, a, b);
+    return cudaGetLastError();
+}
+cudaError_t axpby(int64_t n, double a, const double *x, double b, double *y, cudaStream_t s) {
+    k_axpby<<<grid_for(n), VB, 0, s>>>(n, a, x, b, y);
     return cudaGetLastError();
 }
 cudaError_t sub(int64_t n, const double *a, const double *b, double *y, cudaStream_t s) {

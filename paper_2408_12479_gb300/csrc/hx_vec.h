@@ -30,6 +30,8 @@ cudaError_t cg_p(int64_t n, const CgScalars *sc, const double *z, double *p, dou
 cudaError_t to_f32(int64_t n, const double *a, float *b, cudaStream_t s);
 cudaError_t to_f64(int64_t n, const float *a, double *b, cudaStream_t s);
 cudaError_t sub(int64_t n, const double *a, const double *b, double *y, cudaStream_t s);
+// y = a x + b y (b == 0: y = a x)
+cudaError_t axpby(int64_t n, double a, const double *x, double b, double *y, cudaStream_t s);
 cudaError_t normalize(int64_t n, const double *nrm2, const double *x, double *y, cudaStream_t s);
 cudaError_t scale(int64_t n, const double *dinv, const double *x, double *y, cudaStream_t s);
 cudaError_t invert(int64_t n, const void *x, void *y, int prec, cudaStream_t s);

@@ -33,7 +33,7 @@ STORAGE_NAMES = {HX_RECOMPUTE: "recompute", HX_CACHE_F: "cache_F", HX_CACHE_TENS
 EXPORTS = ["hx_create", "hx_destroy", "hx_set_stream", "hx_last_error", "hx_sync", "hx_setup_mesh",
            "hx_destroy_mesh", "hx_mesh_info", "hx_node_coords", "hx_apply_bytes", "hx_precompute_qp",
            "hx_residual", "hx_tangent_apply", "hx_tangent_apply_host", "hx_diagonal", "hx_chebyshev_smooth",
-           "hx_estimate_lambda_max", "hx_cg_solve", "hx_fibre_dispersion", "hx_batch_create",
+           "hx_estimate_lambda_max", "hx_cg_solve", "hx_body_force", "hx_newton_solve", "hx_fibre_dispersion", "hx_batch_create",
            "hx_batch_destroy", "hx_batch_tangent_apply", "hx_measure_fma_peak", "hx_launch_count",
            "hx_autotune", "hx_set_apply_variant", "hx_chebyshev_smooth_noalloc"]
 
@@ -59,6 +59,18 @@ class hx_mesh_desc(C.Structure):
 class hx_cg_options(C.Structure):
     _fields_ = [("degree", C.c_int32), ("lambda_max", C.c_double), ("smoothing_range", C.c_double),
                 ("precond_prec", C.c_int32), ("use_graph", C.c_int32)]
+
+
+class hx_newton_options(C.Structure):
+    _fields_ = [("eps_abs", C.c_double), ("eps_rel", C.c_double), ("max_newton", C.c_int32),
+                ("storage", C.c_int32), ("cg_degree", C.c_int32), ("smoothing_range", C.c_double),
+                ("precond_prec", C.c_int32), ("cg_tol", C.c_double), ("cg_max_iter", C.c_int32),
+                ("lambda_iters", C.c_int32)]
+
+
+class hx_newton_report(C.Structure):
+    _fields_ = [("newton_iters", C.c_int32), ("cg_iters", C.c_int32), ("res0", C.c_double), ("res", C.c_double),
+                ("converged", C.c_int32)]
 
 
 _lock = threading.Lock()
@@ -94,6 +106,8 @@ def lib():
             "hx_chebyshev_smooth": (I32, [P, P, P, P, I32, D, D, I32, I32]),
             "hx_estimate_lambda_max": (I32, [P, P, I32, U64, C.POINTER(D)]),
             "hx_cg_solve": (I32, [P, P, P, D, I32, C.POINTER(hx_cg_options), C.POINTER(I32), C.POINTER(D)]),
+            "hx_body_force": (I32, [P, C.POINTER(D), P]),
+            "hx_newton_solve": (I32, [P, P, P, C.POINTER(hx_newton_options), C.POINTER(hx_newton_report)]),
             "hx_fibre_dispersion": (I32, [D, D, C.POINTER(D)]),
             "hx_batch_create": (I32, [P, C.POINTER(P), I32, C.POINTER(P)]),
             "hx_batch_destroy": (None, [P]),
@@ -284,6 +298,28 @@ def hx_cg_solve(ctx, mesh, rhs, x, tol, max_iter, degree, lambda_max, smoothing_
     if st not in (HX_OK, HX_ERR_NOT_CONVERGED):
         _check(st, ctx)
     return it.value, rel.value, st
+
+
+def hx_body_force(ctx, mesh, b, f):
+    bb = (C.c_double * 3)(*[float(x) for x in b])
+    _check(lib().hx_body_force(mesh, bb, _ptr(f)), ctx)
+
+
+def hx_newton_solve(ctx, mesh, u, f_ext=None, eps_abs=1e-10, eps_rel=1e-8, max_newton=20, storage=HX_CACHE_TENSORS,
+                    cg_degree=5, smoothing_range=15.0, precond_prec=HX_FP32, cg_tol=1e-6, cg_max_iter=5000,
+                    lambda_iters=30):
+    """Newton's method (Alg. 1); returns (report dict, status). u is updated in
+    place; HX_ERR_NOT_CONVERGED is returned, not raised."""
+    opt = hx_newton_options(float(eps_abs), float(eps_rel), int(max_newton), int(storage), int(cg_degree),
+                            float(smoothing_range), int(precond_prec), float(cg_tol), int(cg_max_iter),
+                            int(lambda_iters))
+    rep = hx_newton_report()
+    st = lib().hx_newton_solve(mesh, _ptr(u), _ptr(f_ext) if f_ext is not None else None, C.byref(opt),
+                               C.byref(rep))
+    if st not in (HX_OK, HX_ERR_NOT_CONVERGED):
+        _check(st, ctx)
+    return {"newton_iters": rep.newton_iters, "cg_iters": rep.cg_iters, "res0": rep.res0, "res": rep.res,
+            "converged": bool(rep.converged)}, st
 
 
 def hx_set_apply_variant(ctx, mesh, prec, storage, variant):

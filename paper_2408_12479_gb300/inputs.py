@@ -330,6 +330,23 @@ def box_dirichlet_symmetry(nx, ny, nz, p):
     return m.ravel()
 
 
+def workload_uniaxial(n, p, stretch, lengths=(1.0, 1.0, 1.0)):
+    """Unit box (no jitter) under uniaxial stretch: symmetry clamps on x = 0,
+    y = 0, z = 0 and the prescribed u_x = (stretch - 1) L_x on the face
+    x = L_x; the lateral faces are free. Returns the mesh and the initial
+    iterate u_0 = ((stretch - 1) x, 0, 0), which carries the prescribed values
+    on the clamped faces."""
+    m = box_mesh(n, p, lengths=lengths, name=f"uniaxial{n}_p{p}")
+    Nx, Ny, Nz = n * p + 1, n * p + 1, n * p + 1
+    mask = box_dirichlet_symmetry(n, n, n, p).reshape(-1, 3).copy()
+    I_ = np.arange(Nx * Ny * Nz) % Nx
+    mask[I_ == Nx - 1, 0] = 1
+    m.dirichlet = mask.ravel().astype(np.uint8)
+    u0 = np.zeros((Nx * Ny * Nz, 3))
+    u0[:, 0] = (stretch - 1.0) * lengths[0] * I_ / (Nx - 1)
+    return m, u0.ravel()
+
+
 @dataclass
 class CompressionField:
     """u_c = s X_c + a X_c sum_j sin(pi k_cj . X + phi_cj): uniform compression

@@ -423,3 +423,53 @@ def test_pcg_solves_constrained_system():
     xs = spla.spsolve(K.tocsc(), b)
     assert rel < 1e-10 and rel_inf(x, xs) < 1e-8
     assert np.all(x[M.dirichlet] == 0.0) or np.abs(x[M.dirichlet]).max() < 1e-14
+
+
+# --------------------------------------------------------------------------
+# external loads and Newton's method (Alg. 1)
+# --------------------------------------------------------------------------
+
+def test_body_force_partition_of_unity_and_first_moment():
+    """sum_j f_j = b |Omega| (the basis sums to one) and sum_j X_j f_j =
+    b int X dV (linear fields are reproduced), on a jittered box."""
+    m = I.box_mesh(3, 2, jitter=0.1, seed=9, lengths=(1.0, 0.7, 1.3))
+    M = O.OracleMesh(m)
+    b = np.array([0.3, -0.2, 0.5])
+    f = O.body_force(M, b).reshape(-1, 3)
+    vol = 1.0 * 0.7 * 1.3   # the jitter moves interior vertices only
+    assert np.abs(f.sum(axis=0) - b * vol).max() < 1e-13
+    X = O.node_coords(M)
+    centroid = np.array([0.5, 0.35, 0.65])
+    assert np.abs(X.reshape(-1, 3).T @ f - np.outer(centroid * vol, b)).max() < 1e-12
+
+
+def _lateral_stretch(law, mat, l1):
+    """Lateral stretch of homogeneous uniaxial tension with free lateral
+    faces: S_22 = 0 with F = diag(l1, l2, l2) (Sec. 3 stresses, C^-1_22 = 1/l2^2)."""
+    from scipy.optimize import brentq
+
+    def s22(l2):
+        J = l1 * l2 * l2
+        if law == "cNH":
+            return mat.mu - (mat.mu - 2.0 * mat.lam * np.log(J)) / l2 ** 2
+        j = J ** (-2.0 / 3.0)
+        I1 = l1 ** 2 + 2 * l2 ** 2
+        c1 = 0.5 * mat.kappa * (J * J - 1.0) - mat.mu / 3.0 * j * I1
+        return mat.mu * j + c1 / l2 ** 2
+    return brentq(s22, 0.5, 1.5)
+
+
+@pytest.mark.parametrize("law,mat", [("cNH", CNH), ("iNH", INH)])
+def test_newton_uniaxial_matches_homogeneous_closed_form(law, mat):
+    l1 = 1.2
+    m, u0 = I.workload_uniaxial(2, 2, l1)
+    M = O.OracleMesh(m)
+    u, norms = O.newton(M, mat, u0)
+    assert norms[-1] < 1e-10 and len(norms) < 12
+    # quadratic convergence once close
+    tail = [b / a ** 2 for a, b in zip(norms[:-1], norms[1:]) if a < 1e-2 and b > 1e-12]  # above round-off
+    assert all(t < 1e3 for t in tail)
+    l2 = _lateral_stretch(law, mat, l1)
+    X = O.node_coords(M).reshape(-1, 3)
+    exact = X * (np.array([l1, l2, l2]) - 1.0)
+    assert np.abs(u.reshape(-1, 3) - exact).max() < 1e-10
