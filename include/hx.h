@@ -250,6 +250,18 @@ typedef struct {
 hx_status hx_cg_solve(hx_mesh *mesh, const double *rhs_dev, double *x_dev, double tol, int32_t max_iter,
                       const hx_cg_options *opt, int32_t *iters, double *rel_residual);
 
+/* Pointwise evaluation of the mesh's law for the forward-stability study
+ * (Sec. 6.1): at n displacement gradients G (Grad u) and directions H, all
+ * FP64 device arrays [n][9] row-major, compute S, P = F S and dP = H S +
+ * F D_uS[H] ([n][9], FP64 device) in precision `prec` (inputs rounded to it
+ * first). form 0: the stable forms of Sec. 4 (J-1 from the components of G,
+ * ln J = ln_{+1}(J-1), C^-1 = F^-1 F^-T, E = (G + G^T + G^T G)/2,
+ * J^-2/3 = exp(-2/3 ln J)); 1: the same with J^-2/3 by Alg. 2; 2: the
+ * standard forms of Sec. 3 / App. A (F = I + G, C = F^T F inverted directly,
+ * det F, log, pow). Fibre structure tensors are those of element `elem`. */
+hx_status hx_material_eval(hx_mesh *mesh, int32_t elem, int32_t form, int32_t prec, int64_t n, const double *G_dev,
+                           const double *H_dev, double *S_dev, double *P_dev, double *dP_dev);
+
 /* Load vector of a constant body force b[3] (Sec. 2, the (v, B) term of the
  * residual): f_i = sum_e sum_q JxW_q N_i(x_q) b, FP64, f_dev[n_nodes][3]
  * overwritten; constrained rows are zero. */

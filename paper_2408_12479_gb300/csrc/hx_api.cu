@@ -6,6 +6,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <mutex>
@@ -1259,5 +1260,17 @@ hx_status hx_newton_solve(hx_mesh *m, double *u, const double *f_ext, const hx_n
         rep->converged = ok ? 1 : 0;
     }
     if (!ok) return fail(ctx, HX_ERR_NOT_CONVERGED, "hx_newton_solve: Newton iteration limit reached");
+    return HX_OK;
+}
+
+hx_status hx_material_eval(hx_mesh *m, int32_t elem, int32_t form, int32_t prec, int64_t n, const double *G,
+                           const double *H, double *S, double *P, double *dP) {
+    if (!m || bad_prec(prec) || form < 0 || form > 2 || n < 0 || elem < 0 || elem >= std::max(m->n_elem, 1) ||
+        (n > 0 && (!G || !H || !S || !P || !dP)))
+        return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_material_eval: bad argument");
+    hx_ctx *ctx = m->ctx;
+    const hx::MeshView v = view(m, prec);
+    HX_CUDA(ctx, hx::prec_ops(m->p, prec)->material_eval(v, elem, form, n, G, H, S, P, dP, ctx->stream));
+    ctx->launches += 1;
     return HX_OK;
 }

@@ -1846,6 +1846,172 @@ __global__ void __launch_bounds__(threads_for(2)) k_diagonal(const hx::MeshView 
     scatter_add(m, e0, EPB, U, diag, true);
 }
 
+// ---------------------------------------------------------------------------
+// Pointwise law evaluation for the forward-stability study (Sec. 6.1): S,
+// P = F S and dP = H S + F D_uS[H] at Grad u = G in this unit's precision.
+// FORM 0: the stable forms with J^-2/3 = exp(-2/3 ln_{+1}(J-1)); FORM 1: the
+// stable forms with Alg. 2 for J^-2/3; FORM 2: the standard forms, from
+// F = I + G, C = F^T F, C^-1 = C^{-1} (adjugate), J = det F, ln J, J^-2/3 by
+// pow, E = (C - I)/2 (Sec. 3 and App. A as printed, before the Sec. 4
+// rewrites).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T det3(const T *A) {
+    return A[0] * (A[4] * A[8] - A[5] * A[7]) - A[1] * (A[3] * A[8] - A[5] * A[6]) + A[2] * (A[3] * A[7] - A[4] * A[6]);
+}
+template <typename T>
+__device__ __forceinline__ void inv3(const T *A, T *Ai) {
+    const T id = T(1) / det3(A);
+    Ai[0] = (A[4] * A[8] - A[5] * A[7]) * id;
+    Ai[1] = (A[2] * A[7] - A[1] * A[8]) * id;
+    Ai[2] = (A[1] * A[5] - A[2] * A[4]) * id;
+    Ai[3] = (A[5] * A[6] - A[3] * A[8]) * id;
+    Ai[4] = (A[0] * A[8] - A[2] * A[6]) * id;
+    Ai[5] = (A[2] * A[3] - A[0] * A[5]) * id;
+    Ai[6] = (A[3] * A[7] - A[4] * A[6]) * id;
+    Ai[7] = (A[1] * A[6] - A[0] * A[7]) * id;
+    Ai[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+}
+template <typename T>
+__device__ __forceinline__ void mm3(const T *A, const T *B, T *C, bool ta = false) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T s = T(0);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) s += (ta ? A[k * 3 + i] : A[i * 3 + k]) * B[k * 3 + j];
+            C[i * 3 + j] = s;
+        }
+}
+
+template <typename T, int LAW>
+__device__ void standard_eval(const hx::MeshView &m, int e, const T *G, const T *H, T *S9, T *P, T *dP) {
+    const Mat<T> mp = mat_of<T>(m);
+    T F[9], C[9], Ci[9], Fi[9], FtH[9], dC[9], X1[9], dCi[9], dS[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) F[k] = G[k] + ((k % 4) == 0 ? T(1) : T(0));
+    mm3(F, F, C, true);
+    inv3(C, Ci);
+    inv3(F, Fi);
+    const T J = det3(F);
+    const T lnJ = log(J);
+    const T I1 = C[0] + C[4] + C[8];
+    mm3(F, H, FtH, true);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) dC[i * 3 + j] = FtH[i * 3 + j] + FtH[j * 3 + i];
+    mm3(Ci, dC, X1);
+    mm3(X1, Ci, dCi);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) dCi[k] = -dCi[k];
+    T A[9];
+    mm3(Fi, H, A);
+    const T t = A[0] + A[4] + A[8];  // (1/J) D_u J
+    if constexpr (LAW == HX_CNH) {
+        const T a = mp.mu - T(2) * mp.lambda * lnJ;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            S9[k] = -a * Ci[k] + ((k % 4) == 0 ? mp.mu : T(0));
+            dS[k] = -a * dCi[k] + T(2) * mp.lambda * t * Ci[k];
+        }
+    } else {
+        const T j23 = pow(J, T(-2.0 / 3.0));
+        const T c1 = T(0.5) * mp.kappa * (J * J - T(1)) - mp.mu / T(3) * j23 * I1;
+        const T c2 = T(2) * mp.mu / T(9) * j23 * I1 + mp.kappa * J * J;
+        const T dI1 = T(2) * (FtH[0] + FtH[4] + FtH[8]);
+        const T cC = c2 * t - mp.mu / T(3) * j23 * dI1;
+        const T cI = T(-2) * mp.mu / T(3) * j23 * t;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            S9[k] = c1 * Ci[k] + ((k % 4) == 0 ? mp.mu * j23 : T(0));
+            dS[k] = c1 * dCi[k] + cC * Ci[k] + ((k % 4) == 0 ? cI : T(0));
+        }
+        if constexpr (LAW == HX_FIBER) {
+            State<T> fs;
+            load_fibH(m, e, fs);
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {
+                const T *Hs = f ? fs.H6 : fs.H4;
+                T Hf[9];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) Hf[i * 3 + j] = Hs[SI(i, j)];
+                T HC = T(0), HdC = T(0), Is = T(0);
+#pragma unroll
+                for (int k = 0; k < 9; ++k) {
+                    HC += Hf[k] * C[k];
+                    HdC += Hf[k] * dC[k];
+                }
+                T M1[3];
+#pragma unroll
+                for (int d = 0; d < 3; ++d) M1[d] = (T)m.fibM[(int64_t)(3 * f + d) * m.n_elem + e];
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) Is += M1[i] * C[i * 3 + j] * M1[j];
+                if (Is > T(1)) {
+                    const T E = HC - T(1);
+                    const T c3 = T(2) * mp.k1 * exp(mp.k2 * E * E);
+                    const T cd = c3 * (T(2) * mp.k2 * E * E + T(1)) * HdC;
+#pragma unroll
+                    for (int k = 0; k < 9; ++k) {
+                        S9[k] += c3 * E * Hf[k];
+                        dS[k] += cd * Hf[k];
+                    }
+                }
+            }
+        }
+    }
+    T HS[9], FdS[9];
+    mm3(F, S9, P);
+    mm3(H, S9, HS);
+    mm3(F, dS, FdS);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) dP[k] = HS[k] + FdS[k];
+}
+
+template <int LAW, int FORM>
+__global__ void __launch_bounds__(128) k_material_eval(const hx::MeshView m, int e, int64_t n, const double *__restrict__ G,
+                                                       const double *__restrict__ H, double *__restrict__ S,
+                                                       double *__restrict__ P, double *__restrict__ dP) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        Real g[9], h[9], s9[9], p9[9], d9[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            g[k] = (Real)G[i * 9 + k];
+            h[k] = (Real)H[i * 9 + k];
+        }
+        if constexpr (FORM == 2) {
+            standard_eval<Real, LAW>(m, e, g, h, s9, p9, d9);
+        } else {
+            State<Real> st;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) st.Hk[k] = g[k];
+            state_from_Hk<Real, LAW, FORM == 1>(m, e, st);
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    s9[a * 3 + b] = st.S[SI(a, b)];
+                    Real v = st.S[SI(a, b)];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) v = fma(st.Hk[a * 3 + k], st.S[SI(k, b)], v);
+                    p9[a * 3 + b] = v;
+                }
+            tangent_dP<Real, LAW>(st, h, d9);
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            S[i * 9 + k] = (double)s9[k];
+            P[i * 9 + k] = (double)p9[k];
+            dP[i * 9 + k] = (double)d9[k];
+        }
+    }
+}
+
 // External load vector of a constant body force b (Sec. 2, the (v, B) term
 // of the residual): f_i += sum_q JxW_q N_i(x_q) b, by the transposed value
 // sweeps Bz^T, By^T, Bx^T of JxW b and a scatter (constrained rows skipped).

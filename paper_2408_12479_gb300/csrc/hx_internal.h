@@ -81,6 +81,10 @@ struct PrecOps {
     cudaError_t (*apply)(const MeshView &m, int storage, const void *du, void *out, cudaStream_t s, int variant);
     cudaError_t (*residual)(const MeshView &m, const void *u, void *r, cudaStream_t s);
     cudaError_t (*diagonal)(const MeshView &m, int storage, void *diag, cudaStream_t s);
+    // pointwise law evaluation at n gradients (form: 0 stable, 1 stable with
+    // Alg. 2 for J^-2/3, 2 standard), fibre data of element e
+    cudaError_t (*material_eval)(const MeshView &m, int e, int form, int64_t n, const double *G, const double *H,
+                                 double *S, double *P, double *dP, cudaStream_t s);
     // f += load vector of a constant body force (FP64 unit only)
     cudaError_t (*body_force)(const MeshView &m, const double *b, double *f, cudaStream_t s);
     int n_variants;  // tile variants of apply available to the autotuner

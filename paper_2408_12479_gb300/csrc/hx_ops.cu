@@ -3,6 +3,7 @@
 // keeps its own 1D tables in constant memory and exports one PrecOps table.
 // The kernel bodies are in hx_core.cuh.
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <stdint.h>
 
 #include <type_traits>
@@ -233,6 +234,19 @@ cudaError_t op_node_coords(const hx::MeshView &m, const double *X, const int32_t
     return cudaGetLastError();
 }
 
+cudaError_t op_material_eval(const hx::MeshView &m, int e, int form, int64_t n, const double *G, const double *H,
+                             double *S, double *P, double *dP, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int grid = (int)std::min<int64_t>((n + 127) / 128, 4096);
+#define HX_ME_CASE(L, F) \
+    if (m.law == L && form == F) { k_material_eval<L, F><<<grid, 128, 0, s>>>(m, e, n, G, H, S, P, dP); return cudaGetLastError(); }
+    HX_ME_CASE(HX_CNH, 0) HX_ME_CASE(HX_CNH, 1) HX_ME_CASE(HX_CNH, 2)
+    HX_ME_CASE(HX_INH, 0) HX_ME_CASE(HX_INH, 1) HX_ME_CASE(HX_INH, 2)
+    HX_ME_CASE(HX_FIBER, 0) HX_ME_CASE(HX_FIBER, 1) HX_ME_CASE(HX_FIBER, 2)
+#undef HX_ME_CASE
+    return cudaErrorInvalidValue;
+}
+
 #if !HX_UNIT_F32
 cudaError_t op_body_force(const hx::MeshView &m, const double *b, double *f, cudaStream_t s) {
     constexpr int EPB = 2;
@@ -266,6 +280,7 @@ extern "C++" const hx::PrecOps *HX_OPS_NAME() {
         op_apply,
         op_residual,
         op_diagonal,
+        op_material_eval,
 #if HX_UNIT_F32
         nullptr,
 #else

@@ -33,7 +33,7 @@ STORAGE_NAMES = {HX_RECOMPUTE: "recompute", HX_CACHE_F: "cache_F", HX_CACHE_TENS
 EXPORTS = ["hx_create", "hx_destroy", "hx_set_stream", "hx_last_error", "hx_sync", "hx_setup_mesh",
            "hx_destroy_mesh", "hx_mesh_info", "hx_node_coords", "hx_apply_bytes", "hx_precompute_qp",
            "hx_residual", "hx_tangent_apply", "hx_tangent_apply_host", "hx_diagonal", "hx_chebyshev_smooth",
-           "hx_estimate_lambda_max", "hx_cg_solve", "hx_body_force", "hx_newton_solve", "hx_fibre_dispersion", "hx_batch_create",
+           "hx_estimate_lambda_max", "hx_cg_solve", "hx_body_force", "hx_newton_solve", "hx_material_eval", "hx_fibre_dispersion", "hx_batch_create",
            "hx_batch_destroy", "hx_batch_tangent_apply", "hx_measure_fma_peak", "hx_launch_count",
            "hx_autotune", "hx_set_apply_variant", "hx_chebyshev_smooth_noalloc"]
 
@@ -107,6 +107,7 @@ def lib():
             "hx_estimate_lambda_max": (I32, [P, P, I32, U64, C.POINTER(D)]),
             "hx_cg_solve": (I32, [P, P, P, D, I32, C.POINTER(hx_cg_options), C.POINTER(I32), C.POINTER(D)]),
             "hx_body_force": (I32, [P, C.POINTER(D), P]),
+            "hx_material_eval": (I32, [P, I32, I32, I32, C.c_int64, P, P, P, P, P]),
             "hx_newton_solve": (I32, [P, P, P, C.POINTER(hx_newton_options), C.POINTER(hx_newton_report)]),
             "hx_fibre_dispersion": (I32, [D, D, C.POINTER(D)]),
             "hx_batch_create": (I32, [P, C.POINTER(P), I32, C.POINTER(P)]),
@@ -298,6 +299,19 @@ def hx_cg_solve(ctx, mesh, rhs, x, tol, max_iter, degree, lambda_max, smoothing_
     if st not in (HX_OK, HX_ERR_NOT_CONVERGED):
         _check(st, ctx)
     return it.value, rel.value, st
+
+
+def hx_material_eval(ctx, mesh, G, H, prec, form=0, elem=0):
+    """S, P, dP ([n, 3, 3] FP64 tensors on the device) of the mesh's law at
+    gradients G and directions H ([n, 3, 3] FP64 device tensors)."""
+    import torch
+    n = G.shape[0]
+    G = G.reshape(n, 9).contiguous()
+    H = H.reshape(n, 9).contiguous()
+    S, P, dP = (torch.empty_like(G) for _ in range(3))
+    _check(lib().hx_material_eval(mesh, int(elem), int(form), int(prec), int(n), _ptr(G), _ptr(H), _ptr(S), _ptr(P),
+                                  _ptr(dP)), ctx)
+    return S.reshape(n, 3, 3), P.reshape(n, 3, 3), dP.reshape(n, 3, 3)
 
 
 def hx_body_force(ctx, mesh, b, f):
