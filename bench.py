@@ -260,6 +260,71 @@ def run_solve(device, n=48, p=4, tol=1e-8, max_iter=20000, degree=5, smoothing_r
     return res
 
 
+def run_stability(device):
+    """Forward-stability study (Sec. 6.1): 200 strain scales 1e-8..1e2, 1000
+    samples each, FP32 vs FP64 with the stable and the standard forms, per
+    law; reports every 20th scale of the relative-error curves of P and dP."""
+    import math
+    from paper_2408_12479_gb300 import hx
+    from paper_2408_12479_gb300 import inputs as I
+    from paper_2408_12479_gb300 import stability
+    mats = {"cNH": dict(I.MAT_CNH), "iNH": dict(I.MAT_INH), "fiber": dict(I.MAT_FIBER)}
+    t0 = time.perf_counter()
+    out = {}
+    for law, mat in mats.items():
+        m = I.box_mesh(1, 1, name="point")
+        if law == "fiber":
+            m.frames = I.constant_frames(1)
+        G = hx.Mesh(m, mat, device=device)
+        res = stability.study(G, samples=1000)
+        G.close()
+        out[law] = {f: {"eps": [rec["eps"][i] for i in range(0, 200, 20)],
+                        "P": [rec["P"][i] for i in range(0, 200, 20)],
+                        "dP": [rec["dP"][i] for i in range(0, 200, 20)],
+                        "max_P_eps_le_1e-2": max(x for e, x in zip(rec["eps"], rec["P"]) if e <= 1e-2),
+                        "max_dP_eps_le_1e-2": max(x for e, x in zip(rec["eps"], rec["dP"]) if e <= 1e-2)}
+                    for f, rec in res.items()}
+        for f in out[law]:
+            for k in ("P", "dP"):
+                out[law][f][k] = [None if math.isnan(x) else float("%.3g" % x) for x in out[law][f][k]]
+    out["seconds"] = round(time.perf_counter() - t0, 2)
+    out["samples_per_scale"] = 1000
+    out["scales"] = 200
+    return out
+
+
+def run_newton(device, n=8, p=4, stretch=1.1, steps=5):
+    """Newton's method (Alg. 1) on uniaxial tension of an n^3 cube, p, cNH,
+    reached in load steps; FP32- and FP64-preconditioned CG updates."""
+    import torch
+    from paper_2408_12479_gb300 import hx
+    from paper_2408_12479_gb300 import inputs as I
+    res = {"workload": f"cNH uniaxial stretch {stretch} in {steps} load steps, {n}^3 cube, p={p}"}
+    for name, pp in (("fp32_precond", hx.HX_FP32), ("fp64_precond", hx.HX_FP64)):
+        m, _ = I.workload_uniaxial(n, p, 1.0)
+        G = hx.Mesh(m, dict(I.MAT_CNH), device=device)
+        X = G.node_coords()
+        inc = torch.zeros_like(X)
+        inc[:, 0] = (stretch - 1.0) / steps * X[:, 0]
+        u = torch.zeros(m.n_dofs, dtype=torch.float64, device=G.device)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its, cg = [], 0
+        for _ in range(steps):
+            u += inc.reshape(-1)
+            rep, st = hx.hx_newton_solve(G.ctx, G.handle, u, None, eps_abs=1e-12, eps_rel=1e-9, max_newton=15,
+                                         storage=hx.HX_SPATIAL_TENSORS, precond_prec=pp, cg_tol=1e-6,
+                                         cg_max_iter=20000)
+            its.append(rep["newton_iters"])
+            cg += rep["cg_iters"]
+        torch.cuda.synchronize()
+        res["n_dofs"] = m.n_dofs
+        res[name] = {"newton_iters_per_step": its, "cg_iters": cg, "seconds": round(time.perf_counter() - t0, 3),
+                     "final_res_rel": rep["res"] / max(rep["res0"], 1e-300), "status": hx.STATUS_NAMES.get(st, st)}
+        G.close()
+    return res
+
+
 def cpu_baseline(m, field, seed, p, mat_d, target_s=12.0):
     """The FP64 oracle's full-tensor apply on a bounded sample of the same mesh
     (leading elements), on all host cores; scaled to GDoF/s of the whole mesh."""
@@ -396,10 +461,12 @@ def main():
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")  # profilers can restrict capture to this range
         e0.record(s)
         for _ in range(args.steps):
             hx.hx_tangent_apply(G.ctx, G.handle, du, out)
         e1.record(s)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
     launches = hx.hx_launch_count(G.ctx)
     G.sync(60000)
@@ -454,6 +521,11 @@ def main():
     if rank == 0 and args.solve and not args.no_sweep:
         solve = run_solve(local, n=args.solve)
 
+    stab = newton = None
+    if rank == 0 and not args.no_sweep:
+        stab = run_stability(local)
+        newton = run_newton(local)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         m2, field, seed = I.workload_jittered_cube(p)
@@ -481,6 +553,8 @@ def main():
             "sweep": sweep,
             "batch": batch,
             "solve": solve,
+            "newton": newton,
+            "stability": stab,
         }
         print(json.dumps(line))
     if world > 1:
