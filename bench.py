@@ -241,6 +241,25 @@ def run_solve(device, n=48, p=4, tol=1e-8, max_iter=20000, degree=5, smoothing_r
         res[name] = {"iterations": it, "true_rel_residual": rel, "seconds": round(time.perf_counter() - t0, 3),
                      "status": hx.STATUS_NAMES.get(st, st)}
     res["speedup_fp32_precond"] = round(res["fp64_precond"]["seconds"] / res["fp32_precond"]["seconds"], 3)
+    # the same system with the p-multigrid V-cycle (degrees p, p/2, ..., 1) as preconditioner
+    mg = hx.Multigrid(G, smoother_degree=3, coarse_degree=20, coarse_range=200.0, precond_prec=hx.HX_FP32,
+                      storage=hx.HX_CACHE_TENSORS, lambda_iters=20)
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mg.setup(u)
+        t_setup = time.perf_counter() - t0
+        x = torch.zeros_like(u)
+        t0 = time.perf_counter()
+        it, rel, st = mg.cg_solve(rhs, x, tol, max_iter)
+        torch.cuda.synchronize()
+        res["mg_fp32_precond"] = {"levels": mg.levels(), "iterations": it, "true_rel_residual": rel,
+                                  "seconds": round(time.perf_counter() - t0, 3), "setup_seconds": round(t_setup, 3),
+                                  "status": hx.STATUS_NAMES.get(st, st)}
+    except hx.HxError as e:
+        res["mg_fp32_precond"] = {"status": str(e)[:160]}
+    finally:
+        mg.close()
     G.close()
     # the literal J ~ 0.9 state: CG must stop with a non-positive-curvature status
     m9, f9, _ = I.workload_compressed_cube(n=n, p=p, J_target=0.9, sine_amp=0.005)

@@ -300,6 +300,51 @@ typedef struct {
 hx_status hx_newton_solve(hx_mesh *mesh, double *u_dev, const double *f_ext_dev, const hx_newton_options *opt,
                           hx_newton_report *report);
 
+/* ---- p-multigrid preconditioner (Sec. 5) -------------------------------- */
+/* Levels of degree p, floor(p/2), ... down to min_degree, built on the mesh's structured box
+ * (same elements and geometry; the Dirichlet constraints must be whole faces,
+ * component by component, and are carried to every level; other meshes give
+ * HX_ERR_UNSUPPORTED). The V-cycle smooths with smoother_degree steps of
+ * Chebyshev-Jacobi on [lambda_max/smoothing_range, lambda_max] of D^-1 K per
+ * level (before and after the coarse correction), and applies coarse_degree
+ * steps of Chebyshev-Jacobi on [lambda_max/coarse_range, lambda_max] on the
+ * degree-1 level. Transfers: prolongation = interpolation of the coarser
+ * Lagrange function at the finer nodes, restriction = its transpose; the
+ * linearization point of a coarser level is the finer state evaluated at its
+ * nodes. All level operators are the matrix-free tangent in precond_prec with
+ * the `storage` strategy. The mesh must outlive the multigrid object. */
+typedef struct hx_mg hx_mg;
+typedef struct {
+    int32_t smoother_degree;
+    double smoothing_range;
+    int32_t coarse_degree;
+    double coarse_range;
+    int32_t precond_prec;
+    int32_t storage;
+    int32_t lambda_iters;     /* power iterations per level (x1.2 safety) */
+    int32_t min_degree;       /* coarsest degree (>= 1): levels stop once p/2 would fall below it */
+    double coarse_weight;     /* coarse corrections are added scaled by this weight (0 < w <= 1) */
+} hx_mg_options;
+hx_status hx_mg_create(hx_mesh *mesh, const hx_mg_options *opt, hx_mg **mg);
+void hx_mg_destroy(hx_mg *mg);
+/* Number of levels and their degrees (degrees may be NULL; at most 8). */
+hx_status hx_mg_info(const hx_mg *mg, int32_t *n_levels, int32_t *degrees);
+/* Per Newton state (Alg. 1): transfer u_dev (FP64) to every level, refresh the
+ * quadrature-point data (FP64 and precond_prec), the inverse diagonals and the
+ * eigenvalue bounds. Synchronous; reports J <= 0 as HX_ERR_NONINVERTIBLE. */
+hx_status hx_mg_setup(hx_mg *mg, const double *u_dev);
+/* x = one V-cycle applied to b (finest level, precond_prec vectors). */
+hx_status hx_mg_vcycle(hx_mg *mg, const void *b_dev, void *x_dev);
+/* Transfer between level `level` and level+1 in `prec`: dir 0 prolongation
+ * (src on level+1, dst on level), 1 restriction (src on level, dst on
+ * level+1, overwritten), 2 state transfer (src on level, dst on level+1). */
+hx_status hx_mg_transfer(hx_mg *mg, int32_t level, int32_t dir, const void *src_dev, void *dst_dev, int32_t prec);
+/* FP64 flexible CG on the finest tangent with one V-cycle as preconditioner
+ * (same stopping rule and statuses as hx_cg_solve); needs hx_mg_setup at the
+ * current state. */
+hx_status hx_mg_cg_solve(hx_mg *mg, const double *rhs_dev, double *x_dev, double tol, int32_t max_iter,
+                         int32_t use_graph, int32_t *iters, double *rel_residual);
+
 /* Fibre dispersion constants H11, H22, H33 from (a, b) (Sec. 3). Host only. */
 hx_status hx_fibre_dispersion(double a, double b, double H[3]);
 

@@ -467,3 +467,37 @@ def newton(M: OracleMesh, mat: Material, u0, f_ext=None, eps_abs=1e-10, eps_rel=
         r = res(u)
         norms.append(float(np.linalg.norm(r)))
     return u, norms
+
+
+def box_transfer_matrix(nx, ny, nz, pc, pf):
+    """Dense prolongation of the degree-pc Lagrange space into the degree-pf
+    space on a structured box of nx*ny*nz elements (per displacement
+    component): P[I, J] = value of the coarse global basis function J at fine
+    node I, evaluated in reference coordinates of an element containing the
+    node (the element map is shared by both spaces). Plain loops; small boxes."""
+    xc, xf = gll_points(pc), gll_points(pf)
+
+    def lag(xs, a, x):
+        v = 1.0
+        for b in range(len(xs)):
+            if b != a:
+                v *= (x - xs[b]) / (xs[a] - xs[b])
+        return v
+    Nf = [n * pf + 1 for n in (nx, ny, nz)]
+    Nc = [n * pc + 1 for n in (nx, ny, nz)]
+    P = np.zeros((Nf[0] * Nf[1] * Nf[2], Nc[0] * Nc[1] * Nc[2]))
+    for K in range(Nf[2]):
+        for J in range(Nf[1]):
+            for I in range(Nf[0]):
+                row = I + Nf[0] * (J + Nf[1] * K)
+                loc = []
+                for L, n in zip((I, J, K), (nx, ny, nz)):
+                    e = min(L // pf, n - 1)
+                    loc.append((e, L - e * pf))
+                for c in range(pc + 1):
+                    for b in range(pc + 1):
+                        for a in range(pc + 1):
+                            w = lag(xc, a, xf[loc[0][1]]) * lag(xc, b, xf[loc[1][1]]) * lag(xc, c, xf[loc[2][1]])
+                            col = (loc[0][0] * pc + a) + Nc[0] * ((loc[1][0] * pc + b) + Nc[1] * (loc[2][0] * pc + c))
+                            P[row, col] = w
+    return P

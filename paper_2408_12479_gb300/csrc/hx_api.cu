@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <functional>
 #include <cmath>
 #include <mutex>
 #include <string>
@@ -230,6 +231,11 @@ struct hx_mesh {
     void *w_stage_in = nullptr, *w_stage_out = nullptr;
     double *w_cg = nullptr;   // r z zold p Ap dinv (FP64)
     double *w_newton = nullptr;  // Newton: residual, update, inverse diagonal (FP64)
+    // host copies of the description (multigrid levels are rebuilt from them)
+    std::vector<double> h_geo_nodes, h_frames;
+    std::vector<int32_t> h_geo_conn;
+    std::vector<uint8_t> h_dirichlet;
+    hx_material h_mat{};
     float *w_cg32 = nullptr;  // r32 z32 dinv32
     cudaStream_t solve_stream = nullptr;
     hx::CgScalars *d_sc = nullptr;
@@ -445,6 +451,11 @@ hx_status hx_setup_mesh(hx_ctx *ctx, const hx_mesh_desc *d, const hx_material *m
     m->nz = d->nz;
     m->law = mat->law;
     m->mat = hx::MatParams{mat->mu, mat->lambda, mat->kappa, mat->k1, mat->k2};
+    m->h_mat = *mat;
+    m->h_geo_nodes.assign(d->geo_nodes, d->geo_nodes + 3 * d->n_geo_nodes);
+    m->h_geo_conn.assign(d->geo_conn, d->geo_conn + (size_t)d->n_elem * ngg);
+    if (d->fibre_frames && mat->law == HX_FIBER) m->h_frames.assign(d->fibre_frames, d->fibre_frames + 9 * (size_t)d->n_elem);
+    if (d->dirichlet) m->h_dirichlet.assign(d->dirichlet, d->dirichlet + 3 * d->n_nodes);
     auto bail = [&](hx_status st) {
         hx_destroy_mesh(m);
         return st;
@@ -917,18 +928,15 @@ static hx_status cg_precond(hx_mesh *m, int pp, int degree, double lmax, double 
     return HX_OK;
 }
 
-hx_status hx_cg_solve(hx_mesh *m, const double *rhs, double *x, double tol, int32_t max_iter, const hx_cg_options *opt,
-                      int32_t *iters, double *rel_residual) {
-    if (!m || !rhs || !x || !opt || max_iter < 0 || !(tol > 0.0) || bad_prec(opt->precond_prec) || opt->degree < 0 ||
-        (opt->degree > 0 && (!(opt->lambda_max > 0.0) || !(opt->smoothing_range > 1.0))))
-        return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_cg_solve: bad argument");
+// Flexible (Polak-Ribiere) CG in FP64 on the mesh's constrained tangent with
+// the preconditioner z = M r given by `prec_setup` (run once, on the solve
+// stream) and `precond` (r in FP64, and in FP32 in w_cg32 when r32_ready).
+typedef std::function<hx_status(const double *r, double *z, bool r32_ready)> PrecondFn;
+static hx_status cg_core(hx_mesh *m, const double *rhs, double *x, double tol, int32_t max_iter, int pp, int use_graph,
+                         const std::function<hx_status()> &prec_setup, const PrecondFn &precond, int32_t *iters,
+                         double *rel_residual) {
     hx_ctx *ctx = m->ctx;
-    if (!m->cache[HX_FP64].valid || !m->cache[opt->precond_prec].valid)
-        return fail(ctx, HX_ERR_NOT_READY, "hx_cg_solve: quadrature-point data missing (FP64 and preconditioner precision)");
     hx_status st = ensure_cg_ws(m);
-    if (st != HX_OK) return st;
-    const int pp = opt->precond_prec;
-    st = ensure_cheb_ws(m, pp);
     if (st != HX_OK) return st;
     if (!m->solve_stream) HX_CUDA(ctx, cudaStreamCreateWithFlags(&m->solve_stream, cudaStreamNonBlocking));
     // run the solve on a private (capturable) stream ordered after the caller's stream
@@ -952,18 +960,14 @@ hx_status hx_cg_solve(hx_mesh *m, const double *rhs, double *x, double tol, int3
     cudaStream_t s = ctx->stream;
 
     const int64_t n = 3 * m->n_nodes;
-    double *r = m->w_cg, *z = r + n, *zold = r + 2 * n, *p = r + 3 * n, *Ap = r + 4 * n, *dinv64 = r + 5 * n;
-    float *dinv32 = m->w_cg32 + 2 * n;
-    void *dinv = pp == HX_FP64 ? (void *)dinv64 : (void *)dinv32;
-    // Jacobi: inverse diagonal of the preconditioner's operator (its own precision)
-    st = hx_diagonal(m, dinv, pp);
+    double *r = m->w_cg, *z = r + n, *zold = r + 2 * n, *p = r + 3 * n, *Ap = r + 4 * n;
+    st = prec_setup();
     if (st != HX_OK) return st;
-    HX_CUDA(ctx, hx::invert(n, dinv, dinv, pp, s));
     // r = b - K x ; z = M r ; p = zold = z
     st = apply_dev(m, x, Ap, HX_FP64);
     if (st != HX_OK) return st;
     HX_CUDA(ctx, hx::sub(n, rhs, Ap, r, s));
-    st = cg_precond(m, pp, opt->degree, opt->lambda_max, opt->smoothing_range, r, z, dinv, false);
+    st = precond(r, z, false);
     if (st != HX_OK) return st;
     HX_CUDA(ctx, cudaMemcpyAsync(p, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     HX_CUDA(ctx, cudaMemcpyAsync(zold, z, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -991,7 +995,7 @@ hx_status hx_cg_solve(hx_mesh *m, const double *rhs, double *x, double tol, int3
         HX_CUDA(ctx, hx::dots(n, 1, p, Ap, nullptr, nullptr, nullptr, nullptr, m->d_partial, &m->d_sc->pAp, s));
         HX_CUDA(ctx, hx::cg_alpha(m->d_sc, s));
         HX_CUDA(ctx, hx::cg_xr(n, m->d_sc, p, Ap, x, r, pp == HX_FP32 ? m->w_cg32 : nullptr, s));
-        b = cg_precond(m, pp, opt->degree, opt->lambda_max, opt->smoothing_range, r, z, dinv, true);
+        b = precond(r, z, true);
         if (b != HX_OK) return b;
         HX_CUDA(ctx, hx::dots(n, 3, r, z, r, zold, r, r, m->d_partial, m->d_dots, s));
         HX_CUDA(ctx, hx::cg_beta(m->d_sc, m->d_dots, s));
@@ -1002,7 +1006,7 @@ hx_status hx_cg_solve(hx_mesh *m, const double *rhs, double *x, double tol, int3
     };
 
     cudaGraphExec_t exec = nullptr;
-    if (opt->use_graph) {
+    if (use_graph) {
         cudaGraph_t graph = nullptr;
         HX_CUDA(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         hx_status b = body();
@@ -1054,10 +1058,45 @@ hx_status hx_cg_solve(hx_mesh *m, const double *rhs, double *x, double tol, int3
     if (iters) *iters = it;
     if (rel_residual) *rel_residual = true_rel;
     if (bad || !(true_rel == true_rel))
-        return fail(ctx, HX_ERR_NAN, "hx_cg_solve: breakdown (NaN or non-positive curvature p.Kp <= 0) at iteration " +
+        return fail(ctx, HX_ERR_NAN, "CG breakdown (NaN or non-positive curvature p.Kp <= 0) at iteration " +
                                          std::to_string(it));
-    if (true_rel > tol) return fail(ctx, HX_ERR_NOT_CONVERGED, "hx_cg_solve: tolerance not reached");
+    if (true_rel > tol) return fail(ctx, HX_ERR_NOT_CONVERGED, "CG tolerance not reached");
     return HX_OK;
+}
+
+hx_status hx_cg_solve(hx_mesh *m, const double *rhs, double *x, double tol, int32_t max_iter, const hx_cg_options *opt,
+                      int32_t *iters, double *rel_residual) {
+    if (!m || !rhs || !x || !opt || max_iter < 0 || !(tol > 0.0) || bad_prec(opt->precond_prec) || opt->degree < 0 ||
+        (opt->degree > 0 && (!(opt->lambda_max > 0.0) || !(opt->smoothing_range > 1.0))))
+        return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_cg_solve: bad argument");
+    hx_ctx *ctx = m->ctx;
+    if (!m->cache[HX_FP64].valid || !m->cache[opt->precond_prec].valid)
+        return fail(ctx, HX_ERR_NOT_READY, "hx_cg_solve: quadrature-point data missing (FP64 and preconditioner precision)");
+    hx_status st = ensure_cg_ws(m);
+    if (st != HX_OK) return st;
+    const int pp = opt->precond_prec;
+    st = ensure_cheb_ws(m, pp);
+    if (st != HX_OK) return st;
+    const int64_t n = 3 * m->n_nodes;
+    double *dinv64 = m->w_cg + 5 * n;
+    float *dinv32 = m->w_cg32 + 2 * n;
+    void *dinv = pp == HX_FP64 ? (void *)dinv64 : (void *)dinv32;
+    // Jacobi: inverse diagonal of the preconditioner's operator (its own precision)
+    auto setup = [&]() -> hx_status {
+        hx_status s2 = hx_diagonal(m, dinv, pp);
+        if (s2 != HX_OK) return s2;
+        HX_CUDA(ctx, hx::invert(n, dinv, dinv, pp, ctx->stream));
+        return HX_OK;
+    };
+    auto pre = [&](const double *r, double *z, bool r32_ready) {
+        return cg_precond(m, pp, opt->degree, opt->lambda_max, opt->smoothing_range, r, z, dinv, r32_ready);
+    };
+    st = cg_core(m, rhs, x, tol, max_iter, pp, opt->use_graph, setup, pre, iters, rel_residual);
+    if (st != HX_OK) {
+        const std::string e = "hx_cg_solve: " + ctx->err;
+        ctx->err = e;
+    }
+    return st;
 }
 
 hx_status hx_measure_fma_peak(hx_ctx *ctx, int32_t prec, double *flops) {
@@ -1273,4 +1312,301 @@ hx_status hx_material_eval(hx_mesh *m, int32_t elem, int32_t form, int32_t prec,
     HX_CUDA(ctx, hx::prec_ops(m->p, prec)->material_eval(v, elem, form, n, G, H, S, P, dP, ctx->stream));
     ctx->launches += 1;
     return HX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// p-multigrid preconditioner (Sec. 5): degrees p, floor(p/2), ..., 1 on the
+// same structured box, Chebyshev-Jacobi smoothing on every level, Chebyshev
+// iterations on the coarsest, transfers by interpolation between the
+// Lagrange spaces (prolongation) and its transpose (restriction)
+// ---------------------------------------------------------------------------
+struct hx_mg {
+    hx_ctx *ctx = nullptr;
+    std::vector<hx_mesh *> lv;  // lv[0] = the caller's mesh (not owned)
+    std::vector<hx::InterpTab> down;  // lv[l] -> lv[l+1] state transfer: finer function at coarser nodes
+    std::vector<hx::InterpTab> up;    // lv[l+1] -> lv[l] prolongation: coarser function at finer nodes
+    std::vector<void *> b, x, t, dinv;  // per level, in the preconditioner's precision
+    std::vector<double *> dinv64;       // per level, FP64 inverse diagonal (spectral estimate)
+    std::vector<double *> u;  // linearization state per level (FP64), l >= 1
+    std::vector<double> lam;
+    hx_mg_options opt{};
+    bool ready = false;
+};
+
+static hx::InterpTab make_tab(int ps, int pd) {
+    hx::InterpTab t{};
+    t.ps = ps;
+    t.pd = pd;
+    const std::vector<double> xs = gll_points(ps), xd = gll_points(pd);
+    for (int a = 0; a <= pd; ++a)
+        for (int b = 0; b <= ps; ++b) {
+            const double v = lagrange(xs, b, xd[a]);
+            t.M[a][b] = std::fabs(v) < 1e-15 ? 0.0 : v;
+        }
+    return t;
+}
+
+void hx_mg_destroy(hx_mg *g) {
+    if (!g) return;
+    if (g->ctx) cudaStreamSynchronize(g->ctx->stream);
+    for (size_t l = 0; l < g->lv.size(); ++l) {
+        dfree(g->b[l]);
+        dfree(g->x[l]);
+        dfree(g->t[l]);
+        dfree(g->dinv[l]);
+        dfree(g->dinv64[l]);
+        if (l > 0) {
+            dfree(g->u[l]);
+            hx_destroy_mesh(g->lv[l]);
+        }
+    }
+    delete g;
+}
+
+hx_status hx_mg_create(hx_mesh *m, const hx_mg_options *opt, hx_mg **out) {
+    if (!m || !opt || !out || bad_prec(opt->precond_prec) || opt->smoother_degree < 1 || opt->coarse_degree < 1 ||
+        !(opt->smoothing_range > 1.0) || !(opt->coarse_range > 1.0) || opt->lambda_iters < 1 ||
+        opt->storage < HX_RECOMPUTE || opt->storage > HX_SPATIAL_TENSORS || opt->min_degree < 1 ||
+        !(opt->coarse_weight > 0.0) || opt->coarse_weight > 1.0)
+        return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_mg_create: bad argument");
+    hx_ctx *ctx = m->ctx;
+    if (!m->structured)
+        return fail(ctx, HX_ERR_UNSUPPORTED, "hx_mg_create: levels are built for structured boxes only");
+    const int nx = m->nx, ny = m->ny, nz = m->nz;
+    // the constraints must be whole faces, component by component
+    bool face[6][3] = {};
+    const int p = m->p;
+    const int64_t Nx = (int64_t)nx * p + 1, Ny = (int64_t)ny * p + 1, Nz = (int64_t)nz * p + 1;
+    auto on_face = [&](int f, int64_t I, int64_t J, int64_t K, int64_t NX, int64_t NY, int64_t NZ) {
+        return f == 0 ? I == 0 : f == 1 ? I == NX - 1 : f == 2 ? J == 0 : f == 3 ? J == NY - 1 : f == 4 ? K == 0 : K == NZ - 1;
+    };
+    const std::vector<uint8_t> &dm = m->h_dirichlet;
+    if (!dm.empty()) {
+        for (int f = 0; f < 6; ++f)
+            for (int c = 0; c < 3; ++c) {
+                bool all = true;
+                for (int64_t n = 0; n < Nx * Ny * Nz && all; ++n) {
+                    const int64_t I = n % Nx, J = (n / Nx) % Ny, K = n / (Nx * Ny);
+                    if (on_face(f, I, J, K, Nx, Ny, Nz) && !dm[3 * n + c]) all = false;
+                }
+                face[f][c] = all;
+            }
+        for (int64_t n = 0; n < Nx * Ny * Nz; ++n) {
+            const int64_t I = n % Nx, J = (n / Nx) % Ny, K = n / (Nx * Ny);
+            for (int c = 0; c < 3; ++c) {
+                bool want = false;
+                for (int f = 0; f < 6; ++f) want = want || (face[f][c] && on_face(f, I, J, K, Nx, Ny, Nz));
+                if (want != (dm[3 * n + c] != 0))
+                    return fail(ctx, HX_ERR_UNSUPPORTED, "hx_mg_create: constraints must cover whole faces per component");
+            }
+        }
+    }
+    hx_mg *g = new hx_mg();
+    g->ctx = ctx;
+    g->opt = *opt;
+    g->lv.push_back(m);
+    while (g->lv.back()->p / 2 >= opt->min_degree) {
+        const int pc = g->lv.back()->p / 2;
+        const int64_t Mx = (int64_t)nx * pc + 1, My = (int64_t)ny * pc + 1, Mz = (int64_t)nz * pc + 1;
+        std::vector<uint8_t> mask(3 * Mx * My * Mz, 0);
+        bool any = false;
+        for (int64_t n = 0; n < Mx * My * Mz; ++n) {
+            const int64_t I = n % Mx, J = (n / Mx) % My, K = n / (Mx * My);
+            for (int c = 0; c < 3; ++c)
+                for (int f = 0; f < 6; ++f)
+                    if (face[f][c] && on_face(f, I, J, K, Mx, My, Mz)) {
+                        mask[3 * n + c] = 1;
+                        any = true;
+                    }
+        }
+        hx_mesh_desc d{};
+        d.n_elem = m->n_elem;
+        d.p = pc;
+        d.geo_degree = m->g;
+        d.n_nodes = Mx * My * Mz;
+        d.geo_nodes = m->h_geo_nodes.data();
+        d.n_geo_nodes = m->n_geo;
+        d.geo_conn = m->h_geo_conn.data();
+        d.dof_conn = nullptr;
+        d.nx = nx;
+        d.ny = ny;
+        d.nz = nz;
+        d.dirichlet = any ? mask.data() : nullptr;
+        d.fibre_frames = m->h_frames.empty() ? nullptr : m->h_frames.data();
+        hx_mesh *c = nullptr;
+        hx_status st = hx_setup_mesh(ctx, &d, &m->h_mat, &c);
+        if (st != HX_OK) {
+            hx_mg_destroy(g);
+            return st;
+        }
+        g->lv.push_back(c);
+    }
+    const size_t L = g->lv.size();
+    const int pp = opt->precond_prec;
+    g->b.assign(L, nullptr);
+    g->x.assign(L, nullptr);
+    g->t.assign(L, nullptr);
+    g->dinv.assign(L, nullptr);
+    g->dinv64.assign(L, nullptr);
+    g->u.assign(L, nullptr);
+    g->lam.assign(L, 0.0);
+    for (size_t l = 0; l < L; ++l) {
+        const size_t n = 3 * (size_t)g->lv[l]->n_nodes;
+        const size_t bytes = n * prec_size(pp) + 64;
+        cudaError_t e = cudaSuccess;
+        if (e == cudaSuccess) e = cudaMalloc(&g->b[l], bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&g->x[l], bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&g->t[l], bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&g->dinv[l], bytes);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&g->dinv64[l], n * sizeof(double) + 64);
+        if (e == cudaSuccess && l > 0) e = cudaMalloc((void **)&g->u[l], n * sizeof(double) + 64);
+        if (e != cudaSuccess) {
+            hx_mg_destroy(g);
+            return cuda_fail(ctx, e, "hx_mg_create");
+        }
+        if (l + 1 < L) {
+            g->down.push_back(make_tab(g->lv[l]->p, g->lv[l + 1]->p));
+            g->up.push_back(make_tab(g->lv[l + 1]->p, g->lv[l]->p));
+        }
+    }
+    *out = g;
+    return HX_OK;
+}
+
+hx_status hx_mg_info(const hx_mg *g, int32_t *n_levels, int32_t *degrees) {
+    if (!g || !n_levels) return HX_ERR_ARG;
+    *n_levels = (int32_t)g->lv.size();
+    if (degrees)
+        for (size_t l = 0; l < g->lv.size(); ++l) degrees[l] = g->lv[l]->p;
+    return HX_OK;
+}
+
+hx_status hx_mg_setup(hx_mg *g, const double *u_dev) {
+    if (!g || !u_dev) return fail(g ? g->ctx : nullptr, HX_ERR_ARG, "hx_mg_setup: bad argument");
+    hx_ctx *ctx = g->ctx;
+    cudaStream_t s = ctx->stream;
+    const int pp = g->opt.precond_prec;
+    const size_t L = g->lv.size();
+    g->ready = false;
+    for (size_t l = 0; l < L; ++l) {
+        hx_mesh *lm = g->lv[l];
+        const double *ul = u_dev;
+        if (l > 0) {
+            // linearization point of the coarser level: the finer state at its nodes
+            const double *uf = l == 1 ? u_dev : g->u[l - 1];
+            HX_CUDA(ctx, hx::interp(g->down[l - 1], lm->nx, lm->ny, lm->nz, uf, g->u[l], 0, HX_FP64, s));
+            ul = g->u[l];
+            ctx->launches += 1;
+        }
+        hx_status st = hx_precompute_qp(lm, ul, HX_FP64, g->opt.storage);
+        if (st == HX_OK && pp != HX_FP64) st = hx_precompute_qp(lm, ul, pp, g->opt.storage);
+        if (st != HX_OK) return st;
+        // Jacobi and the spectral bound of D^-1 K (FP64), then D^-1 in the
+        // smoother's precision
+        double *d64 = g->dinv64[l];
+        st = hx_diagonal(lm, d64, HX_FP64);
+        if (st != HX_OK) return st;
+        const int64_t n = 3 * lm->n_nodes;
+        HX_CUDA(ctx, hx::invert(n, d64, d64, HX_FP64, s));
+        st = hx_estimate_lambda_max(lm, d64, g->opt.lambda_iters, 11 + l, &g->lam[l]);
+        if (st != HX_OK) return st;
+        g->lam[l] *= 1.2;
+        if (pp == HX_FP32)
+            HX_CUDA(ctx, hx::to_f32(n, d64, (float *)g->dinv[l], s));
+        else
+            HX_CUDA(ctx, cudaMemcpyAsync(g->dinv[l], d64, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        st = ensure_cheb_ws(lm, pp);
+        if (st != HX_OK) return st;
+    }
+    {
+        hx_status st = hx_sync(ctx, -1);  // J <= 0 met at a level's state
+        if (st != HX_OK) return st;
+    }
+    g->ready = true;
+    return HX_OK;
+}
+
+// one V-cycle on level l: x = V(b) (zero start), all vectors in pp precision
+static hx_status vcycle(hx_mg *g, size_t l, const void *b, void *x) {
+    hx_ctx *ctx = g->ctx;
+    cudaStream_t s = ctx->stream;
+    const int pp = g->opt.precond_prec;
+    hx_mesh *lm = g->lv[l];
+    const int64_t n = 3 * lm->n_nodes;
+    if (l + 1 == g->lv.size())
+        return cheb_run(lm, b, x, g->dinv[l], g->opt.coarse_degree, g->lam[l], g->opt.coarse_range, 1, pp);
+    hx_status st = cheb_run(lm, b, x, g->dinv[l], g->opt.smoother_degree, g->lam[l], g->opt.smoothing_range, 1, pp);
+    if (st != HX_OK) return st;
+    // t = b - K x, restricted to the coarser level
+    st = apply_dev(lm, x, g->t[l], pp);
+    if (st != HX_OK) return st;
+    HX_CUDA(ctx, hx::axpby_p(n, 1.0, b, -1.0, g->t[l], pp, s));
+    hx_mesh *cm = g->lv[l + 1];
+    const int64_t nc = 3 * cm->n_nodes;
+    HX_CUDA(ctx, cudaMemsetAsync(g->b[l + 1], 0, nc * prec_size(pp), s));
+    HX_CUDA(ctx, hx::interp_t(g->up[l], lm->nx, lm->ny, lm->nz, g->t[l], g->b[l + 1], pp, s));
+    if (cm->n_constrained) HX_CUDA(ctx, hx::set_idx(cm->d_cidx, cm->n_constrained, 0.0, g->b[l + 1], pp, s));
+    st = vcycle(g, l + 1, g->b[l + 1], g->x[l + 1]);
+    if (st != HX_OK) return st;
+    if (g->opt.coarse_weight != 1.0)
+        HX_CUDA(ctx, hx::axpby_p(3 * cm->n_nodes, g->opt.coarse_weight, g->x[l + 1], 0.0, g->x[l + 1], pp, s));
+    HX_CUDA(ctx, hx::interp(g->up[l], lm->nx, lm->ny, lm->nz, g->x[l + 1], x, 1, pp, s));
+    if (lm->n_constrained) HX_CUDA(ctx, hx::set_idx(lm->d_cidx, lm->n_constrained, 0.0, x, pp, s));
+    ctx->launches += 5;
+    return cheb_run(lm, b, x, g->dinv[l], g->opt.smoother_degree, g->lam[l], g->opt.smoothing_range, 0, pp);
+}
+
+hx_status hx_mg_vcycle(hx_mg *g, const void *b_dev, void *x_dev) {
+    if (!g || !b_dev || !x_dev) return fail(g ? g->ctx : nullptr, HX_ERR_ARG, "hx_mg_vcycle: bad argument");
+    if (!g->ready) return fail(g->ctx, HX_ERR_NOT_READY, "hx_mg_vcycle: call hx_mg_setup first");
+    return vcycle(g, 0, b_dev, x_dev);
+}
+
+hx_status hx_mg_transfer(hx_mg *g, int32_t level, int32_t dir, const void *src_dev, void *dst_dev, int32_t prec) {
+    if (!g || level < 0 || level + 1 >= (int32_t)g->lv.size() || dir < 0 || dir > 2 || bad_prec(prec) || !src_dev ||
+        !dst_dev)
+        return fail(g ? g->ctx : nullptr, HX_ERR_ARG, "hx_mg_transfer: bad argument");
+    hx_ctx *ctx = g->ctx;
+    hx_mesh *fm = g->lv[level];
+    cudaStream_t s = ctx->stream;
+    if (dir == 0) {  // prolongation: level+1 -> level
+        HX_CUDA(ctx, hx::interp(g->up[level], fm->nx, fm->ny, fm->nz, src_dev, dst_dev, 0, prec, s));
+    } else if (dir == 1) {  // restriction (transpose): level -> level+1
+        HX_CUDA(ctx, cudaMemsetAsync(dst_dev, 0, 3 * (size_t)g->lv[level + 1]->n_nodes * prec_size(prec), s));
+        HX_CUDA(ctx, hx::interp_t(g->up[level], fm->nx, fm->ny, fm->nz, src_dev, dst_dev, prec, s));
+    } else {  // state transfer: level -> level+1
+        HX_CUDA(ctx, hx::interp(g->down[level], fm->nx, fm->ny, fm->nz, src_dev, dst_dev, 0, prec, s));
+    }
+    ctx->launches += 1;
+    return HX_OK;
+}
+
+hx_status hx_mg_cg_solve(hx_mg *g, const double *rhs, double *x, double tol, int32_t max_iter, int32_t use_graph,
+                         int32_t *iters, double *rel_residual) {
+    if (!g || !rhs || !x || max_iter < 0 || !(tol > 0.0))
+        return fail(g ? g->ctx : nullptr, HX_ERR_ARG, "hx_mg_cg_solve: bad argument");
+    hx_ctx *ctx = g->ctx;
+    if (!g->ready) return fail(ctx, HX_ERR_NOT_READY, "hx_mg_cg_solve: call hx_mg_setup first");
+    hx_mesh *m = g->lv[0];
+    const int pp = g->opt.precond_prec;
+    hx_status st = ensure_cg_ws(m);
+    if (st != HX_OK) return st;
+    const int64_t n = 3 * m->n_nodes;
+    auto setup = []() -> hx_status { return HX_OK; };
+    auto pre = [&](const double *r, double *z, bool r32_ready) -> hx_status {
+        cudaStream_t s = ctx->stream;
+        if (pp == HX_FP32) {
+            float *r32 = m->w_cg32, *z32 = m->w_cg32 + n;
+            if (!r32_ready) HX_CUDA(ctx, hx::to_f32(n, r, r32, s));
+            hx_status s2 = vcycle(g, 0, r32, z32);
+            if (s2 != HX_OK) return s2;
+            HX_CUDA(ctx, hx::to_f64(n, z32, z, s));
+            ctx->launches += 2;
+            return HX_OK;
+        }
+        return vcycle(g, 0, r, z);
+    };
+    st = cg_core(m, rhs, x, tol, max_iter, pp, use_graph, setup, pre, iters, rel_residual);
+    if (st != HX_OK) ctx->err = "hx_mg_cg_solve: " + ctx->err;
+    return st;
 }

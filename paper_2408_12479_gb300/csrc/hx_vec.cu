@@ -312,4 +312,124 @@ cudaError_t fma_probe(int prec, int sm_count, double *flops) {
     return e;
 }
 
+
+// ---------------------------------------------------------------------------
+// precision-generic update and the transfers between degrees (multigrid)
+// ---------------------------------------------------------------------------
+namespace {
+template <typename T>
+__global__ void k_axpby_p(int64_t n, T a, const T *__restrict__ x, T b, T *__restrict__ y) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = b == T(0) ? a * x[i] : a * x[i] + b * y[i];
+}
+
+// destination node (I, J, K) -> its lowest-index element and local index
+__device__ __forceinline__ void canon(int I, int p, int ne, int &e, int &i) {
+    e = I / p;
+    if (e > ne - 1) e = ne - 1;
+    i = I - e * p;
+}
+
+template <typename T>
+__global__ void k_interp(InterpTab t, int nx, int ny, int nz, const T *__restrict__ src, T *__restrict__ dst,
+                         int add) {
+    const int Nxd = nx * t.pd + 1, Nyd = ny * t.pd + 1, Nzd = nz * t.pd + 1;
+    const int Nxs = nx * t.ps + 1, Nys = ny * t.ps + 1;
+    const int64_t total = (int64_t)Nxd * Nyd * Nzd;
+    const int ns = t.ps + 1;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int I = (int)(idx % Nxd), J = (int)((idx / Nxd) % Nyd), K = (int)(idx / ((int64_t)Nxd * Nyd));
+        int ex, ey, ez, i, j, k;
+        canon(I, t.pd, nx, ex, i);
+        canon(J, t.pd, ny, ey, j);
+        canon(K, t.pd, nz, ez, k);
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int c = 0; c < ns; ++c) {
+            const double wz = t.M[k][c];
+            if (wz == 0.0) continue;
+            for (int b = 0; b < ns; ++b) {
+                const double wyz = wz * t.M[j][b];
+                if (wyz == 0.0) continue;
+                for (int a = 0; a < ns; ++a) {
+                    const double w = wyz * t.M[i][a];
+                    if (w == 0.0) continue;
+                    const int64_t sn = (int64_t)(ex * t.ps + a) + Nxs * ((int64_t)(ey * t.ps + b) + (int64_t)Nys * (ez * t.ps + c));
+                    acc[0] += w * (double)src[3 * sn + 0];
+                    acc[1] += w * (double)src[3 * sn + 1];
+                    acc[2] += w * (double)src[3 * sn + 2];
+                }
+            }
+        }
+        for (int q = 0; q < 3; ++q) dst[3 * idx + q] = add ? dst[3 * idx + q] + (T)acc[q] : (T)acc[q];
+    }
+}
+
+template <typename T>
+__global__ void k_interp_t(InterpTab t, int nx, int ny, int nz, const T *__restrict__ fine, T *__restrict__ coarse) {
+    const int Nxd = nx * t.pd + 1, Nyd = ny * t.pd + 1, Nzd = nz * t.pd + 1;
+    const int Nxs = nx * t.ps + 1, Nys = ny * t.ps + 1;
+    const int64_t total = (int64_t)Nxd * Nyd * Nzd;
+    const int ns = t.ps + 1;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int I = (int)(idx % Nxd), J = (int)((idx / Nxd) % Nyd), K = (int)(idx / ((int64_t)Nxd * Nyd));
+        int ex, ey, ez, i, j, k;
+        canon(I, t.pd, nx, ex, i);
+        canon(J, t.pd, ny, ey, j);
+        canon(K, t.pd, nz, ez, k);
+        const T r0 = fine[3 * idx + 0], r1 = fine[3 * idx + 1], r2 = fine[3 * idx + 2];
+        for (int c = 0; c < ns; ++c) {
+            const double wz = t.M[k][c];
+            if (wz == 0.0) continue;
+            for (int b = 0; b < ns; ++b) {
+                const double wyz = wz * t.M[j][b];
+                if (wyz == 0.0) continue;
+                for (int a = 0; a < ns; ++a) {
+                    const T w = (T)(wyz * t.M[i][a]);
+                    if (w == T(0)) continue;
+                    const int64_t sn = (int64_t)(ex * t.ps + a) + Nxs * ((int64_t)(ey * t.ps + b) + (int64_t)Nys * (ez * t.ps + c));
+                    atomicAdd(coarse + 3 * sn + 0, w * r0);
+                    atomicAdd(coarse + 3 * sn + 1, w * r1);
+                    atomicAdd(coarse + 3 * sn + 2, w * r2);
+                }
+            }
+        }
+    }
+}
+
+int grid_for_nodes(int64_t n) {
+    const int64_t g = (n + 255) / 256;
+    return (int)(g < 8192 ? (g > 0 ? g : 1) : 8192);
+}
+}  // namespace
+
+cudaError_t axpby_p(int64_t n, double a, const void *x, double b, void *y, int prec, cudaStream_t s) {
+    if (prec == HX_FP32)
+        k_axpby_p<float><<<grid_for(n), VB, 0, s>>>(n, (float)a, (const float *)x, (float)b, (float *)y);
+    else
+        k_axpby_p<double><<<grid_for(n), VB, 0, s>>>(n, a, (const double *)x, b, (double *)y);
+    return cudaGetLastError();
+}
+
+cudaError_t interp(const InterpTab &t, int nx, int ny, int nz, const void *src, void *dst, int add, int prec,
+                   cudaStream_t s) {
+    const int64_t n = (int64_t)(nx * t.pd + 1) * (ny * t.pd + 1) * (nz * t.pd + 1);
+    if (prec == HX_FP32)
+        k_interp<float><<<grid_for_nodes(n), 256, 0, s>>>(t, nx, ny, nz, (const float *)src, (float *)dst, add);
+    else
+        k_interp<double><<<grid_for_nodes(n), 256, 0, s>>>(t, nx, ny, nz, (const double *)src, (double *)dst, add);
+    return cudaGetLastError();
+}
+
+cudaError_t interp_t(const InterpTab &t, int nx, int ny, int nz, const void *fine, void *coarse, int prec,
+                     cudaStream_t s) {
+    const int64_t n = (int64_t)(nx * t.pd + 1) * (ny * t.pd + 1) * (nz * t.pd + 1);
+    if (prec == HX_FP32)
+        k_interp_t<float><<<grid_for_nodes(n), 256, 0, s>>>(t, nx, ny, nz, (const float *)fine, (float *)coarse);
+    else
+        k_interp_t<double><<<grid_for_nodes(n), 256, 0, s>>>(t, nx, ny, nz, (const double *)fine, (double *)coarse);
+    return cudaGetLastError();
+}
+
 }  // namespace hx

@@ -36,6 +36,24 @@ cudaError_t normalize(int64_t n, const double *nrm2, const double *x, double *y,
 cudaError_t scale(int64_t n, const double *dinv, const double *x, double *y, cudaStream_t s);
 cudaError_t invert(int64_t n, const void *x, void *y, int prec, cudaStream_t s);
 cudaError_t random_vec(int64_t n, uint64_t seed, double *y, cudaStream_t s);
+// y = a x + b y in precision prec (b == 0: y = a x)
+cudaError_t axpby_p(int64_t n, double a, const void *x, double b, void *y, int prec, cudaStream_t s);
+
+// Transfer between two Lagrange spaces on the same structured box of
+// nx*ny*nz elements (degrees ps and pd). M[a_d][a_s] = l^s_{a_s}(xi^d_{a_d}),
+// the source's 1D basis at the destination's 1D nodes. interp: every
+// destination node takes the source function's value there, evaluated in its
+// lowest-index element (exact for a continuous source; add != 0 adds it).
+// interp_t: the transpose, dst_src += M^T src_dst, through atomic adds (dst
+// zeroed by the caller).
+struct InterpTab {
+    int ps, pd;
+    double M[7][7];
+};
+cudaError_t interp(const InterpTab &t, int nx, int ny, int nz, const void *src, void *dst, int add, int prec,
+                   cudaStream_t s);
+cudaError_t interp_t(const InterpTab &t, int nx, int ny, int nz, const void *src_fine, void *dst_coarse, int prec,
+                     cudaStream_t s);
 cudaError_t fma_probe(int prec, int sm_count, double *flops);
 
 }  // namespace hx

@@ -33,7 +33,8 @@ STORAGE_NAMES = {HX_RECOMPUTE: "recompute", HX_CACHE_F: "cache_F", HX_CACHE_TENS
 EXPORTS = ["hx_create", "hx_destroy", "hx_set_stream", "hx_last_error", "hx_sync", "hx_setup_mesh",
            "hx_destroy_mesh", "hx_mesh_info", "hx_node_coords", "hx_apply_bytes", "hx_precompute_qp",
            "hx_residual", "hx_tangent_apply", "hx_tangent_apply_host", "hx_diagonal", "hx_chebyshev_smooth",
-           "hx_estimate_lambda_max", "hx_cg_solve", "hx_body_force", "hx_newton_solve", "hx_material_eval", "hx_fibre_dispersion", "hx_batch_create",
+           "hx_estimate_lambda_max", "hx_cg_solve", "hx_body_force", "hx_newton_solve", "hx_material_eval", "hx_mg_create",
+           "hx_mg_destroy", "hx_mg_info", "hx_mg_setup", "hx_mg_vcycle", "hx_mg_transfer", "hx_mg_cg_solve", "hx_fibre_dispersion", "hx_batch_create",
            "hx_batch_destroy", "hx_batch_tangent_apply", "hx_measure_fma_peak", "hx_launch_count",
            "hx_autotune", "hx_set_apply_variant", "hx_chebyshev_smooth_noalloc"]
 
@@ -66,6 +67,12 @@ class hx_newton_options(C.Structure):
                 ("storage", C.c_int32), ("cg_degree", C.c_int32), ("smoothing_range", C.c_double),
                 ("precond_prec", C.c_int32), ("cg_tol", C.c_double), ("cg_max_iter", C.c_int32),
                 ("lambda_iters", C.c_int32)]
+
+
+class hx_mg_options(C.Structure):
+    _fields_ = [("smoother_degree", C.c_int32), ("smoothing_range", C.c_double), ("coarse_degree", C.c_int32),
+                ("coarse_range", C.c_double), ("precond_prec", C.c_int32), ("storage", C.c_int32),
+                ("lambda_iters", C.c_int32), ("min_degree", C.c_int32), ("coarse_weight", C.c_double)]
 
 
 class hx_newton_report(C.Structure):
@@ -108,6 +115,13 @@ def lib():
             "hx_cg_solve": (I32, [P, P, P, D, I32, C.POINTER(hx_cg_options), C.POINTER(I32), C.POINTER(D)]),
             "hx_body_force": (I32, [P, C.POINTER(D), P]),
             "hx_material_eval": (I32, [P, I32, I32, I32, C.c_int64, P, P, P, P, P]),
+            "hx_mg_create": (I32, [P, C.POINTER(hx_mg_options), C.POINTER(P)]),
+            "hx_mg_destroy": (None, [P]),
+            "hx_mg_info": (I32, [P, C.POINTER(I32), C.POINTER(I32)]),
+            "hx_mg_setup": (I32, [P, P]),
+            "hx_mg_vcycle": (I32, [P, P, P]),
+            "hx_mg_transfer": (I32, [P, I32, I32, P, P, I32]),
+            "hx_mg_cg_solve": (I32, [P, P, P, D, I32, I32, C.POINTER(I32), C.POINTER(D)]),
             "hx_newton_solve": (I32, [P, P, P, C.POINTER(hx_newton_options), C.POINTER(hx_newton_report)]),
             "hx_fibre_dispersion": (I32, [D, D, C.POINTER(D)]),
             "hx_batch_create": (I32, [P, C.POINTER(P), I32, C.POINTER(P)]),
@@ -312,6 +326,51 @@ def hx_material_eval(ctx, mesh, G, H, prec, form=0, elem=0):
     _check(lib().hx_material_eval(mesh, int(elem), int(form), int(prec), int(n), _ptr(G), _ptr(H), _ptr(S), _ptr(P),
                                   _ptr(dP)), ctx)
     return S.reshape(n, 3, 3), P.reshape(n, 3, 3), dP.reshape(n, 3, 3)
+
+
+class Multigrid:
+    """p-multigrid preconditioner on a structured-box Mesh (hx_mg_*)."""
+
+    def __init__(self, mesh, smoother_degree=3, smoothing_range=15.0, coarse_degree=20, coarse_range=200.0,
+                 precond_prec=HX_FP32, storage=HX_CACHE_TENSORS, lambda_iters=20, min_degree=1, coarse_weight=1.0):
+        self.mesh = mesh
+        opt = hx_mg_options(int(smoother_degree), float(smoothing_range), int(coarse_degree), float(coarse_range),
+                            int(precond_prec), int(storage), int(lambda_iters), int(min_degree),
+                            float(coarse_weight))
+        h = C.c_void_p()
+        _check(lib().hx_mg_create(mesh.handle, C.byref(opt), C.byref(h)), mesh.ctx)
+        self.handle = h
+        self.prec = precond_prec
+
+    def levels(self):
+        n = C.c_int32()
+        d = (C.c_int32 * 8)()
+        _check(lib().hx_mg_info(self.handle, C.byref(n), d), self.mesh.ctx)
+        return [d[i] for i in range(n.value)]
+
+    def setup(self, u):
+        _check(lib().hx_mg_setup(self.handle, _ptr(u)), self.mesh.ctx)
+
+    def vcycle(self, b, x):
+        _check(lib().hx_mg_vcycle(self.handle, _ptr(b), _ptr(x)), self.mesh.ctx)
+
+    def transfer(self, level, direction, src, dst):
+        _check(lib().hx_mg_transfer(self.handle, int(level), int(direction), _ptr(src), _ptr(dst), _prec_of(src)),
+               self.mesh.ctx)
+
+    def cg_solve(self, rhs, x, tol, max_iter, use_graph=True):
+        it = C.c_int32()
+        rel = C.c_double()
+        st = lib().hx_mg_cg_solve(self.handle, _ptr(rhs), _ptr(x), float(tol), int(max_iter), int(use_graph),
+                                  C.byref(it), C.byref(rel))
+        if st not in (HX_OK, HX_ERR_NOT_CONVERGED):
+            _check(st, self.mesh.ctx)
+        return it.value, rel.value, st
+
+    def close(self):
+        if self.handle:
+            lib().hx_mg_destroy(self.handle)
+            self.handle = None
 
 
 def hx_body_force(ctx, mesh, b, f):

@@ -473,3 +473,25 @@ def test_newton_uniaxial_matches_homogeneous_closed_form(law, mat):
     X = O.node_coords(M).reshape(-1, 3)
     exact = X * (np.array([l1, l2, l2]) - 1.0)
     assert np.abs(u.reshape(-1, 3) - exact).max() < 1e-10
+
+
+@pytest.mark.parametrize("pc,pf", [(1, 2), (2, 4), (3, 6), (2, 5)])
+def test_transfer_matrix_reproduces_coarse_polynomials(pc, pf):
+    """Prolongation is exact on the coarse space: a tensor polynomial of
+    degree pc per coordinate sampled at the coarse nodes maps to its samples
+    at the fine nodes (unit box, reference = physical up to scaling)."""
+    nx, ny, nz = 2, 1, 2
+    P = O.box_transfer_matrix(nx, ny, nz, pc, pf)
+
+    def lattice(p):
+        x = np.concatenate([[0.0], *[(e + O.gll_points(p)[1:]) / nx for e in range(nx)]])
+        y = np.concatenate([[0.0], *[(e + O.gll_points(p)[1:]) / ny for e in range(ny)]])
+        z = np.concatenate([[0.0], *[(e + O.gll_points(p)[1:]) / nz for e in range(nz)]])
+        Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+        return X.ravel(), Y.ravel(), Z.ravel()
+    f = lambda X, Y, Z: (1 + X ** pc - 0.5 * X) * (0.3 + Y ** pc) * (Z ** pc - 2 * Z + 0.7)
+    vc = f(*lattice(pc))
+    vf = f(*lattice(pf))
+    assert np.abs(P @ vc - vf).max() < 1e-12
+    # rows sum to one (partition of unity)
+    assert np.abs(P.sum(axis=1) - 1.0).max() < 1e-13
