@@ -319,9 +319,10 @@ def run_newton(device, n=8, p=4, stretch=1.1, steps=5):
     from paper_2408_12479_gb300 import hx
     from paper_2408_12479_gb300 import inputs as I
     res = {"workload": f"cNH uniaxial stretch {stretch} in {steps} load steps, {n}^3 cube, p={p}"}
-    for name, pp in (("fp32_precond", hx.HX_FP32), ("fp64_precond", hx.HX_FP64)):
+    for name, pp in (("fp32_precond", hx.HX_FP32), ("fp64_precond", hx.HX_FP64), ("mg_fp32_precond", hx.HX_FP32)):
         m, _ = I.workload_uniaxial(n, p, 1.0)
         G = hx.Mesh(m, dict(I.MAT_CNH), device=device)
+        mg = hx.Multigrid(G, precond_prec=hx.HX_FP32, storage=hx.HX_SPATIAL_TENSORS) if name.startswith("mg") else None
         X = G.node_coords()
         inc = torch.zeros_like(X)
         inc[:, 0] = (stretch - 1.0) / steps * X[:, 0]
@@ -333,13 +334,16 @@ def run_newton(device, n=8, p=4, stretch=1.1, steps=5):
             u += inc.reshape(-1)
             rep, st = hx.hx_newton_solve(G.ctx, G.handle, u, None, eps_abs=1e-12, eps_rel=1e-9, max_newton=15,
                                          storage=hx.HX_SPATIAL_TENSORS, precond_prec=pp, cg_tol=1e-6,
-                                         cg_max_iter=20000)
+                                         cg_max_iter=20000, mg=mg)
             its.append(rep["newton_iters"])
             cg += rep["cg_iters"]
         torch.cuda.synchronize()
         res["n_dofs"] = m.n_dofs
         res[name] = {"newton_iters_per_step": its, "cg_iters": cg, "seconds": round(time.perf_counter() - t0, 3),
                      "final_res_rel": rep["res"] / max(rep["res0"], 1e-300), "status": hx.STATUS_NAMES.get(st, st)}
+        if mg is not None:
+            res[name]["levels"] = mg.levels()
+            mg.close()
         G.close()
     return res
 

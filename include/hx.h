@@ -280,6 +280,7 @@ hx_status hx_body_force(hx_mesh *mesh, const double b[3], double *f_dev);
  * u (inexact Newton); a CG breakdown returns its status. Returns
  * HX_ERR_NOT_CONVERGED if the tolerances are not met within max_newton steps.
  * Synchronous. */
+typedef struct hx_mg hx_mg;
 typedef struct {
     double eps_abs, eps_rel;
     int32_t max_newton;
@@ -290,6 +291,11 @@ typedef struct {
     double cg_tol;           /* relative tolerance of each linear solve */
     int32_t cg_max_iter;
     int32_t lambda_iters;
+    hx_mg *mg;               /* non-NULL: the linear solves use hx_mg_cg_solve with this
+                                p-multigrid (built on the same mesh), refreshed by
+                                hx_mg_setup at every Newton step; cg_degree,
+                                smoothing_range, precond_prec and lambda_iters are then
+                                taken from the multigrid's own options */
 } hx_newton_options;
 typedef struct {
     int32_t newton_iters;    /* Newton updates performed */
@@ -313,7 +319,6 @@ hx_status hx_newton_solve(hx_mesh *mesh, double *u_dev, const double *f_ext_dev,
  * linearization point of a coarser level is the finer state evaluated at its
  * nodes. All level operators are the matrix-free tangent in precond_prec with
  * the `storage` strategy. The mesh must outlive the multigrid object. */
-typedef struct hx_mg hx_mg;
 typedef struct {
     int32_t smoother_degree;
     double smoothing_range;

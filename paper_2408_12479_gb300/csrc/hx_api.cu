@@ -1263,6 +1263,23 @@ hx_status hx_newton_solve(hx_mesh *m, double *u, const double *f_ext, const hx_n
     int k = 0, cg_total = 0;
     hx_status lin = HX_OK;
     while (res > o->eps_abs && res > o->eps_rel * res0 && k < o->max_newton) {
+        if (o->mg) {  // p-multigrid preconditioned update
+            st = hx_precompute_qp(m, u, HX_FP64, o->storage);
+            if (st == HX_OK) st = hx_mg_setup(o->mg, u);
+            if (st != HX_OK) return st;
+            HX_CUDA(ctx, hx::axpby(n, -1.0, r, 0.0, r, ctx->stream));
+            HX_CUDA(ctx, cudaMemsetAsync(du, 0, n * sizeof(double), ctx->stream));
+            int32_t it = 0;
+            double rel = 0.0;
+            lin = hx_mg_cg_solve(o->mg, r, du, o->cg_tol, o->cg_max_iter, 1, &it, &rel);
+            if (lin != HX_OK && lin != HX_ERR_NOT_CONVERGED) return lin;
+            cg_total += it;
+            HX_CUDA(ctx, hx::axpby(n, 1.0, du, 1.0, u, ctx->stream));
+            ++k;
+            st = residual_norm(&res);
+            if (st != HX_OK) return st;
+            continue;
+        }
         // update quadrature point data at u_k (both precisions the solve uses)
         st = hx_precompute_qp(m, u, HX_FP64, o->storage);
         if (st == HX_OK && pp != HX_FP64) st = hx_precompute_qp(m, u, pp, o->storage);

@@ -66,7 +66,7 @@ class hx_newton_options(C.Structure):
     _fields_ = [("eps_abs", C.c_double), ("eps_rel", C.c_double), ("max_newton", C.c_int32),
                 ("storage", C.c_int32), ("cg_degree", C.c_int32), ("smoothing_range", C.c_double),
                 ("precond_prec", C.c_int32), ("cg_tol", C.c_double), ("cg_max_iter", C.c_int32),
-                ("lambda_iters", C.c_int32)]
+                ("lambda_iters", C.c_int32), ("mg", C.c_void_p)]
 
 
 class hx_mg_options(C.Structure):
@@ -380,12 +380,13 @@ def hx_body_force(ctx, mesh, b, f):
 
 def hx_newton_solve(ctx, mesh, u, f_ext=None, eps_abs=1e-10, eps_rel=1e-8, max_newton=20, storage=HX_CACHE_TENSORS,
                     cg_degree=5, smoothing_range=15.0, precond_prec=HX_FP32, cg_tol=1e-6, cg_max_iter=5000,
-                    lambda_iters=30):
+                    lambda_iters=30, mg=None):
     """Newton's method (Alg. 1); returns (report dict, status). u is updated in
-    place; HX_ERR_NOT_CONVERGED is returned, not raised."""
+    place; HX_ERR_NOT_CONVERGED is returned, not raised. mg: a Multigrid on the
+    same mesh to precondition the linear solves."""
     opt = hx_newton_options(float(eps_abs), float(eps_rel), int(max_newton), int(storage), int(cg_degree),
                             float(smoothing_range), int(precond_prec), float(cg_tol), int(cg_max_iter),
-                            int(lambda_iters))
+                            int(lambda_iters), mg.handle if mg is not None else None)
     rep = hx_newton_report()
     st = lib().hx_newton_solve(mesh, _ptr(u), _ptr(f_ext) if f_ext is not None else None, C.byref(opt),
                                C.byref(rep))

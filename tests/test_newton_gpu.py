@@ -111,3 +111,31 @@ def test_newton_reports_iteration_limit():
         assert rep["res"] < rep["res0"]
     finally:
         G.close()
+
+
+@pytest.mark.parametrize("law", ["cNH", "iNH"])
+def test_newton_with_multigrid_matches_closed_form(law):
+    """The same load-stepped uniaxial problem with p-multigrid-preconditioned
+    linear solves."""
+    l1, steps = 1.2, 10
+    m, _ = I.workload_uniaxial(2, 4, 1.0)
+    mat = dict(cases.MATS[law])
+    G = hx.Mesh(m, mat)
+    mg = hx.Multigrid(G, precond_prec=hx.HX_FP32)
+    try:
+        assert mg.levels() == [4, 2, 1]
+        X = G.node_coords().cpu().numpy().reshape(-1, 3)
+        inc = np.zeros_like(X)
+        inc[:, 0] = (l1 - 1.0) / steps * X[:, 0]
+        u = torch.zeros(m.n_dofs, dtype=torch.float64, device="cuda")
+        for _ in range(steps):
+            u += cuda(inc.ravel())
+            rep, st = hx.hx_newton_solve(G.ctx, G.handle, u, None, eps_abs=1e-11, eps_rel=1e-12, max_newton=15,
+                                         storage=hx.HX_CACHE_TENSORS, cg_tol=1e-11, cg_max_iter=2000, mg=mg)
+            assert st == hx.HX_OK and rep["converged"] and rep["newton_iters"] <= 8, rep
+        l2 = _lateral_stretch(law, mat, l1)
+        exact = X * (np.array([l1, l2, l2]) - 1.0)
+        assert np.abs(u.cpu().numpy().reshape(-1, 3) - exact).max() < 1e-9, rep
+    finally:
+        mg.close()
+        G.close()
