@@ -49,6 +49,72 @@ enum { TB = 0, TD = 1, TG = 2 };
 // threads per CTA of the column-layout apply: n^2 threads per element
 __host__ __device__ constexpr int col_threads(int epb) { return (epb * NN + 31) / 32 * 32; }
 
+// Row-swizzled cubes of the staged FP32 apply at n = 5: every element owns a
+// whole warp (25 of 32 lanes active) and the x-row (j, k) of a cube starts at
+// word RS5[j][k] of its component block. The starts are distinct modulo 32
+// and, along any j or any k, at least five banks apart, so the x-, y- and
+// z-line sweeps (25 lanes, one word each) are free of bank conflicts; rows
+// are packed into 154 words per component.
+constexpr bool ROWSW = N == 5 && sizeof(Real) == 4;
+__constant__ int cRS5[5][5] = {{122, 72, 127, 149, 45},
+                               {39, 56, 12, 34, 50},
+                               {116, 67, 89, 111, 94},
+                               {1, 17, 6, 28, 23},
+                               {78, 61, 83, 105, 100}};
+template <bool SW>
+struct Lay {
+    static constexpr int CZ = SW ? 154 : CCZ;        // component stride (words)
+    static constexpr int ES = SW ? 3 * 154 : CES;    // element stride (words)
+};
+// threads per CTA of the apply for a tile of epb elements
+template <bool SW>
+__host__ __device__ constexpr int apply_threads(int epb) {
+    return SW ? epb * 32 : col_threads(epb);
+}
+// element, line coordinates and activity of thread t
+template <bool SW>
+__device__ __forceinline__ void thread_map(int t, int epb, int &el, int &a0, int &a1, bool &act) {
+    int a;
+    if constexpr (SW) {
+        el = t >> 5;
+        a = t & 31;
+        act = a < NN && el < epb;
+    } else {
+        el = t / NN;
+        a = t - el * NN;
+        act = el < epb;
+    }
+    a0 = a % N;
+    a1 = a / N;
+}
+// element-local word offsets of a thread's lines (component 0): x-line start,
+// y-line points j and z-line points k
+template <bool SW>
+struct LineOffs {
+    int x, y[N], z[N];
+};
+template <bool SW>
+__device__ __forceinline__ LineOffs<SW> line_offsets(int a0, int a1) {
+    LineOffs<SW> o;
+    if constexpr (SW) {
+        const int b0 = a0 < N ? a0 : 0, b1 = a1 < N ? a1 : 0;
+        o.x = cRS5[b0][b1];
+#pragma unroll
+        for (int t = 0; t < N; ++t) {
+            o.y[t] = cRS5[t][b1] + b0;
+            o.z[t] = cRS5[b1][t] + b0;
+        }
+    } else {
+        o.x = a0 * CRS + a1 * CPS;
+#pragma unroll
+        for (int t = 0; t < N; ++t) {
+            o.y[t] = a0 + t * CRS + a1 * CPS;
+            o.z[t] = a0 + a1 * CRS + t * CPS;
+        }
+    }
+    return o;
+}
+
 // threads per CTA for a tile of epb elements: one thread per sweep line
 __host__ __device__ constexpr int threads_for(int epb) {
     return (3 * epb * NN + 31) / 32 * 32 < 64 ? 64 : ((3 * epb * NN + 31) / 32 * 32 > 1024 ? 1024 : (3 * epb * NN + 31) / 32 * 32);
@@ -1002,13 +1068,14 @@ __device__ __forceinline__ void col_forward(const Real *row, Real *X0, Real *X1,
 // quadrature points, (qx, qy) = (a0, a1)) stays in registers gz[c][k], the
 // x-derivative goes to X0 and the y-derivative to X2 (X1 keeps the values).
 // No final barrier (the caller's barrier completes the sweeps).
+template <bool SW>
 __device__ __forceinline__ void col_forward_c(const Real *row, Real *X0, Real *X1, Real *X2, Real (*gz)[N], bool act,
-                                              int eoff, int a0, int a1) {
+                                              int eoff, const LineOffs<SW> &o) {
     // each phase loads all three components' lines before any store: the
     // cubes share one allocation, so the compiler may not move a load above
     // a store itself
+    constexpr int CZ = Lay<SW>::CZ;
     Real x[3][N], y[3][N];
-    const int o0 = eoff + line_off<0>(a0, a1), o1 = eoff + line_off<1>(a0, a1), o2 = eoff + line_off<2>(a0, a1);
     if (act) {  // x-lines: X0 = Bx u
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -1017,36 +1084,48 @@ __device__ __forceinline__ void col_forward_c(const Real *row, Real *X0, Real *X
             mv<TB, false>(x[c], y[c]);
         }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) st_line<0>(X0 + c * CCZ + o0, y[c]);
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int i = 0; i < N; ++i) X0[eoff + c * CZ + o.x + i] = y[c][i];
     }
     __syncthreads();
     if (act) {  // y-lines: X1 = By X0
 #pragma unroll
-        for (int c = 0; c < 3; ++c) ld_line<1>(X0 + c * CCZ + o1, x[c]);
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) x[c][t] = X0[eoff + c * CZ + o.y[t]];
 #pragma unroll
         for (int c = 0; c < 3; ++c) mv<TB, false>(x[c], y[c]);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) st_line<1>(X1 + c * CCZ + o1, y[c]);
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) X1[eoff + c * CZ + o.y[t]] = y[c][t];
     }
     __syncthreads();
     if (act) {  // z-lines: values V = Bz X1 (in place, per line), Dz V kept
 #pragma unroll
-        for (int c = 0; c < 3; ++c) ld_line<2>(X1 + c * CCZ + o2, x[c]);
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) x[c][t] = X1[eoff + c * CZ + o.z[t]];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             mv<TB, false>(x[c], y[c]);
             mv<TD, false>(y[c], gz[c]);
         }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) st_line<2>(X1 + c * CCZ + o2, y[c]);
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) X1[eoff + c * CZ + o.z[t]] = y[c][t];
     }
     __syncthreads();
     if (act) {  // x-lines: X0 = Dx V; y-lines: X2 = Dy V
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            ld_line<0>(X1 + c * CCZ + o0, x[c]);
-            ld_line<1>(X1 + c * CCZ + o1, y[c]);
-        }
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) {
+                x[c][t] = X1[eoff + c * CZ + o.x + t];
+                y[c][t] = X1[eoff + c * CZ + o.y[t]];
+            }
         Real dx[3][N], dy[3][N];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -1054,10 +1133,12 @@ __device__ __forceinline__ void col_forward_c(const Real *row, Real *X0, Real *X
             mv<TD, false>(y[c], dy[c]);
         }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            st_line<0>(X0 + c * CCZ + o0, dx[c]);
-            st_line<1>(X2 + c * CCZ + o1, dy[c]);
-        }
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) {
+                X0[eoff + c * CZ + o.x + t] = dx[c][t];
+                X2[eoff + c * CZ + o.y[t]] = dy[c][t];
+            }
     }
 }
 
@@ -1093,7 +1174,8 @@ struct QpFields {
 template <int EPB, int LAW, int STORAGE, bool STAGED>
 struct ApplySmem {
     static constexpr int arrays = STORAGE == HX_RECOMPUTE ? 6 : 3;
-    static constexpr size_t cube_bytes = (size_t)arrays * EPB * CES * sizeof(Real);
+    static constexpr bool SW = STAGED && ROWSW;
+    static constexpr size_t cube_bytes = (size_t)arrays * EPB * Lay<SW>::ES * sizeof(Real);
     static constexpr size_t field_bytes = (size_t)EPB * NQ * sizeof(Real);
     // bulk copies need 16-byte aligned starts: every tile offset is a
     // multiple of field_bytes, and the field strides are padded to 32 points
@@ -1221,31 +1303,38 @@ __device__ __forceinline__ void col_backward(const hx::MeshView &m, Real *X0, Re
 // Qx, X2 holds Qy and rz[c] = Dz^T Qz of each thread's z-line (registers).
 // Dy^T in place on X2 and rz into X1, then X0 = Bx^T (Dx^T X0 + X1 + X2)
 // in place, X1 = By^T X0 and the scatter of Bz^T X1. Called after a barrier.
+template <bool SW>
 __device__ __forceinline__ void col_backward_c(const hx::MeshView &m, Real *X0, Real *X1, Real *X2, Real (*rz)[N],
-                                               bool act, bool valid, int eoff, int a0, int a1, int e,
-                                               Real *__restrict__ out, uint64_t pol_keep) {
+                                               bool act, bool valid, int eoff, const LineOffs<SW> &o, int a0, int a1,
+                                               int e, Real *__restrict__ out, uint64_t pol_keep) {
+    constexpr int CZ = Lay<SW>::CZ;
     Real x[3][N], y[3][N], w[N];
-    const int o0 = eoff + line_off<0>(a0, a1), o1 = eoff + line_off<1>(a0, a1), o2 = eoff + line_off<2>(a0, a1);
     if (act) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) ld_line<1>(X2 + c * CCZ + o1, x[c]);
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) x[c][t] = X2[eoff + c * CZ + o.y[t]];
 #pragma unroll
         for (int c = 0; c < 3; ++c) mv<TD, true>(x[c], y[c]);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            st_line<2>(X1 + c * CCZ + o2, rz[c]);
-            st_line<1>(X2 + c * CCZ + o1, y[c]);
-        }
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) {
+                X1[eoff + c * CZ + o.z[t]] = rz[c][t];
+                X2[eoff + c * CZ + o.y[t]] = y[c][t];
+            }
     }
     __syncthreads();
     if (act) {  // x-lines, in place: X0 = Bx^T (Dx^T X0 + X1 + X2)
         Real s1[3][N], s2[3][N];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            ld_line<0>(X0 + c * CCZ + o0, x[c]);
-            ld_line<0>(X1 + c * CCZ + o0, s1[c]);
-            ld_line<0>(X2 + c * CCZ + o0, s2[c]);
-        }
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) {
+                x[c][t] = X0[eoff + c * CZ + o.x + t];
+                s1[c][t] = X1[eoff + c * CZ + o.x + t];
+                s2[c][t] = X2[eoff + c * CZ + o.x + t];
+            }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             mv<TD, true>(x[c], y[c]);
@@ -1254,21 +1343,29 @@ __device__ __forceinline__ void col_backward_c(const hx::MeshView &m, Real *X0, 
             mv<TB, true>(w, y[c]);
         }
 #pragma unroll
-        for (int c = 0; c < 3; ++c) st_line<0>(X0 + c * CCZ + o0, y[c]);
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) X0[eoff + c * CZ + o.x + t] = y[c][t];
     }
     __syncthreads();
     if (act) {  // y-lines: X1 = By^T X0
 #pragma unroll
-        for (int c = 0; c < 3; ++c) ld_line<1>(X0 + c * CCZ + o1, x[c]);
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) x[c][t] = X0[eoff + c * CZ + o.y[t]];
 #pragma unroll
         for (int c = 0; c < 3; ++c) mv<TB, true>(x[c], y[c]);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) st_line<1>(X1 + c * CCZ + o1, y[c]);
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) X1[eoff + c * CZ + o.y[t]] = y[c][t];
     }
     __syncthreads();
     if (valid) {  // z-lines: r = Bz^T X1, scattered from registers
 #pragma unroll
-        for (int c = 0; c < 3; ++c) ld_line<2>(X1 + c * CCZ + o2, x[c]);
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) x[c][t] = X1[eoff + c * CZ + o.z[t]];
 #pragma unroll
         for (int c = 0; c < 3; ++c) mv<TB, true>(x[c], y[c]);
         const int64_t base = elem_base(m, e);
@@ -1324,18 +1421,19 @@ template <int EPB, int NT, int LAW, int STORAGE, bool STAGED>
 __device__ __forceinline__ bool apply_tile(const hx::MeshView &m, int tile, int ntile, Real *__restrict__ out,
                                            const Real *cd, const Real *ck, unsigned char *smem_raw, Real *stg,
                                            uint64_t *bar, uint32_t &phase, uint64_t pol_keep, uint64_t pol_stream) {
+    constexpr bool SW = STAGED && ROWSW;  // row-swizzled cubes, one warp per element
+    constexpr int ES = Lay<SW>::ES;
     Real *X0 = (Real *)smem_raw;
-    Real *X1 = X0 + EPB * CES;
-    Real *X2 = X1 + EPB * CES;
-    Real *K0 = X2 + EPB * CES;  // recompute strategy: reference gradient of u_k
-    Real *K1 = K0 + EPB * CES;
-    Real *K2 = K1 + EPB * CES;
+    Real *X1 = X0 + EPB * ES;
+    Real *X2 = X1 + EPB * ES;
+    Real *K0 = X2 + EPB * ES;  // recompute strategy: reference gradient of u_k
+    Real *K1 = K0 + EPB * ES;
+    Real *K2 = K1 + EPB * ES;
     const int t = threadIdx.x;
-    const int el = t / NN;
-    const int a = t - el * NN;
-    const int a0 = a % N, a1 = a / N;
-    const bool act = el < EPB;
-    const int eoff = (act ? el : 0) * CES;
+    int el, a0, a1;
+    bool act;
+    thread_map<SW>(t, EPB, el, a0, a1, act);
+    const int eoff = (act ? el : 0) * ES;
     constexpr bool RC = STORAGE == HX_RECOMPUTE;
     using QF = QpFields<LAW, STORAGE>;
     constexpr int NR = QF::n;
@@ -1380,9 +1478,11 @@ __device__ __forceinline__ bool apply_tile(const hx::MeshView &m, int tile, int 
         // column order: thread (a0, a1) of element el handles the points
         // (a0, a1, k) of its z-line; the stage holds them at el*NQ + a0 +
         // N*a1 + NN*k (consecutive threads, consecutive words)
+        constexpr int CZ = Lay<SW>::CZ;
+        const LineOffs<SW> lo = line_offsets<SW>(a0, a1);
         Real gz[3][N], gk[RC ? 3 : 1][N];
-        if constexpr (RC) col_forward_c(ck, K0, K1, K2, gk, act, eoff, a0, a1);
-        col_forward_c(cd, X0, X1, X2, gz, act, eoff, a0, a1);
+        if constexpr (RC) col_forward_c<SW>(ck, K0, K1, K2, gk, act, eoff, lo);
+        col_forward_c<SW>(cd, X0, X1, X2, gz, act, eoff, lo);
         const bool ok = mbar_wait(bar, phase);
         if (__syncthreads_or(!ok)) {  // also the barrier that completes the forward sweeps
             if (t == 0) {
@@ -1394,7 +1494,6 @@ __device__ __forceinline__ bool apply_tile(const hx::MeshView &m, int tile, int 
         phase ^= 1u;
         if (valid) {
             const Real *sp = stg + el * NQ + a0 + N * a1;
-            const int p0 = eoff + line_off<2>(a0, a1);
             // point k+1's shared loads are issued before point k's stores
             Real r[NR], Gx[3], Gy[3], Ux[3], Uy[3];
             auto fetch = [&](int k) {
@@ -1402,11 +1501,11 @@ __device__ __forceinline__ bool apply_tile(const hx::MeshView &m, int tile, int 
                 for (int f = 0; f < NR; ++f) r[f] = sp[f * (EPB * NQ) + NN * k];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    Gx[c] = X0[p0 + k * CPS + c * CCZ];
-                    Gy[c] = X2[p0 + k * CPS + c * CCZ];
+                    Gx[c] = X0[eoff + lo.z[k] + c * CZ];
+                    Gy[c] = X2[eoff + lo.z[k] + c * CZ];
                     if constexpr (RC) {
-                        Ux[c] = K0[p0 + k * CPS + c * CCZ];
-                        Uy[c] = K2[p0 + k * CPS + c * CCZ];
+                        Ux[c] = K0[eoff + lo.z[k] + c * CZ];
+                        Uy[c] = K2[eoff + lo.z[k] + c * CZ];
                     }
                 }
             };
@@ -1427,11 +1526,11 @@ __device__ __forceinline__ bool apply_tile(const hx::MeshView &m, int tile, int 
                 }
                 qp_tangent<LAW, STORAGE>(m, e, Gr, Gu, r, Q);
                 if (k + 1 < N) fetch(k + 1);
-                const int pk = p0 + k * CPS;
+                const int pk = eoff + lo.z[k];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    X0[pk + c * CCZ] = Q[c * 3 + 0];
-                    X2[pk + c * CCZ] = Q[c * 3 + 1];
+                    X0[pk + c * CZ] = Q[c * 3 + 0];
+                    X2[pk + c * CZ] = Q[c * 3 + 1];
                     gz[c][k] = Q[c * 3 + 2];
                 }
             }
@@ -1441,7 +1540,7 @@ __device__ __forceinline__ bool apply_tile(const hx::MeshView &m, int tile, int 
         for (int c = 0; c < 3; ++c) mv<TD, true>(gz[c], rz[c]);
         __syncthreads();
         if (t == 0 && ntile >= 0) stage_issue<EPB, LAW, STORAGE>(m, ntile, stg, bar);
-        col_backward_c(m, X0, X1, X2, rz, act, valid, eoff, a0, a1, e, out, pol_keep);
+        col_backward_c<SW>(m, X0, X1, X2, rz, act, valid, eoff, lo, a0, a1, e, out, pol_keep);
         return true;
     } else {
         Real rc[NR], rn[NR];
@@ -1577,15 +1676,15 @@ __global__ void __launch_bounds__(col_threads(EPB)) k_residual_col(const hx::Mes
 // quadrature-point phase); a copy that never completes sets the device
 // timeout flag and ends the CTA.
 template <int EPB, int LAW, int STORAGE, bool STAGED>
-__global__ void __launch_bounds__(col_threads(EPB)) k_apply(const hx::MeshView m, const Real *__restrict__ du,
-                                                            Real *__restrict__ out, int ntiles) {
+__global__ void __launch_bounds__(apply_threads<STAGED && ROWSW>(EPB)) k_apply(const hx::MeshView m,
+                                                                               const Real *__restrict__ du,
+                                                                               Real *__restrict__ out, int ntiles) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     const int t = threadIdx.x;
-    const int el = t / NN;
-    const int a = t - el * NN;
-    const int a0 = a % N, a1 = a / N;
-    const bool act = el < EPB;
+    int el, a0, a1;
+    bool act;
+    thread_map<STAGED && ROWSW>(t, EPB, el, a0, a1, act);
     const uint64_t pol_keep = policy_evict_last();
     const uint64_t pol_stream = policy_evict_first();
     constexpr bool RC = STORAGE == HX_RECOMPUTE;
@@ -1623,7 +1722,7 @@ __global__ void __launch_bounds__(col_threads(EPB)) k_apply(const hx::MeshView m
         }
         // no barrier: the previous tile's last phase reads X1 only, the first
         // phase of this one writes X0 (and K0) only
-        if (!apply_tile<EPB, col_threads(EPB), LAW, STORAGE, STAGED>(m, tile, ntile < ntiles ? ntile : -1, out, cd,
+        if (!apply_tile<EPB, apply_threads<STAGED && ROWSW>(EPB), LAW, STORAGE, STAGED>(m, tile, ntile < ntiles ? ntile : -1, out, cd,
                                                                     ck, smem_raw, stg, &bar, phase, pol_keep,
                                                                     pol_stream))
             return;

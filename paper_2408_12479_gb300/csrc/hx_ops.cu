@@ -70,19 +70,20 @@ cudaError_t launch_apply_t(const hx::MeshView &m, const void *du, void *out, cud
     } else {
         auto kern = k_apply<EPB, LAW, STORAGE, STAGED>;
         constexpr size_t smem = SM::bytes;
+        constexpr int NTH = apply_threads<STAGED && ROWSW>(EPB);
         if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
         static int per_sm = [&] {
             if (set_smem(kern, smem) != cudaSuccess) return 0;
             cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
             int b = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, col_threads(EPB), smem) != cudaSuccess) return 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, NTH, smem) != cudaSuccess) return 0;
             return b;
         }();
         if (per_sm <= 0) return cudaErrorInvalidConfiguration;
         const int ntiles = (m.n_elem + EPB - 1) / EPB;
         if (ntiles == 0) return cudaSuccess;
         const int grid = ntiles < per_sm * sm_count() ? ntiles : per_sm * sm_count();
-        kern<<<grid, col_threads(EPB), smem, s>>>(m, (const Real *)du, (Real *)out, ntiles);
+        kern<<<grid, NTH, smem, s>>>(m, (const Real *)du, (Real *)out, ntiles);
         return cudaGetLastError();
     }
 }
