@@ -166,9 +166,9 @@ def time_steps(G, du, out, steps, warmup):
     return e0.elapsed_time(e1) / steps
 
 
-def run_batch(device, steps=20):
+def run_batch(device, steps=20, storage=None):
     """64 cNH cubes of mixed size and degree (each with its own state) applied
-    in one persistent launch per step, FP32, cache-F strategy."""
+    in one persistent launch per step, FP32, the given caching strategy."""
     import torch
     from paper_2408_12479_gb300 import hx
     from paper_2408_12479_gb300 import inputs as I
@@ -178,7 +178,7 @@ def run_batch(device, steps=20):
         G = hx.Mesh(m, dict(I.MAT_CNH), device=device, ctx=ctx)
         X = G.node_coords().cpu().numpy()
         G.precompute(torch.tensor(field(X).ravel(), dtype=torch.float64, device=G.device), hx.HX_FP32,
-                     hx.HX_CACHE_F)
+                     hx.HX_CACHE_F if storage is None else storage)
         meshes.append(G)
         dus.append(torch.tensor(I.random_direction(m.n_dofs, seed), dtype=torch.float32, device=G.device))
         outs.append(torch.empty_like(dus[-1]))
@@ -195,7 +195,8 @@ def run_batch(device, steps=20):
     hx.hx_sync(ctx, 60000)
     ms = e0.elapsed_time(e1) / steps
     n_dofs = sum(G.n_dofs for G in meshes)
-    res = {"workload": "64 cNH cubes, n ~ U{8..24}, p ~ U{2..5}, FP32, cache_F, one persistent launch",
+    name = hx.STORAGE_NAMES[hx.HX_CACHE_F if storage is None else storage]
+    res = {"workload": f"64 cNH cubes, n ~ U{{8..24}}, p ~ U{{2..5}}, FP32, {name}, one persistent launch",
            "n_meshes": len(meshes), "n_dofs": n_dofs, "ms": round(ms, 4),
            "gdofs": round(n_dofs / (ms * 1e-3) / 1e9, 3),
            "degrees": sorted(set(G.input.p for G in meshes))}
@@ -539,7 +540,8 @@ def main():
 
     batch = None
     if rank == 0 and not args.no_sweep:
-        batch = run_batch(local)
+        batch = {"cache_F": run_batch(local, storage=hx.HX_CACHE_F),
+                 "spatial_tensors": run_batch(local, storage=hx.HX_SPATIAL_TENSORS)}
     solve = None
     if rank == 0 and args.solve and not args.no_sweep:
         solve = run_solve(local, n=args.solve)
