@@ -868,16 +868,18 @@ __device__ __forceinline__ void st_line(Real *p, const Real *y) {
 #pragma unroll
     for (int t = 0; t < N; ++t) p[t * line_str<DIR>()] = y[t];
 }
-// y = M x (TR: y = M^T x) with a 1D table from constant memory. FP64 units
-// from five points on use the even-odd decomposition: with e_t = x_t +
-// x_{N-1-t} and d_t = x_t - x_{N-1-t}, a_o = P e (+ M[o][h] x_h), b_o = Q d,
+// y = M x (TR: y = M^T x) with a 1D table from constant memory. With EO and
+// from five points on, the even-odd decomposition: with e_t = x_t + x_{N-1-t}
+// and d_t = x_t - x_{N-1-t}, a_o = P e (+ M[o][h] x_h), b_o = Q d,
 // y_o = a_o + b_o and y_{N-1-o} = +-(a_o - b_o) (N^2 FMAs become about
-// N^2/2 + 2N; the FP64 apply is bound by the FP64 pipe). FP32 units keep the
-// plain products: a_o - b_o loses relative accuracy where the two nearly
-// cancel, and the FP32 apply is not bound by its FMA count.
-template <int TAB, bool TR>
+// N^2/2 + 2N). FP64 units use it everywhere (their apply is bound by the FP64
+// pipe); FP32 units only in the staged apply, which is bound by instruction
+// issue. The FP32 residual and register-path sweeps keep the plain products:
+// a_o - b_o loses relative accuracy where the two nearly cancel, which took
+// the FP32 residual at p = 6 past a relative error of 1e-5.
+template <int TAB, bool TR, bool EO = (sizeof(Real) == 8)>
 __device__ __forceinline__ void mv(const Real *x, Real *y) {
-    if constexpr (N >= 5 && sizeof(Real) == 8) {
+    if constexpr (N >= 5 && EO) {
         constexpr int H = EOH;
         constexpr bool SYM = TAB == TB;
         auto M = [](int o, int t) { return tab<TAB>(TR ? t * N + o : o * N + t); };
@@ -1075,13 +1077,14 @@ __device__ __forceinline__ void col_forward_c(const Real *row, Real *X0, Real *X
     // cubes share one allocation, so the compiler may not move a load above
     // a store itself
     constexpr int CZ = Lay<SW>::CZ;
+    constexpr bool EO = true;  // even-odd sweeps in the staged apply (see mv)
     Real x[3][N], y[3][N];
     if (act) {  // x-lines: X0 = Bx u
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
 #pragma unroll
             for (int i = 0; i < N; ++i) x[c][i] = row[3 * i + c];
-            mv<TB, false>(x[c], y[c]);
+            mv<TB, false, EO>(x[c], y[c]);
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -1095,7 +1098,7 @@ __device__ __forceinline__ void col_forward_c(const Real *row, Real *X0, Real *X
 #pragma unroll
             for (int t = 0; t < N; ++t) x[c][t] = X0[eoff + c * CZ + o.y[t]];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) mv<TB, false>(x[c], y[c]);
+        for (int c = 0; c < 3; ++c) mv<TB, false, EO>(x[c], y[c]);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -1109,8 +1112,8 @@ __device__ __forceinline__ void col_forward_c(const Real *row, Real *X0, Real *X
             for (int t = 0; t < N; ++t) x[c][t] = X1[eoff + c * CZ + o.z[t]];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            mv<TB, false>(x[c], y[c]);
-            mv<TD, false>(y[c], gz[c]);
+            mv<TB, false, EO>(x[c], y[c]);
+            mv<TD, false, EO>(y[c], gz[c]);
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -1129,8 +1132,8 @@ __device__ __forceinline__ void col_forward_c(const Real *row, Real *X0, Real *X
         Real dx[3][N], dy[3][N];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            mv<TD, false>(x[c], dx[c]);
-            mv<TD, false>(y[c], dy[c]);
+            mv<TD, false, EO>(x[c], dx[c]);
+            mv<TD, false, EO>(y[c], dy[c]);
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -1308,6 +1311,7 @@ __device__ __forceinline__ void col_backward_c(const hx::MeshView &m, Real *X0, 
                                                bool act, bool valid, int eoff, const LineOffs<SW> &o, int a0, int a1,
                                                int e, Real *__restrict__ out, uint64_t pol_keep) {
     constexpr int CZ = Lay<SW>::CZ;
+    constexpr bool EO = true;  // even-odd sweeps in the staged apply (see mv)
     Real x[3][N], y[3][N], w[N];
     if (act) {
 #pragma unroll
@@ -1315,7 +1319,7 @@ __device__ __forceinline__ void col_backward_c(const hx::MeshView &m, Real *X0, 
 #pragma unroll
             for (int t = 0; t < N; ++t) x[c][t] = X2[eoff + c * CZ + o.y[t]];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) mv<TD, true>(x[c], y[c]);
+        for (int c = 0; c < 3; ++c) mv<TD, true, EO>(x[c], y[c]);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -1337,10 +1341,10 @@ __device__ __forceinline__ void col_backward_c(const hx::MeshView &m, Real *X0, 
             }
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            mv<TD, true>(x[c], y[c]);
+            mv<TD, true, EO>(x[c], y[c]);
 #pragma unroll
             for (int k = 0; k < N; ++k) w[k] = y[c][k] + s1[c][k] + s2[c][k];
-            mv<TB, true>(w, y[c]);
+            mv<TB, true, EO>(w, y[c]);
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -1354,7 +1358,7 @@ __device__ __forceinline__ void col_backward_c(const hx::MeshView &m, Real *X0, 
 #pragma unroll
             for (int t = 0; t < N; ++t) x[c][t] = X0[eoff + c * CZ + o.y[t]];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) mv<TB, true>(x[c], y[c]);
+        for (int c = 0; c < 3; ++c) mv<TB, true, EO>(x[c], y[c]);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -1367,7 +1371,7 @@ __device__ __forceinline__ void col_backward_c(const hx::MeshView &m, Real *X0, 
 #pragma unroll
             for (int t = 0; t < N; ++t) x[c][t] = X1[eoff + c * CZ + o.z[t]];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) mv<TB, true>(x[c], y[c]);
+        for (int c = 0; c < 3; ++c) mv<TB, true, EO>(x[c], y[c]);
         const int64_t base = elem_base(m, e);
         const bool msk = m.dmask != nullptr;
 #pragma unroll
@@ -1537,7 +1541,7 @@ __device__ __forceinline__ bool apply_tile(const hx::MeshView &m, int tile, int 
         }
         Real rz[3][N];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) mv<TD, true>(gz[c], rz[c]);
+        for (int c = 0; c < 3; ++c) mv<TD, true, true>(gz[c], rz[c]);
         __syncthreads();
         if (t == 0 && ntile >= 0) stage_issue<EPB, LAW, STORAGE>(m, ntile, stg, bar);
         col_backward_c<SW>(m, X0, X1, X2, rz, act, valid, eoff, lo, a0, a1, e, out, pol_keep);
