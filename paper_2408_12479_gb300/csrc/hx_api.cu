@@ -1175,7 +1175,7 @@ hx_status hx_batch_tangent_apply(hx_batch *b, const void *const *du_dev, void *c
             for (int i = 0; i < n; ++i) {
                 const hx_mesh *m = b->meshes[i];
                 if (m->p != p) continue;
-                const int epb = ops->epb(p, storage);
+                const int epb = ops->epb(p, b->law, storage);
                 if (epb < 1) return fail(ctx, HX_ERR_UNSUPPORTED, "hx_batch_tangent_apply: degree not in the batch unit");
                 const int nt = (m->n_elem + epb - 1) / epb;
                 for (int t = 0; t < nt; ++t) items.push_back(make_int2(i, t));

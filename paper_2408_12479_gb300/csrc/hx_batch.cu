@@ -7,8 +7,11 @@
 // CTA mostly stays on one code path -- and dispatches each item to the tile
 // function of its mesh's degree. All items share one block shape (BT threads);
 // the tile size of a degree is the largest that fits BT threads and the
-// shared-memory budget. Batches run the caching strategies (the
-// quadrature-point data of every mesh is refreshed by hx_precompute_qp).
+// shared-memory budget (two CTAs per SM). Items whose tile fits with its
+// quadrature-point fields staged in shared memory take the staged path of the
+// single-mesh apply, the copies issued when the item starts (one mbarrier per
+// CTA). Batches run the caching strategies (the quadrature-point data of every
+// mesh is refreshed by hx_precompute_qp).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -27,7 +30,7 @@ typedef float Real;
 typedef double Real;
 #endif
 constexpr int BT = 256;                    // threads per CTA of the batch kernel
-constexpr size_t BATCH_SMEM = 160 * 1024;  // shared arrays per CTA at most
+constexpr size_t BATCH_SMEM = 112 * 1024;  // shared arrays per CTA at most (two CTAs per SM)
 }  // namespace hx_batch_unit
 
 #define HX_P 1
@@ -70,12 +73,15 @@ namespace hx_batch_unit {
 namespace {
 
 template <int LAW, int STORAGE>
-__global__ void __launch_bounds__(BT) k_batch_apply(const hx::BatchMesh *__restrict__ meshes,
+__global__ void __launch_bounds__(BT, 2) k_batch_apply(const hx::BatchMesh *__restrict__ meshes,
                                                      const int2 *__restrict__ items, int nitems) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ hx::MeshView mv;
     __shared__ const void *sdu;
     __shared__ void *sout;
+    __shared__ __align__(8) uint64_t bar;  // staged items' bulk copies
+    if (threadIdx.x == 0) hxb1::mbar_init(&bar, 1);
+    uint32_t phase = 0;
     for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
         const int2 it = items[w];
         __syncthreads();  // the previous item is done with mv and the shared arrays
@@ -85,14 +91,17 @@ __global__ void __launch_bounds__(BT) k_batch_apply(const hx::BatchMesh *__restr
             sout = meshes[it.x].out;
         }
         __syncthreads();
+        int r;
         switch (mv.p) {
-            case 1: hxb1::tile<LAW, STORAGE>(mv, it.y, sdu, sout, smem_raw); break;
-            case 2: hxb2::tile<LAW, STORAGE>(mv, it.y, sdu, sout, smem_raw); break;
-            case 3: hxb3::tile<LAW, STORAGE>(mv, it.y, sdu, sout, smem_raw); break;
-            case 4: hxb4::tile<LAW, STORAGE>(mv, it.y, sdu, sout, smem_raw); break;
-            case 5: hxb5::tile<LAW, STORAGE>(mv, it.y, sdu, sout, smem_raw); break;
-            default: hxb6::tile<LAW, STORAGE>(mv, it.y, sdu, sout, smem_raw); break;
+            case 1: r = hxb1::tile<LAW, STORAGE>(mv, it.y, sdu, sout, smem_raw, &bar, phase); break;
+            case 2: r = hxb2::tile<LAW, STORAGE>(mv, it.y, sdu, sout, smem_raw, &bar, phase); break;
+            case 3: r = hxb3::tile<LAW, STORAGE>(mv, it.y, sdu, sout, smem_raw, &bar, phase); break;
+            case 4: r = hxb4::tile<LAW, STORAGE>(mv, it.y, sdu, sout, smem_raw, &bar, phase); break;
+            case 5: r = hxb5::tile<LAW, STORAGE>(mv, it.y, sdu, sout, smem_raw, &bar, phase); break;
+            default: r = hxb6::tile<LAW, STORAGE>(mv, it.y, sdu, sout, smem_raw, &bar, phase); break;
         }
+        if (r < 0) return;  // every thread: the wait gave up (flag set by the tile)
+        phase ^= (uint32_t)r;
     }
 }
 
@@ -106,14 +115,14 @@ __global__ void k_batch_zero(const hx::BatchMesh *__restrict__ meshes, int nmesh
         o[j] = Real(0);
 }
 
-template <int STORAGE>
+template <int LAW, int STORAGE>
 constexpr size_t max_smem() {
-    size_t s = hxb1::batch_smem<STORAGE>();
-    s = s > hxb2::batch_smem<STORAGE>() ? s : hxb2::batch_smem<STORAGE>();
-    s = s > hxb3::batch_smem<STORAGE>() ? s : hxb3::batch_smem<STORAGE>();
-    s = s > hxb4::batch_smem<STORAGE>() ? s : hxb4::batch_smem<STORAGE>();
-    s = s > hxb5::batch_smem<STORAGE>() ? s : hxb5::batch_smem<STORAGE>();
-    s = s > hxb6::batch_smem<STORAGE>() ? s : hxb6::batch_smem<STORAGE>();
+    size_t s = hxb1::batch_smem<LAW, STORAGE>();
+    s = s > hxb2::batch_smem<LAW, STORAGE>() ? s : hxb2::batch_smem<LAW, STORAGE>();
+    s = s > hxb3::batch_smem<LAW, STORAGE>() ? s : hxb3::batch_smem<LAW, STORAGE>();
+    s = s > hxb4::batch_smem<LAW, STORAGE>() ? s : hxb4::batch_smem<LAW, STORAGE>();
+    s = s > hxb5::batch_smem<LAW, STORAGE>() ? s : hxb5::batch_smem<LAW, STORAGE>();
+    s = s > hxb6::batch_smem<LAW, STORAGE>() ? s : hxb6::batch_smem<LAW, STORAGE>();
     return s;
 }
 
@@ -130,7 +139,7 @@ int sm_count_b() {
 template <int LAW, int STORAGE>
 cudaError_t launch_t(const hx::BatchMesh *meshes, const int2 *items, int nitems, cudaStream_t s) {
     auto kern = k_batch_apply<LAW, STORAGE>;
-    constexpr size_t smem = max_smem<STORAGE>();
+    constexpr size_t smem = max_smem<LAW, STORAGE>();
     static int per_sm = [&] {
         if (smem > 48 * 1024 &&
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
@@ -169,13 +178,14 @@ cudaError_t op_zero(const hx::BatchMesh *meshes, int nmesh, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-int op_epb(int p, int storage) {
-#define HX_B_EPB(P)                                                                     \
-    case P:                                                                             \
-        return storage == HX_RECOMPUTE   ? hxb##P::batch_epb<HX_RECOMPUTE>()    \
-               : storage == HX_CACHE_F   ? hxb##P::batch_epb<HX_CACHE_F>()      \
-               : storage == HX_CACHE_TENSORS ? hxb##P::batch_epb<HX_CACHE_TENSORS>() \
-                                             : hxb##P::batch_epb<HX_SPATIAL_TENSORS>();
+template <int LAW>
+int epb_law(int p, int storage) {
+#define HX_B_EPB(P)                                                                              \
+    case P:                                                                                      \
+        return storage == HX_RECOMPUTE       ? hxb##P::batch_epb<LAW, HX_RECOMPUTE>()       \
+               : storage == HX_CACHE_F       ? hxb##P::batch_epb<LAW, HX_CACHE_F>()         \
+               : storage == HX_CACHE_TENSORS ? hxb##P::batch_epb<LAW, HX_CACHE_TENSORS>()   \
+                                             : hxb##P::batch_epb<LAW, HX_SPATIAL_TENSORS>();
     switch (p) {
         HX_B_EPB(1)
         HX_B_EPB(2)
@@ -187,6 +197,11 @@ int op_epb(int p, int storage) {
             return 0;
     }
 #undef HX_B_EPB
+}
+int op_epb(int p, int law, int storage) {
+    return law == HX_CNH ? epb_law<HX_CNH>(p, storage)
+           : law == HX_INH ? epb_law<HX_INH>(p, storage)
+                           : epb_law<HX_FIBER>(p, storage);
 }
 
 cudaError_t op_upload_p(int p, const double *B, const double *D, const double *Gd, const double *w,

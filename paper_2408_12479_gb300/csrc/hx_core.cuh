@@ -1756,6 +1756,33 @@ __device__ __forceinline__ void batch_tile(const hx::MeshView &m, int tile, cons
                                              policy_evict_last(), policy_evict_first());
 }
 
+// The same with the quadrature-point fields staged by bulk copies (caching
+// strategies): thread 0 issues the item's copies on `bar` when the item starts
+// (the caller's CTA barrier has retired the previous item's stage), so they
+// overlap the row loads and the forward sweeps; `phase` is the parity of the
+// wait. Returns false (on every thread) if the copies never arrived.
+template <int EPB, int NT, int LAW, int STORAGE>
+__device__ __forceinline__ bool batch_tile_staged(const hx::MeshView &m, int tile, const Real *__restrict__ du,
+                                                  Real *__restrict__ out, unsigned char *smem_raw, uint64_t *bar,
+                                                  uint32_t phase) {
+    static_assert(STORAGE != HX_RECOMPUTE, "the staged tile runs the caching strategies");
+    using SM = ApplySmem<EPB, LAW, STORAGE, true>;
+    static_assert(SM::stageable, "bulk copies need 16-byte aligned tiles");
+    Real *stg = (Real *)(smem_raw + (SM::cube_bytes + 15) / 16 * 16);
+    const int t = threadIdx.x;
+    if (t == 0) stage_issue<EPB, LAW, STORAGE>(m, tile, stg, bar);
+    int el, a0, a1;
+    bool act;
+    thread_map<ROWSW>(t, EPB, el, a0, a1, act);
+    Real cd[3 * N], ck[1];
+    if (act) {
+        const int e1 = tile * EPB + el;
+        load_row(m, e1, elem_base(m, e1), a0, a1, du, true, cd);
+    }
+    return apply_tile<EPB, NT, LAW, STORAGE, true>(m, tile, -1, out, cd, ck, smem_raw, stg, bar, phase,
+                                                   policy_evict_last(), policy_evict_first());
+}
+
 // qp cache at state u: interpolation and state in FP64, stored as Real
 template <int EPB, int LAW, int STORAGE>
 __global__ void __launch_bounds__(threads_for(EPB)) k_precompute(const hx::MeshView m, const double *__restrict__ u, Real *__restrict__ qp) {

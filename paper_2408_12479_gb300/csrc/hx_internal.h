@@ -105,7 +105,7 @@ struct BatchOps {
     int prec;
     cudaError_t (*upload_tables)(int p, const double *B, const double *D, const double *Gd, const double *w,
                                  const double *geoV, const double *geoD, const double *geoVn);
-    int (*epb)(int p, int storage);  // elements per work item of degree p
+    int (*epb)(int p, int law, int storage);  // elements per work item of degree p
     cudaError_t (*apply)(int law, int storage, const BatchMesh *meshes, const int2 *items, int nitems,
                          cudaStream_t s);
     cudaError_t (*zero)(const BatchMesh *meshes, int nmesh, cudaStream_t s);
