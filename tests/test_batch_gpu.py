@@ -89,3 +89,42 @@ def test_batch_statuses():
         for it in items:
             it[3].close()
         hx.hx_destroy(ctx)
+
+
+@pytest.mark.parametrize("law", ["cNH", "fiber"])
+@pytest.mark.parametrize("storage", [hx.HX_CACHE_F, hx.HX_SPATIAL_TENSORS])
+@pytest.mark.parametrize("prec", [hx.HX_FP64, hx.HX_FP32])
+def test_batch_many_items_per_cta(law, storage, prec):
+    """Meshes large enough that every CTA of the persistent launch takes many
+    work items of several degrees in turn (the staged items alternate the
+    parity of the CTA's bulk-copy barrier): the batch must equal the
+    single-mesh apply of every mesh (itself checked against the oracle)."""
+    ctx = hx.hx_create(0)
+    specs = [(16, 4), (20, 2), (12, 3), (8, 5), (6, 6)]
+    Gs, batch = [], None
+    try:
+        dus, outs = [], []
+        for k, (n, p) in enumerate(specs):
+            G = hx.Mesh(cases.small_cube(n, p, law, seed=900 + k), cases.MATS[law], ctx=ctx)
+            X = G.node_coords().cpu().numpy()
+            u = I.sine_field(910 + k, strain=0.05)(X)
+            if law == "fiber":
+                u = u + X @ np.diag([0.0, 0.08, 0.08])
+            G.precompute(torch.tensor(u.ravel(), dtype=torch.float64, device="cuda"), prec, storage)
+            Gs.append(G)
+            dus.append(torch.tensor(I.random_direction(3 * X.shape[0], 920 + k), dtype=DT[prec], device="cuda"))
+            outs.append(torch.full_like(dus[-1], 7.0))
+        batch = hx.hx_batch_create(ctx, Gs)
+        for rep in range(2):
+            hx.hx_batch_tangent_apply(ctx, batch, dus, outs)
+            hx.hx_sync(ctx, 60000)
+            for k, G in enumerate(Gs):
+                single = G.apply(dus[k]).double().cpu().numpy()
+                got = outs[k].double().cpu().numpy()
+                assert rel_inf(got, single) < (1e-14 if prec == hx.HX_FP64 else 1e-6), (k, rel_inf(got, single))
+    finally:
+        if batch is not None:
+            hx.hx_batch_destroy(batch)
+        for G in Gs:
+            G.close()
+        hx.hx_destroy(ctx)
