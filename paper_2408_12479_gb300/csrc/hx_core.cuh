@@ -919,6 +919,111 @@ __device__ __forceinline__ void mv(const Real *x, Real *y) {
     }
 }
 
+// Paired sweeps (FP32 units): two independent lines through one 1D table at
+// once with the packed FP32 instructions of sm_100 and later (FFMA2, one
+// instruction per two products). Each lane performs mv's operations in mv's
+// order, so the results are those of two mv calls. The tables are read as
+// {m, m} pairs from cTab2 and cEO2 (copies of cTab and cEO).
+__constant__ float2 cTab2[3][NN];
+__constant__ float2 cEO2[3][2][2][(EOH > 0 ? EOH : 1) * (EOH > 0 ? EOH : 1)];
+constexpr bool PK = sizeof(Real) == 4;
+
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+template <int TAB, bool TR, bool EO>
+__device__ __forceinline__ void mv2(const float2 *x, float2 *y) {
+    auto M = [](int o, int t) { return cTab2[TAB][TR ? t * N + o : o * N + t]; };
+    if constexpr (N >= 5 && EO) {
+        constexpr int H = EOH;
+        constexpr bool SYM = TAB == TB;
+        float2 ev[H], od[H];
+#pragma unroll
+        for (int t = 0; t < H; ++t) {
+            ev[t] = __fadd2_rn(x[t], x[N - 1 - t]);
+            od[t] = sub2(x[t], x[N - 1 - t]);
+        }
+#pragma unroll
+        for (int o = 0; o < H; ++o) {
+            float2 a = __fmul2_rn(cEO2[TAB][TR][0][o * H], ev[0]);
+            float2 b = __fmul2_rn(cEO2[TAB][TR][1][o * H], od[0]);
+#pragma unroll
+            for (int t = 1; t < H; ++t) {
+                a = __ffma2_rn(cEO2[TAB][TR][0][o * H + t], ev[t], a);
+                b = __ffma2_rn(cEO2[TAB][TR][1][o * H + t], od[t], b);
+            }
+            if constexpr (N % 2 == 1) a = __ffma2_rn(M(o, H), x[H], a);
+            y[o] = __fadd2_rn(a, b);
+            y[N - 1 - o] = SYM ? sub2(a, b) : sub2(b, a);
+        }
+        if constexpr (N % 2 == 1) {
+            float2 c = __fmul2_rn(M(H, 0), SYM ? ev[0] : od[0]);
+#pragma unroll
+            for (int t = 1; t < H; ++t) c = __ffma2_rn(M(H, t), SYM ? ev[t] : od[t], c);
+            if constexpr (SYM) c = __ffma2_rn(M(H, H), x[H], c);
+            y[H] = c;
+        }
+    } else {
+#pragma unroll
+        for (int o = 0; o < N; ++o) {
+            float2 s = __fmul2_rn(M(o, 0), x[0]);
+#pragma unroll
+            for (int t = 1; t < N; ++t) s = __ffma2_rn(M(o, t), x[t], s);
+            y[o] = s;
+        }
+    }
+}
+// y_c = M x_c for the three components of a thread's lines: components 0 and
+// 1 paired, component 2 alone in FP32 units; three mv calls otherwise
+template <int TAB, bool TR, bool EO>
+__device__ __forceinline__ void mv3(const Real (*x)[N], Real (*y)[N]) {
+    if constexpr (PK) {
+        float2 a[N], b[N];
+#pragma unroll
+        for (int t = 0; t < N; ++t) a[t] = make_float2(x[0][t], x[1][t]);
+        mv2<TAB, TR, EO>(a, b);
+#pragma unroll
+        for (int t = 0; t < N; ++t) {
+            y[0][t] = b[t].x;
+            y[1][t] = b[t].y;
+        }
+        mv<TAB, TR, EO>(x[2], y[2]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) mv<TAB, TR, EO>(x[c], y[c]);
+    }
+}
+// y_c = M x_c and v_c = M u_c (six independent lines): three pairs in FP32
+// units, six mv calls otherwise
+template <int TAB, bool TR, bool EO>
+__device__ __forceinline__ void mv6(const Real (*x)[N], const Real (*u)[N], Real (*y)[N], Real (*v)[N]) {
+    if constexpr (PK) {
+        float2 a[3][N], b[3][N];
+#pragma unroll
+        for (int t = 0; t < N; ++t) {
+            a[0][t] = make_float2(x[0][t], x[1][t]);
+            a[1][t] = make_float2(x[2][t], u[0][t]);
+            a[2][t] = make_float2(u[1][t], u[2][t]);
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) mv2<TAB, TR, EO>(a[k], b[k]);
+#pragma unroll
+        for (int t = 0; t < N; ++t) {
+            y[0][t] = b[0][t].x;
+            y[1][t] = b[0][t].y;
+            y[2][t] = b[1][t].x;
+            v[0][t] = b[1][t].y;
+            v[1][t] = b[2][t].x;
+            v[2][t] = b[2][t].y;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            mv<TAB, TR, EO>(x[c], y[c]);
+            mv<TAB, TR, EO>(u[c], v[c]);
+        }
+    }
+}
+
 // node numbering base of an element (structured box: lattice index of its
 // first node; otherwise the element index for the connectivity lookup)
 __device__ __forceinline__ int64_t elem_base(const hx::MeshView &m, int e) {
@@ -1081,11 +1186,10 @@ __device__ __forceinline__ void col_forward_c(const Real *row, Real *X0, Real *X
     Real x[3][N], y[3][N];
     if (act) {  // x-lines: X0 = Bx u
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int i = 0; i < N; ++i) x[c][i] = row[3 * i + c];
-            mv<TB, false, EO>(x[c], y[c]);
-        }
+        mv3<TB, false, EO>(x, y);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -1097,8 +1201,7 @@ __device__ __forceinline__ void col_forward_c(const Real *row, Real *X0, Real *X
         for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int t = 0; t < N; ++t) x[c][t] = X0[eoff + c * CZ + o.y[t]];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) mv<TB, false, EO>(x[c], y[c]);
+        mv3<TB, false, EO>(x, y);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -1110,11 +1213,8 @@ __device__ __forceinline__ void col_forward_c(const Real *row, Real *X0, Real *X
         for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int t = 0; t < N; ++t) x[c][t] = X1[eoff + c * CZ + o.z[t]];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            mv<TB, false, EO>(x[c], y[c]);
-            mv<TD, false, EO>(y[c], gz[c]);
-        }
+        mv3<TB, false, EO>(x, y);
+        mv3<TD, false, EO>(y, gz);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -1130,11 +1230,7 @@ __device__ __forceinline__ void col_forward_c(const Real *row, Real *X0, Real *X
                 y[c][t] = X1[eoff + c * CZ + o.y[t]];
             }
         Real dx[3][N], dy[3][N];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            mv<TD, false, EO>(x[c], dx[c]);
-            mv<TD, false, EO>(y[c], dy[c]);
-        }
+        mv6<TD, false, EO>(x, y, dx, dy);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -1312,14 +1408,13 @@ __device__ __forceinline__ void col_backward_c(const hx::MeshView &m, Real *X0, 
                                                int e, Real *__restrict__ out, uint64_t pol_keep) {
     constexpr int CZ = Lay<SW>::CZ;
     constexpr bool EO = true;  // even-odd sweeps in the staged apply (see mv)
-    Real x[3][N], y[3][N], w[N];
+    Real x[3][N], y[3][N], w[3][N];
     if (act) {
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int t = 0; t < N; ++t) x[c][t] = X2[eoff + c * CZ + o.y[t]];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) mv<TD, true, EO>(x[c], y[c]);
+        mv3<TD, true, EO>(x, y);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -1339,13 +1434,12 @@ __device__ __forceinline__ void col_backward_c(const hx::MeshView &m, Real *X0, 
                 s1[c][t] = X1[eoff + c * CZ + o.x + t];
                 s2[c][t] = X2[eoff + c * CZ + o.x + t];
             }
+        mv3<TD, true, EO>(x, y);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            mv<TD, true, EO>(x[c], y[c]);
+        for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int k = 0; k < N; ++k) w[k] = y[c][k] + s1[c][k] + s2[c][k];
-            mv<TB, true, EO>(w, y[c]);
-        }
+            for (int k = 0; k < N; ++k) w[c][k] = y[c][k] + s1[c][k] + s2[c][k];
+        mv3<TB, true, EO>(w, y);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -1357,8 +1451,7 @@ __device__ __forceinline__ void col_backward_c(const hx::MeshView &m, Real *X0, 
         for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int t = 0; t < N; ++t) x[c][t] = X0[eoff + c * CZ + o.y[t]];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) mv<TB, true, EO>(x[c], y[c]);
+        mv3<TB, true, EO>(x, y);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -1370,8 +1463,7 @@ __device__ __forceinline__ void col_backward_c(const hx::MeshView &m, Real *X0, 
         for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int t = 0; t < N; ++t) x[c][t] = X1[eoff + c * CZ + o.z[t]];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) mv<TB, true, EO>(x[c], y[c]);
+        mv3<TB, true, EO>(x, y);
         const int64_t base = elem_base(m, e);
         const bool msk = m.dmask != nullptr;
 #pragma unroll
@@ -1540,8 +1632,7 @@ __device__ __forceinline__ bool apply_tile(const hx::MeshView &m, int tile, int 
             }
         }
         Real rz[3][N];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) mv<TD, true, true>(gz[c], rz[c]);
+        mv3<TD, true, true>(gz, rz);
         __syncthreads();
         if (t == 0 && ntile >= 0) stage_issue<EPB, LAW, STORAGE>(m, ntile, stg, bar);
         col_backward_c<SW>(m, X0, X1, X2, rz, act, valid, eoff, lo, a0, a1, e, out, pol_keep);
@@ -2262,6 +2353,12 @@ cudaError_t op_upload(const double *B, const double *D, const double *Gd, const 
         t[2][i] = (Real)Gd[i];
     }
     cudaError_t e = cudaMemcpyToSymbol(cTab, t, sizeof t);
+    if (PK && e == cudaSuccess) {  // {m, m} pairs for the paired sweeps
+        float2 t2[3][NN];
+        for (int k = 0; k < 3; ++k)
+            for (int i = 0; i < NN; ++i) t2[k][i] = make_float2((float)t[k][i], (float)t[k][i]);
+        e = cudaMemcpyToSymbol(cTab2, t2, sizeof t2);
+    }
     if (EOH > 0) {
         Real eo[3][2][2][(EOH > 0 ? EOH : 1) * (EOH > 0 ? EOH : 1)];
         const double *src[3] = {B, D, Gd};
@@ -2274,6 +2371,15 @@ cudaError_t op_upload(const double *B, const double *D, const double *Gd, const 
                         eo[k][tr][1][o * EOH + c] = (Real)(0.5 * (Mx(o, c) - Mx(o, N - 1 - c)));
                     }
         if (e == cudaSuccess) e = cudaMemcpyToSymbol(cEO, eo, sizeof eo);
+        if (PK && e == cudaSuccess) {
+            float2 eo2[3][2][2][(EOH > 0 ? EOH : 1) * (EOH > 0 ? EOH : 1)];
+            for (int k = 0; k < 3; ++k)
+                for (int tr = 0; tr < 2; ++tr)
+                    for (int h = 0; h < 2; ++h)
+                        for (int i = 0; i < EOH * EOH; ++i)
+                            eo2[k][tr][h][i] = make_float2((float)eo[k][tr][h][i], (float)eo[k][tr][h][i]);
+            e = cudaMemcpyToSymbol(cEO2, eo2, sizeof eo2);
+        }
     }
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(cW, w, sizeof(double) * N);
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(cGeoV, geoV, sizeof(double) * 2 * 3 * N);
