@@ -166,6 +166,98 @@ def time_steps(G, du, out, steps, warmup):
     return e0.elapsed_time(e1) / steps
 
 
+def _event_ms(fn, steps, warmup):
+    """Mean ms of fn() over `steps` calls after `warmup`, by CUDA events on the
+    current stream (the library's calls run on it)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(steps):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def residual_bytes(n_dofs, n_qp, s):
+    """Algorithmic bytes of one cNH residual: read u, write r, and the stored
+    J0^-1 (9) and JxW (1) per quadrature point; the state is recomputed from u
+    at every point, so nothing else is read."""
+    return 2 * n_dofs * s + 10 * n_qp * s
+
+
+def run_residual_sweep(device, hbm_peak, degrees=(2, 3, 4, 5, 6)):
+    """R(u) on the 32^3 jittered cube (cNH), p = 2..6, FP32 and FP64: one call
+    is the zeroing of r plus one fused kernel. A case that fails records its
+    error and the sweep goes on."""
+    import torch
+    from paper_2408_12479_gb300 import hx
+    from paper_2408_12479_gb300 import inputs as I
+    res = []
+    for pp in degrees:
+        for pr in (hx.HX_FP32, hx.HX_FP64):
+            G = None
+            try:
+                m, field, seed = I.workload_jittered_cube(pp)
+                G = hx.Mesh(m, dict(I.MAT_CNH), device=device)
+                X = G.node_coords().cpu().numpy()
+                u = torch.tensor(field(X).ravel(), dtype=torch.float64, device=G.device)
+                if pr == hx.HX_FP32:
+                    u = u.float()
+                r = torch.empty_like(u)
+                t = _event_ms(lambda: hx.hx_residual(G.ctx, G.handle, u, r), 20 if pr == hx.HX_FP32 else 4, 2)
+                G.sync(60000)
+                b = residual_bytes(G.n_dofs, G.n_qp, u.element_size())
+                res.append({"p": pp, "prec": "f32" if pr == hx.HX_FP32 else "f64", "n_dofs": G.n_dofs,
+                            "ms": round(t, 4), "gdofs": round(G.n_dofs / (t * 1e-3) / 1e9, 3),
+                            "hbm_frac": round(b / (t * 1e-3) / 1e9 / hbm_peak, 4)})
+                del u, r
+            except Exception as exc:  # recorded in the report; the headline line still prints
+                res.append({"p": pp, "prec": "f32" if pr == hx.HX_FP32 else "f64", "error": str(exc)[:200]})
+            finally:
+                if G is not None:
+                    G.close()
+                torch.cuda.empty_cache()
+    return res
+
+
+def run_newton_step_costs(device, p):
+    """What each Newton step pays once (Alg. 1): hx_precompute_qp and
+    hx_diagonal on the 32^3 jittered cube at degree p, per storage strategy and
+    precision, in ms and in tangent applies of the same case."""
+    import torch
+    from paper_2408_12479_gb300 import hx
+    res = []
+    for pr in (hx.HX_FP32, hx.HX_FP64):
+        for st in (hx.HX_CACHE_TENSORS, hx.HX_SPATIAL_TENSORS):
+            G = None
+            try:
+                G, m, u, du, out = build_case(p, pr, st, device)
+                t_apply = _event_ms(lambda: hx.hx_tangent_apply(G.ctx, G.handle, du, out), 10, 2)
+                t_pre = _event_ms(lambda: G.precompute(u, pr, st), 5, 1)
+                d = G.zeros(pr)
+                t_diag = _event_ms(lambda: hx.hx_diagonal(G.ctx, G.handle, d), 5, 1)
+                G.sync(60000)
+                res.append({"p": p, "prec": "f32" if pr == hx.HX_FP32 else "f64",
+                            "storage": hx.STORAGE_NAMES[st], "precompute_ms": round(t_pre, 4),
+                            "diagonal_ms": round(t_diag, 4), "apply_ms": round(t_apply, 4),
+                            "precompute_in_applies": round(t_pre / t_apply, 2),
+                            "diagonal_in_applies": round(t_diag / t_apply, 2)})
+                del u, du, out, d
+            except Exception as exc:  # recorded in the report; the headline line still prints
+                res.append({"p": p, "prec": "f32" if pr == hx.HX_FP32 else "f64",
+                            "storage": hx.STORAGE_NAMES[st], "error": str(exc)[:200]})
+            finally:
+                if G is not None:
+                    G.close()
+                torch.cuda.empty_cache()
+    return res
+
+
 def run_batch(device, steps=20, storage=None):
     """64 cNH cubes of mixed size and degree (each with its own state) applied
     in one persistent launch per step, FP32, the given caching strategy."""
@@ -538,6 +630,11 @@ def main():
                     del us, dus, outs
                     torch.cuda.empty_cache()
 
+    resid = step_costs = None
+    if rank == 0 and not args.no_sweep:
+        resid = run_residual_sweep(local, hbm_peak)
+        step_costs = run_newton_step_costs(local, p)
+
     batch = None
     if rank == 0 and not args.no_sweep:
         batch = {"cache_F": run_batch(local, storage=hx.HX_CACHE_F),
@@ -576,6 +673,8 @@ def main():
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
             "sweep": sweep,
+            "residual": resid,
+            "newton_step_costs": step_costs,
             "batch": batch,
             "solve": solve,
             "newton": newton,

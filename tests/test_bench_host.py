@@ -1,0 +1,129 @@
+"""Host logic of the benchmark's side reports (residual sweep, per-Newton-step
+costs), run on the CPU against a stand-in binding and stand-in CUDA events:
+the call sequence, the byte accounting of the residual and the handling of a
+failing case. No kernel runs here; the GPU numbers come from bench.py itself."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import bench
+from paper_2408_12479_gb300 import hx
+from paper_2408_12479_gb300 import inputs as I
+
+
+class _Event:
+    clock = [0.0]
+
+    def __init__(self, enable_timing=True):
+        self.t = None
+
+    def record(self, stream=None):
+        self.t = _Event.clock[0]
+
+    def elapsed_time(self, other):
+        return other.t - self.t
+
+
+class _FakeMesh:
+    calls = []
+    fail_p = None
+
+    def __init__(self, m, mat, device=0, structured=True, ctx=None):
+        if m.p == _FakeMesh.fail_p:
+            raise hx.HxError(hx.HX_ERR_CUDA, "stand-in failure")
+        self.input = m
+        self.n_nodes = m.n_dofs // 3
+        self.n_dofs = m.n_dofs
+        self.n_qp = m.n_elem * (m.p + 1) ** 3
+        self.device = torch.device("cpu")
+        self.ctx, self.handle = object(), object()
+        self.closed = False
+
+    def node_coords(self):
+        return torch.zeros(self.n_nodes, 3, dtype=torch.float64)
+
+    def zeros(self, prec=hx.HX_FP64):
+        return torch.zeros(self.n_dofs, dtype=torch.float64 if prec == hx.HX_FP64 else torch.float32)
+
+    def precompute(self, u, store_prec=hx.HX_FP64, storage=hx.HX_CACHE_TENSORS):
+        assert u.dtype == torch.float64
+        _FakeMesh.calls.append(("precompute", store_prec, storage))
+        _Event.clock[0] += 3.0
+
+    def sync(self, timeout_ms=-1):
+        pass
+
+    def close(self):
+        self.closed = True
+
+
+def _tick(ms):
+    def f(*a, **k):
+        _Event.clock[0] += ms
+    return f
+
+
+@pytest.fixture
+def fake_gpu(monkeypatch):
+    _FakeMesh.calls = []
+    _FakeMesh.fail_p = None
+    _Event.clock[0] = 0.0
+    small = I.workload_jittered_cube
+    monkeypatch.setattr(I, "workload_jittered_cube", lambda p, n=32, seed=I.SEED_BASE + 2: small(p, n=2, seed=seed))
+    monkeypatch.setattr(hx, "Mesh", _FakeMesh)
+    monkeypatch.setattr(hx, "hx_residual", _tick(1e-4))
+    monkeypatch.setattr(hx, "hx_tangent_apply", _tick(2.0))
+    monkeypatch.setattr(hx, "hx_diagonal", _tick(4.0))
+    monkeypatch.setattr(hx, "hx_autotune", lambda *a, **k: (0, [1.0] * 6))
+    monkeypatch.setattr(torch.cuda, "Event", _Event)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    monkeypatch.setattr(torch.cuda, "current_stream", lambda *a: None)
+    monkeypatch.setattr(torch.cuda, "empty_cache", lambda *a: None)
+    return _FakeMesh
+
+
+def test_residual_bytes_counts_vectors_and_geometry():
+    # 3 DoF vectors' worth of reads/writes plus 10 geometry values per point
+    assert bench.residual_bytes(300, 50, 4) == 2 * 300 * 4 + 10 * 50 * 4
+    assert bench.residual_bytes(300, 50, 8) == 2 * bench.residual_bytes(300, 50, 4)
+
+
+def test_residual_sweep_reports_every_case(fake_gpu):
+    res = bench.run_residual_sweep(0, hbm_peak=1000.0, degrees=(2, 3))
+    assert [(r["p"], r["prec"]) for r in res] == [(2, "f32"), (2, "f64"), (3, "f32"), (3, "f64")]
+    for r in res:
+        assert "error" not in r
+        assert r["ms"] == pytest.approx(1e-4)
+        m, _, _ = I.workload_jittered_cube(r["p"])
+        s = 4 if r["prec"] == "f32" else 8
+        n_qp = m.n_elem * (r["p"] + 1) ** 3
+        assert r["n_dofs"] == m.n_dofs
+        assert r["gdofs"] == pytest.approx(m.n_dofs / 1e-7 / 1e9, rel=1e-3)
+        assert r["hbm_frac"] == pytest.approx(bench.residual_bytes(m.n_dofs, n_qp, s) / 1e-7 / 1e9 / 1000.0,
+                                              abs=1e-4)
+
+
+def test_residual_sweep_records_a_failing_case_and_goes_on(fake_gpu):
+    fake_gpu.fail_p = 2
+    res = bench.run_residual_sweep(0, hbm_peak=1000.0, degrees=(2, 3))
+    assert [("error" in r) for r in res] == [True, True, False, False]
+    assert "stand-in failure" in res[0]["error"]
+
+
+def test_newton_step_costs_in_applies(fake_gpu):
+    res = bench.run_newton_step_costs(0, p=2)
+    assert [(r["prec"], r["storage"]) for r in res] == [
+        ("f32", "cache_tensors"), ("f32", "spatial_tensors"), ("f64", "cache_tensors"), ("f64", "spatial_tensors")]
+    for r in res:
+        assert "error" not in r, r
+        assert r["apply_ms"] == pytest.approx(2.0)
+        assert r["precompute_ms"] == pytest.approx(3.0)
+        assert r["diagonal_ms"] == pytest.approx(4.0)
+        assert r["precompute_in_applies"] == pytest.approx(1.5)
+        assert r["diagonal_in_applies"] == pytest.approx(2.0)
+    # every case refreshed its cache at the precision and strategy it reports
+    pre = [c for c in fake_gpu.calls if c[0] == "precompute"]
+    assert (hx.HX_FP32, hx.HX_SPATIAL_TENSORS) in [(c[1], c[2]) for c in pre]
+    assert (hx.HX_FP64, hx.HX_CACHE_TENSORS) in [(c[1], c[2]) for c in pre]
+    assert np.isfinite([r["precompute_ms"] for r in res]).all()
