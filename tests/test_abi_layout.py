@@ -56,3 +56,60 @@ def test_ctypes_structs_match_the_header(tmp_path):
         for f, _t in py._fields_:
             desc = getattr(py, f)
             assert c[(cname, f)] == (desc.offset, desc.size), (cname, f)
+
+
+_SCALARS = {"int32_t": ctypes.c_int32, "int": ctypes.c_int, "int64_t": ctypes.c_int64, "uint64_t": ctypes.c_uint64,
+            "double": ctypes.c_double, "hx_status": ctypes.c_int32}
+
+
+def _prototypes():
+    import re
+    src = open(os.path.join(ROOT, "include", "hx.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    protos = {}
+    for ret, name, params in re.findall(r"(hx_status|void|const char \*|uint64_t)\s*\b(hx_\w+)\s*\(([^;{]*?)\)\s*;",
+                                        src, flags=re.S):
+        ps = [p.strip() for p in params.split(",")] if params.strip() not in ("", "void") else []
+        protos[name] = (ret.strip(), ps)
+    return protos
+
+
+def _base_type(param):
+    toks = param.replace("*", " * ").replace("[", " [ ").split()
+    toks = [t for t in toks if t not in ("const", "*", "[", "]") and not t.rstrip("]").isdigit()]
+    return toks[0]
+
+
+def _matches(param, ct):
+    base = _base_type(param)
+    n_ptr = param.count("*") + param.count("[")
+    if n_ptr == 0:
+        return ct is _SCALARS[base]
+    if ct in (ctypes.c_void_p, ctypes.c_char_p):
+        return True  # any pointer may travel as an untyped address
+    if n_ptr == 2 or (n_ptr == 1 and base.startswith("hx_") and base not in STRUCT_NAMES):
+        # a pointer to an opaque handle, or an array of handles/addresses
+        return ct is ctypes.POINTER(ctypes.c_void_p)
+    pointee = getattr(ct, "_type_", None)
+    if base in STRUCT_NAMES:
+        return pointee is STRUCT_NAMES[base]
+    return pointee is _SCALARS[base]
+
+
+STRUCT_NAMES = {cname: py for py, (cname, _) in STRUCTS.items()}
+
+
+def test_ctypes_signatures_match_the_header():
+    if not os.path.exists(hx.LIB_PATH):
+        from paper_2408_12479_gb300 import build
+        build.build()
+    L = hx.lib()
+    protos = _prototypes()
+    assert sorted(protos) == sorted(hx.EXPORTS)
+    rets = {"hx_status": ctypes.c_int32, "void": None, "const char *": ctypes.c_char_p, "uint64_t": ctypes.c_uint64}
+    for name, (ret, params) in protos.items():
+        f = getattr(L, name)
+        assert f.restype is rets[ret], name
+        assert len(f.argtypes) == len(params), (name, params)
+        for p, ct in zip(params, f.argtypes):
+            assert _matches(p, ct), (name, p, ct)
