@@ -11,6 +11,7 @@ Contents
   quadrature on [0, 1] (numpy's Legendre routines serve as library steps).
 * Fibre dispersion constants H11, H22, H33 from (a, b) (Sec. 3, bivariate von
   Mises dispersion; scipy's Bessel and error functions as library steps).
+* J^(-2/3) by the paper's fixed-count Newton iteration (Alg. 2), in FP64.
 * ctypes wrappers of hx_oracle.c: residual, tangent apply, diagonal, dense
   element matrices, energy, node coordinates, pointwise material evaluation.
 * Plain global algorithms built on those: Dirichlet-constrained operators,
@@ -127,6 +128,21 @@ def dispersion_H(a: float, b: float):
     H11 = 0.5 * (1.0 - H33) * (1.0 + r)
     H22 = 0.5 * (1.0 - H33) * (1.0 - r)
     return float(H11), float(H22), float(H33)
+
+
+def jpow_newton(J: float, n_steps: int) -> float:
+    """J^(-2/3) by the fixed-count Newton iteration of Sec. 3 ("stable and
+    fast numerics", Alg. 2): x solves f(x) = x^-3 - J^2 = 0, f'(x) = -3 x^-4,
+    starting from x_0 = 1 (the undeformed state) and taking n_steps updates
+    x <- x - f(x)/f'(x). Plain FP64 evaluation of the definition; the error
+    against the exact power is what the FP32 on-the-fly paths inherit."""
+    x = 1.0
+    J2 = J * J
+    for _ in range(n_steps):
+        f = x ** -3 - J2
+        df = -3.0 * x ** -4
+        x = x - f / df
+    return x
 
 
 @dataclass

@@ -44,10 +44,47 @@ def _sources_digest(extra: str) -> str:
     return h.hexdigest()
 
 
+def strip_comments(src: str) -> str:
+    """C/C++/CUDA source with every comment replaced by one space and every
+    run of whitespace collapsed to one space; string and character literals
+    are kept as they are."""
+    out = []
+    i, n = 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+            out.append(" ")
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def kernel_digest() -> str:
-    """Digest of the kernel and C-ABI sources alone (no flags): profile
-    summaries record it so that their counters can be matched to the code."""
-    return _sources_digest("")
+    """Digest of the kernel and C-ABI sources (csrc/ and include/) with
+    comments and formatting removed: profile summaries record it so that their
+    counters can be matched to the code, and an edit that changes only
+    comments leaves it as it was."""
+    h = hashlib.sha256()
+    for d in (CSRC, INC):
+        for f in sorted(os.listdir(d)):
+            if f.endswith((".cu", ".h", ".cuh", ".cpp")):
+                with open(os.path.join(d, f), encoding="utf-8") as fh:
+                    h.update(f.encode())
+                    h.update(strip_comments(fh.read()).encode())
+    return h.hexdigest()
 
 
 def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:
