@@ -6,7 +6,7 @@ fastest of the three quadrature-point storage strategies. One step is one
 tangent apply K(u_k) du over the whole mesh (gather, sum-factorized gradient,
 quadrature-point material tangent, integration, scatter: one fused kernel plus
 the zeroing of the output). The qp cache is refreshed once before timing, as
-in the paper's protocol (Sec. 6.2). Metric: GDoF/s over all 3*n_nodes DoFs.
+in the paper's protocol (Sec. 7.2). Metric: GDoF/s over all 3*n_nodes DoFs.
 
 Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 For N > 1 (torchrun) every rank runs an independent replica (weak scaling, no
@@ -373,7 +373,7 @@ def run_solve(device, n=48, p=4, tol=1e-8, max_iter=20000, degree=5, smoothing_r
 
 
 def run_stability(device):
-    """Forward-stability study (Sec. 6.1): 200 strain scales 1e-8..1e2, 1000
+    """Forward-stability study (Sec. 7.1): 200 strain scales 1e-8..1e2, 1000
     samples each, FP32 vs FP64 with the stable and the standard forms, per
     law; reports every 20th scale of the relative-error curves of P and dP."""
     import math

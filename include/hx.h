@@ -9,7 +9,7 @@
  * for three laws (Sec. 3): compressible neo-Hookean (cNH, Eq. NH_compressible),
  * nearly incompressible neo-Hookean (iNH, Eq. NH_nearly_incompressible) and the
  * two-family dispersed fibre model (fiber, Eq. fiber_Psi), in FP64 or FP32,
- * with the quadrature-point storage strategies of Sec. 4 / Table 2.
+ * with the quadrature-point storage strategies of Sec. 5 / Table 2.
  *
  * Discretisation: Lagrange polynomials of degree p on the p+1
  * Gauss-Lobatto-Legendre points per direction, (p+1)^3 Gauss-Legendre
@@ -61,7 +61,7 @@ typedef enum {
 typedef enum { HX_CNH = 0, HX_INH = 1, HX_FIBER = 2 } hx_law;
 typedef enum { HX_FP64 = 0, HX_FP32 = 1 } hx_prec;
 
-/* Storage strategies of Sec. 4 (material configuration), refreshed by
+/* Storage strategies of Sec. 5 (material configuration), refreshed by
  * hx_precompute_qp once per Newton state (Alg. 1, "update quadrature point
  * data"):
  *   HX_RECOMPUTE      nothing per qp but the geometry; the tangent re-reads
@@ -74,7 +74,7 @@ typedef enum { HX_FP64 = 0, HX_FP32 = 1 } hx_prec;
  *                     paper's stage iii "scalars and tensors".
  * Geometry (J0^-1 and JxW per qp) is stored once at mesh setup for all three.
  *   HX_SPATIAL_TENSORS integration over the spatial configuration (Sec. 2,
- *                     Eq. stress_term_in_Ot_with_JC; Sec. 4 "spatial
+ *                     Eq. stress_term_in_Ot_with_JC; Sec. 5 "spatial
  *                     integration" paragraphs; Table 2, Omega_t, tensors):
  *                     the tangent is (grad v, Jc:(grad du)^S + (grad du) tau)
  *                     over Omega_0 with grad = Grad F^-1. Stored per qp: the
@@ -138,7 +138,7 @@ hx_status hx_sync(hx_ctx *ctx, int timeout_ms);
 /* ---- mesh --------------------------------------------------------------- */
 /* Upload a mesh and compute the geometry at every quadrature point (J0^-1 and
  * JxW, FP64 and FP32 copies). Fails with HX_ERR_NONINVERTIBLE if some
- * quadrature point has det J0 <= 0 (mapping check, Sec. 5). Synchronous. */
+ * quadrature point has det J0 <= 0 (mapping check, Sec. 6). Synchronous. */
 hx_status hx_setup_mesh(hx_ctx *ctx, const hx_mesh_desc *desc, const hx_material *mat, hx_mesh **mesh);
 void hx_destroy_mesh(hx_mesh *mesh);
 /* Number of DoF nodes, elements and quadrature points of a mesh. */
@@ -156,7 +156,7 @@ hx_status hx_apply_bytes(const hx_mesh *mesh, int32_t storage, int32_t prec, dou
  * interpolate Grad u_k with sum factorization and store what the strategy
  * keeps, computed in FP64 (J-1 from the components of Grad u, ln J as
  * ln_{+1}(J-1), J^-2/3 exactly) and stored in store_prec. This is Alg. 1's
- * "update quadrature point data" (Sec. 4). The first call per mesh allocates
+ * "update quadrature point data" (Sec. 5). The first call per mesh allocates
  * the cache (call it before any stream capture). Returns HX_ERR_ARG for a bad
  * argument, HX_ERR_CUDA if an allocation or launch fails, else HX_OK without
  * waiting: a J <= 0 or non-finite value met at a quadrature point sets the
@@ -167,7 +167,7 @@ hx_status hx_precompute_qp(hx_mesh *mesh, const double *u_dev, int32_t store_pre
  * is recomputed from u at every quadrature point (no cache needed). */
 hx_status hx_residual(hx_mesh *mesh, const void *u_dev, void *r_dev, int32_t prec);
 
-/* out = K(u_k) du (Sec. 2, Eq. DDu_residual_material; Sec. 4 storage forms),
+/* out = K(u_k) du (Sec. 2, Eq. DDu_residual_material; Sec. 5 storage forms),
  * using the cache of the last hx_precompute_qp; `prec` must equal its
  * store_prec. du_dev and out_dev must not overlap. */
 hx_status hx_tangent_apply(hx_mesh *mesh, const void *du_dev, void *out_dev, int32_t prec);
@@ -196,10 +196,10 @@ hx_status hx_autotune(hx_mesh *mesh, int32_t prec, const void *du_dev, void *out
 hx_status hx_set_apply_variant(hx_mesh *mesh, int32_t prec, int32_t storage, int32_t variant);
 
 /* diag(K(u_k)), constrained entries 1 (needed by the Jacobi smoother,
- * Sec. 5); sum-factorized from the per-qp tangent blocks. */
+ * Sec. 6); sum-factorized from the per-qp tangent blocks. */
 hx_status hx_diagonal(hx_mesh *mesh, void *diag_dev, int32_t prec);
 
-/* `degree` steps of Chebyshev-accelerated Jacobi on K x = rhs (Sec. 5,
+/* `degree` steps of Chebyshev-accelerated Jacobi on K x = rhs (Sec. 6,
  * smoother), in place on x, eigenvalue interval
  * [lambda_max/smoothing_range, lambda_max] of D^-1 K, inv_diag = D^-1.
  * zero_initial != 0 treats x as zero on entry (saves one operator apply).
@@ -233,7 +233,7 @@ hx_status hx_estimate_lambda_max(hx_mesh *mesh, const double *inv_diag_dev, int3
                                  double *out);
 
 /* FP64 preconditioned CG on K(u_k) x = rhs (constrained operator), with a
- * Chebyshev(degree)-Jacobi preconditioner applied in precond_prec (Sec. 5:
+ * Chebyshev(degree)-Jacobi preconditioner applied in precond_prec (Sec. 6:
  * FP64 outer Krylov, FP32 preconditioner). x_dev holds the start and
  * receives the solution; stops when ||rhs - K x|| <= tol ||rhs|| (true
  * residual rechecked at exit) or after max_iter iterations
@@ -251,7 +251,7 @@ hx_status hx_cg_solve(hx_mesh *mesh, const double *rhs_dev, double *x_dev, doubl
                       const hx_cg_options *opt, int32_t *iters, double *rel_residual);
 
 /* Pointwise evaluation of the mesh's law for the forward-stability study
- * (Sec. 6.1): at n displacement gradients G (Grad u) and directions H, all
+ * (Sec. 7.1): at n displacement gradients G (Grad u) and directions H, all
  * FP64 device arrays [n][9] row-major, compute S, P = F S and dP = H S +
  * F D_uS[H] ([n][9], FP64 device) in precision `prec` (inputs rounded to it
  * first). form 0: the stable forms of Sec. 4 (J-1 from the components of G,
@@ -306,7 +306,7 @@ typedef struct {
 hx_status hx_newton_solve(hx_mesh *mesh, double *u_dev, const double *f_ext_dev, const hx_newton_options *opt,
                           hx_newton_report *report);
 
-/* ---- p-multigrid preconditioner (Sec. 5) -------------------------------- */
+/* ---- p-multigrid preconditioner (Sec. 6) -------------------------------- */
 /* Levels of degree p, floor(p/2), ... down to min_degree, built on the mesh's structured box
  * (same elements and geometry; the Dirichlet constraints must be whole faces,
  * component by component, and are carried to every level; other meshes give

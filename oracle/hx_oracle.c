@@ -27,7 +27,7 @@
  *   iNH   Psi = mu/2 (J^-2/3 I1 - 3) + kappa/4 (J^2 - 1 - 2 ln J)          Eq. (NH_nearly_incompressible)
  *         S = mu J^-2/3 I + [kappa/2 (J^2-1) - mu/3 J^-2/3 I1] C^-1
  *         D_uS as Eq. (NH_DDuS) of App. A, whose D_uC^-1 term carries the sign
- *         that follows from differentiating S (the Sec. 4 restatement prints
+ *         that follows from differentiating S (the Sec. 5 restatement prints
  *         the opposite sign in front of 2 c1 [F^-1 H C^-1]^S; it is not used)
  *   fiber Psi = Psi_iNH + sum_{i=4,6} k1/(2 k2) [exp(k2 E_i^2) - 1] if I_i* > 1  Eq. (fiber_Psi)
  *         E_i = H_i : C - 1,  I_i* = M1.C M1,  H_i = sum_k H_kk M_k (x) M_k      Eq. (fiber_Ei)
@@ -272,7 +272,7 @@ static void law_dP(const orc_material *m, const orc_fibres *fb, const orc_state 
     for (int i = 0; i < 9; ++i) dP[i] = T1[i] + T2[i];
 }
 
-/* Spatial quantities of Sec. 4 ("spatial integration" paragraphs), from the
+/* Spatial quantities of Sec. 5 ("spatial integration" paragraphs), from the
  * definitions: b = F F^T, the Kirchhoff stress tau = F S F^T written per law,
  * and the action of the pushed-forward moduli J c on a symmetric tensor e:
  *   cNH   tau = mu b - (mu - 2 lambda ln J) I
@@ -281,9 +281,9 @@ static void law_dP(const orc_material *m, const orc_fibres *fb, const orc_state 
  *         Jc:e = -2 c1 e + c2 tr(e) I - 2 mu/3 J^-2/3 [tr(e) b + (b:e) I]
  *   fiber tau += sum_i c3 E_i F H_i F^T
  *         Jc:e += sum_i 2 c3 (2 k2 E_i^2 + 1) [(F H_i F^T) : e] F H_i F^T
- * with c1, c2 of Sec. 4 and c3 = 2 k1 exp(k2 E_i^2) for an active family.
+ * with c1, c2 of Sec. 5 and c3 = 2 k1 exp(k2 E_i^2) for an active family.
  * The iNH moduli are the push-forward of the material D_uS of App. A: its
- * I (x) C^-1 part maps to tr(e) b + (b:e) I (the Sec. 4 restatement prints
+ * I (x) C^-1 part maps to tr(e) b + (b:e) I (the Sec. 5 restatement prints
  * -4 mu/3 J^-2/3 tr(e) C instead; that form is not used). */
 static void law_tau(const orc_material *m, const orc_fibres *fb, const orc_state *s, double *b, double *tau) {
     double Ft[9];

@@ -18,7 +18,7 @@ Contents
   sparse assembly, the Chebyshev-Jacobi smoother (Chebyshev acceleration as
   in Saad, "Iterative Methods for Sparse Linear Systems", Sec. 12.3, applied
   to D^-1 K), and preconditioned CG (Saad, Alg. 9.1, with the Polak-Ribiere
-  beta so an inexact preconditioner is tolerated) -- the paper's Sec. 5
+  beta so an inexact preconditioner is tolerated) -- the paper's Sec. 6
   smoother and outer Krylov solver.
 """
 from __future__ import annotations
@@ -131,7 +131,7 @@ def dispersion_H(a: float, b: float):
 
 
 def jpow_newton(J: float, n_steps: int) -> float:
-    """J^(-2/3) by the fixed-count Newton iteration of Sec. 3 ("stable and
+    """J^(-2/3) by the fixed-count Newton iteration of Sec. 4 ("stable and
     fast numerics", Alg. 2): x solves f(x) = x^-3 - J^2 = 0, f'(x) = -3 x^-4,
     starting from x_0 = 1 (the undeformed state) and taking n_steps updates
     x <- x - f(x)/f'(x). Plain FP64 evaluation of the definition; the error
@@ -263,7 +263,7 @@ def apply(M: OracleMesh, mat: Material, u, du, elems=None) -> np.ndarray:
 
 def apply_spatial(M: OracleMesh, mat: Material, u, du, elems=None) -> np.ndarray:
     """K(u) du in the spatial form of Sec. 2, Eq. (stress_term_in_Ot_with_JC):
-    (grad v, Jc:(grad du)^S + (grad du) tau) with the Sec. 4 spatial tau and
+    (grad v, Jc:(grad du)^S + (grad du) tau) with the Sec. 5 spatial tau and
     Jc per law (iNH moduli pushed forward from App. A). Equal to apply() in
     exact arithmetic."""
     u = _vec(u, M.n_dofs)
@@ -392,7 +392,7 @@ def diagonal_constrained(M: OracleMesh, mat: Material, u):
 
 
 # ---------------------------------------------------------------------------
-# Chebyshev-Jacobi smoother and preconditioned CG (Sec. 5)
+# Chebyshev-Jacobi smoother and preconditioned CG (Sec. 6)
 # ---------------------------------------------------------------------------
 
 def chebyshev_smooth(Kop, rhs, x, inv_diag, degree, lambda_max, smoothing_range, zero_initial=False):

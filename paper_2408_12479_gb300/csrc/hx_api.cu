@@ -1332,7 +1332,7 @@ hx_status hx_material_eval(hx_mesh *m, int32_t elem, int32_t form, int32_t prec,
 }
 
 // ---------------------------------------------------------------------------
-// p-multigrid preconditioner (Sec. 5): degrees p, floor(p/2), ..., 1 on the
+// p-multigrid preconditioner (Sec. 6): degrees p, floor(p/2), ..., 1 on the
 // same structured box, Chebyshev-Jacobi smoothing on every level, Chebyshev
 // iterations on the coarsest, transfers by interpolation between the
 // Lagrange spaces (prolongation) and its transpose (restriction)

@@ -4,7 +4,7 @@
 // enclosing namespaces; this file has no include guard on purpose.
 //
 // Per element the operators follow the same pipeline (Sec. 2 weak forms,
-// sum factorization as in the paper's matrix-free setting, Sec. 5):
+// sum factorization as in the paper's matrix-free setting, Sec. 6):
 //   gather      x-rows of u_e <- u[conn(e)] into registers
 //   interpolate V = (B (x) B (x) B) u_e                  three 1D sweeps
 //   gradient    dV/dxi_d = D_d V (collocation on the Gauss points, q = p+1)
@@ -674,11 +674,11 @@ __device__ __forceinline__ void pull_flux(const T *P, const T *Ji, T JxW, T *Q) 
 
 // ---------------------------------------------------------------------------
 // Integration over the spatial configuration (Sec. 2, Eq.
-// stress_term_in_Ot_with_JC; Sec. 4 "spatial integration" paragraphs). With
+// stress_term_in_Ot_with_JC; Sec. 5 "spatial integration" paragraphs). With
 // g = grad du = (Grad du) F^-1 = G J_t^-1 (J_t = F J0, the deformed mapping)
 // the tangent integrand is (grad v) : [Jc:g^S + g tau] over Omega_0, i.e.
 //   Q = JxW (Jc:g^S + g tau) J_t^-T.
-// Per law (c1, c2 of Sec. 4; b = F F^T; h_i = F H_i F^T; j = J^-2/3; the iNH
+// Per law (c1, c2 of Sec. 5; b = F F^T; h_i = F H_i F^T; j = J^-2/3; the iNH
 // moduli pushed forward from the material D_uS, whose I (x) C^-1 part gives
 // tr(e) b + (b:e) I):
 //   cNH:   tau = mu b - c I,  Jc:e = 2c e + 2 lambda tr(e) I,  c = mu - 2 lambda ln J
@@ -2068,7 +2068,7 @@ __global__ void __launch_bounds__(threads_for(2)) k_diagonal(const hx::MeshView 
 }
 
 // ---------------------------------------------------------------------------
-// Pointwise law evaluation for the forward-stability study (Sec. 6.1): S,
+// Pointwise law evaluation for the forward-stability study (Sec. 7.1): S,
 // P = F S and dP = H S + F D_uS[H] at Grad u = G in this unit's precision.
 // FORM 0: the stable forms with J^-2/3 = exp(-2/3 ln_{+1}(J-1)); FORM 1: the
 // stable forms with Alg. 2 for J^-2/3; FORM 2: the standard forms, from

@@ -225,7 +225,7 @@ class SlabSystem:
 
     def chebyshev(self, rhs, x, inv_diag, degree, lambda_max, smoothing_range, zero_initial=False):
         """degree steps of Chebyshev-accelerated Jacobi on K_c x = rhs
-        (Sec. 5 smoother; the same three-term recurrence as the single-mesh
+        (Sec. 6 smoother; the same three-term recurrence as the single-mesh
         smoother over the interval [lambda_max/smoothing_range, lambda_max]
         of D^-1 K_c). Returns the new x."""
         a = lambda_max / smoothing_range

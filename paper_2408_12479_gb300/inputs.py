@@ -19,7 +19,7 @@ Conventions shared by every consumer (they describe the data, not the method):
 * Tube meshes: reference axes are (radial, circumferential, axial); the
   circumferential direction is periodic (no duplicated seam nodes).
 
-Workload shapes follow the paper's synthetic cubes (Sec. 6.2, Table 3) and the
+Workload shapes follow the paper's synthetic cubes (Sec. 7.2, Table 3) and the
 five workload descriptions of this project (small affine cube, jittered 32^3
 cube, 48^3 compressed cube, fibre-reinforced tube, batch of cubes).
 """

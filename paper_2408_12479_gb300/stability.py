@@ -1,4 +1,4 @@
-"""Forward-stability study of Sec. 6.1 on the GPU.
+"""Forward-stability study of Sec. 7.1 on the GPU.
 
 Displacement gradients G are sampled with every component uniform in
 [eps/10, eps] with a random sign, for scales eps from 1e-8 to 1e2; at each

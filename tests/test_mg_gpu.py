@@ -1,4 +1,4 @@
-"""p-multigrid (Sec. 5) through the C ABI: level transfers against the
+"""p-multigrid (Sec. 6) through the C ABI: level transfers against the
 oracle's dense transfer matrices, and the V-cycle-preconditioned CG against
 a direct solve of the oracle's assembled constrained tangent."""
 import numpy as np

@@ -313,7 +313,7 @@ def test_tangent_is_residual_derivative_and_symmetric(law):
 @pytest.mark.parametrize("law", ["cNH", "iNH", "fiber"])
 def test_spatial_form_tangent_is_residual_derivative(law):
     """The spatial-configuration tangent (Sec. 2 Eq. stress_term_in_Ot_with_JC
-    with the Sec. 4 tau and Jc, iNH moduli pushed forward from App. A) is the
+    with the Sec. 5 tau and Jc, iNH moduli pushed forward from App. A) is the
     derivative of the material residual and equals the material-form tangent."""
     m, mat = _small(law)
     M = O.OracleMesh(m)
@@ -495,3 +495,22 @@ def test_transfer_matrix_reproduces_coarse_polynomials(pc, pf):
     assert np.abs(P @ vc - vf).max() < 1e-12
     # rows sum to one (partition of unity)
     assert np.abs(P.sum(axis=1) - 1.0).max() < 1e-13
+
+
+@pytest.mark.parametrize("J", [0.8, 0.9, 0.95, 1.05, 1.1, 1.2])
+def test_jpow_newton_converges_quadratically_to_the_power(J):
+    """Alg. 2 (Sec. 4): Newton on x^-3 = J^2 from x = 1 reaches J^(-2/3)
+    (closed form by the library cube root) and its error squares each step
+    with Newton's constant |f''/(2 f')| = 2/x at the root."""
+    exact = 1.0 / np.cbrt(J) ** 2
+    errs = [abs(O.jpow_newton(J, n) - exact) for n in range(0, 7)]
+    assert errs[6] <= 4e-16 * exact
+    for k in range(len(errs) - 1):
+        if errs[k] > 1e-6:  # above rounding: the quadratic model holds
+            ratio = errs[k + 1] / errs[k] ** 2
+            assert abs(ratio / (2.0 / exact) - 1.0) < 0.25 + 3.0 * errs[k], (k, ratio)
+
+
+def test_jpow_newton_exact_at_rest():
+    for n in range(0, 5):
+        assert O.jpow_newton(1.0, n) == 1.0

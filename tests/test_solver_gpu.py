@@ -1,4 +1,4 @@
-"""GPU checks of the solver layer (Sec. 5): power-iteration eigenvalue bound,
+"""GPU checks of the solver layer (Sec. 6): power-iteration eigenvalue bound,
 FP64 CG with an FP32 (or FP64) Chebyshev-Jacobi preconditioner captured as a
 CUDA graph, and the autograd wrapper whose backward is the tangent kernel."""
 import numpy as np

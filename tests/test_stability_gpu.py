@@ -1,4 +1,4 @@
-"""Forward-stability study (Sec. 6.1) on the GPU: the pointwise law
+"""Forward-stability study (Sec. 7.1) on the GPU: the pointwise law
 evaluation in FP64 (stable and standard forms) matches the oracle's
 textbook evaluation; in FP32 the stable forms keep small relative errors
 down to strains of 1e-8 while the standard forms lose accuracy by

@@ -1,4 +1,4 @@
-"""Host logic of the forward-stability study (Sec. 6.1) on the CPU: the
+"""Host logic of the forward-stability study (Sec. 7.1) on the CPU: the
 sampling of displacement gradients, the per-sample normwise error, and the
 skipping of samples that are not deformations (det(I + G) <= 0), with a
 stand-in pointwise evaluation in place of the device kernel."""
