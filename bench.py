@@ -183,6 +183,39 @@ def _event_ms(fn, steps, warmup):
     return e0.elapsed_time(e1) / steps
 
 
+def sweep_flops(n_elem, p):
+    """Algorithmic flops of the sum-factorized sweeps of one tangent apply:
+    per element and component, three interpolation sweeps and three
+    collocation-derivative sweeps forward and their transposes backward, each
+    (p+1)^3 outputs of (p+1) multiply-adds: 72 (p+1)^4 flops per element. The
+    plain count (no even-odd saving) and without the quadrature-point work, so
+    the pipe fraction built on it is a lower bound."""
+    return 72 * (p + 1) ** 4 * n_elem
+
+
+def fma_peaks(device):
+    """Measured FP64 and FP32 FMA peaks of the device (hx_measure_fma_peak),
+    in TFLOP/s; an error is recorded instead if the probe fails."""
+    from paper_2408_12479_gb300 import hx
+    ctx = None
+    try:
+        ctx = hx.hx_create(device)
+        return {"fp64_tflops": round(hx.hx_measure_fma_peak(ctx, hx.HX_FP64) / 1e12, 3),
+                "fp32_tflops": round(hx.hx_measure_fma_peak(ctx, hx.HX_FP32) / 1e12, 3)}
+    except Exception as exc:  # recorded in the report; the headline line still prints
+        return {"error": str(exc)[:200]}
+    finally:
+        if ctx is not None:
+            hx.hx_destroy(ctx)
+
+
+def pipe_fraction(n_elem, p, ms, prec_name, peaks_fp):
+    """(sweep TFLOP/s, fraction of the measured FMA peak of that precision)."""
+    tf = sweep_flops(n_elem, p) / (ms * 1e-3) / 1e12
+    peak = (peaks_fp or {}).get("fp64_tflops" if prec_name == "f64" else "fp32_tflops")
+    return round(tf, 3), (round(tf / peak, 4) if peak else None)
+
+
 def residual_bytes(n_dofs, n_qp, s):
     """Algorithmic bytes of one cNH residual: read u, write r, and the stored
     J0^-1 (9) and JxW (1) per quadrature point; the state is recomputed from u
@@ -610,7 +643,9 @@ def main():
                "d2h_bytes_per_step": bytes_vec}
 
     sweep = []
+    peaks_fp = None
     if rank == 0 and not args.no_sweep:
+        peaks_fp = fma_peaks(local)
         G.close()
         del u, du, out
         torch.cuda.empty_cache()
@@ -621,7 +656,9 @@ def main():
                     reps = 30 if pr == hx.HX_FP32 else 5
                     t = time_steps(Gs, dus, outs, reps, 2)
                     b = Gs.apply_bytes(st, pr)
+                    tf, pf = pipe_fraction(ms_.n_elem, pp, t, "f32" if pr else "f64", peaks_fp)
                     sweep.append({"p": pp, "prec": "f32" if pr else "f64", "storage": hx.STORAGE_NAMES[st],
+                                  "sweep_tflops": tf, "fma_frac": pf,
                                   "n_dofs": ms_.n_dofs, "ms": round(t, 4),
                                   "gdofs": round(ms_.n_dofs / (t * 1e-3) / 1e9, 3),
                                   "tile_variant": Gs.tune[0], "variant_ms": [round(x, 4) for x in Gs.tune[1]],
@@ -672,6 +709,7 @@ def main():
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
+            "fma_peaks": peaks_fp,
             "sweep": sweep,
             "residual": resid,
             "newton_step_costs": step_costs,

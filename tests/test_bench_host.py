@@ -127,3 +127,36 @@ def test_newton_step_costs_in_applies(fake_gpu):
     assert (hx.HX_FP32, hx.HX_SPATIAL_TENSORS) in [(c[1], c[2]) for c in pre]
     assert (hx.HX_FP64, hx.HX_CACHE_TENSORS) in [(c[1], c[2]) for c in pre]
     assert np.isfinite([r["precompute_ms"] for r in res]).all()
+
+
+@pytest.mark.parametrize("p", [1, 2, 4, 6])
+def test_sweep_flops_counts_every_sweep(p):
+    """Count the sweeps one by one: per component, forward interpolation in
+    x, y, z (each n^3 outputs of n multiply-adds), the three collocation
+    derivatives (same size), and the transposes of all six backward."""
+    n = p + 1
+    per_sweep = n ** 3 * n * 2           # n^3 outputs, n FMAs (2 flops) each
+    forward = 3 * (3 + 3) * per_sweep    # 3 components x (3 interpolation + 3 derivative sweeps)
+    assert bench.sweep_flops(1, p) == 2 * forward
+    assert bench.sweep_flops(10, p) == 10 * bench.sweep_flops(1, p)
+
+
+def test_fma_peaks_and_pipe_fraction(monkeypatch):
+    calls = []
+    monkeypatch.setattr(hx, "hx_create", lambda device=0, stream=None: "ctx")
+    monkeypatch.setattr(hx, "hx_destroy", lambda ctx: calls.append(("destroy", ctx)))
+    monkeypatch.setattr(hx, "hx_measure_fma_peak",
+                        lambda ctx, prec: 1.25e12 if prec == hx.HX_FP64 else 75e12)
+    pk = bench.fma_peaks(0)
+    assert pk == {"fp64_tflops": 1.25, "fp32_tflops": 75.0} and calls == [("destroy", "ctx")]
+    # 10 elements of p = 2 in 1 ms: 72 * 81 * 10 flops / 1e-3 s
+    tf, frac = bench.pipe_fraction(10, 2, 1.0, "f64", pk)
+    assert tf == pytest.approx(round(72 * 81 * 10 / 1e-3 / 1e12, 3))
+    assert frac == pytest.approx(round(72 * 81 * 10 / 1e-3 / 1.25e12, 4))
+    assert bench.pipe_fraction(10, 2, 1.0, "f32", {"error": "x"})[1] is None
+
+    def boom(ctx, prec):
+        raise hx.HxError(hx.HX_ERR_CUDA, "probe failed")
+    monkeypatch.setattr(hx, "hx_measure_fma_peak", boom)
+    pk = bench.fma_peaks(0)
+    assert "probe failed" in pk["error"] and calls[-1] == ("destroy", "ctx")
