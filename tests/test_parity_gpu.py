@@ -323,3 +323,50 @@ def test_autotune_keeps_results():
         assert rel_inf(res, ref) < 1e-5
     finally:
         G.close()
+
+
+def test_full_size_headline_configuration_sampled():
+    """The benchmark's timed configuration at its full size: 32^3 jittered
+    cube, p = 4, FP32, spatial-tensors cache, the variant the autotuner keeps
+    and then every variant that launches (staged ones included), checked on
+    sampled DoFs (random nodes, corners, face nodes) against the oracle."""
+    p = 4
+    m, field, seed = I.workload_jittered_cube(p)
+    M = O.OracleMesh(m)
+    X = O.node_coords(M)
+    u = field(X).ravel()
+    du = I.random_direction(m.n_dofs, seed + 3)
+    mat = cases.oracle_material("cNH")
+    g = np.random.Generator(np.random.PCG64(seed + 7))
+    Np = 32 * p + 1
+    corners = [i + Np * (j + Np * k) for i in (0, Np - 1) for j in (0, Np - 1) for k in (0, Np - 1)]
+    faces = [Np // 2 + Np * (Np // 3), 7 + Np * Np * (Np // 2), Np - 1 + Np * (5 + Np * 9)]
+    nodes = np.unique(np.concatenate([g.choice(m.n_nodes, size=64, replace=False), corners, faces]))
+    elems = _adjacent_elements(m.dof_conn, nodes)
+    dofs = (3 * nodes[:, None] + np.arange(3)).ravel()
+    G = hx.Mesh(m, cases.MATS["cNH"])
+    try:
+        G.precompute(cuda(u), hx.HX_FP32, hx.HX_SPATIAL_TENSORS)
+        du_t = cuda(du, hx.HX_FP32)
+        out = torch.empty_like(du_t)
+        best, times = hx.hx_autotune(G.ctx, G.handle, du_t, out, reps=2)
+        assert best in range(6) and times[best] > 0
+        ref = O.apply(M, mat, u, host(du_t), elems=elems)
+        scale = np.abs(ref[dofs]).max()
+        res = host(G.apply(du_t))
+        G.sync(120000)
+        assert np.abs(res[dofs] - ref[dofs]).max() / scale < TOL[hx.HX_FP32], best
+        ran = []
+        for variant in range(6):
+            hx.hx_set_apply_variant(G.ctx, G.handle, hx.HX_FP32, hx.HX_SPATIAL_TENSORS, variant)
+            try:
+                res = host(G.apply(du_t))
+            except hx.HxError as e:
+                assert variant >= 2 and e.status == hx.HX_ERR_CUDA, (variant, str(e))
+                continue
+            G.sync(120000)
+            assert np.abs(res[dofs] - ref[dofs]).max() / scale < TOL[hx.HX_FP32], variant
+            ran.append(variant)
+        assert 0 in ran and any(v >= 3 for v in ran), ran
+    finally:
+        G.close()
