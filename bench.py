@@ -216,6 +216,65 @@ def pipe_fraction(n_elem, p, ms, prec_name, peaks_fp):
     return round(tf, 3), (round(tf / peak, 4) if peak else None)
 
 
+def _rel_inf(a, b):
+    """max |a - b| / max |b| (the parity tests' error measure)."""
+    return float((a - b).abs().max() / b.abs().max())
+
+
+def fp32_error_case(law, n=16, p=4):
+    """Mesh, material and state of the FP32-error report for one law: the
+    n^3 jittered cube at degree p with its 5 % sine state; for the fibre law
+    per-element frames along the axes (families in the x-y plane at +-40
+    degrees) and x, y stretched by 8 % so that every I* is well above 1."""
+    from paper_2408_12479_gb300 import inputs as I
+    m, field, seed = I.workload_jittered_cube(p, n=n)
+    mat = {"cNH": I.MAT_CNH, "iNH": I.MAT_INH, "fiber": I.MAT_FIBER}[law]
+    if law == "fiber":
+        m.frames = I.constant_frames(m.n_elem)
+        field.affine = np.diag([0.08, 0.08, 0.0])
+        field.x0 = np.zeros(3)
+    return m, dict(mat), field, seed
+
+
+def run_fp32_errors(device, n=16, p=4):
+    """Error of every FP32 result against the FP64 result of the same call on
+    the same inputs (the FP64 path matches the oracle to 1e-12 in the parity
+    tests): residual, tangent apply per storage strategy, diagonal; per law.
+    FP32 calls get the FP32-rounded vectors and the FP64 calls the same
+    values, so only arithmetic differences are measured."""
+    import torch
+    from paper_2408_12479_gb300 import hx
+    from paper_2408_12479_gb300 import inputs as I
+    res = {}
+    for law in ("cNH", "iNH", "fiber"):
+        rec = {}
+        G = None
+        try:
+            m, mat, field, seed = fp32_error_case(law, n, p)
+            G = hx.Mesh(m, mat, device=device)
+            X = G.node_coords().cpu().numpy()
+            u64 = torch.tensor(field(X).ravel(), dtype=torch.float64, device=G.device)
+            u32 = u64.float()
+            du32 = torch.tensor(I.random_direction(m.n_dofs, seed + 3), dtype=torch.float32, device=G.device)
+            rec["residual"] = _rel_inf(G.residual(u32).double(), G.residual(u32.double()))
+            for st in (hx.HX_RECOMPUTE, hx.HX_CACHE_F, hx.HX_CACHE_TENSORS, hx.HX_SPATIAL_TENSORS):
+                G.precompute(u64, hx.HX_FP64, st)
+                G.precompute(u64, hx.HX_FP32, st)
+                rec["tangent_" + hx.STORAGE_NAMES[st]] = _rel_inf(G.apply(du32).double(), G.apply(du32.double()))
+            rec["diagonal"] = _rel_inf(G.diagonal(hx.HX_FP32).double(), G.diagonal(hx.HX_FP64))
+            G.sync(60000)
+            rec = {k: float("%.3g" % v) for k, v in rec.items()}
+        except Exception as exc:  # recorded in the report; the headline line still prints
+            rec["error"] = str(exc)[:200]
+        finally:
+            if G is not None:
+                G.close()
+            torch.cuda.empty_cache()
+        res[law] = rec
+    res["workload"] = f"{n}^3 jittered cube, p={p}, 5 % sine state (fibre: +8 % x, y stretch)"
+    return res
+
+
 def residual_bytes(n_dofs, n_qp, s):
     """Algorithmic bytes of one cNH residual: read u, write r, and the stored
     J0^-1 (9) and JxW (1) per quadrature point; the state is recomputed from u
@@ -667,10 +726,11 @@ def main():
                     del us, dus, outs
                     torch.cuda.empty_cache()
 
-    resid = step_costs = None
+    resid = step_costs = fp32_err = None
     if rank == 0 and not args.no_sweep:
         resid = run_residual_sweep(local, hbm_peak)
         step_costs = run_newton_step_costs(local, p)
+        fp32_err = run_fp32_errors(local)
 
     batch = None
     if rank == 0 and not args.no_sweep:
@@ -713,6 +773,7 @@ def main():
             "sweep": sweep,
             "residual": resid,
             "newton_step_costs": step_costs,
+            "fp32_error": fp32_err,
             "batch": batch,
             "solve": solve,
             "newton": newton,

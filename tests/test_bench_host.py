@@ -160,3 +160,50 @@ def test_fma_peaks_and_pipe_fraction(monkeypatch):
     monkeypatch.setattr(hx, "hx_measure_fma_peak", boom)
     pk = bench.fma_peaks(0)
     assert "probe failed" in pk["error"] and calls[-1] == ("destroy", "ctx")
+
+
+class _FakeOpMesh(_FakeMesh):
+    """Operators as exact functions of their inputs, evaluated in the input's
+    precision: the FP32 and FP64 calls agree up to FP32 rounding."""
+
+    def residual(self, u, out=None):
+        if self.input.frames is not None and _FakeOpMesh.fail_fiber:
+            raise hx.HxError(hx.HX_ERR_NAN, "stand-in failure")
+        return u * 2.0 + 1e-3
+
+    def apply(self, du, out=None):
+        return du / 3.0
+
+    def diagonal(self, prec=hx.HX_FP64):
+        return self.zeros(prec) + (1.0 / 3.0)
+
+
+def test_fp32_errors_report_every_result_per_law(fake_gpu, monkeypatch):
+    monkeypatch.setattr(hx, "Mesh", _FakeOpMesh)
+    _FakeOpMesh.fail_fiber = False
+    res = bench.run_fp32_errors(0, n=2, p=2)
+    keys = {"residual", "diagonal", "tangent_recompute", "tangent_cache_F", "tangent_cache_tensors",
+            "tangent_spatial_tensors"}
+    for law in ("cNH", "iNH", "fiber"):
+        assert set(res[law]) == keys, res[law]
+        assert all(0.0 <= v < 1e-7 for v in res[law].values()), res[law]
+    # x/3 and 1/3 are not FP32 numbers: the FP32 results differ from the FP64 ones by rounding
+    assert res["cNH"]["tangent_cache_F"] > 0.0 and res["cNH"]["diagonal"] > 0.0
+    _FakeOpMesh.fail_fiber = True
+    res = bench.run_fp32_errors(0, n=2, p=2)
+    assert "stand-in failure" in res["fiber"]["error"] and "error" not in res["iNH"]
+
+
+def test_fp32_error_fibre_state_keeps_both_families_active():
+    """Every point of the fibre case has M1.C.M1 - 1 well above 0 for both
+    families, so FP32 and FP64 take the same fibre switch decisions."""
+    import math
+    from oracle import oracle as O
+    m, mat, field, seed = bench.fp32_error_case("fiber", n=4, p=2)
+    M = O.OracleMesh(m)
+    u = field(O.node_coords(M)).ravel()
+    _, _, F = O.qp_fields(M, u, np.arange(M.n_elem))
+    C = np.einsum("qki,qkj->qij", F.reshape(-1, 3, 3), F.reshape(-1, 3, 3))
+    for ph in (mat["phi"], -mat["phi"]):
+        M1 = np.array([math.cos(ph), math.sin(ph), 0.0])
+        assert np.einsum("i,qij,j->q", M1, C, M1).min() - 1.0 > 0.05
