@@ -533,10 +533,21 @@ def run_newton(device, n=8, p=4, stretch=1.1, steps=5):
     return res
 
 
+def host_cores() -> int:
+    """Host cores this process may run on (launchers such as torchrun set
+    OMP_NUM_THREADS=1 per rank; the CPU legs run on rank 0 alone and use all
+    cores)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 def cpu_baseline(m, field, seed, p, mat_d, target_s=12.0):
     """The FP64 oracle's full-tensor apply on a bounded sample of the same mesh
     (leading elements), on all host cores; scaled to GDoF/s of the whole mesh."""
     from oracle import oracle as O
+    O.set_threads(host_cores())
     M = O.OracleMesh(m)
     X = O.node_coords(M)
     u = field(X).ravel()
@@ -568,6 +579,7 @@ def run_reference(args):
         return
     from oracle import oracle as O
     from paper_2408_12479_gb300 import inputs as I
+    O.set_threads(host_cores())
     p = args.p
     m, field, seed = I.workload_jittered_cube(p)
     mat_d = dict(I.MAT_CNH)

@@ -207,3 +207,30 @@ def test_fp32_error_fibre_state_keeps_both_families_active():
     for ph in (mat["phi"], -mat["phi"]):
         M1 = np.array([math.cos(ph), math.sin(ph), 0.0])
         assert np.einsum("i,qij,j->q", M1, C, M1).min() - 1.0 > 0.05
+
+
+def test_reference_arm_line_uses_all_host_cores(capsys, monkeypatch):
+    """The reference arm (the oracle on the host cores) prints the contract's
+    JSON line and uses every host core even where the launcher pinned
+    OpenMP to one thread per rank."""
+    import argparse
+    import json
+    from oracle import oracle as O
+    monkeypatch.delenv("RANK", raising=False)
+    O.set_threads(1)
+    args = argparse.Namespace(p=2, steps=1, warmup=3, gpus=1)
+    bench.run_reference(args)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "GDoF/s"
+    assert line["value"] > 0 and line["higher_is_better"] is True and line["steps"] == 1
+    assert line["cpu_baseline"]["cores"] == bench.host_cores() == O.num_threads()
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "GDoF/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_do_nothing(capsys, monkeypatch):
+    import argparse
+    monkeypatch.setenv("RANK", "1")
+    bench.run_reference(argparse.Namespace(p=2, steps=1, warmup=3, gpus=2))
+    assert capsys.readouterr().out == ""
