@@ -49,3 +49,26 @@ def test_product_never_imports_the_oracle():
         # no path into the oracle's sources or its built library
         assert "hx_oracle" not in src and "libhx_oracle" not in src, path
     assert seen >= 10
+
+
+def test_oracle_shares_nothing_with_the_product():
+    """The oracle's Python side imports nothing from the package but (at
+    most) the seeded input recipes, and its C source includes only system
+    headers."""
+    odir = os.path.join(ROOT, "oracle")
+    for f in os.listdir(odir):
+        path = os.path.join(odir, f)
+        if f.endswith(".py"):
+            for node in ast.walk(ast.parse(open(path, encoding="utf-8").read())):
+                mods = []
+                if isinstance(node, ast.Import):
+                    mods = [a.name for a in node.names]
+                elif isinstance(node, ast.ImportFrom):
+                    mods = [(node.module or "") + "." + a.name for a in node.names]
+                for mname in mods:
+                    if mname.startswith("paper_2408_12479_gb300"):
+                        assert mname == "paper_2408_12479_gb300.inputs", (f, mname)
+        elif f.endswith((".c", ".h")):
+            for line in open(path, encoding="utf-8"):
+                if line.lstrip().startswith("#include"):
+                    assert "<" in line and '"' not in line, (f, line)
