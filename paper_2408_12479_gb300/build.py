@@ -72,16 +72,42 @@ def strip_comments(src: str) -> str:
     return " ".join("".join(out).split())
 
 
+def kernel_sources() -> set:
+    """The CUDA translation units (csrc/*.cu) and every header they include,
+    directly or not: the code that defines, launches and feeds the kernels.
+    Host-only units that no kernel unit includes are not part of it."""
+    import re
+    inc = re.compile(r'\s*#\s*include\s+"([^"]+)"')
+    stack = [os.path.join(CSRC, f) for f in sorted(os.listdir(CSRC)) if f.endswith(".cu")]
+    seen = set()
+    while stack:
+        path = os.path.normpath(stack.pop())
+        if path in seen:
+            continue
+        seen.add(path)
+        with open(path, encoding="utf-8") as fh:
+            for line in fh:
+                m = inc.match(line)
+                if m:
+                    for d in (os.path.dirname(path), CSRC, INC):
+                        cand = os.path.join(d, m.group(1))
+                        if os.path.exists(cand):
+                            stack.append(cand)
+                            break
+    return seen
+
+
 def kernel_digest() -> str:
-    """Digest of the kernel and C-ABI sources (csrc/ and include/) with
-    comments and formatting removed: profile summaries record it so that their
-    counters can be matched to the code, and an edit that changes only
-    comments leaves it as it was."""
+    """Digest of kernel_sources() with comments and formatting removed:
+    profile summaries record it so that their counters can be matched to the
+    code, and an edit that changes only comments leaves it as it was."""
+    src = kernel_sources()
     h = hashlib.sha256()
     for d in (CSRC, INC):
         for f in sorted(os.listdir(d)):
-            if f.endswith((".cu", ".h", ".cuh", ".cpp")):
-                with open(os.path.join(d, f), encoding="utf-8") as fh:
+            path = os.path.normpath(os.path.join(d, f))
+            if path in src:
+                with open(path, encoding="utf-8") as fh:
                     h.update(f.encode())
                     h.update(strip_comments(fh.read()).encode())
     return h.hexdigest()
