@@ -12,6 +12,7 @@ Contents
 * Fibre dispersion constants H11, H22, H33 from (a, b) (Sec. 3, bivariate von
   Mises dispersion; scipy's Bessel and error functions as library steps).
 * J^(-2/3) by the paper's fixed-count Newton iteration (Alg. 2), in FP64.
+* Neumann (traction) load vectors on boundary faces, from the definition.
 * ctypes wrappers of hx_oracle.c: residual, tangent apply, diagonal, dense
   element matrices, energy, node coordinates, pointwise material evaluation.
 * Plain global algorithms built on those: Dirichlet-constrained operators,
@@ -281,6 +282,82 @@ def body_force(M: OracleMesh, b) -> np.ndarray:
     bb = np.ascontiguousarray(np.asarray(b, dtype=np.float64).reshape(3))
     f = np.zeros(M.n_dofs)
     _check(lib().orc_body_force(M.cref(), bb.ctypes.data, f.ctypes.data), "body_force")
+    return f
+
+
+def lagrange(nodes, x):
+    """Values and first derivatives of the Lagrange polynomials on `nodes` at
+    the points x, each [len(x), len(nodes)], as plain products (derivative by
+    the product rule)."""
+    nodes = np.asarray(nodes, dtype=np.float64)
+    x = np.atleast_1d(np.asarray(x, dtype=np.float64))
+    V = np.ones((x.size, nodes.size))
+    D = np.zeros((x.size, nodes.size))
+    for a in range(nodes.size):
+        for b in range(nodes.size):
+            if b != a:
+                den = nodes[a] - nodes[b]
+                D[:, a] = D[:, a] * (x - nodes[b]) / den + V[:, a] / den
+                V[:, a] = V[:, a] * (x - nodes[b]) / den
+    return V, D
+
+
+def traction_load(M: OracleMesh, faces, h):
+    """Neumann load vector f_i = (N_i, h_N) over the boundary faces (Sec. 2,
+    Eq. mom_bal_nonlinear_material_residual, the Gamma_N term; a dead load on
+    the reference configuration).
+
+    faces: [n, 2] pairs (element, local face); local face 2d + s is the face
+    xi_d = s of the reference cube (d = 0, 1, 2; s = 0, 1). h(X, N) returns
+    the nominal traction [k, 3] at points X [k, 3] with outward unit
+    reference normals N [k, 3]. Each face is integrated with the
+    (p+1) x (p+1) Gauss rule of the element's volume rule; the area element
+    and the normal come from the cross product of the two in-face tangents of
+    the geometry map."""
+    faces = np.asarray(faces, dtype=np.int64).reshape(-1, 2)
+    n = M.p + 1
+    mg = M.g + 1
+    f = np.zeros(M.n_dofs)
+    xq, wq = M.xi_q, M.w_q
+    for e, lf in faces:
+        d, side = int(lf) // 2, int(lf) % 2
+        a, b = [c for c in range(3) if c != d]
+        # reference coordinates of the face points, [n*n, 3] (first in-face direction fastest)
+        xi = np.zeros((n * n, 3))
+        xi[:, d] = float(side)
+        xi[:, a] = np.tile(xq, n)
+        xi[:, b] = np.repeat(xq, n)
+        w = np.tile(wq, n) * np.repeat(wq, n)
+        # geometry map X(xi) and its three tangents dX/dxi_c
+        Xg = M.geo_nodes[M.geo_conn[e]]              # [(g+1)^3, 3], xi1 fastest
+        Vg = [lagrange(M.xi_geo, xi[:, c]) for c in range(3)]
+        X = np.zeros((n * n, 3))
+        T = np.zeros((3, n * n, 3))
+        for k in range(mg):
+            for j in range(mg):
+                for i in range(mg):
+                    node = Xg[i + mg * (j + mg * k)]
+                    v = (Vg[0][0][:, i], Vg[1][0][:, j], Vg[2][0][:, k])
+                    dv = (Vg[0][1][:, i], Vg[1][1][:, j], Vg[2][1][:, k])
+                    X += np.outer(v[0] * v[1] * v[2], node)
+                    T[0] += np.outer(dv[0] * v[1] * v[2], node)
+                    T[1] += np.outer(v[0] * dv[1] * v[2], node)
+                    T[2] += np.outer(v[0] * v[1] * dv[2], node)
+        nv = np.cross(T[a], T[b])
+        dA = np.linalg.norm(nv, axis=1)
+        N = nv / dA[:, None]
+        # outward: along +xi_d on the face xi_d = 1, along -xi_d on xi_d = 0
+        sgn = np.sign(np.einsum("qi,qi->q", N, T[d])) * (1.0 if side == 1 else -1.0)
+        N = N * sgn[:, None]
+        hq = np.asarray(h(X, N), dtype=np.float64).reshape(n * n, 3) * (w * dA)[:, None]
+        # nodal basis of the displacement space at the face points
+        Vp = [lagrange(M.xi_node, xi[:, c])[0] for c in range(3)]
+        for k in range(n):
+            for j in range(n):
+                for i in range(n):
+                    psi = Vp[0][:, i] * Vp[1][:, j] * Vp[2][:, k]
+                    node = M.dof_conn[e, i + n * (j + n * k)]
+                    f[3 * node:3 * node + 3] += psi @ hq
     return f
 
 

@@ -122,6 +122,18 @@ def box_dirichlet_x0(nx, ny, nz, p):
     return np.repeat(m, 3)
 
 
+def box_boundary_faces(nx, ny, nz, side):
+    """(element, local face) pairs of one side of a box: side 2d + s is the
+    plane x_d = 0 (s = 0) or x_d = L_d (s = 1); the elements' local face has
+    the same number (reference axes along x, y, z)."""
+    ex, ey, ez = _elem_grid(nx, ny, nz)
+    d, s = divmod(int(side), 2)
+    idx = (ex, ey, ez)[d]
+    last = (nx, ny, nz)[d] - 1
+    e = np.nonzero(idx == (last if s else 0))[0]
+    return np.stack([e, np.full(e.size, side)], axis=1).astype(np.int32)
+
+
 def box_mesh(n, p, jitter=0.0, seed=0, lengths=(1.0, 1.0, 1.0), clamp=False, name=""):
     nx = ny = nz = int(n)
     V = box_vertices(nx, ny, nz, lengths, jitter, seed)
@@ -187,6 +199,18 @@ def tube_mesh(p, n_r=8, n_theta=16, n_z=64, r_in=1.0, r_out=1.3, length=10.0,
                      box=None, frames=frames, name=name or f"tube_p{p}",
                      extra=dict(n_r=n_r, n_theta=n_theta, n_z=n_z, r_in=r_in, r_out=r_out,
                                 length=length))
+
+
+def tube_boundary_faces(n_r, n_theta, n_z, which):
+    """(element, local face) pairs of a tube surface: "inner" (r = r_in,
+    local face 0), "outer" (r = r_out, face 1), "bottom" (z = 0, face 4) or
+    "top" (z = length, face 5); elements are ir + n_r*(it + n_theta*iz)."""
+    e = np.arange(n_r * n_theta * n_z)
+    ir, iz = e % n_r, e // (n_r * n_theta)
+    sel, lf = {"inner": (ir == 0, 0), "outer": (ir == n_r - 1, 1),
+               "bottom": (iz == 0, 4), "top": (iz == n_z - 1, 5)}[which]
+    e = e[sel]
+    return np.stack([e, np.full(e.size, lf)], axis=1).astype(np.int32)
 
 
 def constant_frames(n_elem):

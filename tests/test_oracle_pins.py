@@ -514,3 +514,63 @@ def test_jpow_newton_converges_quadratically_to_the_power(J):
 def test_jpow_newton_exact_at_rest():
     for n in range(0, 5):
         assert O.jpow_newton(1.0, n) == 1.0
+
+
+def test_traction_partition_of_unity_and_first_moment():
+    """On the planar unit face x = 1 of a jittered cube (boundary vertices are
+    not jittered): sum_i f_i = t * area and sum_i f_i y_i = t * int y dA."""
+    n, p = 3, 3
+    m = I.box_mesh(n, p, jitter=0.1, seed=9)
+    M = O.OracleMesh(m)
+    X = O.node_coords(M)
+    t = np.array([0.3, -1.2, 0.7])
+    f = O.traction_load(M, I.box_boundary_faces(n, n, n, 1), lambda Xq, Nq: np.tile(t, (len(Xq), 1)))
+    F = f.reshape(-1, 3)
+    assert np.allclose(F.sum(axis=0), t, rtol=0, atol=1e-14)
+    assert np.allclose((F * X[:, 1:2]).sum(axis=0), 0.5 * t, rtol=0, atol=1e-14)
+    # only nodes on the face carry load
+    assert np.abs(F[np.abs(X[:, 0] - 1.0) > 1e-12]).max() == 0.0
+
+
+def _boundary_faces_all(m):
+    if m.box is not None:
+        return np.concatenate([I.box_boundary_faces(*m.box, s) for s in range(6)])
+    e = m.extra
+    return np.concatenate([I.tube_boundary_faces(e["n_r"], e["n_theta"], e["n_z"], w)
+                           for w in ("inner", "outer", "bottom", "top")])
+
+
+@pytest.mark.parametrize("case", ["cube_p2", "cube_p3", "tube_p3"])
+def test_traction_divergence_theorem_against_residual(case):
+    """A homogeneous state (u = A X, constant P): the residual equals the
+    traction load of h = P N over the whole boundary, the divergence theorem
+    applied to each basis function (both quadratures are exact here)."""
+    if case.startswith("cube"):
+        m = I.box_mesh(3, int(case[-1]), jitter=0.1, seed=11)
+    else:
+        m = I.tube_mesh(3, n_r=2, n_theta=8, n_z=2)
+    M = O.OracleMesh(m)
+    X = O.node_coords(M)
+    A = 0.04 * np.random.Generator(np.random.PCG64(12)).uniform(-1, 1, (3, 3))
+    u = (X @ A.T).ravel()
+    mat = CNH
+    P = O.material_point(mat, np.eye(3) + A)["P"]
+    R = O.residual(M, mat, u)
+    f = O.traction_load(M, _boundary_faces_all(m), lambda Xq, Nq: Nq @ P.T)
+    # interior rows of R are sums of cancelling element contributions: round-off
+    # there is ~1e-12 of max |R| on the curved tube; a wrong normal, sign or area
+    # element would be of order one
+    assert np.abs(R - f).max() / np.abs(R).max() < 1e-11
+
+
+def test_pressure_on_a_closed_surface_has_no_resultant():
+    """h = -p N over the tube's whole boundary: the resultant is -p times the
+    integral of N over a closed surface, i.e. zero; over the inner surface
+    alone the axial component vanishes (the normals are radial)."""
+    m = I.tube_mesh(3, n_r=2, n_theta=8, n_z=2)
+    M = O.OracleMesh(m)
+    press = lambda Xq, Nq: -2.5 * Nq
+    f = O.traction_load(M, _boundary_faces_all(m), press).reshape(-1, 3)
+    inner = O.traction_load(M, I.tube_boundary_faces(2, 8, 2, "inner"), press).reshape(-1, 3)
+    assert np.abs(f.sum(axis=0)).max() < 1e-12 * np.abs(f).sum()
+    assert abs(inner.sum(axis=0)[2]) < 1e-13 * np.abs(inner).sum()
