@@ -1,8 +1,9 @@
 """Build libhx.so in-tree with nvcc for sm_103a.
 
 Each (degree, precision) kernel unit is hx_ops.cu compiled with -DHX_P and
--DHX_UNIT_F32; the units, the vector kernels and the C-ABI layer are compiled
-in parallel and linked into paper_2408_12479_gb300/_lib/libhx.so.
+-DHX_UNIT_F32; the units, the vector kernels, the C-ABI layer and the host-only
+load vectors are compiled in parallel and linked into
+paper_2408_12479_gb300/_lib/libhx.so.
 """
 from __future__ import annotations
 
@@ -136,6 +137,9 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
     for name in ("hx_vec", "hx_api"):
         jobs_list.append([nvcc] + flags + ["-c", os.path.join(CSRC, name + ".cu"), "-o",
                                            os.path.join(objdir, name + ".o")])
+    # host-only C++ (load vectors): no device code, so no -gencode
+    jobs_list.append([nvcc, "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INC, "-c",
+                      os.path.join(CSRC, "hx_loads.cpp"), "-o", os.path.join(objdir, "hx_loads.o")])
     # longest units first (the batch units include every degree)
     jobs_list.sort(key=lambda c: -(99 if any("hx_batch" in a for a in c) else
                                    int(next((a.split("=")[1] for a in c if a.startswith("-DHX_P=")), "0"))))

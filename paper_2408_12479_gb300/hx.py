@@ -1,4 +1,5 @@
-"""ctypes binding of libhx (include/hx.h): same names, argument marshalling only.
+"""ctypes binding of libhx (include/hx.h, include/hx_loads.h): same names,
+argument marshalling only.
 
 Device vectors are torch CUDA tensors (contiguous, float64 for HX_FP64 or
 float32 for HX_FP32); their data pointers and the current torch stream are
@@ -36,7 +37,7 @@ EXPORTS = ["hx_create", "hx_destroy", "hx_set_stream", "hx_last_error", "hx_sync
            "hx_estimate_lambda_max", "hx_cg_solve", "hx_body_force", "hx_newton_solve", "hx_material_eval", "hx_mg_create",
            "hx_mg_destroy", "hx_mg_info", "hx_mg_setup", "hx_mg_vcycle", "hx_mg_transfer", "hx_mg_cg_solve", "hx_fibre_dispersion", "hx_batch_create",
            "hx_batch_destroy", "hx_batch_tangent_apply", "hx_measure_fma_peak", "hx_launch_count",
-           "hx_autotune", "hx_set_apply_variant", "hx_chebyshev_smooth_noalloc"]
+           "hx_autotune", "hx_set_apply_variant", "hx_chebyshev_smooth_noalloc", "hx_traction_load"]
 
 
 class HxError(RuntimeError):
@@ -132,6 +133,7 @@ def lib():
             "hx_autotune": (I32, [P, I32, P, P, I32, C.POINTER(I32), C.POINTER(D)]),
             "hx_set_apply_variant": (I32, [P, I32, I32, I32]),
             "hx_chebyshev_smooth_noalloc": (I32, [P, P, P, P, I32, D, D, I32, I32]),
+            "hx_traction_load": (I32, [C.POINTER(hx_mesh_desc), I32, P, I32, C.POINTER(D), P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -187,10 +189,10 @@ def material_struct(mat: dict) -> hx_material:
                        mat.get("phi", 0.0))
 
 
-def hx_setup_mesh(ctx, mesh_input: "_inputs.MeshInput", mat: dict, structured: bool = True):
-    """Upload a MeshInput. For boxes the structured numbering is used (no
-    connectivity array) unless structured=False."""
-    m = mesh_input
+def _mesh_desc(m: "_inputs.MeshInput", structured: bool = True):
+    """hx_mesh_desc of a MeshInput and the arrays it points into (keep them
+    alive while the descriptor is used). For boxes the structured numbering
+    is used (no connectivity array) unless structured=False."""
     keep = {}
     geo = np.ascontiguousarray(m.geo_nodes, dtype=np.float64)
     gconn = np.ascontiguousarray(m.geo_conn, dtype=np.int32)
@@ -218,11 +220,41 @@ def hx_setup_mesh(ctx, mesh_input: "_inputs.MeshInput", mat: dict, structured: b
         fr = np.ascontiguousarray(m.frames, dtype=np.float64)
         keep["fr"] = fr
         d.fibre_frames = fr.ctypes.data
+    return d, keep
+
+
+def hx_setup_mesh(ctx, mesh_input: "_inputs.MeshInput", mat: dict, structured: bool = True):
+    """Upload a MeshInput. For boxes the structured numbering is used (no
+    connectivity array) unless structured=False."""
+    d, keep = _mesh_desc(mesh_input, structured)
     ms = material_struct(mat)
     out = C.c_void_p()
     st = lib().hx_setup_mesh(ctx, C.byref(d), C.byref(ms), C.byref(out))
     _check(st, ctx)
     return out
+
+
+def hx_traction_load(mesh_input: "_inputs.MeshInput", faces, traction=None, pressure=None, out=None,
+                     structured: bool = True):
+    """Neumann load vector of a dead traction on boundary faces (host; see
+    include/hx_loads.h): faces [n, 2] (element, local face); either a constant
+    traction vector or a pressure along the inward reference normal. Returns
+    the [3 n_nodes] FP64 numpy vector `out` (new zeros if None) with the load
+    added."""
+    if (traction is None) == (pressure is None):
+        raise ValueError("give exactly one of traction and pressure")
+    d, keep = _mesh_desc(mesh_input, structured)
+    fc = np.ascontiguousarray(np.asarray(faces, dtype=np.int32).reshape(-1, 2))
+    mode = 0 if traction is not None else 1
+    val = np.ascontiguousarray(np.asarray(traction if mode == 0 else [pressure, 0.0, 0.0],
+                                          dtype=np.float64).reshape(3))
+    f = np.zeros(3 * mesh_input.n_nodes) if out is None else out
+    if f.dtype != np.float64 or not f.flags.c_contiguous or f.size != 3 * mesh_input.n_nodes:
+        raise ValueError("out must be a contiguous float64 array of 3*n_nodes entries")
+    _check(lib().hx_traction_load(C.byref(d), int(fc.shape[0]), fc.ctypes.data, mode,
+                                  val.ctypes.data_as(C.POINTER(C.c_double)), f.ctypes.data),
+           None, "hx_traction_load")
+    return f
 
 
 def hx_destroy_mesh(mesh):

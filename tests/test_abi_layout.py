@@ -64,7 +64,8 @@ _SCALARS = {"int32_t": ctypes.c_int32, "int": ctypes.c_int, "int64_t": ctypes.c_
 
 def _prototypes():
     import re
-    src = open(os.path.join(ROOT, "include", "hx.h")).read()
+    inc = os.path.join(ROOT, "include")
+    src = "\n".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     protos = {}
     for ret, name, params in re.findall(r"(hx_status|void|const char \*|uint64_t)\s*\b(hx_\w+)\s*\(([^;{]*?)\)\s*;",
