@@ -40,16 +40,21 @@ def interface_sum(partial, nx: int, ny: int, p: int, slabs, rank: int, group=Non
     flattened, zero outside its slab). Each interior interface (one node plane
     of (Nx*Ny) nodes between slabs r and r+1) is exchanged with the neighbour
     by point-to-point send/recv of that plane only."""
+    plane = 3 * (nx * p + 1) * (ny * p + 1)
+    z0, z1 = slabs[rank]
+    return _add_neighbour_planes(partial, plane, [(rank - 1, z0 * p * plane), (rank + 1, z1 * p * plane)],
+                                 len(slabs), group)
+
+
+def _add_neighbour_planes(v, plane, pairs, world, group):
+    """For each (neighbour rank, offset) with a valid neighbour: send this
+    rank's `plane` values at the offset, receive the neighbour's, and add them
+    in place once every exchange has completed."""
     import torch
     import torch.distributed as dist
-    Nx, Ny = nx * p + 1, ny * p + 1
-    plane = 3 * Nx * Ny
-    v = partial
-    z0, z1 = slabs[rank]
     reqs, bufs = [], []
-    for nb, zplane in ((rank - 1, z0), (rank + 1, z1)):
-        if 0 <= nb < len(slabs):
-            off = zplane * p * plane
+    for nb, off in pairs:
+        if 0 <= nb < world:
             mine = v[off:off + plane].clone()
             other = torch.empty_like(mine)
             reqs.append(dist.isend(mine, nb, group=group))
@@ -123,23 +128,9 @@ def interface_sum_local(v, nx, ny, p, slabs, rank, group=None):
     """In place: add the neighbours' partial values on the shared node planes
     of a rank-local vector (lowest local plane with rank-1, highest with
     rank+1), one plane exchanged per neighbour by isend/irecv."""
-    import torch.distributed as dist
-    import torch
     z0, z1 = slabs[rank]
     plane = 3 * (nx * p + 1) * (ny * p + 1)
-    reqs, bufs = [], []
-    for nb, off in ((rank - 1, 0), (rank + 1, (z1 - z0) * p * plane)):
-        if 0 <= nb < len(slabs):
-            mine = v[off:off + plane].clone()
-            other = torch.empty_like(mine)
-            reqs.append(dist.isend(mine, nb, group=group))
-            reqs.append(dist.irecv(other, nb, group=group))
-            bufs.append((off, other))
-    for r in reqs:
-        r.wait()
-    for off, other in bufs:
-        v[off:off + plane] += other
-    return v
+    return _add_neighbour_planes(v, plane, [(rank - 1, 0), (rank + 1, (z1 - z0) * p * plane)], len(slabs), group)
 
 
 class SlabSystem:
