@@ -29,6 +29,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "tangent-operator apply GDoF/s (p=2-6, FP64 vs FP32) and fraction of HBM roofline"
 L2_BYTES = 129 * 1024 * 1024
+# The paper's own node-level figures (Sec. 7.2), quoted for context: another
+# machine and FP64, so no ratio is formed with them.
+PAPER_CONTEXT = {"hardware": "2x Intel Xeon Platinum 8360Y (72 cores, AVX-512), DDR4-3200", "precision": "f64",
+                 "workload": "uniformly refined cubes, 2.5-5 MDoF, p = 1..8",
+                 "tangent_apply_peak_gdofs": {"cNH": 1.75, "iNH": 1.75, "fiber": 1.25},
+                 "dram_gbs_p4_tensors": [260, 280], "residual_spatial_gdofs": [0.05, 0.08], "source": "Sec. 7.2"}
 
 
 def peaks():
@@ -786,6 +792,7 @@ def main():
             "residual": resid,
             "newton_step_costs": step_costs,
             "fp32_error": fp32_err,
+            "paper_context": PAPER_CONTEXT,
             "batch": batch,
             "solve": solve,
             "newton": newton,
