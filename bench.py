@@ -281,6 +281,79 @@ def run_fp32_errors(device, n=16, p=4):
     return res
 
 
+def _event_ms_flushed(fn, steps, warmup, flush):
+    """Mean ms of fn() with an L2 flush (a write of `flush`, larger than L2)
+    before every call; CUDA events enclose fn() alone."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    s = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for e0, e1 in ev:
+        flush.zero_()
+        e0.record(s)
+        fn()
+        e1.record(s)
+    torch.cuda.synchronize()
+    return sum(e0.elapsed_time(e1) for e0, e1 in ev) / steps
+
+
+def law_workloads():
+    """The iNH and fibre workloads at full size: (name, mesh, material,
+    state field)."""
+    from paper_2408_12479_gb300 import inputs as I
+    m, field, _ = I.workload_compressed_cube(n=48, p=4, J_target=0.9)
+    yield "iNH kappa=1e3 mu, 48^3 jittered cube, p=4, J~0.9", m, dict(I.MAT_INH), field
+    yield ("fiber, tube 16x8x64 with Q2 geometry, p=3, 2 % inflation + 1 % sines", I.tube_mesh(3),
+           dict(I.MAT_FIBER), I.inflation_field(I.SEED_BASE + 4))
+
+
+def run_law_workloads(device, hbm_peak, steps=10, flush_bytes=256 << 20, workloads=None):
+    """Tangent-apply throughput of the iNH and fibre workloads per precision
+    and storage strategy (autotuned variant), with an L2 flush before every
+    timed apply. A case that fails records its error."""
+    import torch
+    from paper_2408_12479_gb300 import hx
+    from paper_2408_12479_gb300 import inputs as I
+    res = []
+    flush = None
+    for name, m, mat, field in (workloads if workloads is not None else law_workloads()):
+        rec = {"workload": name, "n_dofs": m.n_dofs, "cases": []}
+        G = None
+        try:
+            G = hx.Mesh(m, mat, device=device)
+            if flush is None:
+                flush = torch.empty(flush_bytes, dtype=torch.uint8, device=G.device)
+            X = G.node_coords().cpu().numpy()
+            u = torch.tensor(field(X).ravel(), dtype=torch.float64, device=G.device)
+            du64 = torch.tensor(I.random_direction(m.n_dofs, 7), dtype=torch.float64, device=G.device)
+            for pr in (hx.HX_FP32, hx.HX_FP64):
+                du = du64.float() if pr == hx.HX_FP32 else du64
+                out = torch.empty_like(du)
+                for st in (hx.HX_RECOMPUTE, hx.HX_CACHE_F, hx.HX_CACHE_TENSORS, hx.HX_SPATIAL_TENSORS):
+                    case = {"prec": "f32" if pr == hx.HX_FP32 else "f64", "storage": hx.STORAGE_NAMES[st]}
+                    try:
+                        G.precompute(u, pr, st)
+                        variant, _ = hx.hx_autotune(G.ctx, G.handle, du, out, reps=3)
+                        t = _event_ms_flushed(lambda: hx.hx_tangent_apply(G.ctx, G.handle, du, out), steps, 2, flush)
+                        G.sync(60000)
+                        b = G.apply_bytes(st, pr)
+                        case.update({"ms": round(t, 4), "gdofs": round(m.n_dofs / (t * 1e-3) / 1e9, 3),
+                                     "hbm_frac": round(b / (t * 1e-3) / 1e9 / hbm_peak, 4), "tile_variant": variant})
+                    except Exception as exc:  # recorded; the other cases go on
+                        case["error"] = str(exc)[:200]
+                    rec["cases"].append(case)
+        except Exception as exc:  # recorded in the report; the headline line still prints
+            rec["error"] = str(exc)[:200]
+        finally:
+            if G is not None:
+                G.close()
+            torch.cuda.empty_cache()
+        res.append(rec)
+    return res
+
+
 def residual_bytes(n_dofs, n_qp, s):
     """Algorithmic bytes of one cNH residual: read u, write r, and the stored
     J0^-1 (9) and JxW (1) per quadrature point; the state is recomputed from u
@@ -744,11 +817,12 @@ def main():
                     del us, dus, outs
                     torch.cuda.empty_cache()
 
-    resid = step_costs = fp32_err = None
+    resid = step_costs = fp32_err = laws = None
     if rank == 0 and not args.no_sweep:
         resid = run_residual_sweep(local, hbm_peak)
         step_costs = run_newton_step_costs(local, p)
         fp32_err = run_fp32_errors(local)
+        laws = run_law_workloads(local, hbm_peak)
 
     batch = None
     if rank == 0 and not args.no_sweep:
@@ -792,6 +866,7 @@ def main():
             "residual": resid,
             "newton_step_costs": step_costs,
             "fp32_error": fp32_err,
+            "law_workloads": laws,
             "paper_context": PAPER_CONTEXT,
             "batch": batch,
             "solve": solve,

@@ -234,3 +234,42 @@ def test_reference_arm_other_ranks_do_nothing(capsys, monkeypatch):
     monkeypatch.setenv("RANK", "1")
     bench.run_reference(argparse.Namespace(p=2, steps=1, warmup=3, gpus=2))
     assert capsys.readouterr().out == ""
+
+
+class _FakeLawMesh(_FakeMesh):
+    bad_storage = None
+
+    def precompute(self, u, store_prec=hx.HX_FP64, storage=hx.HX_CACHE_TENSORS):
+        if storage == _FakeLawMesh.bad_storage:
+            raise hx.HxError(hx.HX_ERR_UNSUPPORTED, "stand-in failure")
+        super().precompute(u, store_prec, storage)
+
+    def apply_bytes(self, storage, prec):
+        return 2.0e6 if prec == hx.HX_FP32 else 4.0e6
+
+
+def test_law_workloads_report(fake_gpu, monkeypatch):
+    monkeypatch.setattr(hx, "Mesh", _FakeLawMesh)
+    _FakeLawMesh.bad_storage = hx.HX_RECOMPUTE
+    flushes = []
+    orig_zero = torch.Tensor.zero_
+
+    def zero_(t):  # the flush happens outside the events' bracket
+        flushes.append(_Event.clock[0])
+        _Event.clock[0] += 100.0
+        return orig_zero(t)
+    monkeypatch.setattr(torch.Tensor, "zero_", zero_)
+    wl = [("small cube", I.box_mesh(2, 2), dict(I.MAT_CNH), I.sine_field(1, strain=0.05))]
+    res = bench.run_law_workloads(0, hbm_peak=1000.0, steps=4, flush_bytes=1024, workloads=wl)
+    assert len(res) == 1 and res[0]["workload"] == "small cube" and "error" not in res[0]
+    cases = res[0]["cases"]
+    assert [(c["prec"], c["storage"]) for c in cases] == [
+        (pr, st) for pr in ("f32", "f64") for st in ("recompute", "cache_F", "cache_tensors", "spatial_tensors")]
+    for c in cases:
+        if c["storage"] == "recompute":
+            assert "stand-in failure" in c["error"]
+            continue
+        assert c["ms"] == pytest.approx(2.0)  # the stand-in apply's time only, not the flush's
+        b = 2.0e6 if c["prec"] == "f32" else 4.0e6
+        assert c["hbm_frac"] == pytest.approx(round(b / 2e-3 / 1e9 / 1000.0, 4))
+    assert len(flushes) == 6 * 4  # one flush before every timed apply
