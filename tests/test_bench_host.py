@@ -273,3 +273,23 @@ def test_law_workloads_report(fake_gpu, monkeypatch):
         b = 2.0e6 if c["prec"] == "f32" else 4.0e6
         assert c["hbm_frac"] == pytest.approx(round(b / 2e-3 / 1e9 / 1000.0, 4))
     assert len(flushes) == 6 * 4  # one flush before every timed apply
+
+
+def test_newton_traction_report(fake_gpu, monkeypatch):
+    """The load is stepped up to the full Neumann vector of hx_traction_load
+    (the real host routine); every step is reported."""
+    seen = []
+
+    def newton(ctx, mesh, u, f_ext=None, **kw):
+        seen.append(f_ext.clone())
+        u -= 0.001
+        return {"newton_iters": 3, "cg_iters": 40, "res0": 1.0, "res": 1e-10, "converged": True}, hx.HX_OK
+    monkeypatch.setattr(hx, "hx_newton_solve", newton)
+    res = bench.run_newton_traction(0, n=2, p=2, steps=4)
+    assert "error" not in res, res
+    assert res["newton_iters_per_step"] == [3, 3, 3, 3] and res["cg_iters"] == 160 and res["status"] == "HX_OK"
+    m = I.box_mesh(2, 2, jitter=0.1, seed=I.SEED_BASE + 6, clamp=True)
+    full = hx.hx_traction_load(m, I.box_boundary_faces(2, 2, 2, 1), traction=(0.0, 0.0, -0.02))
+    for k, f in enumerate(seen, start=1):
+        assert np.allclose(f.numpy(), full * k / 4, rtol=0, atol=1e-15)
+    assert res["mean_face_deflection"] == [-0.004] * 3
