@@ -274,3 +274,51 @@ class SlabSystem:
         r_true = b - self.apply(x)
         true_rel = self.dot(r_true, r_true) ** 0.5 / bn
         return x, it, true_rel
+
+    def newton(self, u, residual_local, set_state, diagonal_local, f_ext=None, eps_abs=1e-10, eps_rel=1e-8,
+               max_newton=20, cg_tol=1e-8, cg_max_iter=5000, cheb_degree=0, smoothing_range=15.0):
+        """Newton's method (Alg. 1) on R(u) - f_ext = 0 over the free DoFs,
+        partitioned by slabs. u: this rank's consistent state, with the
+        Dirichlet values already in its constrained entries (left unchanged);
+        residual_local(u) -> the partial residual of the rank's elements (pure
+        operator); set_state(u) refreshes the linearization point that
+        apply_local and diagonal_local use (Alg. 1's quadrature-point update);
+        diagonal_local() -> the partial diagonal of the pure operator; f_ext:
+        consistent external load (or None). Each update solves K_c du = -r by
+        CG with Jacobi (cheb_degree 0) or Chebyshev(cheb_degree)-Jacobi
+        preconditioning. Returns (u, report) with the iteration counts and
+        the first and last residual norms."""
+        import torch
+        self._to(u)
+        u = u.clone()
+        rep = {"newton_iters": 0, "cg_iters": 0, "res0": None, "res": None, "converged": False}
+        for k in range(max_newton + 1):
+            r = self.assemble(residual_local(u))
+            if f_ext is not None:
+                r = r - f_ext
+            r = torch.where(self.cmask, torch.zeros((), dtype=r.dtype, device=r.device), r)
+            nrm = self.dot(r, r) ** 0.5
+            if k == 0:
+                rep["res0"] = nrm
+            rep["res"] = nrm
+            if nrm <= eps_abs or nrm <= eps_rel * rep["res0"]:
+                rep["converged"] = True
+                break
+            if k == max_newton:
+                break
+            set_state(u)
+            inv_d = 1.0 / self.diagonal(diagonal_local())
+            if cheb_degree > 0:
+                lam = self.lambda_max(inv_d)
+
+                def precond(v):
+                    return self.chebyshev(v, torch.zeros_like(v), inv_d, cheb_degree, lam, smoothing_range,
+                                          zero_initial=True)
+            else:
+                def precond(v):
+                    return inv_d * v
+            du, its, _ = self.cg(-r, precond=precond, tol=cg_tol, max_iter=cg_max_iter)
+            u = u + du
+            rep["newton_iters"] += 1
+            rep["cg_iters"] += its
+        return u, rep

@@ -204,3 +204,68 @@ def test_cg_over_slabs_matches_direct_solve(world):
             assert abs(it - it1) <= 1, (key, it, it1)  # the partition changes only round-off
         # the smoother preconditions: fewer iterations than plain Jacobi
         assert res["chebcg"][0] < res["jacobi"][0]
+
+
+def _newton_case(world, rank):
+    """Clamped 2^3 Q2 jittered cube (cNH) under a body force, split into
+    slabs: the rank's SlabSystem with oracle callables for its elements."""
+    from oracle import oracle as O
+    from paper_2408_12479_gb300 import dd
+    from paper_2408_12479_gb300 import inputs as I
+    from tests import cases
+    n, p = 2, 2
+    m = I.box_mesh(n, p, jitter=0.1, seed=41, clamp=True)
+    mat = cases.oracle_material("cNH")
+    slabs = dd.slab_partition(n, world)
+    sl = dd.local_slice(n, n, p, slabs[rank])
+    Ms = O.OracleMesh(dd.slab_mesh(m, slabs[rank]))
+    state = {"u": np.zeros(Ms.n_dofs)}
+
+    def apply_local(v):
+        return torch.tensor(O.apply(Ms, mat, state["u"], v.numpy()))
+
+    S = dd.SlabSystem(n, n, p, slabs, rank, apply_local, m.dirichlet[sl].astype(bool))
+    f = S.assemble(torch.tensor(O.body_force(Ms, [0.0, 0.0, -0.05])))
+    calls = dict(residual_local=lambda u: torch.tensor(O.residual(Ms, mat, u.numpy())),
+                 set_state=lambda u: state.update(u=u.numpy().copy()),
+                 diagonal_local=lambda: torch.tensor(O.diagonal(Ms, mat, state["u"])))
+    return m, mat, sl, S, f, calls
+
+
+def _newton_worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from oracle import oracle as O
+        O.set_threads(2)  # the ranks share the host's cores
+        m, mat, sl, S, f, calls = _newton_case(world, rank)
+        u0 = torch.zeros(sl.stop - sl.start, dtype=torch.float64)
+        u, rep = S.newton(u0, f_ext=f, eps_rel=1e-11, cg_tol=1e-12, **calls)
+        uc, repc = S.newton(u0, f_ext=f, eps_rel=1e-11, cg_tol=1e-12, cheb_degree=3, **calls)
+        out[rank] = (u.numpy(), rep, uc.numpy(), repc, (sl.start, sl.stop))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2])
+def test_newton_over_slabs_matches_oracle_newton(world):
+    """Alg. 1 over slabs (residual and load assembled by interface sums,
+    norms by owned-DoF reductions, updates by slab CG) reaches the oracle's
+    global Newton solution, with the iteration count of the one-slab run."""
+    from oracle import oracle as O
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    mp.start_processes(_newton_worker, args=(world, port, out), nprocs=world, start_method="spawn")
+    m, mat, sl1, S1, f1, calls1 = _newton_case(1, 0)
+    M = O.OracleMesh(m)
+    u_ref, norms = O.newton(M, mat, np.zeros(m.n_dofs), f_ext=O.body_force(M, [0.0, 0.0, -0.05]), eps_rel=1e-13)
+    _, rep1 = S1.newton(torch.zeros(m.n_dofs, dtype=torch.float64), f_ext=f1, eps_rel=1e-11, cg_tol=1e-12, **calls1)
+    assert rep1["converged"] and rep1["newton_iters"] >= 3
+    for r in range(world):
+        u, rep, uc, repc, (a, b) = out[r]
+        for uu, rr in ((u, rep), (uc, repc)):
+            assert rr["converged"], rr
+            assert np.abs(uu - u_ref[a:b]).max() / np.abs(u_ref).max() < 1e-8
+        assert rep["newton_iters"] == rep1["newton_iters"]
+        assert repc["cg_iters"] < rep["cg_iters"]  # the Chebyshev preconditioner pays off
