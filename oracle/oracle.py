@@ -101,7 +101,8 @@ def lib():
 
 def gll_points(p: int) -> np.ndarray:
     """p+1 Gauss-Lobatto-Legendre points on [0, 1]: the end points and the
-    roots of P_p'."""
+    roots of P_p'. The nodes of the Lagrange basis; the paper's deal.II
+    elements (Sec. 2) do not name them, and these are the reading taken."""
     if p == 1:
         x = np.array([-1.0, 1.0])
     else:
@@ -111,12 +112,16 @@ def gll_points(p: int) -> np.ndarray:
 
 
 def gauss_rule(nq: int):
-    """nq-point Gauss-Legendre points and weights on [0, 1] (weights sum to 1)."""
+    """nq-point Gauss-Legendre points and weights on [0, 1] (weights sum to 1);
+    nq = p+1 per direction is the quadrature of the integrals of Sec. 2."""
     x, w = np.polynomial.legendre.leggauss(nq)
     return 0.5 * (x + 1.0), 0.5 * w
 
 
 def equispaced(g: int) -> np.ndarray:
+    """Parameter points of a degree-g geometry map (trilinear or triquadratic
+    elements with equispaced nodes; the paper's higher-order mapping of Sec. 6
+    is the reading for the curved tube)."""
     return np.linspace(0.0, 1.0, g + 1)
 
 
@@ -236,6 +241,8 @@ def _check(nbad, what):
 # ---------------------------------------------------------------------------
 
 def node_coords(M: OracleMesh) -> np.ndarray:
+    """Positions of the DoF nodes: the geometry map at the nodal points (the
+    reference configuration of Sec. 2)."""
     X = np.zeros((M.n_nodes, 3))
     if lib().orc_node_coords(M.cref(), X.ctypes.data) != 0:
         raise MemoryError("node_coords")
@@ -243,6 +250,9 @@ def node_coords(M: OracleMesh) -> np.ndarray:
 
 
 def residual(M: OracleMesh, mat: Material, u, elems=None) -> np.ndarray:
+    """R(u)_i = (Grad N_i, P(F)) by full quadrature (Sec. 2, Eq.
+    mom_bal_nonlinear_material_residual, without loads); P from the laws of
+    Sec. 3. elems restricts the sum to those elements."""
     u = _vec(u, M.n_dofs)
     r = np.zeros(M.n_dofs)
     e, ne = _elems(elems)
@@ -252,6 +262,8 @@ def residual(M: OracleMesh, mat: Material, u, elems=None) -> np.ndarray:
 
 
 def apply(M: OracleMesh, mat: Material, u, du, elems=None) -> np.ndarray:
+    """K(u) du = (Grad N_i, Grad du S + F D_uS[Grad du]) by full quadrature
+    (Sec. 2, Eq. DDu_residual_material; D_uS of App. A, readings R3 and R4)."""
     u = _vec(u, M.n_dofs)
     du = _vec(du, M.n_dofs)
     out = np.zeros(M.n_dofs)
@@ -288,7 +300,7 @@ def body_force(M: OracleMesh, b) -> np.ndarray:
 def lagrange(nodes, x):
     """Values and first derivatives of the Lagrange polynomials on `nodes` at
     the points x, each [len(x), len(nodes)], as plain products (derivative by
-    the product rule)."""
+    the product rule): the tensor-product basis of Sec. 2 in one direction."""
     nodes = np.asarray(nodes, dtype=np.float64)
     x = np.atleast_1d(np.asarray(x, dtype=np.float64))
     V = np.ones((x.size, nodes.size))
@@ -362,6 +374,8 @@ def traction_load(M: OracleMesh, faces, h):
 
 
 def diagonal(M: OracleMesh, mat: Material, u, elems=None) -> np.ndarray:
+    """diag K(u), the Jacobi scaling of the smoother (Sec. 6), summed from the
+    diagonals of the element matrices."""
     u = _vec(u, M.n_dofs)
     d = np.zeros(M.n_dofs)
     e, ne = _elems(elems)
@@ -371,6 +385,8 @@ def diagonal(M: OracleMesh, mat: Material, u, elems=None) -> np.ndarray:
 
 
 def element_matrices(M: OracleMesh, mat: Material, u, elems=None) -> np.ndarray:
+    """Dense element tangent matrices of Sec. 2, Eq. DDu_residual_material
+    (one column per unit direction), [n_elem, 3 (p+1)^3, 3 (p+1)^3]."""
     u = _vec(u, M.n_dofs)
     e, ne = _elems(elems)
     n_list = ne if e is not None else M.n_elem
@@ -381,12 +397,15 @@ def element_matrices(M: OracleMesh, mat: Material, u, elems=None) -> np.ndarray:
 
 
 def energy(M: OracleMesh, mat: Material, u) -> float:
+    """Stored energy Pi(u) = sum over points of JxW Psi(F) (Sec. 3 laws)."""
     u = _vec(u, M.n_dofs)
     mc = mat.c()
     return float(lib().orc_energy(M.cref(), C.byref(mc), u.ctypes.data))
 
 
 def qp_fields(M: OracleMesh, u, elems):
+    """Quadrature points of the given elements: their positions, weights JxW
+    and deformation gradients F = I + Grad u (Sec. 2)."""
     u = _vec(u, M.n_dofs)
     e = np.ascontiguousarray(elems, dtype=np.int32)
     qq = (M.p + 1) ** 3
@@ -399,7 +418,9 @@ def qp_fields(M: OracleMesh, u, elems):
 
 
 def material_point(mat: Material, F, H=None, frame=None):
-    """Psi, S, P, dP (and fibre auxiliaries) at one deformation gradient."""
+    """Psi, S, P, dP (and fibre auxiliaries) at one deformation gradient:
+    the laws of Sec. 3 (Eq. NH_compressible, NH_nearly_incompressible,
+    fiber_Psi) and their derivatives of App. A."""
     F = np.ascontiguousarray(np.asarray(F, dtype=np.float64).reshape(9))
     Hh = None if H is None else np.ascontiguousarray(np.asarray(H, dtype=np.float64).reshape(9))
     fr = None if frame is None else np.ascontiguousarray(np.asarray(frame, dtype=np.float64).reshape(9))
@@ -429,7 +450,7 @@ def num_threads() -> int:
 
 def assemble_sparse(M: OracleMesh, mat: Material, u):
     """Global sparse K(u) (pure operator, no constraints) from the dense
-    element matrices."""
+    element matrices (Sec. 2, Eq. DDu_residual_material)."""
     import scipy.sparse as sp
     Ke = element_matrices(M, mat, u)
     nn = (M.p + 1) ** 3
@@ -440,7 +461,8 @@ def assemble_sparse(M: OracleMesh, mat: Material, u):
 
 
 def constrain_matrix(K, mask):
-    """Replace constrained rows/columns by identity rows (out_c = du_c)."""
+    """Replace constrained rows/columns by identity rows (out_c = du_c): the
+    Dirichlet part of the boundary conditions of Sec. 2."""
     import scipy.sparse as sp
     free = sp.diags((~mask).astype(np.float64))
     fix = sp.diags(mask.astype(np.float64))
@@ -449,7 +471,7 @@ def constrain_matrix(K, mask):
 
 def apply_constrained(M: OracleMesh, mat: Material, u, du):
     """K_c du: free rows of K applied to du with constrained entries zeroed;
-    constrained rows return du itself."""
+    constrained rows return du itself (Sec. 2 tangent with Dirichlet rows)."""
     mask = M.dirichlet
     d = np.where(mask, 0.0, _vec(du, M.n_dofs))
     out = apply(M, mat, u, d)
@@ -457,12 +479,14 @@ def apply_constrained(M: OracleMesh, mat: Material, u, du):
 
 
 def residual_constrained(M: OracleMesh, mat: Material, u):
+    """R(u) with the Dirichlet rows set to zero (Sec. 2)."""
     r = residual(M, mat, u)
     r[M.dirichlet] = 0.0
     return r
 
 
 def diagonal_constrained(M: OracleMesh, mat: Material, u):
+    """diag K(u) with the Dirichlet rows set to one (Sec. 2, Sec. 6)."""
     d = diagonal(M, mat, u)
     d[M.dirichlet] = 1.0
     return d
@@ -473,8 +497,8 @@ def diagonal_constrained(M: OracleMesh, mat: Material, u):
 # ---------------------------------------------------------------------------
 
 def chebyshev_smooth(Kop, rhs, x, inv_diag, degree, lambda_max, smoothing_range, zero_initial=False):
-    """Chebyshev acceleration of the Jacobi iteration on D^-1 K x = D^-1 rhs
-    with eigenvalue interval [lambda_max/smoothing_range, lambda_max]; degree
+    """The Chebyshev-Jacobi smoother of Sec. 6: Chebyshev acceleration (Saad,
+    Sec. 12.3) of the Jacobi iteration on D^-1 K x = D^-1 rhs with eigenvalue interval [lambda_max/smoothing_range, lambda_max]; degree
     steps, each using one residual rhs - K x (the first is rhs itself when x
     starts at zero). Written as the three-term recurrence
         d_0 = r_0 / theta,  rho_0 = delta/theta,
@@ -508,8 +532,9 @@ def chebyshev_smooth(Kop, rhs, x, inv_diag, degree, lambda_max, smoothing_range,
 
 
 def pcg(Kop, b, Mop, tol=1e-8, maxit=10000, x0=None):
-    """Preconditioned CG with the Polak-Ribiere beta; stops when
-    ||b - K x|| <= tol ||b|| (recomputed residual checked at exit)."""
+    """Preconditioned CG with the Polak-Ribiere beta (the outer Krylov
+    solver of Sec. 6; Saad, Alg. 9.1); stops when ||b - K x|| <= tol ||b||
+    (recomputed residual checked at exit)."""
     x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64, copy=True)
     r = b - Kop(x)
     bn = np.linalg.norm(b)
@@ -567,7 +592,8 @@ def box_transfer_matrix(nx, ny, nz, pc, pf):
     space on a structured box of nx*ny*nz elements (per displacement
     component): P[I, J] = value of the coarse global basis function J at fine
     node I, evaluated in reference coordinates of an element containing the
-    node (the element map is shared by both spaces). Plain loops; small boxes."""
+    node (the element map is shared by both spaces). The p-transfer of the
+    multigrid hierarchy of Sec. 6. Plain loops; small boxes."""
     xc, xf = gll_points(pc), gll_points(pf)
 
     def lag(xs, a, x):
