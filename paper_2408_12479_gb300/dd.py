@@ -5,10 +5,17 @@ partition of the elements over ranks gives, on each rank, the partial
 vector of its own elements; the full result on the nodes a rank touches is
 the sum of the partial vectors of every rank touching them. The exchange is
 therefore one sum over the interface nodes after each apply, plus the scalar
-reductions of the Krylov solver (dot products). This module holds that
-exchange: a slab partition of a structured box, the interface node sets, and
-the interface sum over torch.distributed (any backend). The local apply is a
-callable supplied by the caller (the device apply of the rank's sub-mesh).
+reductions of the Krylov solver (dot products). This module holds:
+
+* the slab partition of a structured box, each slab's sub-mesh and its node
+  range, and the interface sum over torch.distributed (any backend);
+* SlabSystem: the Dirichlet-constrained tangent on rank-local vectors, its
+  owner-rule dot product, the Chebyshev-Jacobi smoother, CG (Sec. 6) and
+  Newton's method (Alg. 1) over the slabs.
+
+The local work (apply, residual, diagonal, state refresh of the rank's
+sub-mesh) is supplied by the caller as callables: the device kernels of the
+library on GPU ranks, the oracle in the CPU tests.
 """
 from __future__ import annotations
 
