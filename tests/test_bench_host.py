@@ -293,3 +293,32 @@ def test_newton_traction_report(fake_gpu, monkeypatch):
     for k, f in enumerate(seen, start=1):
         assert np.allclose(f.numpy(), full * k / 4, rtol=0, atol=1e-15)
     assert res["mean_face_deflection"] == [-0.004] * 3
+
+
+def test_strip_comments_keeps_code_and_literals():
+    from paper_2408_12479_gb300 import build as B
+    src = 'int a = 1; // note\n/* block\n comment */ const char *s = "// not a comment /* */";\nchar c = \'"\';  x =\n y;'
+    assert B.strip_comments(src) == 'int a = 1; const char *s = "// not a comment /* */"; char c = \'"\'; x = y;'
+    # comment-only and formatting-only edits leave the result unchanged; a code edit does not
+    assert B.strip_comments("a  =  b; /* x */\n") == B.strip_comments("a = b; // y\n")
+    assert B.strip_comments("a = b;") != B.strip_comments("a = c;")
+
+
+def test_kernel_sources_follow_the_includes():
+    import os
+    from paper_2408_12479_gb300 import build as B
+    names = {os.path.basename(f) for f in B.kernel_sources()}
+    assert {"hx_ops.cu", "hx_core.cuh", "hx_internal.h", "hx.h", "hx_api.cu", "hx_batch_degree.cuh"} <= names
+    assert "hx_loads.cpp" not in names and "hx_loads.h" not in names  # host-only, outside the kernels
+
+
+def test_measured_traffic_needs_the_current_digest(tmp_path, monkeypatch):
+    from paper_2408_12479_gb300 import build as B
+    (tmp_path / "profiles").mkdir()
+    prof = tmp_path / "profiles" / "k_apply_cNH_p4_f32_spatial_tensors.md"
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    prof.write_text(f"traffic_bytes_per_launch: 123456\nsource_digest: {B.kernel_digest()}\n")
+    assert bench.measured_traffic(4, "f32", "spatial_tensors") == 123456.0
+    prof.write_text("traffic_bytes_per_launch: 123456\nsource_digest: 0123abcd\n")
+    assert bench.measured_traffic(4, "f32", "spatial_tensors") is None
+    assert bench.measured_traffic(5, "f32", "spatial_tensors") is None  # no summary for that case
