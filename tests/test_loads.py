@@ -25,7 +25,7 @@ def _rel(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
-@pytest.mark.parametrize("p", [1, 2, 3, 4, 6])
+@pytest.mark.parametrize("p", [1, 2, 3, 4, 6, 8])
 @pytest.mark.parametrize("structured", [True, False])
 def test_constant_traction_on_every_box_side(p, structured):
     n = 3
