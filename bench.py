@@ -318,7 +318,11 @@ def run_law_workloads(device, hbm_peak, steps=10, flush_bytes=256 << 20, workloa
     from paper_2408_12479_gb300 import inputs as I
     res = []
     flush = None
-    for name, m, mat, field in (workloads if workloads is not None else law_workloads()):
+    try:
+        workloads = list(workloads if workloads is not None else law_workloads())
+    except Exception as exc:  # recorded in the report; the headline line still prints
+        return [{"error": str(exc)[:200]}]
+    for name, m, mat, field in workloads:
         rec = {"workload": name, "n_dofs": m.n_dofs, "cases": []}
         G = None
         try:
