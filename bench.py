@@ -2,11 +2,17 @@
 
 Default workload: compressible neo-Hookean on the 32^3 cube with interior
 vertices jittered by +-10% of h, p = 4 (6,440,067 DoFs), FP32, with the
-fastest of the three quadrature-point storage strategies. One step is one
-tangent apply K(u_k) du over the whole mesh (gather, sum-factorized gradient,
-quadrature-point material tangent, integration, scatter: one fused kernel plus
-the zeroing of the output). The qp cache is refreshed once before timing, as
-in the paper's protocol (Sec. 7.2). Metric: GDoF/s over all 3*n_nodes DoFs.
+fastest of the quadrature-point storage strategies. One apply is K(u_k) du over
+the whole mesh (gather, sum-factorized gradient, quadrature-point material
+tangent, integration, scatter: one fused kernel plus the zeroing of the
+output). As in the paper's protocol (Sec. 7.2: repeat until at least a second
+has passed), one timed step is a block of R back-to-back applies, R chosen so
+that the K timed steps last at least a second; the qp cache is refreshed once
+before timing. Metric: GDoF/s over all 3*n_nodes DoFs.
+
+Output: one JSON line per side report ({"report": name, ...}: storage sweep,
+residual, Newton-step costs, FP32 errors, other laws, batch, solve, Newton,
+stability), then, LAST, the compact headline line of the contract.
 
 Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 For N > 1 (torchrun) every rank runs an independent replica (weak scaling, no
@@ -16,6 +22,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -60,7 +67,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -670,9 +677,68 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
-def cpu_baseline(m, field, seed, p, mat_d, target_s=12.0):
-    """The FP64 oracle's full-tensor apply on a bounded sample of the same mesh
-    (leading elements), on all host cores; scaled to GDoF/s of the whole mesh."""
+def strict(o):
+    """o with every non-finite float replaced by None (and numpy scalars by
+    Python numbers), so that json.dumps(..., allow_nan=False) accepts it."""
+    if isinstance(o, (float, np.floating)):
+        return float(o) if math.isfinite(o) else None
+    if isinstance(o, np.integer):
+        return int(o)
+    if isinstance(o, dict):
+        return {k: strict(v) for k, v in o.items()}
+    if isinstance(o, (list, tuple)):
+        return [strict(v) for v in o]
+    return o
+
+
+def emit(obj):
+    """Print one strict-JSON line."""
+    print(json.dumps(strict(obj), allow_nan=False), flush=True)
+
+
+def guarded(fn, *a, **k):
+    """fn(*a, **k), or {"error": ...} if it raises: a failing side report is
+    recorded and the headline line still prints."""
+    try:
+        return fn(*a, **k)
+    except Exception as exc:  # recorded in the report
+        return {"error": f"{type(exc).__name__}: {str(exc)[:200]}"}
+
+
+def reps_per_step(apply_ms, steps, target_s=1.2):
+    """Applies per timed step so that `steps` steps last at least target_s
+    (the paper's protocol repeats an operation until a second has passed)."""
+    return max(1, int(math.ceil(target_s * 1e3 / (max(steps, 1) * max(apply_ms, 1e-6)))))
+
+
+def sweep_summary(sweep):
+    """Best storage strategy per (precision, degree) of the sweep:
+    {prec: {p: [GDoF/s, HBM fraction, strategy]}}."""
+    out = {}
+    for r in sweep or []:
+        if "gdofs" not in r:
+            continue
+        cur = out.setdefault(r["prec"], {}).get(str(r["p"]))
+        if cur is None or r["gdofs"] > cur[0]:
+            out[r["prec"]][str(r["p"])] = [r["gdofs"], r["hbm_frac"], r["storage"]]
+    return out
+
+
+HEADLINE_KEYS = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                 "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "e2e", "gpu_launches", "clocks",
+                 "cpu_baseline", "fma_peaks", "sweep_best")
+
+
+def headline_line(fields):
+    """The final stdout line: the contract's keys only (side reports go on
+    earlier lines), strict JSON."""
+    line = {k: fields.get(k) for k in HEADLINE_KEYS}
+    return json.dumps(strict(line), allow_nan=False)
+
+
+def cpu_baseline(m, field, seed, p, mat_d, target_s=10.0):
+    """The FP64 oracle's full-tensor apply over the whole mesh, on all host
+    cores, repeated until target_s has passed (at least once)."""
     from oracle import oracle as O
     O.set_threads(host_cores())
     M = O.OracleMesh(m)
@@ -681,26 +747,24 @@ def cpu_baseline(m, field, seed, p, mat_d, target_s=12.0):
     from paper_2408_12479_gb300 import inputs as I
     du = I.random_direction(m.n_dofs, seed + 3)
     mat = O.Material.from_dict(mat_d)
-    k = 64
-    while True:
-        t0 = time.perf_counter()
-        O.apply(M, mat, u, du, elems=np.arange(k, dtype=np.int32))
-        dt = time.perf_counter() - t0
-        if dt > 1.0 or k >= m.n_elem:
-            break
-        k = min(m.n_elem, k * 4)
-    k = int(min(m.n_elem, max(k, k * target_s / max(dt, 1e-3))))
+    reps = 0
     t0 = time.perf_counter()
-    O.apply(M, mat, u, du, elems=np.arange(k, dtype=np.int32))
-    dt = time.perf_counter() - t0
-    gdofs = m.n_dofs * (k / m.n_elem) / dt / 1e9
-    return {"value": gdofs, "unit": "GDoF/s", "cores": O.num_threads(), "kind": "oracle",
-            "sample": f"FP64 full-tensor oracle apply over the first {k} of {m.n_elem} elements "
-                      f"({dt:.1f} s), scaled by the element fraction"}
+    while True:
+        O.apply(M, mat, u, du)
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= target_s:
+            break
+    return {"value": m.n_dofs * reps / dt / 1e9, "unit": "GDoF/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"{reps} FP64 full-tensor oracle applies of the whole mesh ({m.n_elem} elements) in {dt:.1f} s"}
 
 
-def run_reference(args):
-    """Reference arm: the FP64 CPU oracle, timed as it stands on the host cores."""
+def run_reference(args, budget_s=150.0):
+    """Reference arm: the FP64 CPU oracle, timed as it stands on the host
+    cores. Each step applies the whole mesh; only if K + W whole-mesh steps
+    would take longer than budget_s does a step apply the leading elements
+    instead (the line then names that sample). ms_per_step is the measured
+    time of the work one step does."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -715,43 +779,80 @@ def run_reference(args):
     u = field(X).ravel()
     du = I.random_direction(m.n_dofs, seed + 3)
     mat = O.Material.from_dict(mat_d)
-    # elements per step: sized so that the whole run stays near two minutes
+    k_probe = min(m.n_elem, 256)
     t0 = time.perf_counter()
-    O.apply(M, mat, u, du, elems=np.arange(64, dtype=np.int32))
-    per_elem = (time.perf_counter() - t0) / 64
-    k = int(min(1024, max(8, 120.0 / (args.steps + args.warmup) / per_elem)))
-    elems = np.arange(k, dtype=np.int32)
+    O.apply(M, mat, u, du, elems=np.arange(k_probe, dtype=np.int32))
+    per_elem = (time.perf_counter() - t0) / k_probe
+    n_run = args.steps + args.warmup
+    k = m.n_elem if n_run * per_elem * m.n_elem <= budget_s else max(8, int(budget_s / n_run / per_elem))
+    elems = None if k >= m.n_elem else np.arange(k, dtype=np.int32)
     for _ in range(args.warmup):
         O.apply(M, mat, u, du, elems=elems)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         O.apply(M, mat, u, du, elems=elems)
     dt = (time.perf_counter() - t0) / max(args.steps, 1)
-    gdofs = m.n_dofs * (k / m.n_elem) / dt / 1e9
+    dofs = m.n_dofs if elems is None else m.n_dofs * k / m.n_elem
+    gdofs = dofs / dt / 1e9
+    sample = ("the whole mesh per step" if elems is None else
+              f"the first {k} of {m.n_elem} elements per step ({dofs:.0f} DoFs by element fraction)")
     line = {"impl": "reference", "metric": METRIC, "value": gdofs, "unit": "GDoF/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 * m.n_elem / k,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": f"cNH tangent apply, 32^3 jittered cube, p={p}", "p": p,
                                             "n_dofs": m.n_dofs, "law": "cNH", "prec": "f64",
-                                            "storage": "none (full-tensor oracle)"},
+                                            "storage": "none (full-tensor oracle)", "step": sample},
             "cpu_baseline": {"value": gdofs, "unit": "GDoF/s", "cores": O.num_threads(), "kind": "oracle",
-                             "sample": f"first {k} of {m.n_elem} elements per step, scaled by the element fraction"},
+                             "sample": sample},
             "e2e": {"value": gdofs, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
+    emit(line)
+
+
+def run_sweep(local, hbm_peak, peaks_fp):
+    """Tangent apply on the 32^3 jittered cube, p = 2..6 x FP32/FP64 x every
+    storage strategy (autotuned variant), with HBM and FMA-pipe fractions."""
+    import torch
+    from paper_2408_12479_gb300 import hx
+    sweep = []
+    for pp in (2, 3, 4, 5, 6):
+        for pr in (hx.HX_FP32, hx.HX_FP64):
+            for st in (hx.HX_RECOMPUTE, hx.HX_CACHE_F, hx.HX_CACHE_TENSORS, hx.HX_SPATIAL_TENSORS):
+                rec = {"p": pp, "prec": "f32" if pr else "f64", "storage": hx.STORAGE_NAMES[st]}
+                Gs = None
+                try:
+                    Gs, ms_, us, dus, outs = build_case(pp, pr, st, local)
+                    reps = 30 if pr == hx.HX_FP32 else 5
+                    t = time_steps(Gs, dus, outs, reps, 2)
+                    b = Gs.apply_bytes(st, pr)
+                    tf, pf = pipe_fraction(ms_.n_elem, pp, t, rec["prec"], peaks_fp)
+                    rec.update({"sweep_tflops": tf, "fma_frac": pf, "n_dofs": ms_.n_dofs, "ms": round(t, 4),
+                                "gdofs": round(ms_.n_dofs / (t * 1e-3) / 1e9, 3), "tile_variant": Gs.tune[0],
+                                "variant_ms": [round(x, 4) for x in Gs.tune[1]],
+                                "hbm_frac": round(b / (t * 1e-3) / 1e9 / hbm_peak, 4)})
+                    del us, dus, outs
+                except Exception as exc:  # recorded; the sweep goes on
+                    rec["error"] = str(exc)[:200]
+                finally:
+                    if Gs is not None:
+                        Gs.close()
+                    torch.cuda.empty_cache()
+                sweep.append(rec)
+    return sweep
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5000)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="hx")
     ap.add_argument("--p", type=int, default=4)
-    ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="headline only (no side reports)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--storage", default="best", choices=["best", "recompute", "cache_F", "cache_tensors", "spatial_tensors"])
     ap.add_argument("--prec", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--min-seconds", type=float, default=1.2, help="least length of the timed region")
     ap.add_argument("--solve", type=int, default=16,
                     help="also run the FP32- vs FP64-preconditioned CG solve on an n^3 compressed cube (n given)")
     args = ap.parse_args()
@@ -796,10 +897,17 @@ def main():
     G, m, u, du, out = build_case(p, prec, storage, local)
     n_dofs = m.n_dofs
     bytes_alg = G.apply_bytes(storage, prec)
+    # applies per timed step: the K steps last at least --min-seconds
+    R = reps_per_step(time_steps(G, du, out, 50, 5), args.steps, args.min_seconds)
+    if world > 1:  # every rank runs the same R (the slowest rank's choice)
+        R = int(round(max_over_ranks(float(R), world)))
 
-    hx.hx_launch_count(G.ctx, reset=True)
+    def step():
+        for _ in range(R):
+            hx.hx_tangent_apply(G.ctx, G.handle, du, out)
+
     for _ in range(args.warmup):
-        hx.hx_tangent_apply(G.ctx, G.handle, du, out)
+        step()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -811,18 +919,19 @@ def main():
         torch.cuda.nvtx.range_push("timed")  # profilers can restrict capture to this range
         e0.record(s)
         for _ in range(args.steps):
-            hx.hx_tangent_apply(G.ctx, G.handle, du, out)
+            step()
         e1.record(s)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
     launches = hx.hx_launch_count(G.ctx)
     G.sync(60000)
-    ms = e0.elapsed_time(e1) / args.steps
-    t_max = max_over_ranks(ms, world)
+    ms_step = e0.elapsed_time(e1) / args.steps
+    t_max = max_over_ranks(ms_step, world)
     if world > 1:
         dist.barrier()
-    value = weak_value(n_dofs, t_max, world)
-    achieved = bytes_alg / (ms * 1e-3) / 1e9
+    value = weak_value(n_dofs * R, t_max, world)
+    ms_apply = ms_step / R
+    achieved = bytes_alg / (ms_apply * 1e-3) / 1e9
 
     # end to end through the host-buffer C-ABI call (pinned host vectors)
     bytes_vec = n_dofs * du.element_size()
@@ -838,91 +947,62 @@ def main():
             hx.hx_tangent_apply_host(G.ctx, G.handle, du_h, out_h, prec)
         e2e_s = (time.perf_counter() - t0) / k_e2e
         e2e = {"value": round(n_dofs / e2e_s / 1e9, 4), "unit": "GDoF/s", "h2d_bytes_per_step": bytes_vec,
-               "d2h_bytes_per_step": bytes_vec}
+               "d2h_bytes_per_step": bytes_vec, "steps": k_e2e,
+               "path": "hx_tangent_apply_host: pinned du -> device, apply, out -> pinned host"}
+    tune = G.tune
+    G.close()
+    del u, du, out
+    torch.cuda.empty_cache()
 
-    sweep = []
-    peaks_fp = None
+    peaks_fp = sweep = None
     if rank == 0 and not args.no_sweep:
         peaks_fp = fma_peaks(local)
-        G.close()
-        del u, du, out
-        torch.cuda.empty_cache()
-        for pp in (2, 3, 4, 5, 6):
-            for pr in (hx.HX_FP32, hx.HX_FP64):
-                for st in (hx.HX_RECOMPUTE, hx.HX_CACHE_F, hx.HX_CACHE_TENSORS, hx.HX_SPATIAL_TENSORS):
-                    Gs, ms_, us, dus, outs = build_case(pp, pr, st, local)
-                    reps = 30 if pr == hx.HX_FP32 else 5
-                    t = time_steps(Gs, dus, outs, reps, 2)
-                    b = Gs.apply_bytes(st, pr)
-                    tf, pf = pipe_fraction(ms_.n_elem, pp, t, "f32" if pr else "f64", peaks_fp)
-                    sweep.append({"p": pp, "prec": "f32" if pr else "f64", "storage": hx.STORAGE_NAMES[st],
-                                  "sweep_tflops": tf, "fma_frac": pf,
-                                  "n_dofs": ms_.n_dofs, "ms": round(t, 4),
-                                  "gdofs": round(ms_.n_dofs / (t * 1e-3) / 1e9, 3),
-                                  "tile_variant": Gs.tune[0], "variant_ms": [round(x, 4) for x in Gs.tune[1]],
-                                  "hbm_frac": round(b / (t * 1e-3) / 1e9 / hbm_peak, 4)})
-                    Gs.close()
-                    del us, dus, outs
-                    torch.cuda.empty_cache()
-
-    resid = step_costs = fp32_err = laws = None
-    if rank == 0 and not args.no_sweep:
-        resid = run_residual_sweep(local, hbm_peak)
-        step_costs = run_newton_step_costs(local, p)
-        fp32_err = run_fp32_errors(local)
-        laws = run_law_workloads(local, hbm_peak)
-
-    batch = None
-    if rank == 0 and not args.no_sweep:
-        batch = {"cache_F": run_batch(local, storage=hx.HX_CACHE_F),
-                 "spatial_tensors": run_batch(local, storage=hx.HX_SPATIAL_TENSORS)}
-    solve = None
-    if rank == 0 and args.solve and not args.no_sweep:
-        solve = run_solve(local, n=args.solve)
-
-    stab = newton = None
-    if rank == 0 and not args.no_sweep:
-        stab = run_stability(local)
-        newton = run_newton(local)
-        newton["traction"] = run_newton_traction(local)
+        sweep = run_sweep(local, hbm_peak, peaks_fp)
+        emit({"report": "sweep", "fma_peaks": peaks_fp, "cases": sweep})
+        emit({"report": "residual", "cases": guarded(run_residual_sweep, local, hbm_peak)})
+        emit({"report": "newton_step_costs", "cases": guarded(run_newton_step_costs, local, p)})
+        emit({"report": "fp32_error", **guarded(run_fp32_errors, local)})
+        emit({"report": "law_workloads", "cases": guarded(run_law_workloads, local, hbm_peak)})
+        emit({"report": "batch", "cache_F": guarded(run_batch, local, storage=hx.HX_CACHE_F),
+              "spatial_tensors": guarded(run_batch, local, storage=hx.HX_SPATIAL_TENSORS)})
+        if args.solve:
+            emit({"report": "solve", **guarded(run_solve, local, n=args.solve)})
+        newton = guarded(run_newton, local)
+        newton["traction"] = guarded(run_newton_traction, local)
+        emit({"report": "newton", **newton})
+        emit({"report": "stability", **guarded(run_stability, local)})
+        emit({"report": "paper_context", **PAPER_CONTEXT})
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         m2, field, seed = I.workload_jittered_cube(p)
-        cpu = cpu_baseline(m2, field, seed, p, dict(I.MAT_CNH))
+        cpu = guarded(cpu_baseline, m2, field, seed, p, dict(I.MAT_CNH))
 
     if rank == 0:
-        line = {
+        fields = {
             "metric": METRIC, "value": round(value, 4), "unit": "GDoF/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(t_max, 5), "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": round(t_max, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
             "config": {"workload": f"cNH tangent apply, 32^3 jittered cube, p={p}",
                        "p": p, "n_dofs": n_dofs, "law": "cNH", "prec": args.prec,
-                       "storage": hx.STORAGE_NAMES[storage],
+                       "storage": hx.STORAGE_NAMES[storage], "applies_per_step": R,
+                       "ms_per_apply": round(ms_apply, 5),
                        "l2": "inputs larger than L2 (vectors + qp data %.0f MB > 129 MB)" % (bytes_alg / 1e6),
                        "per_storage_ms": {k: round(v, 4) for k, v in per_storage.items() if v},
-                       "tile_variant": G.tune[0], "variant_ms": [round(x, 4) for x in G.tune[1]]},
+                       "tile_variant": tune[0]},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                          "frac": round(achieved / hbm_peak, 4),
                          "traffic": measured_traffic(p, args.prec, hx.STORAGE_NAMES[storage]),
-                         "peak_kind": peak_kind, "bytes_per_launch": bytes_alg},
+                         "peak_kind": peak_kind, "bytes_per_launch": bytes_alg,
+                         "duration": "CUDA events over the timed steps / applies (output zeroing + k_apply)"},
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
             "fma_peaks": peaks_fp,
-            "sweep": sweep,
-            "residual": resid,
-            "newton_step_costs": step_costs,
-            "fp32_error": fp32_err,
-            "law_workloads": laws,
-            "paper_context": PAPER_CONTEXT,
-            "batch": batch,
-            "solve": solve,
-            "newton": newton,
-            "stability": stab,
+            "sweep_best": sweep_summary(sweep),
         }
-        print(json.dumps(line))
+        print(headline_line(fields), flush=True)
     if world > 1:
         dist.destroy_process_group()
 

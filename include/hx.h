@@ -31,6 +31,11 @@
  *  - Constrained DoFs (Dirichlet mask): residual rows are zero; tangent and
  *    diagonal rows are the identity (out_i = du_i, diag_i = 1); the operator
  *    sees constrained entries of du as zero.
+ *  - Calls that work on a mesh or context expect its device to be current on
+ *    the calling thread. Calls that select a device themselves (hx_create,
+ *    hx_setup_mesh, hx_measure_fma_peak, the first
+ *    hx_chebyshev_smooth_noalloc call on a device) make it current only while
+ *    they run and restore the caller's current device before returning.
  */
 #ifndef HX_H
 #define HX_H

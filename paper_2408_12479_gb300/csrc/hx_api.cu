@@ -304,6 +304,25 @@ void dfree(void *p) {
 
 bool bad_prec(int prec) { return prec != HX_FP64 && prec != HX_FP32; }
 
+// Makes `device` current for the guard's lifetime and then makes the caller's
+// previous device current again, so that no entry point leaves the calling
+// thread switched to another device.
+struct DeviceGuard {
+    int prev = -1;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int device) {
+        int cur = -1;
+        err = cudaGetDevice(&cur);
+        if (err == cudaSuccess && cur != device) {
+            err = cudaSetDevice(device);
+            if (err == cudaSuccess) prev = cur;
+        }
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -317,8 +336,8 @@ hx_status hx_create(hx_ctx **ctx, int device, void *cuda_stream) {
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess || device < 0 || device >= ndev) return HX_ERR_CUDA;
-    e = cudaSetDevice(device);
-    if (e != cudaSuccess) return HX_ERR_CUDA;
+    DeviceGuard dg(device);
+    if (dg.err != cudaSuccess) return HX_ERR_CUDA;
     hx_ctx *c = new hx_ctx();
     c->device = device;
     c->stream = (cudaStream_t)cuda_stream;
@@ -433,7 +452,8 @@ hx_status hx_setup_mesh(hx_ctx *ctx, const hx_mesh_desc *d, const hx_material *m
     if ((int64_t)d->n_elem * nq >= ((int64_t)1 << 31) * 8)
         return fail(ctx, HX_ERR_ARG, "hx_setup_mesh: mesh too large");
 
-    HX_CUDA(ctx, cudaSetDevice(ctx->device));
+    DeviceGuard dg(ctx->device);
+    HX_CUDA(ctx, dg.err);
     HX_CUDA(ctx, ensure_tables(ctx->device, p));
 
     hx_mesh *m = new hx_mesh();
@@ -806,7 +826,8 @@ static hx_status noalloc_scratch(hx_ctx *ctx, void **addr) {
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     if (ctx->device < 0 || ctx->device >= 64) return fail(ctx, HX_ERR_ARG, "noalloc: device index out of range");
     if (!g_noalloc_addr[ctx->device]) {
-        HX_CUDA(ctx, cudaSetDevice(ctx->device));
+        DeviceGuard dg(ctx->device);  // the caller's current device is restored on return
+        HX_CUDA(ctx, dg.err);
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGetSymbolAddress(g_noalloc_scratch)");
@@ -1101,7 +1122,8 @@ hx_status hx_cg_solve(hx_mesh *m, const double *rhs, double *x, double tol, int3
 
 hx_status hx_measure_fma_peak(hx_ctx *ctx, int32_t prec, double *flops) {
     if (!ctx || !flops || bad_prec(prec)) return HX_ERR_ARG;
-    HX_CUDA(ctx, cudaSetDevice(ctx->device));
+    DeviceGuard dg(ctx->device);
+    HX_CUDA(ctx, dg.err);
     HX_CUDA(ctx, hx::fma_probe(prec, ctx->sm_count, flops));
     return HX_OK;
 }

@@ -218,11 +218,18 @@ def test_reference_arm_line_uses_all_host_cores(capsys, monkeypatch):
     from oracle import oracle as O
     monkeypatch.delenv("RANK", raising=False)
     O.set_threads(1)
-    args = argparse.Namespace(p=2, steps=1, warmup=3, gpus=1)
+    import time
+    args = argparse.Namespace(p=2, steps=2, warmup=3, gpus=1)
+    t0 = time.perf_counter()
     bench.run_reference(args)
+    wall = time.perf_counter() - t0
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    # the timed steps did the work the line claims: whole mesh, within the run
+    assert line["config"]["step"] == "the whole mesh per step"
+    assert line["ms_per_step"] * 1e-3 * line["steps"] < wall
+    assert abs(line["value"] - line["config"]["n_dofs"] / (line["ms_per_step"] * 1e-3) / 1e9) < 1e-9 * line["value"]
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "GDoF/s"
-    assert line["value"] > 0 and line["higher_is_better"] is True and line["steps"] == 1
+    assert line["value"] > 0 and line["higher_is_better"] is True and line["steps"] == 2
     assert line["cpu_baseline"]["cores"] == bench.host_cores() == O.num_threads()
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": "GDoF/s", "h2d_bytes_per_step": 0,
@@ -322,3 +329,53 @@ def test_measured_traffic_needs_the_current_digest(tmp_path, monkeypatch):
     prof.write_text("traffic_bytes_per_launch: 123456\nsource_digest: 0123abcd\n")
     assert bench.measured_traffic(4, "f32", "spatial_tensors") is None
     assert bench.measured_traffic(5, "f32", "spatial_tensors") is None  # no summary for that case
+
+
+def test_headline_line_is_short_strict_json():
+    """The last stdout line carries the contract's keys only, stays within a
+    few KB with a full sweep summary, and non-finite numbers become null."""
+    import json
+    sweep = [{"p": p, "prec": pr, "storage": st, "gdofs": 10.0 * p + (st == "spatial_tensors"),
+              "hbm_frac": 0.4, "ms": 0.1}
+             for p in (2, 3, 4, 5, 6) for pr in ("f32", "f64")
+             for st in ("recompute", "cache_F", "cache_tensors", "spatial_tensors")]
+    fields = {k: None for k in bench.HEADLINE_KEYS}
+    fields.update({"metric": bench.METRIC, "value": 55.0, "unit": "GDoF/s", "steps": 20, "warmup": 5,
+                   "ms_per_step": float("nan"),
+                   "config": {"workload": "w", "per_storage_ms": {"a": 1.0}, "x": float("inf")},
+                   "roofline": {"frac": np.float32(0.41), "traffic": None}, "clocks": {"sm_mhz": 2070.0},
+                   "sweep_best": bench.sweep_summary(sweep), "residual": [1.0] * 10000})
+    line = bench.headline_line(fields)
+    assert len(line) < 2048
+    d = json.loads(line)
+    assert list(d) == list(bench.HEADLINE_KEYS)
+    assert "residual" not in d
+    assert d["ms_per_step"] is None and d["config"]["x"] is None
+    assert abs(d["roofline"]["frac"] - 0.41) < 1e-6
+    assert d["sweep_best"]["f32"]["4"] == [41.0, 0.4, "spatial_tensors"]
+    assert set(d["sweep_best"]["f64"]) == {"2", "3", "4", "5", "6"}
+
+
+def test_emit_prints_strict_json(capsys):
+    import json
+    bench.emit({"report": "x", "v": [float("nan"), 1.0, float("-inf")], "n": np.int64(3)})
+    out = capsys.readouterr().out
+    assert "NaN" not in out and "Infinity" not in out
+    assert json.loads(out) == {"report": "x", "v": [None, 1.0, None], "n": 3}
+
+
+def test_guarded_records_the_error():
+    def bad():
+        raise RuntimeError("boom")
+    r = bench.guarded(bad)
+    assert r == {"error": "RuntimeError: boom"}
+    assert bench.guarded(lambda a, b=1: a + b, 1, b=2) == 3
+
+
+@pytest.mark.parametrize("apply_ms,steps", [(0.1175, 20), (0.1175, 5000), (3.0, 20), (50.0, 1)])
+def test_reps_per_step_lasts_the_minimum(apply_ms, steps):
+    R = bench.reps_per_step(apply_ms, steps, 1.2)
+    assert R >= 1
+    assert R * steps * apply_ms >= 1200.0 or R == 1
+    if R > 1:  # and not much longer than needed
+        assert (R - 1) * steps * apply_ms < 1200.0

@@ -68,3 +68,55 @@ def test_noalloc_rejects_meshes_beyond_the_limit():
         assert "1048576" in str(e.value)
     finally:
         G.close()
+
+
+def _large_case(prec):
+    """A 24^3 Q2 cube (352,947 DoFs): the allocating smoother's workspace
+    (two vectors, 5.6 MB in FP64) is larger than the device's allocation
+    granularity, so cudaMemGetInfo sees it."""
+    dt = torch.float64 if prec == hx.HX_FP64 else torch.float32
+    m, field, seed = I.workload_jittered_cube(2, n=24)
+    G = hx.Mesh(m, cases.MATS["cNH"])
+    X = G.node_coords().cpu().numpy()
+    G.precompute(torch.tensor(field(X).ravel(), dtype=torch.float64, device="cuda"), prec, hx.HX_CACHE_TENSORS)
+    dinv = 1.0 / G.diagonal(prec)
+    rhs = torch.tensor(I.random_direction(m.n_dofs, seed + 5), dtype=dt, device="cuda")
+    x = torch.zeros_like(rhs)
+    return G, rhs, dinv, x
+
+
+def test_noalloc_call_allocates_nothing():
+    """On a mesh whose smoother workspace does not exist yet, the no-allocation
+    call leaves the device's free memory as it was; the allocating smoother on
+    the same mesh then takes its workspace, so the measurement does see an
+    allocation of that size."""
+    prec = hx.HX_FP64
+    # first call in this process: the array's address lookup and the loading
+    # of the kernels that the call launches happen here, not in the measured call
+    G0, rhs0, dinv0, x00 = _large_case(prec)
+    try:
+        hx.hx_chebyshev_smooth_noalloc(G0.ctx, G0.handle, rhs0, x00, dinv0, 3, 2.0, 15.0, 0)
+        G0.sync(60000)
+    finally:
+        G0.close()
+    G, rhs, dinv, x = _large_case(prec)
+    try:
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        dev0 = torch.cuda.current_device()
+        hx.hx_chebyshev_smooth_noalloc(G.ctx, G.handle, rhs, x, dinv, 3, 2.0, 15.0, 0)
+        G.sync(60000)
+        torch.cuda.synchronize()
+        free1 = torch.cuda.mem_get_info()[0]
+        assert free1 == free0
+        assert torch.cuda.current_device() == dev0
+        ref = torch.zeros_like(x)
+        hx.hx_chebyshev_smooth(G.ctx, G.handle, rhs, ref, dinv, 3, 2.0, 15.0, 0)
+        G.sync(60000)
+        torch.cuda.synchronize()
+        free2 = torch.cuda.mem_get_info()[0]
+        work = 2 * G.n_dofs * 8
+        assert free0 - free2 >= work - (2 << 20)
+        assert (x - ref).abs().max().item() <= 1e-12 * ref.abs().max().item()
+    finally:
+        G.close()
