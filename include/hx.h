@@ -183,15 +183,20 @@ hx_status hx_tangent_apply(hx_mesh *mesh, const void *du_dev, void *out_dev, int
 hx_status hx_tangent_apply_host(hx_mesh *mesh, const void *du_host, void *out_host, int32_t prec);
 
 /* Autotuner: time every compiled variant of the tangent apply for the mesh's
- * current cache at `prec` -- tile shape (elements per CTA: default, half,
- * double) times how the quadrature-point data arrives (0-2: per-thread loads
- * one point ahead plus an L2 prefetch of the next tile; 3-5: bulk copies into
- * shared memory one tile ahead, quadrature points taken in column order) --
- * keep the fastest for later hx_tangent_apply calls, and return its index and
- * the six mean times in ms (a variant that cannot launch, e.g. a staged tile
- * whose chunks would not be 16-byte aligned or would not fit in shared
- * memory, reports a negative time). Uses du_dev/out_dev as scratch vectors of
- * the mesh's size; synchronous. */
+ * current cache at `prec` and keep the fastest for later hx_tangent_apply
+ * calls. The variants differ in how the quadrature-point data arrives and in
+ * the tile (elements per CTA):
+ *   0, 1: per-thread loads one point ahead plus an L2 prefetch of the next
+ *         tile (default tile, half tile);
+ *   3, 4: bulk copies into shared memory one tile ahead, quadrature points
+ *         taken in column order (default tile, half tile);
+ *   2, 5: as 3/4 with two elements per thread, whose lines and points run in
+ *         the two lanes of the packed FP32 instructions (half tile, default
+ *         tile; caching strategies only).
+ * Returns the fastest index and the six mean times in ms (a variant that
+ * cannot launch, e.g. a staged tile whose chunks would not be 16-byte aligned
+ * or would not fit in shared memory, reports a negative time). Uses
+ * du_dev/out_dev as scratch vectors of the mesh's size; synchronous. */
 hx_status hx_autotune(hx_mesh *mesh, int32_t prec, const void *du_dev, void *out_dev, int32_t reps,
                       int32_t *best_variant, double times_ms[6]);
 /* Pin the tangent-apply variant (0-5, as numbered by hx_autotune) used for the
@@ -199,6 +204,16 @@ hx_status hx_autotune(hx_mesh *mesh, int32_t prec, const void *du_dev, void *out
  * variant that cannot launch on this mesh makes hx_tangent_apply return
  * HX_ERR_CUDA. */
 hx_status hx_set_apply_variant(hx_mesh *mesh, int32_t prec, int32_t storage, int32_t variant);
+
+/* Test hook for the device-side wait limits (no counterpart in the paper):
+ * with skip_stage_copies != 0 the staged apply variants (2-5) issue no bulk
+ * copy, so their stage never fills and each CTA's bounded wait gives up after
+ * wait_limit_cycles clock cycles (0 = the default, 2^32); the CTA then sets
+ * the device timeout flag and returns, and the next hx_sync reports
+ * HX_ERR_TIMEOUT. No fault or trap is raised and the context stays usable;
+ * the output of such an apply is incomplete. Call again with 0, 0 to restore
+ * normal operation. HX_ERR_ARG for a negative limit. */
+hx_status hx_set_wait_test(hx_mesh *mesh, int32_t skip_stage_copies, int64_t wait_limit_cycles);
 
 /* diag(K(u_k)), constrained entries 1 (needed by the Jacobi smoother,
  * Sec. 6); sum-factorized from the per-qp tangent blocks. */

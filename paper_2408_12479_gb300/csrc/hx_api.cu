@@ -225,6 +225,8 @@ struct hx_mesh {
     double *d_fibM = nullptr;
     QpCache cache[2];
     int variant[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};  // autotuned apply variant per (prec, storage)
+    int skip_stage_copies = 0;                // hx_set_wait_test
+    long long wait_limit = 1ll << 32;        // cycles a bounded device wait polls
     // workspace (allocated on first use)
     std::vector<void *> ws;
     void *w_cheb_d[2] = {nullptr, nullptr}, *w_cheb_Kx[2] = {nullptr, nullptr};
@@ -288,6 +290,8 @@ hx::MeshView view(const hx_mesh *m, int prec) {
     v.matf = hx::MatParamsF{(float)m->mat.mu, (float)m->mat.lambda, (float)m->mat.kappa, (float)m->mat.k1,
                             (float)m->mat.k2};
     v.law = m->law;
+    v.skip_stage_copies = m->skip_stage_copies;
+    v.wait_limit = m->wait_limit;
     return v;
 }
 
@@ -647,6 +651,13 @@ hx_status hx_tangent_apply(hx_mesh *m, const void *du_dev, void *out_dev, int32_
     if (!m || !du_dev || !out_dev || bad_prec(prec) || du_dev == out_dev)
         return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_tangent_apply: bad argument");
     return apply_dev(m, du_dev, out_dev, prec);
+}
+
+hx_status hx_set_wait_test(hx_mesh *m, int32_t skip_stage_copies, int64_t wait_limit_cycles) {
+    if (!m || wait_limit_cycles < 0) return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_set_wait_test: bad argument");
+    m->skip_stage_copies = skip_stage_copies ? 1 : 0;
+    m->wait_limit = wait_limit_cycles ? (long long)wait_limit_cycles : (1ll << 32);
+    return HX_OK;
 }
 
 hx_status hx_set_apply_variant(hx_mesh *m, int32_t prec, int32_t storage, int32_t variant) {

@@ -1292,11 +1292,13 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
-// Wait for the phase of the given parity; gives up after 2^20 polls or about
-// 2^32 clock cycles and returns false.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// Wait for the phase of the given parity; gives up after 2^20 polls or
+// `limit` clock cycles (the mesh's wait_limit, 2^32 by default) and returns
+// false.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit) {
     const uint32_t a = smem_u32(bar);
     const long long t0 = clock64();
+    if (limit <= 0) limit = 1ll << 32;
     for (int it = 0;; ++it) {
         uint32_t ok;
         asm volatile(
@@ -1305,7 +1307,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
             : "r"(a), "r"(parity)
             : "memory");
         if (ok) return true;
-        if (it >= (1 << 20) || clock64() - t0 > (1ll << 32)) return false;
+        if (it >= (1 << 20) || clock64() - t0 > limit) return false;
     }
 }
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar, uint64_t pol) {
@@ -1326,6 +1328,7 @@ __device__ __forceinline__ void stage_issue(const hx::MeshView &m, int tile, Rea
     const int cnt = min(EPB, m.n_elem - e0);
     const uint32_t bytes = (uint32_t)((cnt * NQ * (int)sizeof(Real) + 15) / 16 * 16);
     const uint64_t pol = policy_evict_first();
+    if (m.skip_stage_copies) return;  // test hook: the stage never fills and the wait runs out
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(bar, QF::n * bytes);
 #pragma unroll 1
@@ -1579,11 +1582,11 @@ __device__ __forceinline__ bool apply_tile(const hx::MeshView &m, int tile, int 
         Real gz[3][N], gk[RC ? 3 : 1][N];
         if constexpr (RC) col_forward_c<SW>(ck, K0, K1, K2, gk, act, eoff, lo);
         col_forward_c<SW>(cd, X0, X1, X2, gz, act, eoff, lo);
-        const bool ok = mbar_wait(bar, phase);
+        const bool ok = mbar_wait(bar, phase, m.wait_limit);
         if (__syncthreads_or(!ok)) {  // also the barrier that completes the forward sweeps
             if (t == 0) {
                 atomicOr(m.err + 2, 1);
-                mbar_wait(bar, phase);  // let a copy still in flight land before the CTA exits
+                mbar_wait(bar, phase, m.wait_limit);  // let a copy still in flight land before the CTA exits
             }
             return false;
         }
@@ -1653,6 +1656,358 @@ __device__ __forceinline__ bool apply_tile(const hx::MeshView &m, int tile, int 
         __syncthreads();
     }
     col_backward(m, X0, X1, X2, act, valid, eoff, a0, a1, e, out, pol_keep);
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Two elements per thread (staged apply, variant 5). Thread (a0, a1) of slot
+// el carries the lines of element A = e0 + el and of element B = A + EPB/2,
+// whose cubes sit HB = (EPB/2) * ES words after A's. Every sweep phase then
+// holds six independent lines (two elements x three components), which mv6
+// runs as three FFMA2 pairs in FP32 units, and the spatial-tensor point phase
+// runs A's and B's points in the two lanes of the packed FP32 instructions;
+// one set of line offsets and loop counters serves both elements.
+// ---------------------------------------------------------------------------
+
+// Two FP32 values computed lane-wise with the packed FP32 instructions
+// (FFMA2, FADD2, FMUL2): each lane performs the scalar operation with one
+// rounding, so a function templated on its scalar type gives, per lane, the
+// scalar function's result.
+struct F2 {
+    float2 v;
+    __device__ __forceinline__ F2() {}
+    __device__ __forceinline__ F2(int z) : v(make_float2((float)z, (float)z)) {}
+    __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
+    // hidden friends: found for F2 arguments only, so that the scalar fma and
+    // operators keep their meaning everywhere else
+    __device__ __forceinline__ friend F2 operator+(F2 a, F2 b) {
+        F2 r;
+        r.v = __fadd2_rn(a.v, b.v);
+        return r;
+    }
+    __device__ __forceinline__ friend F2 operator*(F2 a, F2 b) {
+        F2 r;
+        r.v = __fmul2_rn(a.v, b.v);
+        return r;
+    }
+    __device__ __forceinline__ friend F2 &operator+=(F2 &a, F2 b) {
+        a.v = __fadd2_rn(a.v, b.v);
+        return a;
+    }
+    __device__ __forceinline__ friend F2 fma(F2 a, F2 b, F2 c) {
+        F2 r;
+        r.v = __ffma2_rn(a.v, b.v, c.v);
+        return r;
+    }
+};
+
+// col_forward_c for two elements per thread: x[c] / x[3 + c] are component
+// c of element A / B. Leaves Dx V in X0, Dy V in X2 and Dz V of each
+// thread's z-lines in gz[6][N]; no final barrier.
+template <bool SW, int HB>
+__device__ __forceinline__ void col_forward_pc(const Real *rowA, const Real *rowB, Real *X0, Real *X1, Real *X2,
+                                               Real (*gz)[N], bool act, int eoff, const LineOffs<SW> &o) {
+    constexpr int CZ = Lay<SW>::CZ;
+    constexpr bool EO = true;
+    Real x[6][N], y[6][N];
+    if (act) {  // x-lines: X0 = Bx u
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                x[c][i] = rowA[3 * i + c];
+                x[3 + c][i] = rowB[3 * i + c];
+            }
+        mv6<TB, false, EO>(x, x + 3, y, y + 3);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+                X0[eoff + c * CZ + o.x + i] = y[c][i];
+                X0[eoff + HB + c * CZ + o.x + i] = y[3 + c][i];
+            }
+    }
+    __syncthreads();
+    if (act) {  // y-lines: X1 = By X0
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) {
+                x[c][t] = X0[eoff + c * CZ + o.y[t]];
+                x[3 + c][t] = X0[eoff + HB + c * CZ + o.y[t]];
+            }
+        mv6<TB, false, EO>(x, x + 3, y, y + 3);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) {
+                X1[eoff + c * CZ + o.y[t]] = y[c][t];
+                X1[eoff + HB + c * CZ + o.y[t]] = y[3 + c][t];
+            }
+    }
+    __syncthreads();
+    if (act) {  // z-lines: values V = Bz X1 (in place, per line), Dz V kept
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) {
+                x[c][t] = X1[eoff + c * CZ + o.z[t]];
+                x[3 + c][t] = X1[eoff + HB + c * CZ + o.z[t]];
+            }
+        mv6<TB, false, EO>(x, x + 3, y, y + 3);
+        mv6<TD, false, EO>(y, y + 3, gz, gz + 3);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) {
+                X1[eoff + c * CZ + o.z[t]] = y[c][t];
+                X1[eoff + HB + c * CZ + o.z[t]] = y[3 + c][t];
+            }
+    }
+    __syncthreads();
+    if (act) {  // x-lines: X0 = Dx V; y-lines: X2 = Dy V
+        Real v[6][N];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) {
+                x[c][t] = X1[eoff + c * CZ + o.x + t];
+                x[3 + c][t] = X1[eoff + HB + c * CZ + o.x + t];
+                v[c][t] = X1[eoff + c * CZ + o.y[t]];
+                v[3 + c][t] = X1[eoff + HB + c * CZ + o.y[t]];
+            }
+        mv6<TD, false, EO>(x, x + 3, y, y + 3);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) {
+                X0[eoff + c * CZ + o.x + t] = y[c][t];
+                X0[eoff + HB + c * CZ + o.x + t] = y[3 + c][t];
+            }
+        mv6<TD, false, EO>(v, v + 3, x, x + 3);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) {
+                X2[eoff + c * CZ + o.y[t]] = x[c][t];
+                X2[eoff + HB + c * CZ + o.y[t]] = x[3 + c][t];
+            }
+    }
+}
+
+// col_backward_c for two elements per thread: X0 holds Qx, X2 holds Qy and
+// rz[c] / rz[3 + c] = Dz^T Qz of element A / B (registers). Ends with the
+// atomic scatter of both elements (each only if it exists).
+template <bool SW, int HB>
+__device__ __forceinline__ void col_backward_pc(const hx::MeshView &m, Real *X0, Real *X1, Real *X2, Real (*rz)[N],
+                                                bool act, bool validA, bool validB, int eoff, const LineOffs<SW> &o,
+                                                int a0, int a1, int eA, int eB, Real *__restrict__ out,
+                                                uint64_t pol_keep) {
+    constexpr int CZ = Lay<SW>::CZ;
+    constexpr bool EO = true;
+    Real x[6][N], y[6][N];
+    if (act) {  // y-lines: X2 = Dy^T X2 in place; z-lines: X1 = rz
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) {
+                x[c][t] = X2[eoff + c * CZ + o.y[t]];
+                x[3 + c][t] = X2[eoff + HB + c * CZ + o.y[t]];
+            }
+        mv6<TD, true, EO>(x, x + 3, y, y + 3);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) {
+                X1[eoff + c * CZ + o.z[t]] = rz[c][t];
+                X1[eoff + HB + c * CZ + o.z[t]] = rz[3 + c][t];
+                X2[eoff + c * CZ + o.y[t]] = y[c][t];
+                X2[eoff + HB + c * CZ + o.y[t]] = y[3 + c][t];
+            }
+    }
+    __syncthreads();
+    if (act) {  // x-lines, in place: X0 = Bx^T (Dx^T X0 + X1 + X2)
+        Real s[6][N];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) {
+                x[c][t] = X0[eoff + c * CZ + o.x + t];
+                x[3 + c][t] = X0[eoff + HB + c * CZ + o.x + t];
+                s[c][t] = X1[eoff + c * CZ + o.x + t] + X2[eoff + c * CZ + o.x + t];
+                s[3 + c][t] = X1[eoff + HB + c * CZ + o.x + t] + X2[eoff + HB + c * CZ + o.x + t];
+            }
+        mv6<TD, true, EO>(x, x + 3, y, y + 3);
+#pragma unroll
+        for (int c = 0; c < 6; ++c)
+#pragma unroll
+            for (int k = 0; k < N; ++k) s[c][k] = y[c][k] + s[c][k];
+        mv6<TB, true, EO>(s, s + 3, y, y + 3);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) {
+                X0[eoff + c * CZ + o.x + t] = y[c][t];
+                X0[eoff + HB + c * CZ + o.x + t] = y[3 + c][t];
+            }
+    }
+    __syncthreads();
+    if (act) {  // y-lines: X1 = By^T X0
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) {
+                x[c][t] = X0[eoff + c * CZ + o.y[t]];
+                x[3 + c][t] = X0[eoff + HB + c * CZ + o.y[t]];
+            }
+        mv6<TB, true, EO>(x, x + 3, y, y + 3);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) {
+                X1[eoff + c * CZ + o.y[t]] = y[c][t];
+                X1[eoff + HB + c * CZ + o.y[t]] = y[3 + c][t];
+            }
+    }
+    __syncthreads();
+    if (validA) {  // z-lines: r = Bz^T X1, scattered from registers
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int t = 0; t < N; ++t) {
+                x[c][t] = X1[eoff + c * CZ + o.z[t]];
+                x[3 + c][t] = X1[eoff + HB + c * CZ + o.z[t]];
+            }
+        mv6<TB, true, EO>(x, x + 3, y, y + 3);
+        const bool msk = m.dmask != nullptr;
+        const int64_t baseA = elem_base(m, eA);
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const int64_t d = 3 * node_at(m, baseA, a0, a1, k);
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                if (!(msk && m.dmask[d + c])) red_add(out + d + c, y[c][k], pol_keep);
+        }
+        if (validB) {
+            const int64_t baseB = elem_base(m, eB);
+#pragma unroll
+            for (int k = 0; k < N; ++k) {
+                const int64_t d = 3 * node_at(m, baseB, a0, a1, k);
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    if (!(msk && m.dmask[d + c])) red_add(out + d + c, y[3 + c][k], pol_keep);
+            }
+        }
+    }
+}
+
+// One tile (EPB elements from tile*EPB) of the staged apply with two elements
+// per thread on NT = threads for EPB/2 elements; the tile's point fields were
+// bulk-copied into the stage on `bar` a tile earlier, and the copies of tile
+// `ntile` (< 0: none) are issued once the stage is consumed. Returns false
+// (on every thread) if the staged data never arrived. Caching strategies only.
+template <int EPB, int LAW, int STORAGE>
+__device__ __forceinline__ bool apply_tile_pair(const hx::MeshView &m, int tile, int ntile, Real *__restrict__ out,
+                                                const Real *cdA, const Real *cdB, unsigned char *smem_raw, Real *stg,
+                                                uint64_t *bar, uint32_t &phase, uint64_t pol_keep) {
+    static_assert(STORAGE != HX_RECOMPUTE && EPB % 2 == 0, "pair tiles: caching strategies, even tiles");
+    constexpr bool SW = ROWSW;
+    constexpr int ES = Lay<SW>::ES;
+    constexpr int CZ = Lay<SW>::CZ;
+    constexpr int HE = EPB / 2;   // thread slots; B = A + HE
+    constexpr int HB = HE * ES;   // word offset of B's cubes
+    Real *X0 = (Real *)smem_raw;
+    Real *X1 = X0 + EPB * ES;
+    Real *X2 = X1 + EPB * ES;
+    const int t = threadIdx.x;
+    int el, a0, a1;
+    bool act;
+    thread_map<SW>(t, HE, el, a0, a1, act);
+    const int eoff = (act ? el : 0) * ES;
+    using QF = QpFields<LAW, STORAGE>;
+    constexpr int NR = QF::n;
+    const int eA = tile * EPB + el, eB = eA + HE;
+    const bool validA = act && eA < m.n_elem, validB = act && eB < m.n_elem;
+    const LineOffs<SW> lo = line_offsets<SW>(a0, a1);
+    Real gz[6][N];
+    col_forward_pc<SW, HB>(cdA, cdB, X0, X1, X2, gz, act, eoff, lo);
+    const bool ok = mbar_wait(bar, phase, m.wait_limit);
+    if (__syncthreads_or(!ok)) {  // also the barrier that completes the forward sweeps
+        if (t == 0) {
+            atomicOr(m.err + 2, 1);
+            mbar_wait(bar, phase, m.wait_limit);  // let a copy still in flight land before the CTA exits
+        }
+        return false;
+    }
+    phase ^= 1u;
+    if (validA) {  // B past the end of the mesh runs on stale stage words and is never scattered
+        const Real *spA = stg + el * NQ + a0 + N * a1;
+        const Real *spB = spA + HE * NQ;
+        Real rA[NR], rB[NR], Gx[6], Gy[6];
+        auto fetch = [&](int k) {
+#pragma unroll
+            for (int f = 0; f < NR; ++f) {
+                rA[f] = spA[f * (EPB * NQ) + NN * k];
+                rB[f] = spB[f * (EPB * NQ) + NN * k];
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                Gx[c] = X0[eoff + lo.z[k] + c * CZ];
+                Gx[3 + c] = X0[eoff + HB + lo.z[k] + c * CZ];
+                Gy[c] = X2[eoff + lo.z[k] + c * CZ];
+                Gy[3 + c] = X2[eoff + HB + lo.z[k] + c * CZ];
+            }
+        };
+        fetch(0);
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            Real QA[9], QB[9];
+            if constexpr (STORAGE == HX_SPATIAL_TENSORS && PK) {
+                F2 G2[9], Q2[9];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    G2[c * 3 + 0] = F2(Gx[c], Gx[3 + c]);
+                    G2[c * 3 + 1] = F2(Gy[c], Gy[3 + c]);
+                    G2[c * 3 + 2] = F2(gz[c][k], gz[3 + c][k]);
+                }
+                spatial_Q<F2, LAW>(G2, [&](int f) { return F2(rA[f], rB[f]); }, Q2);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    QA[i] = Q2[i].v.x;
+                    QB[i] = Q2[i].v.y;
+                }
+            } else {
+                Real GA[9], GB[9];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    GA[c * 3 + 0] = Gx[c];
+                    GA[c * 3 + 1] = Gy[c];
+                    GA[c * 3 + 2] = gz[c][k];
+                    GB[c * 3 + 0] = Gx[3 + c];
+                    GB[c * 3 + 1] = Gy[3 + c];
+                    GB[c * 3 + 2] = gz[3 + c][k];
+                }
+                qp_tangent<LAW, STORAGE>(m, eA, GA, nullptr, rA, QA);
+                qp_tangent<LAW, STORAGE>(m, validB ? eB : eA, GB, nullptr, rB, QB);
+            }
+            if (k + 1 < N) fetch(k + 1);
+            const int pk = eoff + lo.z[k];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                X0[pk + c * CZ] = QA[c * 3 + 0];
+                X2[pk + c * CZ] = QA[c * 3 + 1];
+                X0[pk + HB + c * CZ] = QB[c * 3 + 0];
+                X2[pk + HB + c * CZ] = QB[c * 3 + 1];
+                gz[c][k] = QA[c * 3 + 2];
+                gz[3 + c][k] = QB[c * 3 + 2];
+            }
+        }
+    }
+    Real rz[6][N];
+    mv6<TD, true, true>(gz, gz + 3, rz, rz + 3);
+    __syncthreads();
+    if (t == 0 && ntile >= 0) stage_issue<EPB, LAW, STORAGE>(m, ntile, stg, bar);
+    col_backward_pc<SW, HB>(m, X0, X1, X2, rz, act, validA, validB, eoff, lo, a0, a1, eA, eB, out, pol_keep);
     return true;
 }
 
@@ -1820,6 +2175,53 @@ __global__ void __launch_bounds__(apply_threads<STAGED && ROWSW>(EPB)) k_apply(c
         if (!apply_tile<EPB, apply_threads<STAGED && ROWSW>(EPB), LAW, STORAGE, STAGED>(m, tile, ntile < ntiles ? ntile : -1, out, cd,
                                                                     ck, smem_raw, stg, &bar, phase, pol_keep,
                                                                     pol_stream))
+            return;
+    }
+}
+
+// out += K(u_k) du with two elements per thread (staged path, caching
+// strategies): as k_apply with STAGED, but slot el of a tile of EPB elements
+// carries elements el and el + EPB/2, and each thread loads the x-rows of both
+// one tile ahead.
+template <int EPB, int LAW, int STORAGE>
+__global__ void __launch_bounds__(apply_threads<ROWSW>(EPB / 2)) k_apply_pair(const hx::MeshView m,
+                                                                             const Real *__restrict__ du,
+                                                                             Real *__restrict__ out, int ntiles) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    constexpr int HE = EPB / 2;
+    const int t = threadIdx.x;
+    int el, a0, a1;
+    bool act;
+    thread_map<ROWSW>(t, HE, el, a0, a1, act);
+    const uint64_t pol_keep = policy_evict_last();
+    using SM = ApplySmem<EPB, LAW, STORAGE, true>;
+    Real *stg = (Real *)(smem_raw + (SM::cube_bytes + 15) / 16 * 16);
+    uint32_t phase = 0;
+    if (t == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (t == 0 && (int)blockIdx.x < ntiles) stage_issue<EPB, LAW, STORAGE>(m, blockIdx.x, stg, &bar);
+    Real rowA[3 * N], rowB[3 * N];
+    if (act && (int)blockIdx.x < ntiles) {
+        const int e1 = blockIdx.x * EPB + el;
+        load_row(m, e1, elem_base(m, e1), a0, a1, du, true, rowA);
+        load_row(m, e1 + HE, elem_base(m, e1 + HE), a0, a1, du, true, rowB);
+    }
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int ntile = tile + gridDim.x;
+        Real cA[3 * N], cB[3 * N];
+#pragma unroll
+        for (int i = 0; i < 3 * N; ++i) {
+            cA[i] = rowA[i];
+            cB[i] = rowB[i];
+        }
+        if (act && ntile < ntiles) {
+            const int e1 = ntile * EPB + el;
+            load_row(m, e1, elem_base(m, e1), a0, a1, du, true, rowA);
+            load_row(m, e1 + HE, elem_base(m, e1 + HE), a0, a1, du, true, rowB);
+        }
+        if (!apply_tile_pair<EPB, LAW, STORAGE>(m, tile, ntile < ntiles ? ntile : -1, out, cA, cB, smem_raw, stg,
+                                                &bar, phase, pol_keep))
             return;
     }
 }

@@ -57,6 +57,11 @@ struct MeshView {
     MatParamsF matf;  // the same constants rounded once to FP32
     int law;
     int l2pf;         // apply kernel (register-prefetch variants): prefetch the next tile's qp data into L2
+    // test hook (hx_set_wait_test): 1 = the staged apply issues no bulk copy,
+    // so its bounded wait runs out; wait_limit = cycles a bounded wait polls
+    // before it gives up
+    int skip_stage_copies;
+    long long wait_limit;
 };
 
 // Kernel entry points provided by each (degree, precision) translation unit

@@ -37,7 +37,8 @@ EXPORTS = ["hx_create", "hx_destroy", "hx_set_stream", "hx_last_error", "hx_sync
            "hx_estimate_lambda_max", "hx_cg_solve", "hx_body_force", "hx_newton_solve", "hx_material_eval", "hx_mg_create",
            "hx_mg_destroy", "hx_mg_info", "hx_mg_setup", "hx_mg_vcycle", "hx_mg_transfer", "hx_mg_cg_solve", "hx_fibre_dispersion", "hx_batch_create",
            "hx_batch_destroy", "hx_batch_tangent_apply", "hx_measure_fma_peak", "hx_launch_count",
-           "hx_autotune", "hx_set_apply_variant", "hx_chebyshev_smooth_noalloc", "hx_traction_load"]
+           "hx_autotune", "hx_set_apply_variant", "hx_chebyshev_smooth_noalloc", "hx_traction_load",
+           "hx_set_wait_test"]
 
 
 class HxError(RuntimeError):
@@ -134,6 +135,7 @@ def lib():
             "hx_set_apply_variant": (I32, [P, I32, I32, I32]),
             "hx_chebyshev_smooth_noalloc": (I32, [P, P, P, P, I32, D, D, I32, I32]),
             "hx_traction_load": (I32, [C.POINTER(hx_mesh_desc), I32, P, I32, C.POINTER(D), P]),
+            "hx_set_wait_test": (I32, [P, I32, C.c_int64]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -430,6 +432,13 @@ def hx_newton_solve(ctx, mesh, u, f_ext=None, eps_abs=1e-10, eps_rel=1e-8, max_n
 
 def hx_set_apply_variant(ctx, mesh, prec, storage, variant):
     _check(lib().hx_set_apply_variant(mesh, int(prec), int(storage), int(variant)), ctx)
+
+
+def hx_set_wait_test(ctx, mesh, skip_stage_copies, wait_limit_cycles=0):
+    """Test hook: staged applies issue no bulk copy, so their bounded wait
+    runs out after wait_limit_cycles (0 = default) and hx_sync reports
+    HX_ERR_TIMEOUT."""
+    _check(lib().hx_set_wait_test(mesh, int(bool(skip_stage_copies)), int(wait_limit_cycles)), ctx)
 
 
 def hx_autotune(ctx, mesh, du, out, reps=10):
