@@ -840,6 +840,35 @@ def run_sweep(local, hbm_peak, peaks_fp):
     return sweep
 
 
+def run_profile_op(args):
+    """One operator on the benchmark's mesh (32^3 jittered cube, --p, --prec,
+    --storage; the autotuned apply variant unless --variant is given), run
+    --warmup + --steps times: the command the committed ncu summaries of the
+    individual kernels were taken with. Prints one short line, no contract."""
+    import torch
+    from paper_2408_12479_gb300 import hx
+    names = {v: k for k, v in hx.STORAGE_NAMES.items()}
+    prec = hx.HX_FP32 if args.prec == "f32" else hx.HX_FP64
+    storage = names["spatial_tensors" if args.storage == "best" else args.storage]
+    G, m, u, du, out = build_case(args.p, prec, storage, 0)
+    if args.variant >= 0:
+        hx.hx_set_apply_variant(G.ctx, G.handle, prec, storage, args.variant)
+    up = u if prec == hx.HX_FP64 else u.float()
+    d = G.zeros(prec)
+    ops = {"apply": lambda: hx.hx_tangent_apply(G.ctx, G.handle, du, out),
+           "residual": lambda: hx.hx_residual(G.ctx, G.handle, up, out),
+           "precompute": lambda: G.precompute(u, prec, storage),
+           "diagonal": lambda: hx.hx_diagonal(G.ctx, G.handle, d)}
+    torch.cuda.nvtx.range_push("timed")  # profilers restrict capture to this range
+    ms = _event_ms(ops[args.profile_op], max(args.steps, 1), args.warmup)
+    torch.cuda.nvtx.range_pop()
+    G.sync(60000)
+    print(json.dumps({"profile_op": args.profile_op, "p": args.p, "prec": args.prec,
+                      "storage": hx.STORAGE_NAMES[storage], "variant": args.variant if args.variant >= 0 else G.tune[0],
+                      "ms": round(ms, 4)}))
+    G.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -853,12 +882,18 @@ def main():
     ap.add_argument("--storage", default="best", choices=["best", "recompute", "cache_F", "cache_tensors", "spatial_tensors"])
     ap.add_argument("--prec", default="f32", choices=["f32", "f64"])
     ap.add_argument("--min-seconds", type=float, default=1.2, help="least length of the timed region")
+    ap.add_argument("--profile-op", default=None, choices=["apply", "residual", "precompute", "diagonal"],
+                    help="run one operator --warmup + --steps times for a profiler and exit (no contract line)")
+    ap.add_argument("--variant", type=int, default=-1, help="with --profile-op apply: the apply variant (0-5)")
     ap.add_argument("--solve", type=int, default=16,
                     help="also run the FP32- vs FP64-preconditioned CG solve on an n^3 compressed cube (n given)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.profile_op:
+        run_profile_op(args)
         return
 
     import torch

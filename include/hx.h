@@ -205,6 +205,24 @@ hx_status hx_autotune(hx_mesh *mesh, int32_t prec, const void *du_dev, void *out
  * HX_ERR_CUDA. */
 hx_status hx_set_apply_variant(hx_mesh *mesh, int32_t prec, int32_t storage, int32_t variant);
 
+/* How the operator kernels (tangent apply, residual, diagonal) of one mesh
+ * assemble element contributions into the output vector.
+ * HX_SCATTER_ATOMIC (default): atomic adds into the zeroed output. The order
+ *   of the additions at a shared node varies between runs, so results agree
+ *   only to rounding (each node sums at most 8 contributions on a box).
+ * HX_SCATTER_ORDERED: each element stores its local vector into a
+ *   mesh-owned element buffer (n_elem (p+1)^3 * 3 values, allocated on first
+ *   use), and a second kernel sums every node's contributions in ascending
+ *   element order: bitwise repeatable results, for one more pass over that
+ *   buffer. On a connectivity mesh the first switch to ordered mode builds a
+ *   node -> element list on the host (synchronous).
+ * The batch apply and the multigrid levels keep atomic adds. The paper's
+ * element loops are serial per MPI rank; this mode is the GPU's way to the
+ * same fixed summation order (a conflict-free scatter without colouring).
+ * HX_ERR_ARG for an unknown mode. */
+typedef enum { HX_SCATTER_ATOMIC = 0, HX_SCATTER_ORDERED = 1 } hx_scatter;
+hx_status hx_set_scatter_mode(hx_mesh *mesh, int32_t mode);
+
 /* Test hook for the device-side wait limits (no counterpart in the paper):
  * with skip_stage_copies != 0 the staged apply variants (2-5) issue no bulk
  * copy, so their stage never fills and each CTA's bounded wait gives up after
@@ -326,19 +344,33 @@ typedef struct {
 hx_status hx_newton_solve(hx_mesh *mesh, double *u_dev, const double *f_ext_dev, const hx_newton_options *opt,
                           hx_newton_report *report);
 
-/* ---- p-multigrid preconditioner (Sec. 6) -------------------------------- */
-/* Levels of degree p, floor(p/2), ... down to min_degree, built on the mesh's structured box
- * (same elements and geometry; the Dirichlet constraints must be whole faces,
- * component by component, and are carried to every level; other meshes give
- * HX_ERR_UNSUPPORTED). The V-cycle smooths with smoother_degree steps of
- * Chebyshev-Jacobi on [lambda_max/smoothing_range, lambda_max] of D^-1 K per
- * level (before and after the coarse correction), and applies coarse_degree
- * steps of Chebyshev-Jacobi on [lambda_max/coarse_range, lambda_max] on the
- * degree-1 level. Transfers: prolongation = interpolation of the coarser
+/* ---- hp-multigrid preconditioner (Sec. 6) ------------------------------- */
+/* p-levels of degree p, floor(p/2), ... down to min_degree on the mesh's
+ * structured box (same elements and geometry), then, once the degree is 1,
+ * up to h_levels h-levels: the degree-1 box halved in every direction while
+ * all three element counts are even (trilinear geometry only). A coarse
+ * vertex is the finer box's vertex at twice its lattice index, so jittered
+ * boxes coarsen too; the hierarchy is then not nested and the h-transfers
+ * act in lattice coordinates (prolongation = trilinear interpolation of the
+ * coarser lattice function at the finer lattice nodes, which is the exact
+ * embedding when the boxes are nested). The Dirichlet constraints must be
+ * whole faces, component by component, and are carried to every level;
+ * other meshes give HX_ERR_UNSUPPORTED. At most 16 levels.
+ * The V-cycle smooths with smoother_degree steps of Chebyshev-Jacobi on
+ * [lambda_max/smoothing_range, lambda_max] of D^-1 K per level (before and
+ * after the coarse correction). On the coarsest level it runs, if
+ * coarse_cg_iters > 0, FP64 Jacobi-preconditioned CG on that level's tangent
+ * (assembled once per hx_mg_setup from the matrix-free operator; at most
+ * 1024 DoFs, else HX_ERR_UNSUPPORTED) for at most coarse_cg_iters
+ * iterations or down to a relative residual of coarse_cg_tol -- the paper's
+ * coarse solver is AMG or a direct solve; this is its stand-in -- and else
+ * coarse_degree steps of Chebyshev-Jacobi on [lambda_max/coarse_range,
+ * lambda_max]. p-transfers: prolongation = interpolation of the coarser
  * Lagrange function at the finer nodes, restriction = its transpose; the
  * linearization point of a coarser level is the finer state evaluated at its
- * nodes. All level operators are the matrix-free tangent in precond_prec with
- * the `storage` strategy. The mesh must outlive the multigrid object. */
+ * nodes (for an h-level: at the shared lattice nodes). All level operators
+ * are the matrix-free tangent in precond_prec with the `storage` strategy.
+ * The mesh must outlive the multigrid object. */
 typedef struct {
     int32_t smoother_degree;
     double smoothing_range;
@@ -349,11 +381,19 @@ typedef struct {
     int32_t lambda_iters;     /* power iterations per level (x1.2 safety) */
     int32_t min_degree;       /* coarsest degree (>= 1): levels stop once p/2 would fall below it */
     double coarse_weight;     /* coarse corrections are added scaled by this weight (0 < w <= 1) */
+    int32_t h_levels;         /* at most this many h-coarsenings after the p-levels (0: none) */
+    int32_t coarse_cg_iters;  /* > 0: coarse FP64 Jacobi-CG with this iteration limit; 0: Chebyshev */
+    double coarse_cg_tol;     /* relative residual at which the coarse CG stops (> 0 if used) */
 } hx_mg_options;
 hx_status hx_mg_create(hx_mesh *mesh, const hx_mg_options *opt, hx_mg **mg);
 void hx_mg_destroy(hx_mg *mg);
-/* Number of levels and their degrees (degrees may be NULL; at most 8). */
+/* Number of levels and their degrees (degrees may be NULL; at most 16). */
 hx_status hx_mg_info(const hx_mg *mg, int32_t *n_levels, int32_t *degrees);
+/* Degree and element counts of one level. */
+hx_status hx_mg_level(const hx_mg *mg, int32_t level, int32_t *p, int32_t *nx, int32_t *ny, int32_t *nz);
+/* Iterations the coarse CG took in the last V-cycle (synchronous; -1 if the
+ * coarsest level runs Chebyshev or no V-cycle ran yet). */
+hx_status hx_mg_coarse_iters(const hx_mg *mg, int32_t *iters);
 /* Per Newton state (Alg. 1): transfer u_dev (FP64) to every level, refresh the
  * quadrature-point data (FP64 and precond_prec), the inverse diagonals and the
  * eigenvalue bounds. Synchronous; reports J <= 0 as HX_ERR_NONINVERTIBLE. */
@@ -362,7 +402,8 @@ hx_status hx_mg_setup(hx_mg *mg, const double *u_dev);
 hx_status hx_mg_vcycle(hx_mg *mg, const void *b_dev, void *x_dev);
 /* Transfer between level `level` and level+1 in `prec`: dir 0 prolongation
  * (src on level+1, dst on level), 1 restriction (src on level, dst on
- * level+1, overwritten), 2 state transfer (src on level, dst on level+1). */
+ * level+1, overwritten), 2 state transfer (src on level, dst on level+1;
+ * FP64 only between h-levels). */
 hx_status hx_mg_transfer(hx_mg *mg, int32_t level, int32_t dir, const void *src_dev, void *dst_dev, int32_t prec);
 /* FP64 flexible CG on the finest tangent with one V-cycle as preconditioner
  * (same stopping rule and statuses as hx_cg_solve); needs hx_mg_setup at the

@@ -620,3 +620,30 @@ def box_transfer_matrix(nx, ny, nz, pc, pf):
                             col = (loc[0][0] * pc + a) + Nc[0] * ((loc[1][0] * pc + b) + Nc[1] * (loc[2][0] * pc + c))
                             P[row, col] = w
     return P
+
+
+def box_h_transfer_matrix(nxc, nyc, nzc):
+    """Dense prolongation between the degree-1 spaces of a structured box of
+    nxc*nyc*nzc elements (coarse) and the box with every direction split in
+    two (fine), per displacement component: P[I, J] = value at fine lattice
+    node I of the coarse lattice's piecewise-trilinear hat function J, both
+    lattices in the coarse lattice's coordinates (fine node (i, j, k) sits at
+    (i/2, j/2, k/2)). This is the h-step of the hp-multigrid hierarchy of
+    Sec. 6 (Fehn et al.), the embedding of the coarse space in the fine one
+    when the boxes are nested. Plain loops; small boxes."""
+    def hat(t, c):
+        return max(0.0, 1.0 - abs(t - c))
+    Mc = [nxc + 1, nyc + 1, nzc + 1]
+    Mf = [2 * nxc + 1, 2 * nyc + 1, 2 * nzc + 1]
+    P = np.zeros((Mf[0] * Mf[1] * Mf[2], Mc[0] * Mc[1] * Mc[2]))
+    for fk in range(Mf[2]):
+        for fj in range(Mf[1]):
+            for fi in range(Mf[0]):
+                row = fi + Mf[0] * (fj + Mf[1] * fk)
+                for ck in range(Mc[2]):
+                    for cj in range(Mc[1]):
+                        for ci in range(Mc[0]):
+                            w = hat(fi / 2.0, ci) * hat(fj / 2.0, cj) * hat(fk / 2.0, ck)
+                            if w != 0.0:
+                                P[row, ci + Mc[0] * (cj + Mc[1] * ck)] = w
+    return P

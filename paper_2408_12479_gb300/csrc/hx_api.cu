@@ -226,6 +226,9 @@ struct hx_mesh {
     QpCache cache[2];
     int variant[2][4] = {{0, 0, 0, 0}, {0, 0, 0, 0}};  // autotuned apply variant per (prec, storage)
     int skip_stage_copies = 0;                // hx_set_wait_test
+    int scatter_ordered = 0;                  // hx_set_scatter_mode
+    void *w_elem[2] = {nullptr, nullptr};     // ordered assembly: element-local results per precision
+    int64_t *d_gptr = nullptr, *d_gslot = nullptr;  // ordered assembly on a connectivity mesh: node -> slots
     long long wait_limit = 1ll << 32;        // cycles a bounded device wait polls
     // workspace (allocated on first use)
     std::vector<void *> ws;
@@ -420,7 +423,8 @@ void hx_destroy_mesh(hx_mesh *m) {
     void *ptrs[] = {m->d_dof_conn, m->d_dmask, m->d_cidx, m->d_geo_nodes, m->d_geo_conn, m->d_geo64, m->d_geo32,
                     m->d_fibH64, m->d_fibH32, m->d_fibM, m->cache[0].buf, m->cache[1].buf, m->w_cheb_d[0],
                     m->w_cheb_d[1], m->w_cheb_Kx[0], m->w_cheb_Kx[1], m->w_stage_in, m->w_stage_out, m->w_cg, m->w_newton,
-                    m->w_cg32, m->d_sc, m->d_dots, m->d_partial};
+                    m->w_cg32, m->d_sc, m->d_dots, m->d_partial, m->w_elem[0], m->w_elem[1], m->d_gptr,
+                    m->d_gslot};
     for (void *p : ptrs) dfree(p);
     if (m->h_pinned) cudaFreeHost(m->h_pinned);
     if (m->solve_stream) cudaStreamDestroy(m->solve_stream);
@@ -632,14 +636,52 @@ hx_status hx_precompute_qp(hx_mesh *m, const double *u_dev, int32_t store_prec, 
     return HX_OK;
 }
 
+// Ordered assembly: the element buffer of `prec` (n_elem (p+1)^3 * 3 values),
+// allocated on first use.
+static hx_status ensure_elem_ws(hx_mesh *m, int prec) {
+    if (!m->w_elem[prec])
+        HX_CUDA(m->ctx, cudaMalloc(&m->w_elem[prec], 3 * (size_t)m->n_qp * prec_size(prec) + 64));
+    return HX_OK;
+}
+
+// Operator kernels write their output either by atomic adds into the zeroed
+// vector (default) or, in ordered mode, element by element into the element
+// buffer, which gather_out then sums node by node in ascending element order.
+static hx_status begin_out(hx_mesh *m, int prec, void *out, hx::MeshView &v) {
+    hx_ctx *ctx = m->ctx;
+    if (!m->scatter_ordered) {
+        HX_CUDA(ctx, cudaMemsetAsync(out, 0, 3 * (size_t)m->n_nodes * prec_size(prec), ctx->stream));
+        return HX_OK;
+    }
+    hx_status st = ensure_elem_ws(m, prec);
+    if (st != HX_OK) return st;
+    v.elem_out = m->w_elem[prec];
+    return HX_OK;
+}
+static hx_status gather_out(hx_mesh *m, int prec, const hx::MeshView &v, void *out) {
+    hx_ctx *ctx = m->ctx;
+    if (!m->scatter_ordered) return HX_OK;
+    if (m->structured)
+        HX_CUDA(ctx, hx::gather_box(m->n_nodes, m->p, m->nx, m->ny, m->nz, m->w_elem[prec], v.dmask, out, prec,
+                                    ctx->stream));
+    else
+        HX_CUDA(ctx, hx::gather_csr(m->n_nodes, m->d_gptr, m->d_gslot, m->w_elem[prec], v.dmask, out, prec,
+                                    ctx->stream));
+    ctx->launches++;
+    return HX_OK;
+}
+
 static hx_status apply_dev(hx_mesh *m, const void *du, void *out, int prec) {
     hx_ctx *ctx = m->ctx;
     const QpCache &c = m->cache[prec];
     if (!c.valid) return fail(ctx, HX_ERR_NOT_READY, "hx_tangent_apply: no quadrature-point data at this precision (call hx_precompute_qp)");
-    HX_CUDA(ctx, cudaMemsetAsync(out, 0, 3 * (size_t)m->n_nodes * prec_size(prec), ctx->stream));
-    const hx::MeshView v = view(m, prec);
+    hx::MeshView v = view(m, prec);
+    hx_status st = begin_out(m, prec, out, v);
+    if (st != HX_OK) return st;
     HX_CUDA(ctx, hx::prec_ops(m->p, prec)->apply(v, c.storage, du, out, ctx->stream, m->variant[prec][c.storage]));
     ctx->launches++;
+    st = gather_out(m, prec, v, out);
+    if (st != HX_OK) return st;
     if (m->n_constrained) {
         HX_CUDA(ctx, hx::copy_idx(m->d_cidx, m->n_constrained, du, out, prec, ctx->stream));
         ctx->launches++;
@@ -651,6 +693,30 @@ hx_status hx_tangent_apply(hx_mesh *m, const void *du_dev, void *out_dev, int32_
     if (!m || !du_dev || !out_dev || bad_prec(prec) || du_dev == out_dev)
         return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_tangent_apply: bad argument");
     return apply_dev(m, du_dev, out_dev, prec);
+}
+
+hx_status hx_set_scatter_mode(hx_mesh *m, int32_t mode) {
+    if (!m || (mode != HX_SCATTER_ATOMIC && mode != HX_SCATTER_ORDERED))
+        return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_set_scatter_mode: bad argument");
+    hx_ctx *ctx = m->ctx;
+    if (mode == HX_SCATTER_ORDERED && !m->structured && !m->d_gptr) {
+        // node -> (element, local node) slots, ascending in element and local node
+        const int64_t nq = (int64_t)(m->p + 1) * (m->p + 1) * (m->p + 1);
+        std::vector<int32_t> conn((size_t)(m->n_elem * nq));
+        HX_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        HX_CUDA(ctx, cudaMemcpy(conn.data(), m->d_dof_conn, conn.size() * sizeof(int32_t), cudaMemcpyDeviceToHost));
+        std::vector<int64_t> ptr((size_t)m->n_nodes + 1, 0), slot(conn.size());
+        for (int32_t v : conn) ptr[(size_t)v + 1]++;
+        for (int64_t i = 0; i < m->n_nodes; ++i) ptr[(size_t)i + 1] += ptr[(size_t)i];
+        std::vector<int64_t> fill(ptr.begin(), ptr.end() - 1);
+        for (int64_t s = 0; s < (int64_t)conn.size(); ++s) slot[(size_t)fill[(size_t)conn[(size_t)s]]++] = s;
+        HX_CUDA(ctx, cudaMalloc((void **)&m->d_gptr, ptr.size() * sizeof(int64_t)));
+        HX_CUDA(ctx, cudaMalloc((void **)&m->d_gslot, (slot.size() + 1) * sizeof(int64_t)));
+        HX_CUDA(ctx, cudaMemcpy(m->d_gptr, ptr.data(), ptr.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+        HX_CUDA(ctx, cudaMemcpy(m->d_gslot, slot.data(), slot.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    }
+    m->scatter_ordered = mode == HX_SCATTER_ORDERED;
+    return HX_OK;
 }
 
 hx_status hx_set_wait_test(hx_mesh *m, int32_t skip_stage_copies, int64_t wait_limit_cycles) {
@@ -737,11 +803,12 @@ hx_status hx_residual(hx_mesh *m, const void *u_dev, void *r_dev, int32_t prec) 
     if (!m || !u_dev || !r_dev || bad_prec(prec) || u_dev == r_dev)
         return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_residual: bad argument");
     hx_ctx *ctx = m->ctx;
-    HX_CUDA(ctx, cudaMemsetAsync(r_dev, 0, 3 * (size_t)m->n_nodes * prec_size(prec), ctx->stream));
-    const hx::MeshView v = view(m, prec);
+    hx::MeshView v = view(m, prec);
+    hx_status st = begin_out(m, prec, r_dev, v);
+    if (st != HX_OK) return st;
     HX_CUDA(ctx, hx::prec_ops(m->p, prec)->residual(v, u_dev, r_dev, ctx->stream));
     ctx->launches++;
-    return HX_OK;
+    return gather_out(m, prec, v, r_dev);
 }
 
 hx_status hx_diagonal(hx_mesh *m, void *diag_dev, int32_t prec) {
@@ -749,10 +816,13 @@ hx_status hx_diagonal(hx_mesh *m, void *diag_dev, int32_t prec) {
     hx_ctx *ctx = m->ctx;
     const QpCache &c = m->cache[prec];
     if (!c.valid) return fail(ctx, HX_ERR_NOT_READY, "hx_diagonal: no quadrature-point data at this precision");
-    HX_CUDA(ctx, cudaMemsetAsync(diag_dev, 0, 3 * (size_t)m->n_nodes * prec_size(prec), ctx->stream));
-    const hx::MeshView v = view(m, prec);
+    hx::MeshView v = view(m, prec);
+    hx_status st = begin_out(m, prec, diag_dev, v);
+    if (st != HX_OK) return st;
     HX_CUDA(ctx, hx::prec_ops(m->p, prec)->diagonal(v, c.storage, diag_dev, ctx->stream));
     ctx->launches++;
+    st = gather_out(m, prec, v, diag_dev);
+    if (st != HX_OK) return st;
     if (m->n_constrained) {
         HX_CUDA(ctx, hx::set_idx(m->d_cidx, m->n_constrained, 1.0, diag_dev, prec, ctx->stream));
         ctx->launches++;
@@ -1379,6 +1449,11 @@ struct hx_mg {
     std::vector<double *> dinv64;       // per level, FP64 inverse diagonal (spectral estimate)
     std::vector<double *> u;  // linearization state per level (FP64), l >= 1
     std::vector<double> lam;
+    std::vector<int> hpair;   // hpair[l] = 1: lv[l+1] is the 2x h-coarsening of lv[l] (degree 1)
+    double *A_c = nullptr;    // coarsest level: assembled FP64 tangent (column-major), for the coarse CG
+    double *I_c = nullptr;    // identity of the coarsest level's size (the assembly's unit vectors)
+    int n_c = 0;
+    int *d_cit = nullptr;     // iterations of the last coarse CG
     hx_mg_options opt{};
     bool ready = false;
 };
@@ -1410,6 +1485,9 @@ void hx_mg_destroy(hx_mg *g) {
             hx_destroy_mesh(g->lv[l]);
         }
     }
+    dfree(g->A_c);
+    dfree(g->I_c);
+    dfree(g->d_cit);
     delete g;
 }
 
@@ -1417,7 +1495,8 @@ hx_status hx_mg_create(hx_mesh *m, const hx_mg_options *opt, hx_mg **out) {
     if (!m || !opt || !out || bad_prec(opt->precond_prec) || opt->smoother_degree < 1 || opt->coarse_degree < 1 ||
         !(opt->smoothing_range > 1.0) || !(opt->coarse_range > 1.0) || opt->lambda_iters < 1 ||
         opt->storage < HX_RECOMPUTE || opt->storage > HX_SPATIAL_TENSORS || opt->min_degree < 1 ||
-        !(opt->coarse_weight > 0.0) || opt->coarse_weight > 1.0)
+        !(opt->coarse_weight > 0.0) || opt->coarse_weight > 1.0 || opt->h_levels < 0 || opt->coarse_cg_iters < 0 ||
+        (opt->coarse_cg_iters > 0 && !(opt->coarse_cg_tol > 0.0)))
         return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_mg_create: bad argument");
     hx_ctx *ctx = m->ctx;
     if (!m->structured)
@@ -1491,8 +1570,99 @@ hx_status hx_mg_create(hx_mesh *m, const hx_mg_options *opt, hx_mg **out) {
         }
         g->lv.push_back(c);
     }
+    g->hpair.assign(g->lv.size(), 0);
+    // h-levels: halve the degree-1 box while every direction has an even
+    // number of elements; a coarse vertex is the fine lattice vertex at twice
+    // its index (found through the fine element's corner), so any trilinear
+    // box coarsens, nested or not
+    for (int h = 0; h < opt->h_levels; ++h) {
+        hx_mesh *f = g->lv.back();
+        if (f->p != 1 || f->g != 1 || f->nx % 2 || f->ny % 2 || f->nz % 2) break;
+        const int cx = f->nx / 2, cy = f->ny / 2, cz = f->nz / 2;
+        const int64_t Vx = cx + 1, Vy = cy + 1, Vz = cz + 1;
+        std::vector<double> verts(3 * Vx * Vy * Vz);
+        for (int64_t n = 0; n < Vx * Vy * Vz; ++n) {
+            const int64_t I = 2 * (n % Vx), J = 2 * ((n / Vx) % Vy), K = 2 * (n / (Vx * Vy));
+            const int64_t ex = I < f->nx ? I : f->nx - 1, ey = J < f->ny ? J : f->ny - 1, ez = K < f->nz ? K : f->nz - 1;
+            const int64_t e = ex + f->nx * (ey + (int64_t)f->ny * ez);
+            const int corner = (int)(I - ex) + 2 * (int)(J - ey) + 4 * (int)(K - ez);
+            const int64_t v = f->h_geo_conn[8 * e + corner];
+            for (int c = 0; c < 3; ++c) verts[3 * n + c] = f->h_geo_nodes[3 * v + c];
+        }
+        const int64_t ne = (int64_t)cx * cy * cz;
+        std::vector<int32_t> gconn(8 * ne);
+        std::vector<double> frames;
+        if (!f->h_frames.empty()) frames.resize(9 * ne);
+        for (int64_t e = 0; e < ne; ++e) {
+            const int64_t ex = e % cx, ey = (e / cx) % cy, ez = e / ((int64_t)cx * cy);
+            for (int corner = 0; corner < 8; ++corner)
+                gconn[8 * e + corner] = (int32_t)((ex + (corner & 1)) + Vx * ((ey + ((corner >> 1) & 1)) + Vy * (ez + (corner >> 2))));
+            if (!frames.empty()) {  // the frame of the coarse element's first child
+                const int64_t fe = 2 * ex + f->nx * (2 * ey + (int64_t)f->ny * 2 * ez);
+                for (int k = 0; k < 9; ++k) frames[9 * e + k] = f->h_frames[9 * fe + k];
+            }
+        }
+        std::vector<uint8_t> mask(3 * Vx * Vy * Vz, 0);
+        bool any = false;
+        for (int64_t n = 0; n < Vx * Vy * Vz; ++n) {
+            const int64_t I = n % Vx, J = (n / Vx) % Vy, K = n / (Vx * Vy);
+            for (int c = 0; c < 3; ++c)
+                for (int fc = 0; fc < 6; ++fc)
+                    if (face[fc][c] && on_face(fc, I, J, K, Vx, Vy, Vz)) {
+                        mask[3 * n + c] = 1;
+                        any = true;
+                    }
+        }
+        hx_mesh_desc d{};
+        d.n_elem = (int32_t)ne;
+        d.p = 1;
+        d.geo_degree = 1;
+        d.n_nodes = Vx * Vy * Vz;
+        d.geo_nodes = verts.data();
+        d.n_geo_nodes = Vx * Vy * Vz;
+        d.geo_conn = gconn.data();
+        d.dof_conn = nullptr;
+        d.nx = cx;
+        d.ny = cy;
+        d.nz = cz;
+        d.dirichlet = any ? mask.data() : nullptr;
+        d.fibre_frames = frames.empty() ? nullptr : frames.data();
+        hx_mesh *c = nullptr;
+        hx_status st = hx_setup_mesh(ctx, &d, &m->h_mat, &c);
+        if (st != HX_OK) {
+            hx_mg_destroy(g);
+            return st;
+        }
+        g->hpair.back() = 1;
+        g->lv.push_back(c);
+        g->hpair.push_back(0);
+    }
     const size_t L = g->lv.size();
     const int pp = opt->precond_prec;
+    if (L > 16) {
+        hx_mg_destroy(g);
+        return fail(ctx, HX_ERR_UNSUPPORTED, "hx_mg_create: more than 16 levels");
+    }
+    if (opt->coarse_cg_iters > 0) {
+        const int64_t nc = 3 * g->lv.back()->n_nodes;
+        if (nc > hx::COARSE_MAX) {
+            hx_mg_destroy(g);
+            return fail(ctx, HX_ERR_UNSUPPORTED, "hx_mg_create: the coarsest level has " + std::to_string(nc) +
+                                                     " DoFs, more than the coarse CG's " +
+                                                     std::to_string(hx::COARSE_MAX));
+        }
+        g->n_c = (int)nc;
+        std::vector<double> eye((size_t)nc * nc, 0.0);
+        for (int64_t i = 0; i < nc; ++i) eye[(size_t)(i * nc + i)] = 1.0;
+        cudaError_t e = cudaMalloc((void **)&g->A_c, eye.size() * sizeof(double) + 64);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&g->I_c, eye.size() * sizeof(double) + 64);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&g->d_cit, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemcpy(g->I_c, eye.data(), eye.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            hx_mg_destroy(g);
+            return cuda_fail(ctx, e, "hx_mg_create (coarse matrix)");
+        }
+    }
     g->b.assign(L, nullptr);
     g->x.assign(L, nullptr);
     g->t.assign(L, nullptr);
@@ -1514,7 +1684,7 @@ hx_status hx_mg_create(hx_mesh *m, const hx_mg_options *opt, hx_mg **out) {
             hx_mg_destroy(g);
             return cuda_fail(ctx, e, "hx_mg_create");
         }
-        if (l + 1 < L) {
+        if (l + 1 < L) {  // (unused for an h-pair: both levels have degree 1)
             g->down.push_back(make_tab(g->lv[l]->p, g->lv[l + 1]->p));
             g->up.push_back(make_tab(g->lv[l + 1]->p, g->lv[l]->p));
         }
@@ -1531,6 +1701,27 @@ hx_status hx_mg_info(const hx_mg *g, int32_t *n_levels, int32_t *degrees) {
     return HX_OK;
 }
 
+hx_status hx_mg_level(const hx_mg *g, int32_t level, int32_t *p, int32_t *nx, int32_t *ny, int32_t *nz) {
+    if (!g || level < 0 || level >= (int32_t)g->lv.size() || !p || !nx || !ny || !nz) return HX_ERR_ARG;
+    const hx_mesh *lm = g->lv[level];
+    *p = lm->p;
+    *nx = lm->nx;
+    *ny = lm->ny;
+    *nz = lm->nz;
+    return HX_OK;
+}
+
+hx_status hx_mg_coarse_iters(const hx_mg *g, int32_t *iters) {
+    if (!g || !iters) return HX_ERR_ARG;
+    *iters = -1;
+    if (!g->d_cit) return HX_OK;
+    int v = -1;
+    HX_CUDA(g->ctx, cudaStreamSynchronize(g->ctx->stream));
+    HX_CUDA(g->ctx, cudaMemcpy(&v, g->d_cit, sizeof v, cudaMemcpyDeviceToHost));
+    *iters = v;
+    return HX_OK;
+}
+
 hx_status hx_mg_setup(hx_mg *g, const double *u_dev) {
     if (!g || !u_dev) return fail(g ? g->ctx : nullptr, HX_ERR_ARG, "hx_mg_setup: bad argument");
     hx_ctx *ctx = g->ctx;
@@ -1544,7 +1735,10 @@ hx_status hx_mg_setup(hx_mg *g, const double *u_dev) {
         if (l > 0) {
             // linearization point of the coarser level: the finer state at its nodes
             const double *uf = l == 1 ? u_dev : g->u[l - 1];
-            HX_CUDA(ctx, hx::interp(g->down[l - 1], lm->nx, lm->ny, lm->nz, uf, g->u[l], 0, HX_FP64, s));
+            if (g->hpair[l - 1])
+                HX_CUDA(ctx, hx::h_inject(lm->nx, lm->ny, lm->nz, uf, g->u[l], s));
+            else
+                HX_CUDA(ctx, hx::interp(g->down[l - 1], lm->nx, lm->ny, lm->nz, uf, g->u[l], 0, HX_FP64, s));
             ul = g->u[l];
             ctx->launches += 1;
         }
@@ -1568,6 +1762,13 @@ hx_status hx_mg_setup(hx_mg *g, const double *u_dev) {
         st = ensure_cheb_ws(lm, pp);
         if (st != HX_OK) return st;
     }
+    if (g->n_c > 0) {  // the coarse CG's matrix: the coarsest tangent (FP64) applied to unit vectors
+        hx_mesh *cm = g->lv.back();
+        for (int j = 0; j < g->n_c; ++j) {
+            hx_status st = apply_dev(cm, g->I_c + (size_t)j * g->n_c, g->A_c + (size_t)j * g->n_c, HX_FP64);
+            if (st != HX_OK) return st;
+        }
+    }
     {
         hx_status st = hx_sync(ctx, -1);  // J <= 0 met at a level's state
         if (st != HX_OK) return st;
@@ -1583,8 +1784,15 @@ static hx_status vcycle(hx_mg *g, size_t l, const void *b, void *x) {
     const int pp = g->opt.precond_prec;
     hx_mesh *lm = g->lv[l];
     const int64_t n = 3 * lm->n_nodes;
-    if (l + 1 == g->lv.size())
+    if (l + 1 == g->lv.size()) {
+        if (g->n_c > 0) {  // FP64 Jacobi-CG on the assembled coarsest tangent
+            HX_CUDA(ctx, hx::coarse_pcg(g->n_c, g->A_c, g->dinv64[l], b, x, g->opt.coarse_cg_iters, g->opt.coarse_cg_tol,
+                                        g->d_cit, pp, s));
+            ctx->launches++;
+            return HX_OK;
+        }
         return cheb_run(lm, b, x, g->dinv[l], g->opt.coarse_degree, g->lam[l], g->opt.coarse_range, 1, pp);
+    }
     hx_status st = cheb_run(lm, b, x, g->dinv[l], g->opt.smoother_degree, g->lam[l], g->opt.smoothing_range, 1, pp);
     if (st != HX_OK) return st;
     // t = b - K x, restricted to the coarser level
@@ -1593,14 +1801,21 @@ static hx_status vcycle(hx_mg *g, size_t l, const void *b, void *x) {
     HX_CUDA(ctx, hx::axpby_p(n, 1.0, b, -1.0, g->t[l], pp, s));
     hx_mesh *cm = g->lv[l + 1];
     const int64_t nc = 3 * cm->n_nodes;
-    HX_CUDA(ctx, cudaMemsetAsync(g->b[l + 1], 0, nc * prec_size(pp), s));
-    HX_CUDA(ctx, hx::interp_t(g->up[l], lm->nx, lm->ny, lm->nz, g->t[l], g->b[l + 1], pp, s));
+    if (g->hpair[l]) {
+        HX_CUDA(ctx, hx::h_restrict(cm->nx, cm->ny, cm->nz, g->t[l], g->b[l + 1], pp, s));
+    } else {
+        HX_CUDA(ctx, cudaMemsetAsync(g->b[l + 1], 0, nc * prec_size(pp), s));
+        HX_CUDA(ctx, hx::interp_t(g->up[l], lm->nx, lm->ny, lm->nz, g->t[l], g->b[l + 1], pp, s));
+    }
     if (cm->n_constrained) HX_CUDA(ctx, hx::set_idx(cm->d_cidx, cm->n_constrained, 0.0, g->b[l + 1], pp, s));
     st = vcycle(g, l + 1, g->b[l + 1], g->x[l + 1]);
     if (st != HX_OK) return st;
     if (g->opt.coarse_weight != 1.0)
         HX_CUDA(ctx, hx::axpby_p(3 * cm->n_nodes, g->opt.coarse_weight, g->x[l + 1], 0.0, g->x[l + 1], pp, s));
-    HX_CUDA(ctx, hx::interp(g->up[l], lm->nx, lm->ny, lm->nz, g->x[l + 1], x, 1, pp, s));
+    if (g->hpair[l])
+        HX_CUDA(ctx, hx::h_prolong(cm->nx, cm->ny, cm->nz, g->x[l + 1], x, 1, pp, s));
+    else
+        HX_CUDA(ctx, hx::interp(g->up[l], lm->nx, lm->ny, lm->nz, g->x[l + 1], x, 1, pp, s));
     if (lm->n_constrained) HX_CUDA(ctx, hx::set_idx(lm->d_cidx, lm->n_constrained, 0.0, x, pp, s));
     ctx->launches += 5;
     return cheb_run(lm, b, x, g->dinv[l], g->opt.smoother_degree, g->lam[l], g->opt.smoothing_range, 0, pp);
@@ -1619,7 +1834,17 @@ hx_status hx_mg_transfer(hx_mg *g, int32_t level, int32_t dir, const void *src_d
     hx_ctx *ctx = g->ctx;
     hx_mesh *fm = g->lv[level];
     cudaStream_t s = ctx->stream;
-    if (dir == 0) {  // prolongation: level+1 -> level
+    hx_mesh *cmh = g->lv[level + 1];
+    if (g->hpair[level]) {
+        if (dir == 0)
+            HX_CUDA(ctx, hx::h_prolong(cmh->nx, cmh->ny, cmh->nz, src_dev, dst_dev, 0, prec, s));
+        else if (dir == 1)
+            HX_CUDA(ctx, hx::h_restrict(cmh->nx, cmh->ny, cmh->nz, src_dev, dst_dev, prec, s));
+        else if (prec == HX_FP64)
+            HX_CUDA(ctx, hx::h_inject(cmh->nx, cmh->ny, cmh->nz, (const double *)src_dev, (double *)dst_dev, s));
+        else
+            return fail(ctx, HX_ERR_ARG, "hx_mg_transfer: the state transfer is FP64");
+    } else if (dir == 0) {  // prolongation: level+1 -> level
         HX_CUDA(ctx, hx::interp(g->up[level], fm->nx, fm->ny, fm->nz, src_dev, dst_dev, 0, prec, s));
     } else if (dir == 1) {  // restriction (transpose): level -> level+1
         HX_CUDA(ctx, cudaMemsetAsync(dst_dev, 0, 3 * (size_t)g->lv[level + 1]->n_nodes * prec_size(prec), s));

@@ -265,6 +265,10 @@ __device__ __forceinline__ void scatter_add(const hx::MeshView &m, int e0, int e
         const int e = e0 + el;
         if (e >= m.n_elem) continue;
         const int i = a % N, j = (a / N) % N, k = a / NN;
+        if (m.elem_out) {  // ordered assembly: the gather pass sums and masks
+            ((T *)m.elem_out)[3 * ((int64_t)e * NQ + a) + c] = U[(el * 3 + c) * SZ + cidx(i, j, k)];
+            continue;
+        }
         const int64_t d = 3 * node_of(m, e, i, j, k) + c;
         if (mask && m.dmask && m.dmask[d]) continue;
         atomicAdd(out + d, U[(el * 3 + c) * SZ + cidx(i, j, k)]);
@@ -1024,6 +1028,38 @@ __device__ __forceinline__ void mv6(const Real (*x)[N], const Real (*u)[N], Real
     }
 }
 
+// Two FP32 values computed lane-wise with the packed FP32 instructions
+// (FFMA2, FADD2, FMUL2): each lane performs the scalar operation with one
+// rounding, so a function templated on its scalar type gives, per lane, the
+// scalar function's result.
+struct F2 {
+    float2 v;
+    __device__ __forceinline__ F2() {}
+    __device__ __forceinline__ F2(int z) : v(make_float2((float)z, (float)z)) {}
+    __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
+    // hidden friends: found for F2 arguments only, so that the scalar fma and
+    // operators keep their meaning everywhere else
+    __device__ __forceinline__ friend F2 operator+(F2 a, F2 b) {
+        F2 r;
+        r.v = __fadd2_rn(a.v, b.v);
+        return r;
+    }
+    __device__ __forceinline__ friend F2 operator*(F2 a, F2 b) {
+        F2 r;
+        r.v = __fmul2_rn(a.v, b.v);
+        return r;
+    }
+    __device__ __forceinline__ friend F2 &operator+=(F2 &a, F2 b) {
+        a.v = __fadd2_rn(a.v, b.v);
+        return a;
+    }
+    __device__ __forceinline__ friend F2 fma(F2 a, F2 b, F2 c) {
+        F2 r;
+        r.v = __ffma2_rn(a.v, b.v, c.v);
+        return r;
+    }
+};
+
 // node numbering base of an element (structured box: lattice index of its
 // first node; otherwise the element index for the connectivity lookup)
 __device__ __forceinline__ int64_t elem_base(const hx::MeshView &m, int e) {
@@ -1388,12 +1424,17 @@ __device__ __forceinline__ void col_backward(const hx::MeshView &m, Real *X0, Re
     if (valid) {  // z-lines: r = Bz^T X1, scattered from registers
         const int64_t base = elem_base(m, e);
         const bool msk = m.dmask != nullptr;
+        Real *eo = m.elem_out ? (Real *)m.elem_out + 3 * ((int64_t)e * NQ + a0 + N * a1) : nullptr;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             ld_line<2>(X1 + c * CCZ + o2, x);
             mv<TB, true>(x, y);
 #pragma unroll
             for (int k = 0; k < N; ++k) {
+                if (eo) {  // ordered assembly: the gather pass sums and masks
+                    eo[3 * NN * k + c] = y[k];
+                    continue;
+                }
                 const int64_t d = 3 * node_at(m, base, a0, a1, k) + c;
                 if (!(msk && m.dmask[d])) red_add(out + d, y[k], pol_keep);
             }
@@ -1467,6 +1508,14 @@ __device__ __forceinline__ void col_backward_c(const hx::MeshView &m, Real *X0, 
 #pragma unroll
             for (int t = 0; t < N; ++t) x[c][t] = X1[eoff + c * CZ + o.z[t]];
         mv3<TB, true, EO>(x, y);
+        if (m.elem_out) {  // ordered assembly: the gather pass sums and masks
+            Real *eo = (Real *)m.elem_out + 3 * ((int64_t)e * NQ + a0 + N * a1);
+#pragma unroll
+            for (int k = 0; k < N; ++k)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) eo[3 * NN * k + c] = y[c][k];
+            return;
+        }
         const int64_t base = elem_base(m, e);
         const bool msk = m.dmask != nullptr;
 #pragma unroll
@@ -1591,7 +1640,68 @@ __device__ __forceinline__ bool apply_tile(const hx::MeshView &m, int tile, int 
             return false;
         }
         phase ^= 1u;
-        if (valid) {
+        if constexpr (STORAGE == HX_SPATIAL_TENSORS && PK) {
+            // FP32 spatial tensors: the column's points run two at a time in
+            // the two lanes of the packed FP32 instructions (points k, k+1;
+            // an odd last point alone); the next pair's shared loads are
+            // issued before this pair's stores
+            if (valid) {
+                const Real *sp = stg + el * NQ + a0 + N * a1;
+                Real ra[NR], rb[NR], Ga[6], Gb[6];
+                auto fetch1 = [&](int k, Real *r, Real *G) {
+#pragma unroll
+                    for (int f = 0; f < NR; ++f) r[f] = sp[f * (EPB * NQ) + NN * k];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        G[c] = X0[eoff + lo.z[k] + c * CZ];
+                        G[3 + c] = X2[eoff + lo.z[k] + c * CZ];
+                    }
+                };
+                fetch1(0, ra, Ga);
+                if (N > 1) fetch1(1, rb, Gb);
+#pragma unroll
+                for (int k = 0; k + 1 < N; k += 2) {
+                    F2 G2[9], Q2[9];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        G2[c * 3 + 0] = F2(Ga[c], Gb[c]);
+                        G2[c * 3 + 1] = F2(Ga[3 + c], Gb[3 + c]);
+                        G2[c * 3 + 2] = F2(gz[c][k], gz[c][k + 1]);
+                    }
+                    spatial_Q<F2, LAW>(G2, [&](int f) { return F2(ra[f], rb[f]); }, Q2);
+                    if (k + 2 < N) fetch1(k + 2, ra, Ga);
+                    if (k + 3 < N) fetch1(k + 3, rb, Gb);
+                    const int pk = eoff + lo.z[k], pk1 = eoff + lo.z[k + 1];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        X0[pk + c * CZ] = Q2[c * 3 + 0].v.x;
+                        X2[pk + c * CZ] = Q2[c * 3 + 1].v.x;
+                        X0[pk1 + c * CZ] = Q2[c * 3 + 0].v.y;
+                        X2[pk1 + c * CZ] = Q2[c * 3 + 1].v.y;
+                        gz[c][k] = Q2[c * 3 + 2].v.x;
+                        gz[c][k + 1] = Q2[c * 3 + 2].v.y;
+                    }
+                }
+                if constexpr (N % 2 == 1) {  // the last point alone (fetched into ra, Ga)
+                    constexpr int k = N - 1;
+                    Real Gr[9], Q[9];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        Gr[c * 3 + 0] = Ga[c];
+                        Gr[c * 3 + 1] = Ga[3 + c];
+                        Gr[c * 3 + 2] = gz[c][k];
+                    }
+                    spatial_Q<Real, LAW>(Gr, [&](int f) { return ra[f]; }, Q);
+                    const int pk = eoff + lo.z[k];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        X0[pk + c * CZ] = Q[c * 3 + 0];
+                        X2[pk + c * CZ] = Q[c * 3 + 1];
+                        gz[c][k] = Q[c * 3 + 2];
+                    }
+                }
+            }
+        } else if (valid) {
             const Real *sp = stg + el * NQ + a0 + N * a1;
             // point k+1's shared loads are issued before point k's stores
             Real r[NR], Gx[3], Gy[3], Ux[3], Uy[3];
@@ -1668,38 +1778,6 @@ __device__ __forceinline__ bool apply_tile(const hx::MeshView &m, int tile, int 
 // runs A's and B's points in the two lanes of the packed FP32 instructions;
 // one set of line offsets and loop counters serves both elements.
 // ---------------------------------------------------------------------------
-
-// Two FP32 values computed lane-wise with the packed FP32 instructions
-// (FFMA2, FADD2, FMUL2): each lane performs the scalar operation with one
-// rounding, so a function templated on its scalar type gives, per lane, the
-// scalar function's result.
-struct F2 {
-    float2 v;
-    __device__ __forceinline__ F2() {}
-    __device__ __forceinline__ F2(int z) : v(make_float2((float)z, (float)z)) {}
-    __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
-    // hidden friends: found for F2 arguments only, so that the scalar fma and
-    // operators keep their meaning everywhere else
-    __device__ __forceinline__ friend F2 operator+(F2 a, F2 b) {
-        F2 r;
-        r.v = __fadd2_rn(a.v, b.v);
-        return r;
-    }
-    __device__ __forceinline__ friend F2 operator*(F2 a, F2 b) {
-        F2 r;
-        r.v = __fmul2_rn(a.v, b.v);
-        return r;
-    }
-    __device__ __forceinline__ friend F2 &operator+=(F2 &a, F2 b) {
-        a.v = __fadd2_rn(a.v, b.v);
-        return a;
-    }
-    __device__ __forceinline__ friend F2 fma(F2 a, F2 b, F2 c) {
-        F2 r;
-        r.v = __ffma2_rn(a.v, b.v, c.v);
-        return r;
-    }
-};
 
 // col_forward_c for two elements per thread: x[c] / x[3 + c] are component
 // c of element A / B. Leaves Dx V in X0, Dy V in X2 and Dz V of each
@@ -1879,6 +1957,21 @@ __device__ __forceinline__ void col_backward_pc(const hx::MeshView &m, Real *X0,
                 x[3 + c][t] = X1[eoff + HB + c * CZ + o.z[t]];
             }
         mv6<TB, true, EO>(x, x + 3, y, y + 3);
+        if (m.elem_out) {  // ordered assembly: the gather pass sums and masks
+            Real *eo = (Real *)m.elem_out + 3 * ((int64_t)eA * NQ + a0 + N * a1);
+#pragma unroll
+            for (int k = 0; k < N; ++k)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) eo[3 * NN * k + c] = y[c][k];
+            if (validB) {
+                eo += 3 * (int64_t)(eB - eA) * NQ;
+#pragma unroll
+                for (int k = 0; k < N; ++k)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) eo[3 * NN * k + c] = y[3 + c][k];
+            }
+            return;
+        }
         const bool msk = m.dmask != nullptr;
         const int64_t baseA = elem_base(m, eA);
 #pragma unroll

@@ -62,6 +62,9 @@ struct MeshView {
     // before it gives up
     int skip_stage_copies;
     long long wait_limit;
+    // ordered assembly: element-local results go to elem_out[3 (e NQ + a) + c]
+    // with plain stores instead of atomic adds into the output (null: atomic)
+    void *elem_out;
 };
 
 // Kernel entry points provided by each (degree, precision) translation unit

@@ -32,6 +32,199 @@ __global__ void k_set_idx(const int64_t *__restrict__ idx, int64_t n, T val, T *
         dst[idx[i]] = val;
 }
 
+// Ordered assembly on a structured box: one thread per node sums the entries
+// of the (at most eight) elements that contain it, in ascending element
+// order (ez, then ey, then ex): element ex contains node column I iff
+// 0 <= I - ex p <= p, which leaves ex in {I/p - 1, I/p}.
+template <typename T>
+__global__ void k_gather_box(int64_t n_nodes, int p, int nx, int ny, int nz, const T *__restrict__ E,
+                             const uint8_t *__restrict__ dmask, T *__restrict__ out) {
+    const int n = p + 1;
+    const int64_t NQ = (int64_t)n * n * n;
+    const int64_t Nx = (int64_t)nx * p + 1, Ny = (int64_t)ny * p + 1;
+    for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < n_nodes; I += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t ix = I % Nx, iy = (I / Nx) % Ny, iz = I / (Nx * Ny);
+        T s0 = T(0), s1 = T(0), s2 = T(0);
+        for (int bz = 0; bz < 2; ++bz) {
+            const int64_t ez = iz / p - 1 + bz, k = iz - ez * p;
+            if (ez < 0 || ez >= nz || k < 0 || k > p) continue;
+            for (int by = 0; by < 2; ++by) {
+                const int64_t ey = iy / p - 1 + by, j = iy - ey * p;
+                if (ey < 0 || ey >= ny || j < 0 || j > p) continue;
+                for (int bx = 0; bx < 2; ++bx) {
+                    const int64_t ex = ix / p - 1 + bx, i = ix - ex * p;
+                    if (ex < 0 || ex >= nx || i < 0 || i > p) continue;
+                    const int64_t e = ex + nx * (ey + (int64_t)ny * ez);
+                    const T *src = E + 3 * (e * NQ + i + n * (j + n * k));
+                    s0 += src[0];
+                    s1 += src[1];
+                    s2 += src[2];
+                }
+            }
+        }
+        const bool m = dmask != nullptr;
+        out[3 * I + 0] = (m && dmask[3 * I + 0]) ? T(0) : s0;
+        out[3 * I + 1] = (m && dmask[3 * I + 1]) ? T(0) : s1;
+        out[3 * I + 2] = (m && dmask[3 * I + 2]) ? T(0) : s2;
+    }
+}
+
+// Ordered assembly through a node -> (element, local node) list sorted by
+// element: one thread per node, entries summed in list order.
+template <typename T>
+__global__ void k_gather_csr(int64_t n_nodes, const int64_t *__restrict__ ptr, const int64_t *__restrict__ slot,
+                             const T *__restrict__ E, const uint8_t *__restrict__ dmask, T *__restrict__ out) {
+    for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < n_nodes; I += (int64_t)gridDim.x * blockDim.x) {
+        T s0 = T(0), s1 = T(0), s2 = T(0);
+        for (int64_t q = ptr[I]; q < ptr[I + 1]; ++q) {
+            const T *src = E + 3 * slot[q];
+            s0 += src[0];
+            s1 += src[1];
+            s2 += src[2];
+        }
+        const bool m = dmask != nullptr;
+        out[3 * I + 0] = (m && dmask[3 * I + 0]) ? T(0) : s0;
+        out[3 * I + 1] = (m && dmask[3 * I + 1]) ? T(0) : s1;
+        out[3 * I + 2] = (m && dmask[3 * I + 2]) ? T(0) : s2;
+    }
+}
+
+// ---- h-transfers (degree-1 boxes, 2x refinement in index space) ----------
+// weight of coarse lattice index c for fine lattice index f (|f - 2c| <= 1)
+__device__ __forceinline__ double hw(int64_t f, int64_t c) {
+    const int64_t d = f - 2 * c;
+    return d == 0 ? 1.0 : ((d == 1 || d == -1) ? 0.5 : 0.0);
+}
+
+template <typename T>
+__global__ void k_h_prolong(int nxc, int nyc, int nzc, const T *__restrict__ xc, T *__restrict__ xf, int add) {
+    const int64_t Mx = nxc + 1, My = nyc + 1;
+    const int64_t Fx = 2 * nxc + 1, Fy = 2 * nyc + 1, Fz = 2 * nzc + 1;
+    const int64_t nf = Fx * Fy * Fz;
+    for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < nf; I += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t fx = I % Fx, fy = (I / Fx) % Fy, fz = I / (Fx * Fy);
+        T s0 = T(0), s1 = T(0), s2 = T(0);
+        for (int64_t cz = fz / 2; cz <= (fz + 1) / 2; ++cz)
+            for (int64_t cy = fy / 2; cy <= (fy + 1) / 2; ++cy)
+                for (int64_t cx = fx / 2; cx <= (fx + 1) / 2; ++cx) {
+                    const T w = (T)(hw(fx, cx) * hw(fy, cy) * hw(fz, cz));
+                    const T *src = xc + 3 * (cx + Mx * (cy + My * cz));
+                    s0 += w * src[0];
+                    s1 += w * src[1];
+                    s2 += w * src[2];
+                }
+        if (add) {
+            xf[3 * I + 0] += s0;
+            xf[3 * I + 1] += s1;
+            xf[3 * I + 2] += s2;
+        } else {
+            xf[3 * I + 0] = s0;
+            xf[3 * I + 1] = s1;
+            xf[3 * I + 2] = s2;
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_h_restrict(int nxc, int nyc, int nzc, const T *__restrict__ rf, T *__restrict__ bc) {
+    const int64_t Mx = nxc + 1, My = nyc + 1, Mz = nzc + 1;
+    const int64_t Fx = 2 * nxc + 1, Fy = 2 * nyc + 1, Fz = 2 * nzc + 1;
+    const int64_t nc = Mx * My * Mz;
+    for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < nc; I += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t cx = I % Mx, cy = (I / Mx) % My, cz = I / (Mx * My);
+        T s0 = T(0), s1 = T(0), s2 = T(0);
+        for (int64_t fz = 2 * cz - 1; fz <= 2 * cz + 1; ++fz) {
+            if (fz < 0 || fz >= Fz) continue;
+            for (int64_t fy = 2 * cy - 1; fy <= 2 * cy + 1; ++fy) {
+                if (fy < 0 || fy >= Fy) continue;
+                for (int64_t fx = 2 * cx - 1; fx <= 2 * cx + 1; ++fx) {
+                    if (fx < 0 || fx >= Fx) continue;
+                    const T w = (T)(hw(fx, cx) * hw(fy, cy) * hw(fz, cz));
+                    const T *src = rf + 3 * (fx + Fx * (fy + Fy * fz));
+                    s0 += w * src[0];
+                    s1 += w * src[1];
+                    s2 += w * src[2];
+                }
+            }
+        }
+        bc[3 * I + 0] = s0;
+        bc[3 * I + 1] = s1;
+        bc[3 * I + 2] = s2;
+    }
+}
+
+__global__ void k_h_inject(int nxc, int nyc, int nzc, const double *__restrict__ uf, double *__restrict__ uc) {
+    const int64_t Mx = nxc + 1, My = nyc + 1, Mz = nzc + 1;
+    const int64_t Fx = 2 * nxc + 1, Fy = 2 * nyc + 1;
+    const int64_t nc = Mx * My * Mz;
+    for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < nc; I += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t cx = I % Mx, cy = (I / Mx) % My, cz = I / (Mx * My);
+        const int64_t F = 2 * cx + Fx * (2 * cy + Fy * 2 * cz);
+        for (int c = 0; c < 3; ++c) uc[3 * I + c] = uf[3 * F + c];
+    }
+}
+
+// ---- coarse-level FP64 Jacobi-PCG on a dense matrix, one CTA ---------------
+constexpr int CB = 1024;  // threads of the coarse solver's CTA
+
+__device__ double block_sum(double v, double *red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();  // red is free again
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x < 32) {
+        t = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) red[32] = t;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(CB) k_coarse_pcg(int n, const double *__restrict__ A, const double *__restrict__ dinv,
+                                                   const T *__restrict__ b, T *__restrict__ xo, int max_iter, double tol,
+                                                   int *iters) {
+    __shared__ double x[COARSE_MAX], r[COARSE_MAX], z[COARSE_MAX], p[COARSE_MAX], red[33];
+    const int i = threadIdx.x;
+    const bool own = i < n;
+    double ri = own ? (double)b[i] : 0.0;
+    if (own) {
+        x[i] = 0.0;
+        r[i] = ri;
+        z[i] = dinv[i] * ri;
+        p[i] = z[i];
+    }
+    double rz = block_sum(own ? ri * z[i] : 0.0, red);
+    const double bb = block_sum(own ? ri * ri : 0.0, red);
+    double rr = bb;
+    int it = 0;
+    while (it < max_iter && rr > tol * tol * bb && rz > 0.0) {
+        double api = 0.0;
+        if (own)
+            for (int j = 0; j < n; ++j) api += A[i + (int64_t)j * n] * p[j];
+        const double pap = block_sum(own ? p[i] * api : 0.0, red);
+        if (!(pap > 0.0)) break;  // non-positive curvature: keep the last iterate
+        const double alpha = rz / pap;
+        if (own) {
+            x[i] += alpha * p[i];
+            r[i] -= alpha * api;
+            z[i] = dinv[i] * r[i];
+        }
+        const double rz_new = block_sum(own ? r[i] * z[i] : 0.0, red);
+        rr = block_sum(own ? r[i] * r[i] : 0.0, red);
+        const double beta = rz_new / rz;
+        rz = rz_new;
+        if (own) p[i] = z[i] + beta * p[i];
+        __syncthreads();
+        ++it;
+    }
+    if (own) xo[i] = (T)x[i];
+    if (iters && i == 0) *iters = it;
+}
+
 // Chebyshev step: r = D^-1 (rhs - Kx) (Kx null: r = D^-1 rhs), d = cd d + cr r, x += d
 template <typename T>
 __global__ void k_cheb(int64_t n, const T *__restrict__ rhs, const T *__restrict__ Kx, const T *__restrict__ dinv,
@@ -191,6 +384,64 @@ __global__ void k_fma_probe(int iters, T *sink) {
 }
 
 }  // namespace
+
+cudaError_t h_prolong(int nxc, int nyc, int nzc, const void *xc, void *xf, int add, int prec, cudaStream_t s) {
+    const int64_t nf = (int64_t)(2 * nxc + 1) * (2 * nyc + 1) * (2 * nzc + 1);
+    if (prec == HX_FP64)
+        k_h_prolong<double><<<grid_for(nf), VB, 0, s>>>(nxc, nyc, nzc, (const double *)xc, (double *)xf, add);
+    else
+        k_h_prolong<float><<<grid_for(nf), VB, 0, s>>>(nxc, nyc, nzc, (const float *)xc, (float *)xf, add);
+    return cudaGetLastError();
+}
+
+cudaError_t h_restrict(int nxc, int nyc, int nzc, const void *rf, void *bc, int prec, cudaStream_t s) {
+    const int64_t nc = (int64_t)(nxc + 1) * (nyc + 1) * (nzc + 1);
+    if (prec == HX_FP64)
+        k_h_restrict<double><<<grid_for(nc), VB, 0, s>>>(nxc, nyc, nzc, (const double *)rf, (double *)bc);
+    else
+        k_h_restrict<float><<<grid_for(nc), VB, 0, s>>>(nxc, nyc, nzc, (const float *)rf, (float *)bc);
+    return cudaGetLastError();
+}
+
+cudaError_t h_inject(int nxc, int nyc, int nzc, const double *uf, double *uc, cudaStream_t s) {
+    const int64_t nc = (int64_t)(nxc + 1) * (nyc + 1) * (nzc + 1);
+    k_h_inject<<<grid_for(nc), VB, 0, s>>>(nxc, nyc, nzc, uf, uc);
+    return cudaGetLastError();
+}
+
+cudaError_t coarse_pcg(int n, const double *A, const double *dinv, const void *b, void *x, int max_iter, double tol,
+                       int *iters, int prec, cudaStream_t s) {
+    if (n < 0 || n > COARSE_MAX) return cudaErrorInvalidValue;
+    if (prec == HX_FP64)
+        k_coarse_pcg<double><<<1, CB, 0, s>>>(n, A, dinv, (const double *)b, (double *)x, max_iter, tol, iters);
+    else
+        k_coarse_pcg<float><<<1, CB, 0, s>>>(n, A, dinv, (const float *)b, (float *)x, max_iter, tol, iters);
+    return cudaGetLastError();
+}
+
+cudaError_t gather_box(int64_t n_nodes, int p, int nx, int ny, int nz, const void *E, const uint8_t *dmask, void *out,
+                       int prec, cudaStream_t s) {
+    if (n_nodes == 0) return cudaSuccess;
+    if (prec == HX_FP64)
+        k_gather_box<double><<<grid_for(n_nodes), VB, 0, s>>>(n_nodes, p, nx, ny, nz, (const double *)E, dmask,
+                                                               (double *)out);
+    else
+        k_gather_box<float><<<grid_for(n_nodes), VB, 0, s>>>(n_nodes, p, nx, ny, nz, (const float *)E, dmask,
+                                                              (float *)out);
+    return cudaGetLastError();
+}
+
+cudaError_t gather_csr(int64_t n_nodes, const int64_t *ptr, const int64_t *slot, const void *E, const uint8_t *dmask,
+                       void *out, int prec, cudaStream_t s) {
+    if (n_nodes == 0) return cudaSuccess;
+    if (prec == HX_FP64)
+        k_gather_csr<double><<<grid_for(n_nodes), VB, 0, s>>>(n_nodes, ptr, slot, (const double *)E, dmask,
+                                                               (double *)out);
+    else
+        k_gather_csr<float><<<grid_for(n_nodes), VB, 0, s>>>(n_nodes, ptr, slot, (const float *)E, dmask,
+                                                              (float *)out);
+    return cudaGetLastError();
+}
 
 cudaError_t copy_idx(const int64_t *idx, int64_t n, const void *src, void *dst, int prec, cudaStream_t s) {
     if (n == 0) return cudaSuccess;

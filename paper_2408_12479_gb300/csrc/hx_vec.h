@@ -56,4 +56,36 @@ cudaError_t interp_t(const InterpTab &t, int nx, int ny, int nz, const void *src
                      cudaStream_t s);
 cudaError_t fma_probe(int prec, int sm_count, double *flops);
 
+// h-transfers between degree-1 spaces on a structured box of nxc*nyc*nzc
+// elements (coarse) and its 2x refinement in index space (fine: 2nxc*2nyc*2nzc
+// elements; node lattices x fastest). A coarse lattice node (i, j, k) sits at
+// fine lattice node (2i, 2j, 2k), and a coarse function is carried to the
+// fine nodes by trilinear interpolation in lattice coordinates (weights 1 and
+// 1/2 per direction).
+// h_prolong: xf (+)= P xc (add != 0 adds); h_restrict: bc = P^T rf (a 27-point
+// gather per coarse node, no atomics); h_inject: uc = uf at the shared nodes.
+cudaError_t h_prolong(int nxc, int nyc, int nzc, const void *xc, void *xf, int add, int prec, cudaStream_t s);
+cudaError_t h_restrict(int nxc, int nyc, int nzc, const void *rf, void *bc, int prec, cudaStream_t s);
+cudaError_t h_inject(int nxc, int nyc, int nzc, const double *uf, double *uc, cudaStream_t s);
+// Coarse solve: x = the Jacobi-preconditioned CG iterate (FP64, one CTA) for
+// A x = b from x = 0, with A the dense column-major n x n matrix (n <=
+// COARSE_MAX), dinv its inverse diagonal; stops after max_iter iterations or
+// once ||r|| <= tol ||b|| or at non-positive curvature; b and x in `prec`.
+// iters (device int, may be null) receives the iterations taken.
+constexpr int COARSE_MAX = 1024;
+cudaError_t coarse_pcg(int n, const double *A, const double *dinv, const void *b, void *x, int max_iter, double tol,
+                       int *iters, int prec, cudaStream_t s);
+
+// Ordered assembly (deterministic scatter): E holds every element's local
+// vector, E[3 (e NQ + a) + c] for local node a = i + n (j + n k), n = p + 1.
+// out[3 I + c] = the sum over the elements containing node I, taken in
+// ascending element order, of their entries at I; constrained DoFs (dmask)
+// get 0. gather_box: structured box of nx*ny*nz elements (node lattice x
+// fastest); gather_csr: any mesh, with ptr[I]..ptr[I+1] indexing slot[] =
+// e*NQ + a in ascending order.
+cudaError_t gather_box(int64_t n_nodes, int p, int nx, int ny, int nz, const void *E, const uint8_t *dmask, void *out,
+                       int prec, cudaStream_t s);
+cudaError_t gather_csr(int64_t n_nodes, const int64_t *ptr, const int64_t *slot, const void *E, const uint8_t *dmask,
+                       void *out, int prec, cudaStream_t s);
+
 }  // namespace hx

@@ -38,7 +38,7 @@ EXPORTS = ["hx_create", "hx_destroy", "hx_set_stream", "hx_last_error", "hx_sync
            "hx_mg_destroy", "hx_mg_info", "hx_mg_setup", "hx_mg_vcycle", "hx_mg_transfer", "hx_mg_cg_solve", "hx_fibre_dispersion", "hx_batch_create",
            "hx_batch_destroy", "hx_batch_tangent_apply", "hx_measure_fma_peak", "hx_launch_count",
            "hx_autotune", "hx_set_apply_variant", "hx_chebyshev_smooth_noalloc", "hx_traction_load",
-           "hx_set_wait_test"]
+           "hx_set_wait_test", "hx_set_scatter_mode", "hx_mg_level", "hx_mg_coarse_iters"]
 
 
 class HxError(RuntimeError):
@@ -74,7 +74,8 @@ class hx_newton_options(C.Structure):
 class hx_mg_options(C.Structure):
     _fields_ = [("smoother_degree", C.c_int32), ("smoothing_range", C.c_double), ("coarse_degree", C.c_int32),
                 ("coarse_range", C.c_double), ("precond_prec", C.c_int32), ("storage", C.c_int32),
-                ("lambda_iters", C.c_int32), ("min_degree", C.c_int32), ("coarse_weight", C.c_double)]
+                ("lambda_iters", C.c_int32), ("min_degree", C.c_int32), ("coarse_weight", C.c_double),
+                ("h_levels", C.c_int32), ("coarse_cg_iters", C.c_int32), ("coarse_cg_tol", C.c_double)]
 
 
 class hx_newton_report(C.Structure):
@@ -136,6 +137,9 @@ def lib():
             "hx_chebyshev_smooth_noalloc": (I32, [P, P, P, P, I32, D, D, I32, I32]),
             "hx_traction_load": (I32, [C.POINTER(hx_mesh_desc), I32, P, I32, C.POINTER(D), P]),
             "hx_set_wait_test": (I32, [P, I32, C.c_int64]),
+            "hx_set_scatter_mode": (I32, [P, I32]),
+            "hx_mg_level": (I32, [P, I32, C.POINTER(I32), C.POINTER(I32), C.POINTER(I32), C.POINTER(I32)]),
+            "hx_mg_coarse_iters": (I32, [P, C.POINTER(I32)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -363,14 +367,17 @@ def hx_material_eval(ctx, mesh, G, H, prec, form=0, elem=0):
 
 
 class Multigrid:
-    """p-multigrid preconditioner on a structured-box Mesh (hx_mg_*)."""
+    """hp-multigrid preconditioner on a structured-box Mesh (hx_mg_*): p-levels
+    down to degree 1, then up to h_levels h-coarsenings; the coarsest level
+    runs FP64 Jacobi-CG (coarse_cg_iters > 0) or Chebyshev-Jacobi."""
 
     def __init__(self, mesh, smoother_degree=3, smoothing_range=15.0, coarse_degree=20, coarse_range=200.0,
-                 precond_prec=HX_FP32, storage=HX_CACHE_TENSORS, lambda_iters=20, min_degree=1, coarse_weight=1.0):
+                 precond_prec=HX_FP32, storage=HX_CACHE_TENSORS, lambda_iters=20, min_degree=1, coarse_weight=1.0,
+                 h_levels=0, coarse_cg_iters=0, coarse_cg_tol=1e-3):
         self.mesh = mesh
         opt = hx_mg_options(int(smoother_degree), float(smoothing_range), int(coarse_degree), float(coarse_range),
                             int(precond_prec), int(storage), int(lambda_iters), int(min_degree),
-                            float(coarse_weight))
+                            float(coarse_weight), int(h_levels), int(coarse_cg_iters), float(coarse_cg_tol))
         h = C.c_void_p()
         _check(lib().hx_mg_create(mesh.handle, C.byref(opt), C.byref(h)), mesh.ctx)
         self.handle = h
@@ -378,9 +385,20 @@ class Multigrid:
 
     def levels(self):
         n = C.c_int32()
-        d = (C.c_int32 * 8)()
+        d = (C.c_int32 * 16)()
         _check(lib().hx_mg_info(self.handle, C.byref(n), d), self.mesh.ctx)
         return [d[i] for i in range(n.value)]
+
+    def level(self, l):
+        """(degree, nx, ny, nz) of level l."""
+        v = [C.c_int32() for _ in range(4)]
+        _check(lib().hx_mg_level(self.handle, int(l), *[C.byref(x) for x in v]), self.mesh.ctx)
+        return tuple(x.value for x in v)
+
+    def coarse_iters(self):
+        it = C.c_int32()
+        _check(lib().hx_mg_coarse_iters(self.handle, C.byref(it)), self.mesh.ctx)
+        return it.value
 
     def setup(self, u):
         _check(lib().hx_mg_setup(self.handle, _ptr(u)), self.mesh.ctx)
@@ -432,6 +450,15 @@ def hx_newton_solve(ctx, mesh, u, f_ext=None, eps_abs=1e-10, eps_rel=1e-8, max_n
 
 def hx_set_apply_variant(ctx, mesh, prec, storage, variant):
     _check(lib().hx_set_apply_variant(mesh, int(prec), int(storage), int(variant)), ctx)
+
+
+HX_SCATTER_ATOMIC, HX_SCATTER_ORDERED = 0, 1
+
+
+def hx_set_scatter_mode(ctx, mesh, mode):
+    """HX_SCATTER_ATOMIC (default) or HX_SCATTER_ORDERED (bitwise repeatable
+    assembly through an element buffer and an ordered node gather)."""
+    _check(lib().hx_set_scatter_mode(mesh, int(mode)), ctx)
 
 
 def hx_set_wait_test(ctx, mesh, skip_stage_copies, wait_limit_cycles=0):

@@ -574,3 +574,42 @@ def test_pressure_on_a_closed_surface_has_no_resultant():
     inner = O.traction_load(M, I.tube_boundary_faces(2, 8, 2, "inner"), press).reshape(-1, 3)
     assert np.abs(f.sum(axis=0)).max() < 1e-12 * np.abs(f).sum()
     assert abs(inner.sum(axis=0)[2]) < 1e-13 * np.abs(inner).sum()
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (2, 1, 3), (2, 2, 2)])
+def test_h_transfer_reproduces_coarse_trilinear_functions(dims):
+    """The h-prolongation is exact on the coarse degree-1 space: on an
+    unjittered box (nested levels) a trilinear function sampled at the coarse
+    vertices maps to its samples at the fine vertices, each fine vertex's
+    value being the coarse trilinear interpolant there, computed here through
+    the coarse element that contains it (physical coordinates, an independent
+    route); rows sum to one."""
+    nxc, nyc, nzc = dims
+    P = O.box_h_transfer_matrix(nxc, nyc, nzc)
+
+    def lattice(nx, ny, nz):
+        x, y, z = np.linspace(0, 1, nx + 1), np.linspace(0, 2, ny + 1), np.linspace(0, 0.5, nz + 1)
+        Z, Y, X = np.meshgrid(z, y, x, indexing="ij")
+        return X.ravel(), Y.ravel(), Z.ravel()
+    f = lambda X, Y, Z: (1.0 + 0.7 * X) * (2.0 - Y) * (0.3 + Z) + 0.2 * X * Z
+    assert np.abs(P @ f(*lattice(nxc, nyc, nzc)) - f(*lattice(2 * nxc, 2 * nyc, 2 * nzc))).max() < 1e-13
+    assert np.abs(P.sum(axis=1) - 1.0).max() < 1e-14
+    # a function that is not trilinear on the coarse cells is not reproduced
+    g = lambda X, Y, Z: X ** 2 + Y * Z
+    if nxc >= 1:
+        assert np.abs(P @ g(*lattice(nxc, nyc, nzc)) - g(*lattice(2 * nxc, 2 * nyc, 2 * nzc))).max() > 1e-3
+    # the coarse trilinear interpolant at each fine vertex, from the coarse
+    # cell that contains it: a second construction of every row of P
+    Xf, Yf, Zf = lattice(2 * nxc, 2 * nyc, 2 * nzc)
+    h = np.array([1.0 / nxc, 2.0 / nyc, 0.5 / nzc])
+    Mc = np.array([nxc + 1, nyc + 1, nzc + 1])
+    for row, pt in enumerate(zip(Xf, Yf, Zf)):
+        cell = np.minimum((np.array(pt) / h + 1e-12).astype(int), Mc - 2)
+        t = np.array(pt) / h - cell
+        ref = np.zeros(P.shape[1])
+        for c in range(8):
+            b = np.array([c & 1, (c >> 1) & 1, c >> 2])
+            w = np.prod(np.where(b == 1, t, 1.0 - t))
+            J = cell + b
+            ref[J[0] + Mc[0] * (J[1] + Mc[1] * J[2])] += w
+        assert np.abs(P[row] - ref).max() < 1e-13

@@ -258,7 +258,7 @@ def test_chebyshev_matches_oracle(prec, zero_initial):
         Kop = lambda v: O.apply_constrained(M, mat, u, v)
         ref = O.chebyshev_smooth(Kop, host(rhs_t), host(cuda(x0, prec)), host(dinv_t), 5, lmax, rng,
                                  zero_initial=zero_initial)
-        assert rel_inf(host(x_t), ref) < (1e-12 if prec == hx.HX_FP64 else 2e-5)
+        assert rel_inf(host(x_t), ref) < TOL[prec]
     finally:
         G.close()
 
