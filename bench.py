@@ -481,6 +481,71 @@ def run_batch(device, steps=20, storage=None):
     return res
 
 
+def run_batch_cg(device, tol=1e-8, max_iter=5000, degree=3, smoothing_range=15.0, storage=None):
+    """The 64-cube workload (cNH, n ~ U{8..24}, p ~ U{2..5}, each with its own
+    5 % sine state), every cube clamped on x = 0: one FP64 CG per cube on
+    K_i x_i = rhs_i with an FP32 Chebyshev(degree)-Jacobi preconditioner,
+    all cubes in lockstep with one CUDA graph per iteration
+    (hx_batch_cg_solve); then the same 64 solves one mesh at a time
+    (hx_cg_solve) for comparison."""
+    import torch
+    from paper_2408_12479_gb300 import hx
+    from paper_2408_12479_gb300 import inputs as I
+    st_ = hx.HX_SPATIAL_TENSORS if storage is None else storage
+    ctx = hx.hx_create(device)
+    meshes, rhss, batch = [], [], None
+    res = {"workload": "64 cNH cubes, n ~ U{8..24}, p ~ U{2..5}, clamped at x=0, FP64 CG, FP32 Chebyshev(%d)-Jacobi, "
+                       "tol %g" % (degree, tol)}
+    try:
+        for m, field, seed in I.workload_batch():
+            n = m.box[0]
+            m.dirichlet = I.box_dirichlet_x0(n, n, n, m.p)
+            G = hx.Mesh(m, dict(I.MAT_CNH), device=device, ctx=ctx)
+            X = G.node_coords().cpu().numpy()
+            u = torch.tensor(field(X).ravel(), dtype=torch.float64, device=G.device)
+            u[torch.tensor(m.dirichlet, device=G.device).bool()] = 0.0
+            G.precompute(u, hx.HX_FP64, st_)
+            G.precompute(u, hx.HX_FP32, st_)
+            r = torch.tensor(I.random_direction(m.n_dofs, seed + 9), dtype=torch.float64, device=G.device)
+            r[torch.tensor(m.dirichlet, device=G.device).bool()] = 0.0
+            meshes.append(G)
+            rhss.append(r)
+        batch = hx.hx_batch_create(ctx, meshes)
+        xs = [torch.zeros_like(r) for r in rhss]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its, rels, st = hx.hx_batch_cg_solve(ctx, batch, rhss, xs, tol, max_iter, degree, smoothing_range, hx.HX_FP32)
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+        res["n_dofs"] = sum(G.n_dofs for G in meshes)
+        res["batched"] = {"seconds": round(t_batch, 3), "status": hx.STATUS_NAMES.get(st, st),
+                          "iters_min_max": [min(its), max(its)], "max_true_rel_residual": max(rels),
+                          "graph_iterations": max(its)}
+        # one mesh at a time, same preconditioner (the eigenvalue estimate as in the batch)
+        t0 = time.perf_counter()
+        its1 = []
+        for G, r in zip(meshes, rhss):
+            dinv = 1.0 / G.diagonal(hx.HX_FP64)
+            lam = hx.hx_estimate_lambda_max(G.ctx, G.handle, dinv, iters=20, seed=7)
+            x = torch.zeros_like(r)
+            it, rel, st1 = hx.hx_cg_solve(G.ctx, G.handle, r, x, tol, max_iter, degree, 1.2 * lam, smoothing_range,
+                                          hx.HX_FP32)
+            its1.append(it)
+        torch.cuda.synchronize()
+        t_seq = time.perf_counter() - t0
+        res["one_at_a_time"] = {"seconds": round(t_seq, 3), "iters_min_max": [min(its1), max(its1)],
+                                "iterations_total": sum(its1)}
+        res["speedup_batched"] = round(t_seq / t_batch, 3)
+    finally:
+        if batch is not None:
+            hx.hx_batch_destroy(batch)
+        for G in meshes:
+            G.close()
+        hx.hx_destroy(ctx)
+        torch.cuda.empty_cache()
+    return res
+
+
 def run_solve(device, n=48, p=4, tol=1e-8, max_iter=20000, degree=5, smoothing_range=15.0, J_target=0.9999,
               sine_amp=1e-5):
     """Newton-step solve on the compressed iNH cube (kappa = 1e3 mu): FP64 CG on
@@ -516,7 +581,27 @@ def run_solve(device, n=48, p=4, tol=1e-8, max_iter=20000, degree=5, smoothing_r
         res[name] = {"iterations": it, "true_rel_residual": rel, "seconds": round(time.perf_counter() - t0, 3),
                      "status": hx.STATUS_NAMES.get(st, st)}
     res["speedup_fp32_precond"] = round(res["fp64_precond"]["seconds"] / res["fp32_precond"]["seconds"], 3)
-    # the same system with the p-multigrid V-cycle (degrees p, p/2, ..., 1) as preconditioner
+    # the same system with the hp-multigrid V-cycle (p-levels, then h-levels
+    # and the coarse FP64 CG) as preconditioner
+    mg = hx.Multigrid(G, smoother_degree=3, precond_prec=hx.HX_FP32, storage=hx.HX_CACHE_TENSORS, lambda_iters=20,
+                      h_levels=10, coarse_cg_iters=200, coarse_cg_tol=1e-6)
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mg.setup(u)
+        t_setup = time.perf_counter() - t0
+        x = torch.zeros_like(u)
+        t0 = time.perf_counter()
+        it, rel, st = mg.cg_solve(rhs, x, tol, max_iter)
+        torch.cuda.synchronize()
+        res["hp_mg_fp32_precond"] = {"levels": mg.levels(), "iterations": it, "true_rel_residual": rel,
+                                     "seconds": round(time.perf_counter() - t0, 3),
+                                     "setup_seconds": round(t_setup, 3), "status": hx.STATUS_NAMES.get(st, st)}
+    except hx.HxError as e:
+        res["hp_mg_fp32_precond"] = {"status": str(e)[:160]}
+    finally:
+        mg.close()
+    # and with the p-levels only (the degree-1 level smoothed by Chebyshev)
     mg = hx.Multigrid(G, smoother_degree=3, coarse_degree=20, coarse_range=200.0, precond_prec=hx.HX_FP32,
                       storage=hx.HX_CACHE_TENSORS, lambda_iters=20)
     try:
@@ -552,6 +637,63 @@ def run_solve(device, n=48, p=4, tol=1e-8, max_iter=20000, degree=5, smoothing_r
         res["J0.9_state"] = {"status": str(e)[:120]}
     G9.close()
     return res
+
+
+def run_solve_full(device, n=48, p=4, tol=1e-8, max_iter=500, J_target=0.9999, sine_amp=1e-5):
+    """The compressed-cube solve at its full size (iNH, kappa = 1e3 mu, n^3
+    jittered elements, p = 4, symmetry clamps): FP64 CG on K(u) du = -R(u)
+    preconditioned by the hp-multigrid V-cycle (p 4 -> 2 -> 1, then h-levels
+    down to the coarse FP64 CG) run in FP32 and, for comparison, in FP64;
+    both stop at the same FP64 true-residual ratio. J ~ 0.9999 keeps K
+    positive definite (at J ~ 0.9 the pressure makes CG meet negative
+    curvature, see the 16^3 solve report)."""
+    import torch
+    from paper_2408_12479_gb300 import hx
+    from paper_2408_12479_gb300 import inputs as I
+    m, field, seed = I.workload_compressed_cube(n=n, p=p, J_target=J_target, sine_amp=sine_amp)
+    G = hx.Mesh(m, dict(I.MAT_INH), device=device)
+    res = {"workload": f"iNH kappa=1e3 mu, {n}^3 jittered cube, p={p}, J~{J_target}, symmetry clamps",
+           "n_dofs": m.n_dofs, "tol": tol}
+    try:
+        u = torch.tensor(field(G.node_coords().cpu().numpy()).ravel(), dtype=torch.float64, device=G.device)
+        G.precompute(u, hx.HX_FP64, hx.HX_CACHE_TENSORS)
+        rhs = -G.residual(u)
+        for name, pp in (("hp_mg_fp32", hx.HX_FP32), ("hp_mg_fp64", hx.HX_FP64)):
+            mg = hx.Multigrid(G, smoother_degree=3, precond_prec=pp, storage=hx.HX_CACHE_TENSORS, lambda_iters=20,
+                              h_levels=10, coarse_cg_iters=200, coarse_cg_tol=1e-6)
+            try:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                mg.setup(u)
+                t_setup = time.perf_counter() - t0
+                x = torch.zeros_like(u)
+                t0 = time.perf_counter()
+                it, rel, st = mg.cg_solve(rhs, x, tol, max_iter)
+                torch.cuda.synchronize()
+                res[name] = {"iterations": it, "true_rel_residual": rel, "seconds": round(time.perf_counter() - t0, 3),
+                             "setup_seconds": round(t_setup, 3), "status": hx.STATUS_NAMES.get(st, st),
+                             "levels": ["p%d:%dx%dx%d" % mg.level(l) for l in range(len(mg.levels()))]}
+            finally:
+                mg.close()
+        a, b = res.get("hp_mg_fp32", {}), res.get("hp_mg_fp64", {})
+        if a.get("seconds") and b.get("seconds"):
+            res["speedup_fp32_precond"] = round(b["seconds"] / a["seconds"], 3)
+    finally:
+        G.close()
+        torch.cuda.empty_cache()
+    return res
+
+
+def solve_summary(r):
+    """The full-size solve's key figures for the headline line."""
+    if not isinstance(r, dict) or "error" in r:
+        return r
+    out = {}
+    for k in ("hp_mg_fp32", "hp_mg_fp64"):
+        v = r.get(k, {})
+        out[k] = [v.get("seconds"), v.get("iterations"), v.get("true_rel_residual")]
+    out["speedup"] = r.get("speedup_fp32_precond")
+    return out
 
 
 def run_stability(device):
@@ -713,20 +855,22 @@ def reps_per_step(apply_ms, steps, target_s=1.2):
 
 def sweep_summary(sweep):
     """Best storage strategy per (precision, degree) of the sweep:
-    {prec: {p: [GDoF/s, HBM fraction, strategy]}}."""
+    {prec: {p: [GDoF/s, HBM fraction, FMA-pipe fraction, strategy]}}."""
     out = {}
     for r in sweep or []:
         if "gdofs" not in r:
             continue
         cur = out.setdefault(r["prec"], {}).get(str(r["p"]))
         if cur is None or r["gdofs"] > cur[0]:
-            out[r["prec"]][str(r["p"])] = [r["gdofs"], r["hbm_frac"], r["storage"]]
+            out[r["prec"]][str(r["p"])] = [r["gdofs"], r["hbm_frac"], r.get("fma_frac"),
+                                           {"recompute": "R", "cache_F": "F", "cache_tensors": "T",
+                                            "spatial_tensors": "S"}.get(r["storage"], r["storage"])]
     return out
 
 
 HEADLINE_KEYS = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
                  "scaling", "vs_baseline", "dtype", "data", "config", "roofline", "e2e", "gpu_launches", "clocks",
-                 "cpu_baseline", "fma_peaks", "sweep_best")
+                 "cpu_baseline", "fma_peaks", "sweep_best", "solve_48")
 
 
 def headline_line(fields):
@@ -885,6 +1029,8 @@ def main():
     ap.add_argument("--profile-op", default=None, choices=["apply", "residual", "precompute", "diagonal"],
                     help="run one operator --warmup + --steps times for a profiler and exit (no contract line)")
     ap.add_argument("--variant", type=int, default=-1, help="with --profile-op apply: the apply variant (0-5)")
+    ap.add_argument("--solve-full", type=int, default=48,
+                    help="the compressed-cube solve at full size with the hp-multigrid preconditioner (n given; 0: off)")
     ap.add_argument("--solve", type=int, default=16,
                     help="also run the FP32- vs FP64-preconditioned CG solve on an n^3 compressed cube (n given)")
     args = ap.parse_args()
@@ -989,7 +1135,7 @@ def main():
     del u, du, out
     torch.cuda.empty_cache()
 
-    peaks_fp = sweep = None
+    peaks_fp = sweep = solve_full = None
     if rank == 0 and not args.no_sweep:
         peaks_fp = fma_peaks(local)
         sweep = run_sweep(local, hbm_peak, peaks_fp)
@@ -1000,8 +1146,12 @@ def main():
         emit({"report": "law_workloads", "cases": guarded(run_law_workloads, local, hbm_peak)})
         emit({"report": "batch", "cache_F": guarded(run_batch, local, storage=hx.HX_CACHE_F),
               "spatial_tensors": guarded(run_batch, local, storage=hx.HX_SPATIAL_TENSORS)})
+        emit({"report": "batch_cg", **guarded(run_batch_cg, local)})
         if args.solve:
             emit({"report": "solve", **guarded(run_solve, local, n=args.solve)})
+        if args.solve_full:
+            solve_full = guarded(run_solve_full, local, n=args.solve_full)
+            emit({"report": "solve_full", **solve_full})
         newton = guarded(run_newton, local)
         newton["traction"] = guarded(run_newton_traction, local)
         emit({"report": "newton", **newton})
@@ -1036,6 +1186,7 @@ def main():
             "cpu_baseline": cpu,
             "fma_peaks": peaks_fp,
             "sweep_best": sweep_summary(sweep),
+            "solve_48": solve_summary(solve_full),
         }
         print(headline_line(fields), flush=True)
     if world > 1:

@@ -428,6 +428,29 @@ void hx_batch_destroy(hx_batch *batch);
  * strategy (HX_CACHE_F, HX_CACHE_TENSORS or HX_SPATIAL_TENSORS; HX_RECOMPUTE
  * gives HX_ERR_UNSUPPORTED). */
 hx_status hx_batch_tangent_apply(hx_batch *batch, const void *const *du_dev, void *const *out_dev, int32_t prec);
+/* Batched FP64 CG (Sec. 6 outer Krylov solver, over many independent
+ * problems): solves K_i x_i = rhs_i for every mesh i of the batch (the
+ * constrained tangent of its last hx_precompute_qp), preconditioned by
+ * `degree` steps of Chebyshev-Jacobi on [lambda_i/smoothing_range, lambda_i]
+ * of D_i^-1 K_i in precond_prec (lambda_i: 1.2 x a 20-step power estimate,
+ * per mesh). The meshes iterate in lockstep: every operator application of
+ * an iteration is one persistent launch over all meshes, the dot products
+ * and the CG scalars are kept per mesh on the device, and a mesh whose
+ * residual reached ||r_i|| <= tol ||rhs_i|| stops changing. With use_graph,
+ * one whole iteration (FP64 operator, dot products, updates and the
+ * preconditioner's applies) is captured once as a CUDA graph and replayed.
+ * rhs_dev/x_dev: host arrays of n_meshes device pointers (x holds the start
+ * and receives the solution); iters / rel_residual: host arrays of n_meshes
+ * receiving each mesh's iterations and true relative residual (may be
+ * NULL). Every mesh needs caches in FP64 and in precond_prec with one
+ * caching strategy. Statuses: HX_ERR_NOT_CONVERGED if some mesh missed tol
+ * within max_iter iterations, HX_ERR_NAN on a breakdown (non-positive
+ * curvature or NaN) of some mesh. Synchronous; workspace (about 10 FP64 and
+ * 5 FP32 vectors of the batch's total size) is allocated by the first call
+ * and kept by the batch. */
+hx_status hx_batch_cg_solve(hx_batch *batch, const double *const *rhs_dev, double *const *x_dev, double tol,
+                            int32_t max_iter, int32_t degree, double smoothing_range, int32_t precond_prec,
+                            int32_t use_graph, int32_t *iters, double *rel_residual);
 
 /* ---- measurement support ------------------------------------------------- */
 /* Peak FMA throughput of this device for `prec`, measured by a dependent-FMA

@@ -1214,6 +1214,19 @@ hx_status hx_measure_fma_peak(hx_ctx *ctx, int32_t prec, double *flops) {
 // ---------------------------------------------------------------------------
 }  // extern "C"
 
+// Workspace of the batched CG (allocated by the first solve, kept for later ones)
+struct BatchCg {
+    int64_t total = 0, max_n = 0;
+    hx::BSeg *d_seg = nullptr;
+    double *w = nullptr;   // r z zold p Ap x b dinv d Kx: 10 concatenated FP64 vectors
+    float *w32 = nullptr;  // r xc d Kx dinv: 5 concatenated FP32 vectors (FP32 preconditioner)
+    hx::BScal *d_sc = nullptr;
+    double *d_partial = nullptr, *d_dots = nullptr, *d_coef = nullptr;
+    hx::BatchMesh *d_role[3] = {nullptr, nullptr, nullptr};  // p -> Ap, x -> Ap (FP64); xc -> Kx (preconditioner)
+    hx::BScal *h_sc = nullptr;  // pinned
+    cudaStream_t stream = nullptr;
+};
+
 struct hx_batch {
     hx_ctx *ctx = nullptr;
     std::vector<hx_mesh *> meshes;
@@ -1222,6 +1235,7 @@ struct hx_batch {
     std::vector<hx::BatchMesh> h;
     int2 *d_items[2][4] = {{nullptr, nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr, nullptr}};
     int nitems[2][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}};
+    BatchCg cg;
 };
 
 extern "C" {
@@ -1251,10 +1265,41 @@ hx_status hx_batch_create(hx_ctx *ctx, hx_mesh *const *meshes, int32_t n_meshes,
 void hx_batch_destroy(hx_batch *b) {
     if (!b) return;
     cudaStreamSynchronize(b->ctx->stream);
+    if (b->cg.stream) cudaStreamSynchronize(b->cg.stream);
     dfree(b->d_meshes);
     for (auto &row : b->d_items)
         for (auto *p : row) dfree(p);
+    void *cg[] = {b->cg.d_seg, b->cg.w, b->cg.w32, b->cg.d_sc, b->cg.d_partial, b->cg.d_dots, b->cg.d_coef,
+                  b->cg.d_role[0], b->cg.d_role[1], b->cg.d_role[2]};
+    for (void *p : cg) dfree(p);
+    if (b->cg.h_sc) cudaFreeHost(b->cg.h_sc);
+    if (b->cg.stream) cudaStreamDestroy(b->cg.stream);
     delete b;
+}
+
+// Work list of (mesh, tile) items of a batch, highest degree first, built once
+// per (prec, storage).
+static hx_status batch_items(hx_batch *b, int prec, int storage) {
+    hx_ctx *ctx = b->ctx;
+    if (b->nitems[prec][storage] >= 0) return HX_OK;
+    const hx::BatchOps *ops = hx::batch_ops(prec);
+    const int n = (int)b->meshes.size();
+    std::vector<int2> items;
+    for (int p = HX_PMAX; p >= HX_PMIN; --p)
+        for (int i = 0; i < n; ++i) {
+            const hx_mesh *m = b->meshes[i];
+            if (m->p != p) continue;
+            const int epb = ops->epb(p, b->law, storage);
+            if (epb < 1) return fail(ctx, HX_ERR_UNSUPPORTED, "batch: degree not in the batch unit");
+            const int nt = (m->n_elem + epb - 1) / epb;
+            for (int t = 0; t < nt; ++t) items.push_back(make_int2(i, t));
+        }
+    HX_CUDA(ctx, cudaMalloc((void **)&b->d_items[prec][storage], sizeof(int2) * (items.size() + 1)));
+    if (!items.empty())
+        HX_CUDA(ctx, cudaMemcpy(b->d_items[prec][storage], items.data(), sizeof(int2) * items.size(),
+                                cudaMemcpyHostToDevice));
+    b->nitems[prec][storage] = (int)items.size();
+    return HX_OK;
 }
 
 hx_status hx_batch_tangent_apply(hx_batch *b, const void *const *du_dev, void *const *out_dev, int32_t prec) {
@@ -1271,24 +1316,8 @@ hx_status hx_batch_tangent_apply(hx_batch *b, const void *const *du_dev, void *c
     if (storage == HX_RECOMPUTE)
         return fail(ctx, HX_ERR_UNSUPPORTED, "hx_batch_tangent_apply: batches run the caching strategies");
     const hx::BatchOps *ops = hx::batch_ops(prec);
-    // work list of (mesh, tile), highest degree first, built once per (prec, storage)
-    if (b->nitems[prec][storage] < 0) {
-        std::vector<int2> items;
-        for (int p = HX_PMAX; p >= HX_PMIN; --p)
-            for (int i = 0; i < n; ++i) {
-                const hx_mesh *m = b->meshes[i];
-                if (m->p != p) continue;
-                const int epb = ops->epb(p, b->law, storage);
-                if (epb < 1) return fail(ctx, HX_ERR_UNSUPPORTED, "hx_batch_tangent_apply: degree not in the batch unit");
-                const int nt = (m->n_elem + epb - 1) / epb;
-                for (int t = 0; t < nt; ++t) items.push_back(make_int2(i, t));
-            }
-        HX_CUDA(ctx, cudaMalloc((void **)&b->d_items[prec][storage], sizeof(int2) * (items.size() + 1)));
-        if (!items.empty())
-            HX_CUDA(ctx, cudaMemcpy(b->d_items[prec][storage], items.data(), sizeof(int2) * items.size(),
-                                    cudaMemcpyHostToDevice));
-        b->nitems[prec][storage] = (int)items.size();
-    }
+    hx_status st = batch_items(b, prec, storage);
+    if (st != HX_OK) return st;
     for (int i = 0; i < n; ++i) {
         hx_mesh *m = b->meshes[i];
         b->h[i].m = view(m, prec);
@@ -1310,6 +1339,284 @@ hx_status hx_batch_tangent_apply(hx_batch *b, const void *const *du_dev, void *c
     }
     return HX_OK;
 }
+
+// ---------------------------------------------------------------------------
+// batched CG: every mesh of a batch solves its own constrained system; the
+// meshes iterate in lockstep so that each operator application is one
+// persistent launch over all of them
+// ---------------------------------------------------------------------------
+// K_i v_i for every mesh in one launch, from a device array of per-mesh
+// (view, du, out) entries prepared before any capture; constrained rows copied
+static hx_status batch_apply_role(hx_batch *b, const hx::BatchMesh *role, int prec, int storage, const void *du,
+                                  void *out) {
+    hx_ctx *ctx = b->ctx;
+    const hx::BatchOps *ops = hx::batch_ops(prec);
+    const int n = (int)b->meshes.size();
+    HX_CUDA(ctx, ops->zero(role, n, ctx->stream));
+    HX_CUDA(ctx, ops->apply(b->law, storage, role, b->d_items[prec][storage], b->nitems[prec][storage], ctx->stream));
+    HX_CUDA(ctx, hx::bcopy_idx(n, b->cg.d_seg, du, out, prec, ctx->stream));
+    ctx->launches += 3;
+    return HX_OK;
+}
+
+hx_status hx_batch_cg_solve(hx_batch *b, const double *const *rhs_dev, double *const *x_dev, double tol,
+                            int32_t max_iter, int32_t degree, double smoothing_range, int32_t precond_prec,
+                            int32_t use_graph, int32_t *iters, double *rel_residual) {
+    if (!b || !rhs_dev || !x_dev || !(tol > 0.0) || max_iter < 0 || degree < 1 || !(smoothing_range > 1.0) ||
+        bad_prec(precond_prec))
+        return fail(b ? b->ctx : nullptr, HX_ERR_ARG, "hx_batch_cg_solve: bad argument");
+    hx_ctx *ctx = b->ctx;
+    const int nm = (int)b->meshes.size();
+    const int pp = precond_prec;
+    const int storage = b->meshes[0]->cache[HX_FP64].storage;
+    for (int i = 0; i < nm; ++i) {
+        const hx_mesh *m = b->meshes[i];
+        if (!m->cache[HX_FP64].valid || !m->cache[pp].valid)
+            return fail(ctx, HX_ERR_NOT_READY, "hx_batch_cg_solve: every mesh needs quadrature-point data in FP64 and in the preconditioner's precision");
+        if (m->cache[HX_FP64].storage != storage || m->cache[pp].storage != storage)
+            return fail(ctx, HX_ERR_ARG, "hx_batch_cg_solve: the meshes' caches must share one storage strategy");
+        if (!rhs_dev[i] || !x_dev[i] || (const void *)rhs_dev[i] == (const void *)x_dev[i])
+            return fail(ctx, HX_ERR_ARG, "hx_batch_cg_solve: bad vector");
+    }
+    if (storage == HX_RECOMPUTE) return fail(ctx, HX_ERR_UNSUPPORTED, "hx_batch_cg_solve: batches run the caching strategies");
+    hx_status st = batch_items(b, HX_FP64, storage);
+    if (st == HX_OK) st = batch_items(b, pp, storage);
+    if (st != HX_OK) return st;
+
+    BatchCg &w = b->cg;
+    // segments (each starts on a multiple of 4 entries)
+    std::vector<hx::BSeg> seg(nm);
+    int64_t total = 0, max_n = 0;
+    for (int i = 0; i < nm; ++i) {
+        const hx_mesh *m = b->meshes[i];
+        seg[i].off = total;
+        seg[i].n = 3 * m->n_nodes;
+        seg[i].x = x_dev[i];
+        seg[i].rhs = rhs_dev[i];
+        seg[i].cidx = m->d_cidx;
+        seg[i].ncon = m->n_constrained;
+        total += (seg[i].n + 3) / 4 * 4;
+        max_n = std::max(max_n, seg[i].n);
+    }
+    if (w.total != total) {
+        void *old[] = {w.d_seg, w.w, w.w32, w.d_sc, w.d_partial, w.d_dots, w.d_coef, w.d_role[0], w.d_role[1],
+                       w.d_role[2]};
+        for (void *p : old) dfree(p);
+        if (w.h_sc) cudaFreeHost(w.h_sc);
+        w = BatchCg{w.total, w.max_n, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                    {nullptr, nullptr, nullptr}, nullptr, w.stream};
+        HX_CUDA(ctx, cudaMalloc((void **)&w.d_seg, sizeof(hx::BSeg) * nm));
+        HX_CUDA(ctx, cudaMalloc((void **)&w.w, 10 * (size_t)total * sizeof(double) + 64));
+        HX_CUDA(ctx, cudaMalloc((void **)&w.w32, 5 * (size_t)total * sizeof(float) + 64));
+        HX_CUDA(ctx, cudaMalloc((void **)&w.d_sc, sizeof(hx::BScal) * nm));
+        HX_CUDA(ctx, cudaMalloc((void **)&w.d_partial, sizeof(double) * 3 * hx::BRB * nm));
+        HX_CUDA(ctx, cudaMalloc((void **)&w.d_dots, sizeof(double) * 3 * nm));
+        for (auto &r : w.d_role) HX_CUDA(ctx, cudaMalloc((void **)&r, sizeof(hx::BatchMesh) * nm));
+        HX_CUDA(ctx, cudaHostAlloc((void **)&w.h_sc, sizeof(hx::BScal) * nm, cudaHostAllocDefault));
+        w.total = total;
+    }
+    w.max_n = max_n;
+    dfree(w.d_coef);
+    w.d_coef = nullptr;
+    HX_CUDA(ctx, cudaMalloc((void **)&w.d_coef, sizeof(double) * 2 * degree * nm));
+    if (!w.stream) HX_CUDA(ctx, cudaStreamCreateWithFlags(&w.stream, cudaStreamNonBlocking));
+    HX_CUDA(ctx, cudaMemcpy(w.d_seg, seg.data(), sizeof(hx::BSeg) * nm, cudaMemcpyHostToDevice));
+    double *r = w.w, *z = r + total, *zold = z + total, *p = zold + total, *Ap = p + total, *xw = Ap + total,
+           *bw = xw + total, *dinv = bw + total, *d64 = dinv + total, *Kx64 = d64 + total;
+    float *r32 = w.w32, *xc32 = r32 + total, *d32 = xc32 + total, *Kx32 = d32 + total, *dinv32 = Kx32 + total;
+
+    // per mesh: D^-1 (FP64, on the caller's stream), lambda_max and the Chebyshev coefficients
+    std::vector<double> coef(2 * (size_t)degree * nm);
+    for (int i = 0; i < nm; ++i) {
+        hx_mesh *m = b->meshes[i];
+        st = hx_diagonal(m, dinv + seg[i].off, HX_FP64);
+        if (st != HX_OK) return st;
+        HX_CUDA(ctx, hx::invert(seg[i].n, dinv + seg[i].off, dinv + seg[i].off, HX_FP64, ctx->stream));
+        double lam = 0.0;
+        st = hx_estimate_lambda_max(m, dinv + seg[i].off, 20, 7, &lam);
+        if (st != HX_OK) return st;
+        lam *= 1.2;
+        const double a = lam / smoothing_range, bl = lam, theta = 0.5 * (bl + a), delta = 0.5 * (bl - a);
+        double rho_prev = 0.0;
+        for (int k = 0; k < degree; ++k) {
+            double cd, cr, rho;
+            if (k == 0) {
+                rho = delta / theta;
+                cd = 0.0;
+                cr = 1.0 / theta;
+            } else {
+                rho = 1.0 / (2.0 * theta / delta - rho_prev);
+                cd = rho * rho_prev;
+                cr = 2.0 * rho / delta;
+            }
+            coef[((size_t)i * degree + k) * 2 + 0] = cd;
+            coef[((size_t)i * degree + k) * 2 + 1] = cr;
+            rho_prev = rho;
+        }
+    }
+    HX_CUDA(ctx, cudaMemcpy(w.d_coef, coef.data(), sizeof(double) * coef.size(), cudaMemcpyHostToDevice));
+    // per-mesh operator entries of the three applies
+    {
+        std::vector<hx::BatchMesh> role(nm);
+        auto fill = [&](int k, int prec, const void *du_base, void *out_base) -> cudaError_t {
+            const size_t sz = prec == HX_FP64 ? sizeof(double) : sizeof(float);
+            for (int i = 0; i < nm; ++i) {
+                role[i].m = view(b->meshes[i], prec);
+                role[i].du = (const char *)du_base + sz * seg[i].off;
+                role[i].out = (char *)out_base + sz * seg[i].off;
+                role[i].n_dofs = seg[i].n;
+            }
+            return cudaMemcpy(w.d_role[k], role.data(), sizeof(hx::BatchMesh) * nm, cudaMemcpyHostToDevice);
+        };
+        HX_CUDA(ctx, fill(0, HX_FP64, p, Ap));
+        HX_CUDA(ctx, fill(1, HX_FP64, xw, Ap));
+        if (pp == HX_FP32)
+            HX_CUDA(ctx, fill(2, HX_FP32, xc32, Kx32));
+        else
+            HX_CUDA(ctx, fill(2, HX_FP64, z, Kx64));
+    }
+
+    // the rest runs on the batch's private stream (capturable), after the caller's work
+    cudaStream_t user = ctx->stream;
+    cudaEvent_t ev;
+    HX_CUDA(ctx, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    HX_CUDA(ctx, cudaEventRecord(ev, user));
+    HX_CUDA(ctx, cudaStreamWaitEvent(w.stream, ev, 0));
+    ctx->stream = w.stream;
+    struct Restore {
+        hx_ctx *c;
+        cudaStream_t u;
+        cudaEvent_t e;
+        ~Restore() {
+            cudaEventRecord(e, c->stream);
+            cudaStreamWaitEvent(u, e, 0);
+            c->stream = u;
+            cudaEventDestroy(e);
+        }
+    } restore{ctx, user, ev};
+    cudaStream_t s = ctx->stream;
+    if (pp == HX_FP32) HX_CUDA(ctx, hx::to_f32(total, dinv, dinv32, s));
+
+    // z = Chebyshev(degree)-Jacobi applied to r, per mesh, in pp
+    auto precond = [&]() -> hx_status {
+        for (int k = 0; k < degree; ++k) {
+            if (pp == HX_FP32) {
+                if (k > 0) {
+                    hx_status q = batch_apply_role(b, w.d_role[2], HX_FP32, storage, xc32, Kx32);
+                    if (q != HX_OK) return q;
+                }
+                HX_CUDA(ctx, hx::bcheb(nm, max_n, w.d_seg, w.d_coef, degree, k, r32, k ? Kx32 : nullptr, dinv32, d32,
+                                       xc32, HX_FP32, s));
+            } else {
+                if (k > 0) {
+                    hx_status q = batch_apply_role(b, w.d_role[2], HX_FP64, storage, z, Kx64);
+                    if (q != HX_OK) return q;
+                }
+                HX_CUDA(ctx, hx::bcheb(nm, max_n, w.d_seg, w.d_coef, degree, k, r, k ? Kx64 : nullptr, dinv, d64, z,
+                                       HX_FP64, s));
+            }
+            ctx->launches++;
+        }
+        if (pp == HX_FP32) {
+            HX_CUDA(ctx, hx::to_f64(total, xc32, z, s));
+            ctx->launches++;
+        }
+        return HX_OK;
+    };
+
+    // r = b - K x; z = M r; p = zold = z
+    HX_CUDA(ctx, hx::bcopy(nm, max_n, w.d_seg, xw, 0, s));
+    HX_CUDA(ctx, hx::bcopy(nm, max_n, w.d_seg, bw, 2, s));
+    st = batch_apply_role(b, w.d_role[1], HX_FP64, storage, xw, Ap);
+    if (st != HX_OK) return st;
+    HX_CUDA(ctx, hx::bsub(total, bw, Ap, r, s));
+    if (pp == HX_FP32) HX_CUDA(ctx, hx::to_f32(total, r, r32, s));
+    st = precond();
+    if (st != HX_OK) return st;
+    HX_CUDA(ctx, cudaMemcpyAsync(p, z, total * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    HX_CUDA(ctx, cudaMemcpyAsync(zold, z, total * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    HX_CUDA(ctx, hx::bdots(nm, w.d_seg, 3, r, z, r, r, bw, bw, w.d_partial, w.d_dots, s));
+    HX_CUDA(ctx, hx::bscal_init(nm, w.d_sc, w.d_dots, tol, s));
+    ctx->launches += 8;
+
+    auto body = [&]() -> hx_status {
+        hx_status q = batch_apply_role(b, w.d_role[0], HX_FP64, storage, p, Ap);
+        if (q != HX_OK) return q;
+        HX_CUDA(ctx, hx::bdots(nm, w.d_seg, 1, p, Ap, nullptr, nullptr, nullptr, nullptr, w.d_partial, w.d_dots, s));
+        HX_CUDA(ctx, hx::bscal_alpha(nm, w.d_sc, w.d_dots, s));
+        HX_CUDA(ctx, hx::bxr(nm, max_n, w.d_seg, w.d_sc, p, Ap, xw, r, pp == HX_FP32 ? r32 : nullptr, s));
+        q = precond();
+        if (q != HX_OK) return q;
+        HX_CUDA(ctx, hx::bdots(nm, w.d_seg, 3, r, z, r, zold, r, r, w.d_partial, w.d_dots, s));
+        HX_CUDA(ctx, hx::bscal_beta(nm, w.d_sc, w.d_dots, s));
+        HX_CUDA(ctx, hx::bp(nm, max_n, w.d_seg, w.d_sc, z, p, zold, s));
+        HX_CUDA(ctx, cudaMemcpyAsync(w.h_sc, w.d_sc, sizeof(hx::BScal) * nm, cudaMemcpyDeviceToHost, s));
+        ctx->launches += 8;
+        return HX_OK;
+    };
+    cudaGraphExec_t exec = nullptr;
+    if (use_graph) {
+        cudaGraph_t graph = nullptr;
+        HX_CUDA(ctx, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        hx_status q = body();
+        cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        if (q != HX_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return q;
+        }
+        if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaStreamEndCapture");
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return cuda_fail(ctx, ce, "cudaGraphInstantiate");
+    }
+    struct ExecGuard {
+        cudaGraphExec_t e;
+        ~ExecGuard() {
+            if (e) cudaGraphExecDestroy(e);
+        }
+    } eg{exec};
+    HX_CUDA(ctx, cudaMemcpyAsync(w.h_sc, w.d_sc, sizeof(hx::BScal) * nm, cudaMemcpyDeviceToHost, s));
+    HX_CUDA(ctx, cudaStreamSynchronize(s));
+    auto any_active = [&]() {
+        for (int i = 0; i < nm; ++i)
+            if (w.h_sc[i].active) return true;
+        return false;
+    };
+    for (int it = 0; it < max_iter && any_active(); ++it) {
+        if (exec) {
+            HX_CUDA(ctx, cudaGraphLaunch(exec, s));
+        } else {
+            st = body();
+            if (st != HX_OK) return st;
+        }
+        HX_CUDA(ctx, cudaStreamSynchronize(s));
+    }
+    // true residuals; the solutions back to the caller's vectors
+    st = batch_apply_role(b, w.d_role[1], HX_FP64, storage, xw, Ap);
+    if (st != HX_OK) return st;
+    HX_CUDA(ctx, hx::bsub(total, bw, Ap, r, s));
+    HX_CUDA(ctx, hx::bdots(nm, w.d_seg, 2, r, r, bw, bw, nullptr, nullptr, w.d_partial, w.d_dots, s));
+    HX_CUDA(ctx, hx::bcopy(nm, max_n, w.d_seg, xw, 1, s));
+    std::vector<double> dots(3 * (size_t)nm);
+    HX_CUDA(ctx, cudaMemcpyAsync(dots.data(), w.d_dots, sizeof(double) * 3 * nm, cudaMemcpyDeviceToHost, s));
+    HX_CUDA(ctx, cudaMemcpyAsync(w.h_sc, w.d_sc, sizeof(hx::BScal) * nm, cudaMemcpyDeviceToHost, s));
+    HX_CUDA(ctx, cudaStreamSynchronize(s));
+    ctx->launches += 4;
+    int n_bad = 0, n_open = 0;
+    for (int i = 0; i < nm; ++i) {
+        const double rel = dots[3 * i + 1] > 0.0 ? std::sqrt(dots[3 * i] / dots[3 * i + 1]) : 0.0;
+        if (iters) iters[i] = w.h_sc[i].iters;
+        if (rel_residual) rel_residual[i] = rel;
+        if (w.h_sc[i].bad || !(rel == rel)) ++n_bad;
+        else if (rel > tol) ++n_open;
+    }
+    if (n_bad) return fail(ctx, HX_ERR_NAN, "hx_batch_cg_solve: CG breakdown (NaN or non-positive curvature) on " +
+                                                std::to_string(n_bad) + " mesh(es)");
+    if (n_open) return fail(ctx, HX_ERR_NOT_CONVERGED, "hx_batch_cg_solve: tolerance not reached on " +
+                                                           std::to_string(n_open) + " mesh(es)");
+    return HX_OK;
+}
+
 
 }  // extern "C"
 

@@ -225,6 +225,158 @@ __global__ void __launch_bounds__(CB) k_coarse_pcg(int n, const double *__restri
     if (iters && i == 0) *iters = it;
 }
 
+// ---- batched CG kernels ------------------------------------------------------
+template <int K>
+__global__ void k_bdots(const BSeg *__restrict__ seg, const double *a0, const double *b0, const double *a1,
+                        const double *b1, const double *a2, const double *b2, double *partial) {
+    __shared__ double sh[3][VB];
+    const int i = blockIdx.y;
+    const int64_t off = seg[i].off, n = seg[i].n;
+    double s[3] = {0, 0, 0};
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        s[0] += a0[off + j] * b0[off + j];
+        if (K > 1) s[1] += a1[off + j] * b1[off + j];
+        if (K > 2) s[2] += a2[off + j] * b2[off + j];
+    }
+    for (int j = 0; j < 3; ++j) sh[j][threadIdx.x] = s[j];
+    __syncthreads();
+    for (int w = VB / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int j = 0; j < 3; ++j) sh[j][threadIdx.x] += sh[j][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 3) partial[((int64_t)i * BRB + blockIdx.x) * 3 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void k_bdots_final(const double *__restrict__ partial, double *__restrict__ dots) {
+    const int i = blockIdx.x;
+    if (threadIdx.x < 3) {
+        double t = 0.0;
+        for (int b = 0; b < BRB; ++b) t += partial[((int64_t)i * BRB + b) * 3 + threadIdx.x];
+        dots[3 * i + threadIdx.x] = t;
+    }
+}
+
+__global__ void k_bcopy(const BSeg *__restrict__ seg, double *__restrict__ y, int dir) {
+    const int i = blockIdx.y;
+    const int64_t off = seg[i].off, n = seg[i].n;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        if (dir == 0)
+            y[off + j] = seg[i].x[j];
+        else if (dir == 1)
+            seg[i].x[j] = y[off + j];
+        else
+            y[off + j] = seg[i].rhs[j];
+    }
+}
+
+template <typename T>
+__global__ void k_bcopy_idx(const BSeg *__restrict__ seg, const T *__restrict__ du, T *__restrict__ out) {
+    const int i = blockIdx.y;
+    const int64_t off = seg[i].off, n = seg[i].ncon;
+    const int64_t *ci = seg[i].cidx;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        out[off + ci[j]] = du[off + ci[j]];
+}
+
+__global__ void k_bscal_init(int nm, BScal *sc, const double *dots, double tol) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nm) return;
+    BScal v{};
+    v.rz = dots[3 * i + 0];
+    v.rr = dots[3 * i + 1];
+    v.bb = dots[3 * i + 2];
+    v.tol2 = tol * tol;
+    v.active = v.bb > 0.0 && v.rr > v.tol2 * v.bb;
+    sc[i] = v;
+}
+
+__global__ void k_bscal_alpha(int nm, BScal *sc, const double *dots) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nm) return;
+    BScal v = sc[i];
+    v.pAp = dots[3 * i];
+    v.alpha = 0.0;
+    if (v.active) {
+        const double a = v.rz / v.pAp;
+        if (!(v.pAp > 0.0) || !(a == a)) {  // non-positive curvature or NaN: this mesh stops
+            v.bad = 1;
+            v.active = 0;
+        } else {
+            v.alpha = a;
+        }
+    }
+    sc[i] = v;
+}
+
+__global__ void k_bxr(const BSeg *__restrict__ seg, const BScal *__restrict__ sc, const double *__restrict__ p,
+                      const double *__restrict__ Ap, double *__restrict__ x, double *__restrict__ r,
+                      float *__restrict__ r32) {
+    const int i = blockIdx.y;
+    const int64_t off = seg[i].off, n = seg[i].n;
+    const double a = sc[i].alpha;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = off + j;
+        x[q] += a * p[q];
+        const double rn = r[q] - a * Ap[q];
+        r[q] = rn;
+        if (r32) r32[q] = (float)rn;
+    }
+}
+
+// dots: [0] r.z_new, [1] r.z_old, [2] r.r
+__global__ void k_bscal_beta(int nm, BScal *sc, const double *dots) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nm) return;
+    BScal v = sc[i];
+    v.beta = 0.0;
+    if (v.active) {
+        const double rz_new = dots[3 * i + 0];
+        const double b = (rz_new - dots[3 * i + 1]) / v.rz;
+        v.rz = rz_new;
+        v.rr = dots[3 * i + 2];
+        v.iters += 1;
+        if (!(b == b)) {
+            v.bad = 1;
+            v.active = 0;
+        } else {
+            v.beta = b;
+            if (v.rr <= v.tol2 * v.bb) v.active = 0;
+        }
+    }
+    sc[i] = v;
+}
+
+__global__ void k_bp(const BSeg *__restrict__ seg, const BScal *__restrict__ sc, const double *__restrict__ z,
+                     double *__restrict__ p, double *__restrict__ zold) {
+    const int i = blockIdx.y;
+    const int64_t off = seg[i].off, n = seg[i].n;
+    const double b = sc[i].beta;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = off + j;
+        const double zi = z[q];
+        p[q] = zi + b * p[q];
+        zold[q] = zi;
+    }
+}
+
+template <typename T>
+__global__ void k_bcheb(const BSeg *__restrict__ seg, const double *__restrict__ coef, int degree, int step,
+                        const T *__restrict__ rhs, const T *__restrict__ Kx, const T *__restrict__ dinv, T *__restrict__ d,
+                        T *__restrict__ x) {
+    const int i = blockIdx.y;
+    const int64_t off = seg[i].off, n = seg[i].n;
+    const T cd = (T)coef[((int64_t)i * degree + step) * 2 + 0];
+    const T cr = (T)coef[((int64_t)i * degree + step) * 2 + 1];
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = off + j;
+        const T r = dinv[q] * (Kx ? rhs[q] - Kx[q] : rhs[q]);
+        const T dn = step == 0 ? cr * r : cd * d[q] + cr * r;
+        d[q] = dn;
+        x[q] = (step == 0 && !Kx) ? dn : x[q] + dn;
+    }
+}
+
 // Chebyshev step: r = D^-1 (rhs - Kx) (Kx null: r = D^-1 rhs), d = cd d + cr r, x += d
 template <typename T>
 __global__ void k_cheb(int64_t n, const T *__restrict__ rhs, const T *__restrict__ Kx, const T *__restrict__ dinv,
@@ -384,6 +536,74 @@ __global__ void k_fma_probe(int iters, T *sink) {
 }
 
 }  // namespace
+
+inline dim3 bgrid(int64_t max_n, int nm) {
+    int64_t g = (max_n + VB - 1) / VB;
+    if (g > 256) g = 256;
+    if (g < 1) g = 1;
+    return dim3((unsigned)g, (unsigned)nm);
+}
+
+cudaError_t bdots(int nm, const BSeg *seg, int k, const double *a0, const double *b0, const double *a1,
+                  const double *b1, const double *a2, const double *b2, double *partial, double *dots, cudaStream_t s) {
+    if (nm == 0) return cudaSuccess;
+    const dim3 g(BRB, nm);
+    if (k == 1)
+        k_bdots<1><<<g, VB, 0, s>>>(seg, a0, b0, a1, b1, a2, b2, partial);
+    else if (k == 2)
+        k_bdots<2><<<g, VB, 0, s>>>(seg, a0, b0, a1, b1, a2, b2, partial);
+    else
+        k_bdots<3><<<g, VB, 0, s>>>(seg, a0, b0, a1, b1, a2, b2, partial);
+    k_bdots_final<<<nm, 32, 0, s>>>(partial, dots);
+    return cudaGetLastError();
+}
+cudaError_t bcopy(int nm, int64_t max_n, const BSeg *seg, double *y, int dir, cudaStream_t s) {
+    if (nm == 0) return cudaSuccess;
+    k_bcopy<<<bgrid(max_n, nm), VB, 0, s>>>(seg, y, dir);
+    return cudaGetLastError();
+}
+cudaError_t bcopy_idx(int nm, const BSeg *seg, const void *du, void *out, int prec, cudaStream_t s) {
+    if (nm == 0) return cudaSuccess;
+    if (prec == HX_FP64)
+        k_bcopy_idx<double><<<dim3(16, nm), VB, 0, s>>>(seg, (const double *)du, (double *)out);
+    else
+        k_bcopy_idx<float><<<dim3(16, nm), VB, 0, s>>>(seg, (const float *)du, (float *)out);
+    return cudaGetLastError();
+}
+cudaError_t bsub(int64_t n, const double *a, const double *b, double *y, cudaStream_t s) { return sub(n, a, b, y, s); }
+cudaError_t bscal_init(int nm, BScal *sc, const double *dots, double tol, cudaStream_t s) {
+    k_bscal_init<<<(nm + 127) / 128, 128, 0, s>>>(nm, sc, dots, tol);
+    return cudaGetLastError();
+}
+cudaError_t bscal_alpha(int nm, BScal *sc, const double *dots, cudaStream_t s) {
+    k_bscal_alpha<<<(nm + 127) / 128, 128, 0, s>>>(nm, sc, dots);
+    return cudaGetLastError();
+}
+cudaError_t bxr(int nm, int64_t max_n, const BSeg *seg, const BScal *sc, const double *p, const double *Ap, double *x,
+                double *r, float *r32, cudaStream_t s) {
+    k_bxr<<<bgrid(max_n, nm), VB, 0, s>>>(seg, sc, p, Ap, x, r, r32);
+    return cudaGetLastError();
+}
+cudaError_t bscal_beta(int nm, BScal *sc, const double *dots, cudaStream_t s) {
+    k_bscal_beta<<<(nm + 127) / 128, 128, 0, s>>>(nm, sc, dots);
+    return cudaGetLastError();
+}
+cudaError_t bp(int nm, int64_t max_n, const BSeg *seg, const BScal *sc, const double *z, double *p, double *zold,
+               cudaStream_t s) {
+    k_bp<<<bgrid(max_n, nm), VB, 0, s>>>(seg, sc, z, p, zold);
+    return cudaGetLastError();
+}
+cudaError_t bcheb(int nm, int64_t max_n, const BSeg *seg, const double *coef, int degree, int step, const void *rhs,
+                  const void *Kx, const void *dinv, void *d, void *x, int prec, cudaStream_t s) {
+    if (prec == HX_FP64)
+        k_bcheb<double><<<bgrid(max_n, nm), VB, 0, s>>>(seg, coef, degree, step, (const double *)rhs,
+                                                         (const double *)Kx, (const double *)dinv, (double *)d,
+                                                         (double *)x);
+    else
+        k_bcheb<float><<<bgrid(max_n, nm), VB, 0, s>>>(seg, coef, degree, step, (const float *)rhs,
+                                                        (const float *)Kx, (const float *)dinv, (float *)d, (float *)x);
+    return cudaGetLastError();
+}
 
 cudaError_t h_prolong(int nxc, int nyc, int nzc, const void *xc, void *xf, int add, int prec, cudaStream_t s) {
     const int64_t nf = (int64_t)(2 * nxc + 1) * (2 * nyc + 1) * (2 * nzc + 1);

@@ -76,6 +76,46 @@ constexpr int COARSE_MAX = 1024;
 cudaError_t coarse_pcg(int n, const double *A, const double *dinv, const void *b, void *x, int max_iter, double tol,
                        int *iters, int prec, cudaStream_t s);
 
+// ---- batched CG: the meshes of a batch iterate in lockstep -----------------
+// Every batched vector is the concatenation of per-mesh segments; mesh i owns
+// [off, off + n) (off a multiple of 4). Kernels run on a (blocks, meshes)
+// grid; per-mesh scalars stay on the device.
+struct BSeg {
+    int64_t off, n;
+    double *x;            // the caller's solution vector of mesh i
+    const double *rhs;    // the caller's right-hand side of mesh i
+    const int64_t *cidx;  // constrained DoFs of mesh i (local indices)
+    int64_t ncon;
+};
+struct BScal {
+    double rz, pAp, alpha, beta, rr, bb, tol2;
+    int active, bad, iters;
+};
+constexpr int BRB = 64;  // reduction blocks per mesh (fixed: repeatable sums)
+// dots[3 i + j] = a_j . b_j over mesh i's segment, j < k (k <= 3)
+cudaError_t bdots(int nm, const BSeg *seg, int k, const double *a0, const double *b0, const double *a1,
+                  const double *b1, const double *a2, const double *b2, double *partial, double *dots, cudaStream_t s);
+// y = x_i (gather, dir 0) or x_i = y (scatter, dir 1) / y = rhs_i (dir 2)
+cudaError_t bcopy(int nm, int64_t max_n, const BSeg *seg, double *y, int dir, cudaStream_t s);
+// out[cidx] = du[cidx] on every mesh's constrained DoFs (identity rows)
+cudaError_t bcopy_idx(int nm, const BSeg *seg, const void *du, void *out, int prec, cudaStream_t s);
+// y = a - b over the concatenation
+cudaError_t bsub(int64_t n, const double *a, const double *b, double *y, cudaStream_t s);
+// scalars after the initial residual: rz = dots[0], rr = dots[1], bb = dots[2]
+cudaError_t bscal_init(int nm, BScal *sc, const double *dots, double tol, cudaStream_t s);
+cudaError_t bscal_alpha(int nm, BScal *sc, const double *dots, cudaStream_t s);
+// x += alpha p, r -= alpha Ap per mesh; r32 = (float) r if non-null
+cudaError_t bxr(int nm, int64_t max_n, const BSeg *seg, const BScal *sc, const double *p, const double *Ap, double *x,
+                double *r, float *r32, cudaStream_t s);
+cudaError_t bscal_beta(int nm, BScal *sc, const double *dots, cudaStream_t s);
+// p = z + beta p, zold = z per mesh
+cudaError_t bp(int nm, int64_t max_n, const BSeg *seg, const BScal *sc, const double *z, double *p, double *zold,
+               cudaStream_t s);
+// Chebyshev step `step` of the per-mesh coefficients coef[(i * degree + step) * 2 + {cd, cr}]:
+// r = dinv (rhs - Kx) (Kx null: dinv rhs), d = cd d + cr r (step 0: cr r), x += d (step 0 with Kx null: x = d)
+cudaError_t bcheb(int nm, int64_t max_n, const BSeg *seg, const double *coef, int degree, int step, const void *rhs,
+                  const void *Kx, const void *dinv, void *d, void *x, int prec, cudaStream_t s);
+
 // Ordered assembly (deterministic scatter): E holds every element's local
 // vector, E[3 (e NQ + a) + c] for local node a = i + n (j + n k), n = p + 1.
 // out[3 I + c] = the sum over the elements containing node I, taken in

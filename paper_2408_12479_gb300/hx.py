@@ -38,7 +38,7 @@ EXPORTS = ["hx_create", "hx_destroy", "hx_set_stream", "hx_last_error", "hx_sync
            "hx_mg_destroy", "hx_mg_info", "hx_mg_setup", "hx_mg_vcycle", "hx_mg_transfer", "hx_mg_cg_solve", "hx_fibre_dispersion", "hx_batch_create",
            "hx_batch_destroy", "hx_batch_tangent_apply", "hx_measure_fma_peak", "hx_launch_count",
            "hx_autotune", "hx_set_apply_variant", "hx_chebyshev_smooth_noalloc", "hx_traction_load",
-           "hx_set_wait_test", "hx_set_scatter_mode", "hx_mg_level", "hx_mg_coarse_iters"]
+           "hx_set_wait_test", "hx_set_scatter_mode", "hx_mg_level", "hx_mg_coarse_iters", "hx_batch_cg_solve"]
 
 
 class HxError(RuntimeError):
@@ -140,6 +140,8 @@ def lib():
             "hx_set_scatter_mode": (I32, [P, I32]),
             "hx_mg_level": (I32, [P, I32, C.POINTER(I32), C.POINTER(I32), C.POINTER(I32), C.POINTER(I32)]),
             "hx_mg_coarse_iters": (I32, [P, C.POINTER(I32)]),
+            "hx_batch_cg_solve": (I32, [P, C.POINTER(P), C.POINTER(P), D, I32, I32, D, I32, I32, C.POINTER(I32),
+                                        C.POINTER(D)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -493,6 +495,23 @@ def hx_batch_tangent_apply(ctx, batch, dus, outs):
     a = (C.c_void_p * len(dus))(*[d.data_ptr() for d in dus])
     b = (C.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
     _check(lib().hx_batch_tangent_apply(batch, a, b, _prec_of(dus[0])), ctx)
+
+
+def hx_batch_cg_solve(ctx, batch, rhss, xs, tol, max_iter, degree, smoothing_range, precond_prec, use_graph=True):
+    """Batched FP64 CG with a per-mesh Chebyshev-Jacobi preconditioner, all
+    meshes in lockstep (one CUDA graph per iteration). Returns (iters list,
+    relative residual list, status); HX_ERR_NOT_CONVERGED is returned, not
+    raised."""
+    n = len(xs)
+    a = (C.c_void_p * n)(*[t.data_ptr() for t in rhss])
+    b = (C.c_void_p * n)(*[t.data_ptr() for t in xs])
+    it = (C.c_int32 * n)()
+    rel = (C.c_double * n)()
+    st = lib().hx_batch_cg_solve(batch, a, b, float(tol), int(max_iter), int(degree), float(smoothing_range),
+                                 int(precond_prec), int(bool(use_graph)), it, rel)
+    if st not in (HX_OK, HX_ERR_NOT_CONVERGED):
+        _check(st, ctx)
+    return list(it), list(rel), st
 
 
 def hx_measure_fma_peak(ctx, prec):

@@ -128,3 +128,81 @@ def test_batch_many_items_per_cta(law, storage, prec):
         for G in Gs:
             G.close()
         hx.hx_destroy(ctx)
+
+
+@pytest.mark.parametrize("pp", [hx.HX_FP32, hx.HX_FP64])
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_cg_matches_direct_solves_and_single_mesh_cg(pp, use_graph):
+    """Six clamped jittered cubes of mixed size, degree and state: the
+    batched CG (lockstep, per-mesh Chebyshev(3)-Jacobi, one graph per
+    iteration) solves every mesh's constrained system to the oracle's direct
+    solution, and each mesh's iteration count is that of the single-mesh
+    hx_cg_solve on the same system (same eigenvalue estimate) up to the
+    rounding differences of the two operator kernels (3 + 5 %)."""
+    import scipy.sparse.linalg as spla
+    ctx = hx.hx_create(0)
+    specs = [(3, 2), (2, 4), (4, 1), (2, 3), (3, 3), (2, 5)]
+    items, batch = [], None
+    try:
+        for k, (n, p) in enumerate(specs):
+            m = cases.small_cube(n, p, "cNH", seed=700 + k, clamp=True)
+            M, X, u = cases.state_for(m, "cNH", seed=710 + k, strain=0.01 + 0.005 * k)
+            u[M.dirichlet] = 0.0
+            G = hx.Mesh(m, cases.MATS["cNH"], ctx=ctx)
+            u_t = torch.tensor(u, dtype=torch.float64, device="cuda")
+            G.precompute(u_t, hx.HX_FP64, hx.HX_CACHE_TENSORS)
+            G.precompute(u_t, pp, hx.HX_CACHE_TENSORS)
+            rhs = I.random_direction(m.n_dofs, 720 + k)
+            rhs[M.dirichlet] = 0.0
+            K = O.constrain_matrix(O.assemble_sparse(M, cases.oracle_material("cNH"), u), M.dirichlet)
+            ref = spla.spsolve(K.tocsc(), rhs)
+            items.append((G, torch.tensor(rhs, dtype=torch.float64, device="cuda"), ref))
+        batch = hx.hx_batch_create(ctx, [G for G, _, _ in items])
+        xs = [torch.zeros_like(r) for _, r, _ in items]
+        its, rels, st = hx.hx_batch_cg_solve(ctx, batch, [r for _, r, _ in items], xs, 1e-10, 3000, 3, 15.0, pp,
+                                             use_graph)
+        assert st == hx.HX_OK, (its, rels)
+        for (G, rhs, ref), x, it, rel in zip(items, xs, its, rels):
+            assert rel <= 1e-10 and it > 0
+            assert rel_inf(x.cpu().numpy(), ref) < 1e-8
+            # the same system through the single-mesh solver
+            dinv = 1.0 / G.diagonal(hx.HX_FP64)
+            lam = hx.hx_estimate_lambda_max(G.ctx, G.handle, dinv, iters=20, seed=7)
+            x1 = torch.zeros_like(rhs)
+            it1, rel1, st1 = hx.hx_cg_solve(G.ctx, G.handle, rhs, x1, 1e-10, 3000, 3, 1.2 * lam, 15.0, pp)
+            assert st1 == hx.HX_OK
+            assert abs(it - it1) <= 3 + 0.05 * it1, (it, it1)
+    finally:
+        if batch is not None:
+            hx.hx_batch_destroy(batch)
+        for G, _, _ in items:
+            G.close()
+        hx.hx_destroy(ctx)
+
+
+def test_batch_cg_reports_a_mesh_that_misses_the_tolerance():
+    ctx = hx.hx_create(0)
+    items, batch = [], None
+    try:
+        for k, (n, p) in enumerate([(3, 2), (3, 4)]):
+            m = cases.small_cube(n, p, "cNH", seed=730 + k, clamp=True)
+            M, X, u = cases.state_for(m, "cNH", seed=740 + k, strain=0.01)
+            u[M.dirichlet] = 0.0
+            G = hx.Mesh(m, cases.MATS["cNH"], ctx=ctx)
+            u_t = torch.tensor(u, dtype=torch.float64, device="cuda")
+            G.precompute(u_t, hx.HX_FP64, hx.HX_CACHE_F)
+            G.precompute(u_t, hx.HX_FP32, hx.HX_CACHE_F)
+            rhs = torch.tensor(I.random_direction(m.n_dofs, 750 + k), dtype=torch.float64, device="cuda")
+            rhs[torch.tensor(M.dirichlet, device="cuda")] = 0.0
+            items.append((G, rhs))
+        batch = hx.hx_batch_create(ctx, [G for G, _ in items])
+        xs = [torch.zeros_like(r) for _, r in items]
+        its, rels, st = hx.hx_batch_cg_solve(ctx, batch, [r for _, r in items], xs, 1e-12, 3, 2, 15.0, hx.HX_FP32)
+        assert st == hx.HX_ERR_NOT_CONVERGED
+        assert its == [3, 3] and all(r > 1e-12 for r in rels)
+    finally:
+        if batch is not None:
+            hx.hx_batch_destroy(batch)
+        for G, _ in items:
+            G.close()
+        hx.hx_destroy(ctx)

@@ -344,7 +344,12 @@ def test_headline_line_is_short_strict_json():
                    "ms_per_step": float("nan"),
                    "config": {"workload": "w", "per_storage_ms": {"a": 1.0}, "x": float("inf")},
                    "roofline": {"frac": np.float32(0.41), "traffic": None}, "clocks": {"sm_mhz": 2070.0},
-                   "sweep_best": bench.sweep_summary(sweep), "residual": [1.0] * 10000})
+                   "sweep_best": bench.sweep_summary(sweep), "residual": [1.0] * 10000,
+                   "solve_48": bench.solve_summary({"hp_mg_fp32": {"seconds": 1.5, "iterations": 40,
+                                                                   "true_rel_residual": 9.9e-9},
+                                                    "hp_mg_fp64": {"seconds": 9.0, "iterations": 40,
+                                                                   "true_rel_residual": 9.8e-9},
+                                                    "speedup_fp32_precond": 6.0, "levels": ["x"] * 50})})
     line = bench.headline_line(fields)
     assert len(line) < 2048
     d = json.loads(line)
@@ -352,8 +357,10 @@ def test_headline_line_is_short_strict_json():
     assert "residual" not in d
     assert d["ms_per_step"] is None and d["config"]["x"] is None
     assert abs(d["roofline"]["frac"] - 0.41) < 1e-6
-    assert d["sweep_best"]["f32"]["4"] == [41.0, 0.4, "spatial_tensors"]
+    assert d["sweep_best"]["f32"]["4"] == [41.0, 0.4, None, "S"]
     assert set(d["sweep_best"]["f64"]) == {"2", "3", "4", "5", "6"}
+    assert d["solve_48"] == {"hp_mg_fp32": [1.5, 40, 9.9e-9], "hp_mg_fp64": [9.0, 40, 9.8e-9], "speedup": 6.0}
+    assert bench.solve_summary({"error": "x"}) == {"error": "x"}
 
 
 def test_emit_prints_strict_json(capsys):
