@@ -190,9 +190,9 @@ hx_status hx_tangent_apply_host(hx_mesh *mesh, const void *du_host, void *out_ho
  *         tile (default tile, half tile);
  *   3, 4: bulk copies into shared memory one tile ahead, quadrature points
  *         taken in column order (default tile, half tile);
- *   2, 5: as 3/4 with two elements per thread, whose lines and points run in
- *         the two lanes of the packed FP32 instructions (half tile, default
- *         tile; caching strategies only).
+ *   2, 5: as 3/4 with a stage and an mbarrier per warp, where one warp
+ *         holds one element (FP32, p = 4; caching strategies): no phase
+ *         waits for more than its own warp (half tile, default tile).
  * Returns the fastest index and the six mean times in ms (a variant that
  * cannot launch, e.g. a staged tile whose chunks would not be 16-byte aligned
  * or would not fit in shared memory, reports a negative time). Uses

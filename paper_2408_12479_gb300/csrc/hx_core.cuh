@@ -1206,12 +1206,22 @@ __device__ __forceinline__ void col_forward(const Real *row, Real *X0, Real *X1,
     }
 }
 
+// Barrier between the phases of a tile: the whole CTA, or (WS) the warp alone
+// when every element's cubes and stage belong to one warp.
+template <bool WS>
+__device__ __forceinline__ void phase_sync() {
+    if constexpr (WS)
+        __syncwarp();
+    else
+        __syncthreads();
+}
+
 // Forward sweeps for the column-ordered quadrature-point phase: as
 // col_forward, but the z-derivative of each thread's z-line (its column of
 // quadrature points, (qx, qy) = (a0, a1)) stays in registers gz[c][k], the
 // x-derivative goes to X0 and the y-derivative to X2 (X1 keeps the values).
 // No final barrier (the caller's barrier completes the sweeps).
-template <bool SW>
+template <bool SW, bool WS = false>
 __device__ __forceinline__ void col_forward_c(const Real *row, Real *X0, Real *X1, Real *X2, Real (*gz)[N], bool act,
                                               int eoff, const LineOffs<SW> &o) {
     // each phase loads all three components' lines before any store: the
@@ -1231,7 +1241,7 @@ __device__ __forceinline__ void col_forward_c(const Real *row, Real *X0, Real *X
 #pragma unroll
             for (int i = 0; i < N; ++i) X0[eoff + c * CZ + o.x + i] = y[c][i];
     }
-    __syncthreads();
+    phase_sync<WS>();
     if (act) {  // y-lines: X1 = By X0
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -1243,7 +1253,7 @@ __device__ __forceinline__ void col_forward_c(const Real *row, Real *X0, Real *X
 #pragma unroll
             for (int t = 0; t < N; ++t) X1[eoff + c * CZ + o.y[t]] = y[c][t];
     }
-    __syncthreads();
+    phase_sync<WS>();
     if (act) {  // z-lines: values V = Bz X1 (in place, per line), Dz V kept
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -1256,7 +1266,7 @@ __device__ __forceinline__ void col_forward_c(const Real *row, Real *X0, Real *X
 #pragma unroll
             for (int t = 0; t < N; ++t) X1[eoff + c * CZ + o.z[t]] = y[c][t];
     }
-    __syncthreads();
+    phase_sync<WS>();
     if (act) {  // x-lines: X0 = Dx V; y-lines: X2 = Dy V
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -1446,7 +1456,7 @@ __device__ __forceinline__ void col_backward(const hx::MeshView &m, Real *X0, Re
 // Qx, X2 holds Qy and rz[c] = Dz^T Qz of each thread's z-line (registers).
 // Dy^T in place on X2 and rz into X1, then X0 = Bx^T (Dx^T X0 + X1 + X2)
 // in place, X1 = By^T X0 and the scatter of Bz^T X1. Called after a barrier.
-template <bool SW>
+template <bool SW, bool WS = false>
 __device__ __forceinline__ void col_backward_c(const hx::MeshView &m, Real *X0, Real *X1, Real *X2, Real (*rz)[N],
                                                bool act, bool valid, int eoff, const LineOffs<SW> &o, int a0, int a1,
                                                int e, Real *__restrict__ out, uint64_t pol_keep) {
@@ -1467,7 +1477,7 @@ __device__ __forceinline__ void col_backward_c(const hx::MeshView &m, Real *X0, 
                 X2[eoff + c * CZ + o.y[t]] = y[c][t];
             }
     }
-    __syncthreads();
+    phase_sync<WS>();
     if (act) {  // x-lines, in place: X0 = Bx^T (Dx^T X0 + X1 + X2)
         Real s1[3][N], s2[3][N];
 #pragma unroll
@@ -1489,7 +1499,7 @@ __device__ __forceinline__ void col_backward_c(const hx::MeshView &m, Real *X0, 
 #pragma unroll
             for (int t = 0; t < N; ++t) X0[eoff + c * CZ + o.x + t] = y[c][t];
     }
-    __syncthreads();
+    phase_sync<WS>();
     if (act) {  // y-lines: X1 = By^T X0
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -1501,7 +1511,7 @@ __device__ __forceinline__ void col_backward_c(const hx::MeshView &m, Real *X0, 
 #pragma unroll
             for (int t = 0; t < N; ++t) X1[eoff + c * CZ + o.y[t]] = y[c][t];
     }
-    __syncthreads();
+    phase_sync<WS>();
     if (valid) {  // z-lines: r = Bz^T X1, scattered from registers
 #pragma unroll
         for (int c = 0; c < 3; ++c)
@@ -1551,6 +1561,122 @@ __device__ __forceinline__ void qp_tangent(const hx::MeshView &m, int e, const R
         push_grad(Gr, Ji, H);
         tangent_dP<Real, LAW>(st, H, dP);
         pull_flux(dP, Ji, JxW, Q);
+    }
+}
+
+// Quadrature-point phase of the column-ordered staged apply: thread (a0, a1)
+// of an element handles its points (a0, a1, k), k = 0..N-1, whose fields sit
+// in the stage at sp[f * FS + NN * k]; Gx, Gy come from X0, X2 at the
+// z-line points and Gz from gz (registers); Q_x, Q_y go back to X0, X2 and
+// Q_z to gz. Recompute: the reference gradient of u_k from K0, K2, gk.
+template <int LAW, int STORAGE, int FS, bool SW>
+__device__ __forceinline__ void qp_columns(const hx::MeshView &m, int e, bool valid, const Real *sp, Real *X0,
+                                           Real *X2, const Real *K0, const Real *K2, Real (*gz)[N],
+                                           const Real (*gk)[N], int eoff, const LineOffs<SW> &lo) {
+    constexpr bool RC = STORAGE == HX_RECOMPUTE;
+    constexpr int CZ = Lay<SW>::CZ;
+    constexpr int NR = QpFields<LAW, STORAGE>::n;
+    if constexpr (STORAGE == HX_SPATIAL_TENSORS && PK) {
+        // FP32 spatial tensors: the column's points run two at a time in
+        // the two lanes of the packed FP32 instructions (points k, k+1;
+        // an odd last point alone); the next pair's shared loads are
+        // issued before this pair's stores
+        if (valid) {
+            Real ra[NR], rb[NR], Ga[6], Gb[6];
+            auto fetch1 = [&](int k, Real *r, Real *G) {
+#pragma unroll
+                for (int f = 0; f < NR; ++f) r[f] = sp[f * FS + NN * k];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    G[c] = X0[eoff + lo.z[k] + c * CZ];
+                    G[3 + c] = X2[eoff + lo.z[k] + c * CZ];
+                }
+            };
+            fetch1(0, ra, Ga);
+            if (N > 1) fetch1(1, rb, Gb);
+#pragma unroll
+            for (int k = 0; k + 1 < N; k += 2) {
+                F2 G2[9], Q2[9];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    G2[c * 3 + 0] = F2(Ga[c], Gb[c]);
+                    G2[c * 3 + 1] = F2(Ga[3 + c], Gb[3 + c]);
+                    G2[c * 3 + 2] = F2(gz[c][k], gz[c][k + 1]);
+                }
+                spatial_Q<F2, LAW>(G2, [&](int f) { return F2(ra[f], rb[f]); }, Q2);
+                if (k + 2 < N) fetch1(k + 2, ra, Ga);
+                if (k + 3 < N) fetch1(k + 3, rb, Gb);
+                const int pk = eoff + lo.z[k], pk1 = eoff + lo.z[k + 1];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    X0[pk + c * CZ] = Q2[c * 3 + 0].v.x;
+                    X2[pk + c * CZ] = Q2[c * 3 + 1].v.x;
+                    X0[pk1 + c * CZ] = Q2[c * 3 + 0].v.y;
+                    X2[pk1 + c * CZ] = Q2[c * 3 + 1].v.y;
+                    gz[c][k] = Q2[c * 3 + 2].v.x;
+                    gz[c][k + 1] = Q2[c * 3 + 2].v.y;
+                }
+            }
+            if constexpr (N % 2 == 1) {  // the last point alone (fetched into ra, Ga)
+                constexpr int k = N - 1;
+                Real Gr[9], Q[9];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    Gr[c * 3 + 0] = Ga[c];
+                    Gr[c * 3 + 1] = Ga[3 + c];
+                    Gr[c * 3 + 2] = gz[c][k];
+                }
+                spatial_Q<Real, LAW>(Gr, [&](int f) { return ra[f]; }, Q);
+                const int pk = eoff + lo.z[k];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    X0[pk + c * CZ] = Q[c * 3 + 0];
+                    X2[pk + c * CZ] = Q[c * 3 + 1];
+                    gz[c][k] = Q[c * 3 + 2];
+                }
+            }
+        }
+    } else if (valid) {
+        // point k+1's shared loads are issued before point k's stores
+        Real r[NR], Gx[3], Gy[3], Ux[3], Uy[3];
+        auto fetch = [&](int k) {
+#pragma unroll
+            for (int f = 0; f < NR; ++f) r[f] = sp[f * FS + NN * k];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                Gx[c] = X0[eoff + lo.z[k] + c * CZ];
+                Gy[c] = X2[eoff + lo.z[k] + c * CZ];
+                if constexpr (RC) {
+                    Ux[c] = K0[eoff + lo.z[k] + c * CZ];
+                    Uy[c] = K2[eoff + lo.z[k] + c * CZ];
+                }
+            }
+        };
+        fetch(0);
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            Real Gr[9], Gu[9], Q[9];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                Gr[c * 3 + 0] = Gx[c];
+                Gr[c * 3 + 1] = Gy[c];
+                Gr[c * 3 + 2] = gz[c][k];
+                if constexpr (RC) {
+                    Gu[c * 3 + 0] = Ux[c];
+                    Gu[c * 3 + 1] = Uy[c];
+                    Gu[c * 3 + 2] = gk[c][k];
+                }
+            }
+            qp_tangent<LAW, STORAGE>(m, e, Gr, Gu, r, Q);
+            if (k + 1 < N) fetch(k + 1);
+            const int pk = eoff + lo.z[k];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                X0[pk + c * CZ] = Q[c * 3 + 0];
+                X2[pk + c * CZ] = Q[c * 3 + 1];
+                gz[c][k] = Q[c * 3 + 2];
+            }
+        }
     }
 }
 
@@ -1640,110 +1766,8 @@ __device__ __forceinline__ bool apply_tile(const hx::MeshView &m, int tile, int 
             return false;
         }
         phase ^= 1u;
-        if constexpr (STORAGE == HX_SPATIAL_TENSORS && PK) {
-            // FP32 spatial tensors: the column's points run two at a time in
-            // the two lanes of the packed FP32 instructions (points k, k+1;
-            // an odd last point alone); the next pair's shared loads are
-            // issued before this pair's stores
-            if (valid) {
-                const Real *sp = stg + el * NQ + a0 + N * a1;
-                Real ra[NR], rb[NR], Ga[6], Gb[6];
-                auto fetch1 = [&](int k, Real *r, Real *G) {
-#pragma unroll
-                    for (int f = 0; f < NR; ++f) r[f] = sp[f * (EPB * NQ) + NN * k];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        G[c] = X0[eoff + lo.z[k] + c * CZ];
-                        G[3 + c] = X2[eoff + lo.z[k] + c * CZ];
-                    }
-                };
-                fetch1(0, ra, Ga);
-                if (N > 1) fetch1(1, rb, Gb);
-#pragma unroll
-                for (int k = 0; k + 1 < N; k += 2) {
-                    F2 G2[9], Q2[9];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        G2[c * 3 + 0] = F2(Ga[c], Gb[c]);
-                        G2[c * 3 + 1] = F2(Ga[3 + c], Gb[3 + c]);
-                        G2[c * 3 + 2] = F2(gz[c][k], gz[c][k + 1]);
-                    }
-                    spatial_Q<F2, LAW>(G2, [&](int f) { return F2(ra[f], rb[f]); }, Q2);
-                    if (k + 2 < N) fetch1(k + 2, ra, Ga);
-                    if (k + 3 < N) fetch1(k + 3, rb, Gb);
-                    const int pk = eoff + lo.z[k], pk1 = eoff + lo.z[k + 1];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        X0[pk + c * CZ] = Q2[c * 3 + 0].v.x;
-                        X2[pk + c * CZ] = Q2[c * 3 + 1].v.x;
-                        X0[pk1 + c * CZ] = Q2[c * 3 + 0].v.y;
-                        X2[pk1 + c * CZ] = Q2[c * 3 + 1].v.y;
-                        gz[c][k] = Q2[c * 3 + 2].v.x;
-                        gz[c][k + 1] = Q2[c * 3 + 2].v.y;
-                    }
-                }
-                if constexpr (N % 2 == 1) {  // the last point alone (fetched into ra, Ga)
-                    constexpr int k = N - 1;
-                    Real Gr[9], Q[9];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        Gr[c * 3 + 0] = Ga[c];
-                        Gr[c * 3 + 1] = Ga[3 + c];
-                        Gr[c * 3 + 2] = gz[c][k];
-                    }
-                    spatial_Q<Real, LAW>(Gr, [&](int f) { return ra[f]; }, Q);
-                    const int pk = eoff + lo.z[k];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        X0[pk + c * CZ] = Q[c * 3 + 0];
-                        X2[pk + c * CZ] = Q[c * 3 + 1];
-                        gz[c][k] = Q[c * 3 + 2];
-                    }
-                }
-            }
-        } else if (valid) {
-            const Real *sp = stg + el * NQ + a0 + N * a1;
-            // point k+1's shared loads are issued before point k's stores
-            Real r[NR], Gx[3], Gy[3], Ux[3], Uy[3];
-            auto fetch = [&](int k) {
-#pragma unroll
-                for (int f = 0; f < NR; ++f) r[f] = sp[f * (EPB * NQ) + NN * k];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    Gx[c] = X0[eoff + lo.z[k] + c * CZ];
-                    Gy[c] = X2[eoff + lo.z[k] + c * CZ];
-                    if constexpr (RC) {
-                        Ux[c] = K0[eoff + lo.z[k] + c * CZ];
-                        Uy[c] = K2[eoff + lo.z[k] + c * CZ];
-                    }
-                }
-            };
-            fetch(0);
-#pragma unroll
-            for (int k = 0; k < N; ++k) {
-                Real Gr[9], Gu[9], Q[9];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    Gr[c * 3 + 0] = Gx[c];
-                    Gr[c * 3 + 1] = Gy[c];
-                    Gr[c * 3 + 2] = gz[c][k];
-                    if constexpr (RC) {
-                        Gu[c * 3 + 0] = Ux[c];
-                        Gu[c * 3 + 1] = Uy[c];
-                        Gu[c * 3 + 2] = gk[c][k];
-                    }
-                }
-                qp_tangent<LAW, STORAGE>(m, e, Gr, Gu, r, Q);
-                if (k + 1 < N) fetch(k + 1);
-                const int pk = eoff + lo.z[k];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    X0[pk + c * CZ] = Q[c * 3 + 0];
-                    X2[pk + c * CZ] = Q[c * 3 + 1];
-                    gz[c][k] = Q[c * 3 + 2];
-                }
-            }
-        }
+        qp_columns<LAW, STORAGE, EPB * NQ, SW>(m, e, valid, stg + el * NQ + a0 + N * a1, X0, X2, K0, K2, gz, gk,
+                                               eoff, lo);
         Real rz[3][N];
         mv3<TD, true, true>(gz, rz);
         __syncthreads();
@@ -1770,338 +1794,97 @@ __device__ __forceinline__ bool apply_tile(const hx::MeshView &m, int tile, int 
 }
 
 // ---------------------------------------------------------------------------
-// Two elements per thread (staged apply, variant 5). Thread (a0, a1) of slot
-// el carries the lines of element A = e0 + el and of element B = A + EPB/2,
-// whose cubes sit HB = (EPB/2) * ES words after A's. Every sweep phase then
-// holds six independent lines (two elements x three components), which mv6
-// runs as three FFMA2 pairs in FP32 units, and the spatial-tensor point phase
-// runs A's and B's points in the two lanes of the packed FP32 instructions;
-// one set of line offsets and loop counters serves both elements.
+// Warp-decoupled staged apply (variants 2 and 5, FP32 at n = 5, where one
+// warp owns one element): every warp has its own stage and mbarrier, so no
+// phase needs more than a warp barrier and the warps of a CTA drift freely.
+// An element's 125-point chunk of a field is 500 bytes and starts 4 (e mod 4)
+// bytes past a 16-byte boundary, so the warp copies the 512-byte aligned
+// window around it (the neighbours' edge words come along unused; they lie
+// in sectors the neighbouring element reads anyway) and reads from word
+// e mod 4 of the window.
 // ---------------------------------------------------------------------------
+constexpr int WIN = 128;  // words of one field's window in a warp's stage
 
-// col_forward_c for two elements per thread: x[c] / x[3 + c] are component
-// c of element A / B. Leaves Dx V in X0, Dy V in X2 and Dz V of each
-// thread's z-lines in gz[6][N]; no final barrier.
-template <bool SW, int HB>
-__device__ __forceinline__ void col_forward_pc(const Real *rowA, const Real *rowB, Real *X0, Real *X1, Real *X2,
-                                               Real (*gz)[N], bool act, int eoff, const LineOffs<SW> &o) {
-    constexpr int CZ = Lay<SW>::CZ;
-    constexpr bool EO = true;
-    Real x[6][N], y[6][N];
-    if (act) {  // x-lines: X0 = Bx u
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int i = 0; i < N; ++i) {
-                x[c][i] = rowA[3 * i + c];
-                x[3 + c][i] = rowB[3 * i + c];
-            }
-        mv6<TB, false, EO>(x, x + 3, y, y + 3);
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int i = 0; i < N; ++i) {
-                X0[eoff + c * CZ + o.x + i] = y[c][i];
-                X0[eoff + HB + c * CZ + o.x + i] = y[3 + c][i];
-            }
-    }
-    __syncthreads();
-    if (act) {  // y-lines: X1 = By X0
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int t = 0; t < N; ++t) {
-                x[c][t] = X0[eoff + c * CZ + o.y[t]];
-                x[3 + c][t] = X0[eoff + HB + c * CZ + o.y[t]];
-            }
-        mv6<TB, false, EO>(x, x + 3, y, y + 3);
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int t = 0; t < N; ++t) {
-                X1[eoff + c * CZ + o.y[t]] = y[c][t];
-                X1[eoff + HB + c * CZ + o.y[t]] = y[3 + c][t];
-            }
-    }
-    __syncthreads();
-    if (act) {  // z-lines: values V = Bz X1 (in place, per line), Dz V kept
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int t = 0; t < N; ++t) {
-                x[c][t] = X1[eoff + c * CZ + o.z[t]];
-                x[3 + c][t] = X1[eoff + HB + c * CZ + o.z[t]];
-            }
-        mv6<TB, false, EO>(x, x + 3, y, y + 3);
-        mv6<TD, false, EO>(y, y + 3, gz, gz + 3);
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int t = 0; t < N; ++t) {
-                X1[eoff + c * CZ + o.z[t]] = y[c][t];
-                X1[eoff + HB + c * CZ + o.z[t]] = y[3 + c][t];
-            }
-    }
-    __syncthreads();
-    if (act) {  // x-lines: X0 = Dx V; y-lines: X2 = Dy V
-        Real v[6][N];
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int t = 0; t < N; ++t) {
-                x[c][t] = X1[eoff + c * CZ + o.x + t];
-                x[3 + c][t] = X1[eoff + HB + c * CZ + o.x + t];
-                v[c][t] = X1[eoff + c * CZ + o.y[t]];
-                v[3 + c][t] = X1[eoff + HB + c * CZ + o.y[t]];
-            }
-        mv6<TD, false, EO>(x, x + 3, y, y + 3);
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int t = 0; t < N; ++t) {
-                X0[eoff + c * CZ + o.x + t] = y[c][t];
-                X0[eoff + HB + c * CZ + o.x + t] = y[3 + c][t];
-            }
-        mv6<TD, false, EO>(v, v + 3, x, x + 3);
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int t = 0; t < N; ++t) {
-                X2[eoff + c * CZ + o.y[t]] = x[c][t];
-                X2[eoff + HB + c * CZ + o.y[t]] = x[3 + c][t];
-            }
+// Lane 0 of element e's warp: the bulk copies of e's point fields into the
+// warp's stage (one 512-byte window per field), on the warp's mbarrier. The
+// windows stay inside the arrays (64 bytes of slack after the last field).
+template <int LAW, int STORAGE>
+__device__ __forceinline__ void stage_issue_elem(const hx::MeshView &m, int e, Real *stg, uint64_t *bar) {
+    using QF = QpFields<LAW, STORAGE>;
+    static_assert(LAW >= 0 && NQ == 125 && sizeof(Real) == 4, "the window layout is that of FP32 elements of 125 points");
+    if (m.skip_stage_copies) return;  // test hook: the stage never fills and the wait runs out
+    const uint64_t pol = policy_evict_first();
+    const int64_t w0 = (int64_t)e * NQ - (e & 3);  // first word of the window: a multiple of 4
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bar, QF::n * WIN * 4);
+#pragma unroll 1
+    for (int f = 0; f < QF::n; ++f) {
+        const Real *src = f < QF::ng ? (const Real *)m.geo + (int64_t)f * m.qs + w0
+                                     : (const Real *)m.qp + (int64_t)(f - QF::ng) * m.qs + w0;
+        bulk_g2s(stg + f * WIN, src, WIN * 4, bar, pol);
     }
 }
 
-// col_backward_c for two elements per thread: X0 holds Qx, X2 holds Qy and
-// rz[c] / rz[3 + c] = Dz^T Qz of element A / B (registers). Ends with the
-// atomic scatter of both elements (each only if it exists).
-template <bool SW, int HB>
-__device__ __forceinline__ void col_backward_pc(const hx::MeshView &m, Real *X0, Real *X1, Real *X2, Real (*rz)[N],
-                                                bool act, bool validA, bool validB, int eoff, const LineOffs<SW> &o,
-                                                int a0, int a1, int eA, int eB, Real *__restrict__ out,
-                                                uint64_t pol_keep) {
-    constexpr int CZ = Lay<SW>::CZ;
-    constexpr bool EO = true;
-    Real x[6][N], y[6][N];
-    if (act) {  // y-lines: X2 = Dy^T X2 in place; z-lines: X1 = rz
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int t = 0; t < N; ++t) {
-                x[c][t] = X2[eoff + c * CZ + o.y[t]];
-                x[3 + c][t] = X2[eoff + HB + c * CZ + o.y[t]];
-            }
-        mv6<TD, true, EO>(x, x + 3, y, y + 3);
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int t = 0; t < N; ++t) {
-                X1[eoff + c * CZ + o.z[t]] = rz[c][t];
-                X1[eoff + HB + c * CZ + o.z[t]] = rz[3 + c][t];
-                X2[eoff + c * CZ + o.y[t]] = y[c][t];
-                X2[eoff + HB + c * CZ + o.y[t]] = y[3 + c][t];
-            }
-    }
-    __syncthreads();
-    if (act) {  // x-lines, in place: X0 = Bx^T (Dx^T X0 + X1 + X2)
-        Real s[6][N];
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int t = 0; t < N; ++t) {
-                x[c][t] = X0[eoff + c * CZ + o.x + t];
-                x[3 + c][t] = X0[eoff + HB + c * CZ + o.x + t];
-                s[c][t] = X1[eoff + c * CZ + o.x + t] + X2[eoff + c * CZ + o.x + t];
-                s[3 + c][t] = X1[eoff + HB + c * CZ + o.x + t] + X2[eoff + HB + c * CZ + o.x + t];
-            }
-        mv6<TD, true, EO>(x, x + 3, y, y + 3);
-#pragma unroll
-        for (int c = 0; c < 6; ++c)
-#pragma unroll
-            for (int k = 0; k < N; ++k) s[c][k] = y[c][k] + s[c][k];
-        mv6<TB, true, EO>(s, s + 3, y, y + 3);
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int t = 0; t < N; ++t) {
-                X0[eoff + c * CZ + o.x + t] = y[c][t];
-                X0[eoff + HB + c * CZ + o.x + t] = y[3 + c][t];
-            }
-    }
-    __syncthreads();
-    if (act) {  // y-lines: X1 = By^T X0
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int t = 0; t < N; ++t) {
-                x[c][t] = X0[eoff + c * CZ + o.y[t]];
-                x[3 + c][t] = X0[eoff + HB + c * CZ + o.y[t]];
-            }
-        mv6<TB, true, EO>(x, x + 3, y, y + 3);
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int t = 0; t < N; ++t) {
-                X1[eoff + c * CZ + o.y[t]] = y[c][t];
-                X1[eoff + HB + c * CZ + o.y[t]] = y[3 + c][t];
-            }
-    }
-    __syncthreads();
-    if (validA) {  // z-lines: r = Bz^T X1, scattered from registers
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int t = 0; t < N; ++t) {
-                x[c][t] = X1[eoff + c * CZ + o.z[t]];
-                x[3 + c][t] = X1[eoff + HB + c * CZ + o.z[t]];
-            }
-        mv6<TB, true, EO>(x, x + 3, y, y + 3);
-        if (m.elem_out) {  // ordered assembly: the gather pass sums and masks
-            Real *eo = (Real *)m.elem_out + 3 * ((int64_t)eA * NQ + a0 + N * a1);
-#pragma unroll
-            for (int k = 0; k < N; ++k)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) eo[3 * NN * k + c] = y[c][k];
-            if (validB) {
-                eo += 3 * (int64_t)(eB - eA) * NQ;
-#pragma unroll
-                for (int k = 0; k < N; ++k)
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) eo[3 * NN * k + c] = y[3 + c][k];
-            }
-            return;
-        }
-        const bool msk = m.dmask != nullptr;
-        const int64_t baseA = elem_base(m, eA);
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-            const int64_t d = 3 * node_at(m, baseA, a0, a1, k);
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-                if (!(msk && m.dmask[d + c])) red_add(out + d + c, y[c][k], pol_keep);
-        }
-        if (validB) {
-            const int64_t baseB = elem_base(m, eB);
-#pragma unroll
-            for (int k = 0; k < N; ++k) {
-                const int64_t d = 3 * node_at(m, baseB, a0, a1, k);
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    if (!(msk && m.dmask[d + c])) red_add(out + d + c, y[3 + c][k], pol_keep);
-            }
-        }
-    }
-}
-
-// One tile (EPB elements from tile*EPB) of the staged apply with two elements
-// per thread on NT = threads for EPB/2 elements; the tile's point fields were
-// bulk-copied into the stage on `bar` a tile earlier, and the copies of tile
-// `ntile` (< 0: none) are issued once the stage is consumed. Returns false
-// (on every thread) if the staged data never arrived. Caching strategies only.
+// out += K(u_k) du, one warp per element with its own stage (caching
+// strategies). Warp w of a CTA takes element tile*EPB + w of each of the
+// CTA's tiles; its lane 0 issues the copies of the warp's next element as
+// soon as the warp has consumed its stage.
 template <int EPB, int LAW, int STORAGE>
-__device__ __forceinline__ bool apply_tile_pair(const hx::MeshView &m, int tile, int ntile, Real *__restrict__ out,
-                                                const Real *cdA, const Real *cdB, unsigned char *smem_raw, Real *stg,
-                                                uint64_t *bar, uint32_t &phase, uint64_t pol_keep) {
-    static_assert(STORAGE != HX_RECOMPUTE && EPB % 2 == 0, "pair tiles: caching strategies, even tiles");
-    constexpr bool SW = ROWSW;
-    constexpr int ES = Lay<SW>::ES;
-    constexpr int CZ = Lay<SW>::CZ;
-    constexpr int HE = EPB / 2;   // thread slots; B = A + HE
-    constexpr int HB = HE * ES;   // word offset of B's cubes
-    Real *X0 = (Real *)smem_raw;
-    Real *X1 = X0 + EPB * ES;
-    Real *X2 = X1 + EPB * ES;
+__global__ void __launch_bounds__(EPB * 32) k_apply_wd(const hx::MeshView m, const Real *__restrict__ du,
+                                                       Real *__restrict__ out, int ntiles) {
+    static_assert(ROWSW && STORAGE != HX_RECOMPUTE, "one warp per element, caching strategies");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bars[EPB];
+    using QF = QpFields<LAW, STORAGE>;
+    constexpr int ES = Lay<true>::ES;
     const int t = threadIdx.x;
     int el, a0, a1;
     bool act;
-    thread_map<SW>(t, HE, el, a0, a1, act);
-    const int eoff = (act ? el : 0) * ES;
-    using QF = QpFields<LAW, STORAGE>;
-    constexpr int NR = QF::n;
-    const int eA = tile * EPB + el, eB = eA + HE;
-    const bool validA = act && eA < m.n_elem, validB = act && eB < m.n_elem;
-    const LineOffs<SW> lo = line_offsets<SW>(a0, a1);
-    Real gz[6][N];
-    col_forward_pc<SW, HB>(cdA, cdB, X0, X1, X2, gz, act, eoff, lo);
-    const bool ok = mbar_wait(bar, phase, m.wait_limit);
-    if (__syncthreads_or(!ok)) {  // also the barrier that completes the forward sweeps
-        if (t == 0) {
-            atomicOr(m.err + 2, 1);
-            mbar_wait(bar, phase, m.wait_limit);  // let a copy still in flight land before the CTA exits
+    thread_map<true>(t, EPB, el, a0, a1, act);
+    const int lane = t & 31;
+    const int eoff = el * ES;
+    Real *X0 = (Real *)smem_raw;
+    Real *X1 = X0 + EPB * ES;
+    Real *X2 = X1 + EPB * ES;
+    Real *stg = (Real *)(smem_raw + ((size_t)3 * EPB * ES * sizeof(Real) + 15) / 16 * 16) + el * (QF::n * WIN);
+    uint64_t *bar = &bars[el];
+    const uint64_t pol_keep = policy_evict_last();
+    const LineOffs<true> lo = line_offsets<true>(a0, a1);
+    uint32_t phase = 0;
+    if (lane == 0) mbar_init(bar, 1);
+    __syncwarp();
+    const int stride = gridDim.x * EPB;
+    int e = blockIdx.x * EPB + el;
+    if (lane == 0 && (int)blockIdx.x < ntiles && e < m.n_elem) stage_issue_elem<LAW, STORAGE>(m, e, stg, bar);
+    Real row[3 * N];
+    if (act) load_row(m, e, elem_base(m, e), a0, a1, du, true, row);
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, e += stride) {
+        if (e >= m.n_elem) break;  // warp-uniform; later tiles lie further out
+        const int en = e + stride;
+        Real cd[3 * N];
+#pragma unroll
+        for (int i = 0; i < 3 * N; ++i) cd[i] = row[i];
+        if (act) load_row(m, en, elem_base(m, en), a0, a1, du, true, row);  // zeros past the end
+        Real gz[3][N], gk[1][N];
+        col_forward_c<true, true>(cd, X0, X1, X2, gz, act, eoff, lo);
+        const bool ok = mbar_wait(bar, phase, m.wait_limit);
+        if (__any_sync(0xffffffffu, !ok)) {
+            if (lane == 0) {
+                atomicOr(m.err + 2, 1);
+                mbar_wait(bar, phase, m.wait_limit);  // let a copy still in flight land before the warp exits
+            }
+            return;
         }
-        return false;
+        __syncwarp();  // completes the forward sweeps
+        phase ^= 1u;
+        qp_columns<LAW, STORAGE, WIN, true>(m, e, act, stg + (e & 3) + a0 + N * a1, X0, X2, nullptr, nullptr, gz,
+                                            gk, eoff, lo);
+        Real rz[3][N];
+        mv3<TD, true, true>(gz, rz);
+        __syncwarp();  // the stage is consumed
+        if (lane == 0 && en < m.n_elem) stage_issue_elem<LAW, STORAGE>(m, en, stg, bar);
+        col_backward_c<true, true>(m, X0, X1, X2, rz, act, act, eoff, lo, a0, a1, e, out, pol_keep);
     }
-    phase ^= 1u;
-    if (validA) {  // B past the end of the mesh runs on stale stage words and is never scattered
-        const Real *spA = stg + el * NQ + a0 + N * a1;
-        const Real *spB = spA + HE * NQ;
-        Real rA[NR], rB[NR], Gx[6], Gy[6];
-        auto fetch = [&](int k) {
-#pragma unroll
-            for (int f = 0; f < NR; ++f) {
-                rA[f] = spA[f * (EPB * NQ) + NN * k];
-                rB[f] = spB[f * (EPB * NQ) + NN * k];
-            }
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                Gx[c] = X0[eoff + lo.z[k] + c * CZ];
-                Gx[3 + c] = X0[eoff + HB + lo.z[k] + c * CZ];
-                Gy[c] = X2[eoff + lo.z[k] + c * CZ];
-                Gy[3 + c] = X2[eoff + HB + lo.z[k] + c * CZ];
-            }
-        };
-        fetch(0);
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-            Real QA[9], QB[9];
-            if constexpr (STORAGE == HX_SPATIAL_TENSORS && PK) {
-                F2 G2[9], Q2[9];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    G2[c * 3 + 0] = F2(Gx[c], Gx[3 + c]);
-                    G2[c * 3 + 1] = F2(Gy[c], Gy[3 + c]);
-                    G2[c * 3 + 2] = F2(gz[c][k], gz[3 + c][k]);
-                }
-                spatial_Q<F2, LAW>(G2, [&](int f) { return F2(rA[f], rB[f]); }, Q2);
-#pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    QA[i] = Q2[i].v.x;
-                    QB[i] = Q2[i].v.y;
-                }
-            } else {
-                Real GA[9], GB[9];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    GA[c * 3 + 0] = Gx[c];
-                    GA[c * 3 + 1] = Gy[c];
-                    GA[c * 3 + 2] = gz[c][k];
-                    GB[c * 3 + 0] = Gx[3 + c];
-                    GB[c * 3 + 1] = Gy[3 + c];
-                    GB[c * 3 + 2] = gz[3 + c][k];
-                }
-                qp_tangent<LAW, STORAGE>(m, eA, GA, nullptr, rA, QA);
-                qp_tangent<LAW, STORAGE>(m, validB ? eB : eA, GB, nullptr, rB, QB);
-            }
-            if (k + 1 < N) fetch(k + 1);
-            const int pk = eoff + lo.z[k];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                X0[pk + c * CZ] = QA[c * 3 + 0];
-                X2[pk + c * CZ] = QA[c * 3 + 1];
-                X0[pk + HB + c * CZ] = QB[c * 3 + 0];
-                X2[pk + HB + c * CZ] = QB[c * 3 + 1];
-                gz[c][k] = QA[c * 3 + 2];
-                gz[3 + c][k] = QB[c * 3 + 2];
-            }
-        }
-    }
-    Real rz[6][N];
-    mv6<TD, true, true>(gz, gz + 3, rz, rz + 3);
-    __syncthreads();
-    if (t == 0 && ntile >= 0) stage_issue<EPB, LAW, STORAGE>(m, ntile, stg, bar);
-    col_backward_pc<SW, HB>(m, X0, X1, X2, rz, act, validA, validB, eoff, lo, a0, a1, eA, eB, out, pol_keep);
-    return true;
 }
 
 // One tile of the residual R(u) (same structure as apply_tile): the state is
@@ -2268,53 +2051,6 @@ __global__ void __launch_bounds__(apply_threads<STAGED && ROWSW>(EPB)) k_apply(c
         if (!apply_tile<EPB, apply_threads<STAGED && ROWSW>(EPB), LAW, STORAGE, STAGED>(m, tile, ntile < ntiles ? ntile : -1, out, cd,
                                                                     ck, smem_raw, stg, &bar, phase, pol_keep,
                                                                     pol_stream))
-            return;
-    }
-}
-
-// out += K(u_k) du with two elements per thread (staged path, caching
-// strategies): as k_apply with STAGED, but slot el of a tile of EPB elements
-// carries elements el and el + EPB/2, and each thread loads the x-rows of both
-// one tile ahead.
-template <int EPB, int LAW, int STORAGE>
-__global__ void __launch_bounds__(apply_threads<ROWSW>(EPB / 2)) k_apply_pair(const hx::MeshView m,
-                                                                             const Real *__restrict__ du,
-                                                                             Real *__restrict__ out, int ntiles) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bar;
-    constexpr int HE = EPB / 2;
-    const int t = threadIdx.x;
-    int el, a0, a1;
-    bool act;
-    thread_map<ROWSW>(t, HE, el, a0, a1, act);
-    const uint64_t pol_keep = policy_evict_last();
-    using SM = ApplySmem<EPB, LAW, STORAGE, true>;
-    Real *stg = (Real *)(smem_raw + (SM::cube_bytes + 15) / 16 * 16);
-    uint32_t phase = 0;
-    if (t == 0) mbar_init(&bar, 1);
-    __syncthreads();
-    if (t == 0 && (int)blockIdx.x < ntiles) stage_issue<EPB, LAW, STORAGE>(m, blockIdx.x, stg, &bar);
-    Real rowA[3 * N], rowB[3 * N];
-    if (act && (int)blockIdx.x < ntiles) {
-        const int e1 = blockIdx.x * EPB + el;
-        load_row(m, e1, elem_base(m, e1), a0, a1, du, true, rowA);
-        load_row(m, e1 + HE, elem_base(m, e1 + HE), a0, a1, du, true, rowB);
-    }
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int ntile = tile + gridDim.x;
-        Real cA[3 * N], cB[3 * N];
-#pragma unroll
-        for (int i = 0; i < 3 * N; ++i) {
-            cA[i] = rowA[i];
-            cB[i] = rowB[i];
-        }
-        if (act && ntile < ntiles) {
-            const int e1 = ntile * EPB + el;
-            load_row(m, e1, elem_base(m, e1), a0, a1, du, true, rowA);
-            load_row(m, e1 + HE, elem_base(m, e1 + HE), a0, a1, du, true, rowB);
-        }
-        if (!apply_tile_pair<EPB, LAW, STORAGE>(m, tile, ntile < ntiles ? ntile : -1, out, cA, cB, smem_raw, stg,
-                                                &bar, phase, pol_keep))
             return;
     }
 }
