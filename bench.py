@@ -407,6 +407,31 @@ def run_residual_sweep(device, hbm_peak, degrees=(2, 3, 4, 5, 6)):
     return res
 
 
+def run_scatter_modes(device, p=4, steps=50):
+    """The headline apply (32^3 jittered cube, FP32, spatial tensors, the
+    autotuned variant) with the default atomic scatter and with the ordered,
+    bitwise repeatable assembly (element buffer plus ordered node gather)."""
+    import torch
+    from paper_2408_12479_gb300 import hx
+    G, m, u, du, out = build_case(p, hx.HX_FP32, hx.HX_SPATIAL_TENSORS, device)
+    try:
+        res = {"workload": f"cNH tangent apply, 32^3 jittered cube, p={p}, FP32, spatial tensors",
+               "n_dofs": m.n_dofs, "tile_variant": G.tune[0]}
+        for name, mode in (("atomic", hx.HX_SCATTER_ATOMIC), ("ordered", hx.HX_SCATTER_ORDERED)):
+            hx.hx_set_scatter_mode(G.ctx, G.handle, mode)
+            t = _event_ms(lambda: hx.hx_tangent_apply(G.ctx, G.handle, du, out), steps, 3)
+            G.sync(60000)
+            res[name] = {"ms": round(t, 4), "gdofs": round(m.n_dofs / (t * 1e-3) / 1e9, 3)}
+        a = out.clone()
+        hx.hx_tangent_apply(G.ctx, G.handle, du, out)
+        res["ordered_repeats_bitwise"] = bool(torch.equal(a, out))
+        return res
+    finally:
+        G.close()
+        del u, du, out
+        torch.cuda.empty_cache()
+
+
 def run_newton_step_costs(device, p):
     """What each Newton step pays once (Alg. 1): hx_precompute_qp and
     hx_diagonal on the 32^3 jittered cube at degree p, per storage strategy and
@@ -481,9 +506,11 @@ def run_batch(device, steps=20, storage=None):
     return res
 
 
-def run_batch_cg(device, tol=1e-8, max_iter=5000, degree=3, smoothing_range=15.0, storage=None):
+def run_batch_cg(device, tol=1e-8, max_iter=5000, degree=3, smoothing_range=15.0, storage=None, strain=0.01):
     """The 64-cube workload (cNH, n ~ U{8..24}, p ~ U{2..5}, each with its own
-    5 % sine state), every cube clamped on x = 0: one FP64 CG per cube on
+    sine state, here scaled to 1 % strain: at the workload's 5 % most cubes'
+    clamped tangents have negative curvature, so CG cannot run on them), every
+    cube clamped on x = 0: one FP64 CG per cube on
     K_i x_i = rhs_i with an FP32 Chebyshev(degree)-Jacobi preconditioner,
     all cubes in lockstep with one CUDA graph per iteration
     (hx_batch_cg_solve); then the same 64 solves one mesh at a time
@@ -494,12 +521,13 @@ def run_batch_cg(device, tol=1e-8, max_iter=5000, degree=3, smoothing_range=15.0
     st_ = hx.HX_SPATIAL_TENSORS if storage is None else storage
     ctx = hx.hx_create(device)
     meshes, rhss, batch = [], [], None
-    res = {"workload": "64 cNH cubes, n ~ U{8..24}, p ~ U{2..5}, clamped at x=0, FP64 CG, FP32 Chebyshev(%d)-Jacobi, "
-                       "tol %g" % (degree, tol)}
+    res = {"workload": "64 cNH cubes, n ~ U{8..24}, p ~ U{2..5}, %g %% sine states, clamped at x=0, FP64 CG, "
+                       "FP32 Chebyshev(%d)-Jacobi, tol %g" % (100 * strain, degree, tol)}
     try:
         for m, field, seed in I.workload_batch():
             n = m.box[0]
             m.dirichlet = I.box_dirichlet_x0(n, n, n, m.p)
+            field.amp *= strain / 0.05
             G = hx.Mesh(m, dict(I.MAT_CNH), device=device, ctx=ctx)
             X = G.node_coords().cpu().numpy()
             u = torch.tensor(field(X).ravel(), dtype=torch.float64, device=G.device)
@@ -646,7 +674,8 @@ def run_solve_full(device, n=48, p=4, tol=1e-8, max_iter=500, J_target=0.9999, s
     down to the coarse FP64 CG) run in FP32 and, for comparison, in FP64;
     both stop at the same FP64 true-residual ratio. J ~ 0.9999 keeps K
     positive definite (at J ~ 0.9 the pressure makes CG meet negative
-    curvature, see the 16^3 solve report)."""
+    curvature, see the 16^3 solve report). All levels and the outer operator
+    use the spatial-tensor cache."""
     import torch
     from paper_2408_12479_gb300 import hx
     from paper_2408_12479_gb300 import inputs as I
@@ -656,10 +685,10 @@ def run_solve_full(device, n=48, p=4, tol=1e-8, max_iter=500, J_target=0.9999, s
            "n_dofs": m.n_dofs, "tol": tol}
     try:
         u = torch.tensor(field(G.node_coords().cpu().numpy()).ravel(), dtype=torch.float64, device=G.device)
-        G.precompute(u, hx.HX_FP64, hx.HX_CACHE_TENSORS)
+        G.precompute(u, hx.HX_FP64, hx.HX_SPATIAL_TENSORS)
         rhs = -G.residual(u)
         for name, pp in (("hp_mg_fp32", hx.HX_FP32), ("hp_mg_fp64", hx.HX_FP64)):
-            mg = hx.Multigrid(G, smoother_degree=3, precond_prec=pp, storage=hx.HX_CACHE_TENSORS, lambda_iters=20,
+            mg = hx.Multigrid(G, smoother_degree=3, precond_prec=pp, storage=hx.HX_SPATIAL_TENSORS, lambda_iters=20,
                               h_levels=10, coarse_cg_iters=200, coarse_cg_tol=1e-6)
             try:
                 torch.cuda.synchronize()
@@ -1129,7 +1158,7 @@ def main():
         e2e_s = (time.perf_counter() - t0) / k_e2e
         e2e = {"value": round(n_dofs / e2e_s / 1e9, 4), "unit": "GDoF/s", "h2d_bytes_per_step": bytes_vec,
                "d2h_bytes_per_step": bytes_vec, "steps": k_e2e,
-               "path": "hx_tangent_apply_host: pinned du -> device, apply, out -> pinned host"}
+               "path": "hx_tangent_apply_host, pinned host vectors"}
     tune = G.tune
     G.close()
     del u, du, out
@@ -1142,6 +1171,7 @@ def main():
         emit({"report": "sweep", "fma_peaks": peaks_fp, "cases": sweep})
         emit({"report": "residual", "cases": guarded(run_residual_sweep, local, hbm_peak)})
         emit({"report": "newton_step_costs", "cases": guarded(run_newton_step_costs, local, p)})
+        emit({"report": "scatter_modes", **guarded(run_scatter_modes, local, p)})
         emit({"report": "fp32_error", **guarded(run_fp32_errors, local)})
         emit({"report": "law_workloads", "cases": guarded(run_law_workloads, local, hbm_peak)})
         emit({"report": "batch", "cache_F": guarded(run_batch, local, storage=hx.HX_CACHE_F),
@@ -1172,14 +1202,14 @@ def main():
                        "p": p, "n_dofs": n_dofs, "law": "cNH", "prec": args.prec,
                        "storage": hx.STORAGE_NAMES[storage], "applies_per_step": R,
                        "ms_per_apply": round(ms_apply, 5),
-                       "l2": "inputs larger than L2 (vectors + qp data %.0f MB > 129 MB)" % (bytes_alg / 1e6),
+                       "l2": "inputs %.0f MB > L2 129 MB" % (bytes_alg / 1e6),
                        "per_storage_ms": {k: round(v, 4) for k, v in per_storage.items() if v},
                        "tile_variant": tune[0]},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                          "frac": round(achieved / hbm_peak, 4),
                          "traffic": measured_traffic(p, args.prec, hx.STORAGE_NAMES[storage]),
                          "peak_kind": peak_kind, "bytes_per_launch": bytes_alg,
-                         "duration": "CUDA events over the timed steps / applies (output zeroing + k_apply)"},
+                         "duration": "events over the timed steps / applies (zeroing + apply)"},
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk.summary(),
