@@ -546,23 +546,31 @@ def run_batch_cg(device, tol=1e-8, max_iter=5000, degree=3, smoothing_range=15.0
         torch.cuda.synchronize()
         t_batch = time.perf_counter() - t0
         res["n_dofs"] = sum(G.n_dofs for G in meshes)
+        broke = [i for i, r in enumerate(rels) if r != r]
+        ok = [i for i, r in enumerate(rels) if r == r]
         res["batched"] = {"seconds": round(t_batch, 3), "status": hx.STATUS_NAMES.get(st, st),
-                          "iters_min_max": [min(its), max(its)], "max_true_rel_residual": max(rels),
-                          "graph_iterations": max(its)}
+                          "iters_min_max": [min(its), max(its)],
+                          "max_true_rel_residual": max(rels[i] for i in ok) if ok else None,
+                          "graph_iterations": max(its), "breakdowns": [[i, meshes[i].input.name] for i in broke]}
         # one mesh at a time, same preconditioner (the eigenvalue estimate as in the batch)
         t0 = time.perf_counter()
-        its1 = []
+        its1, st1s = [], []
         for G, r in zip(meshes, rhss):
             dinv = 1.0 / G.diagonal(hx.HX_FP64)
             lam = hx.hx_estimate_lambda_max(G.ctx, G.handle, dinv, iters=20, seed=7)
             x = torch.zeros_like(r)
-            it, rel, st1 = hx.hx_cg_solve(G.ctx, G.handle, r, x, tol, max_iter, degree, 1.2 * lam, smoothing_range,
-                                          hx.HX_FP32)
+            try:
+                it, rel, st1 = hx.hx_cg_solve(G.ctx, G.handle, r, x, tol, max_iter, degree, 1.2 * lam,
+                                              smoothing_range, hx.HX_FP32)
+            except hx.HxError as e:
+                it, st1 = -1, e.status
             its1.append(it)
+            st1s.append(st1)
         torch.cuda.synchronize()
         t_seq = time.perf_counter() - t0
         res["one_at_a_time"] = {"seconds": round(t_seq, 3), "iters_min_max": [min(its1), max(its1)],
-                                "iterations_total": sum(its1)}
+                                "iterations_total": sum(i for i in its1 if i > 0),
+                                "breakdowns": [i for i, s_ in enumerate(st1s) if s_ == hx.HX_ERR_NAN]}
         res["speedup_batched"] = round(t_seq / t_batch, 3)
     finally:
         if batch is not None:

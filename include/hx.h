@@ -445,7 +445,8 @@ hx_status hx_batch_tangent_apply(hx_batch *batch, const void *const *du_dev, voi
  * NULL). Every mesh needs caches in FP64 and in precond_prec with one
  * caching strategy. Statuses: HX_ERR_NOT_CONVERGED if some mesh missed tol
  * within max_iter iterations, HX_ERR_NAN on a breakdown (non-positive
- * curvature or NaN) of some mesh. Synchronous; workspace (about 10 FP64 and
+ * curvature or NaN) of some mesh, whose rel_residual entry is then NaN (the
+ * other meshes' results stay valid). Synchronous; workspace (about 10 FP64 and
  * 5 FP32 vectors of the batch's total size) is allocated by the first call
  * and kept by the batch. */
 hx_status hx_batch_cg_solve(hx_batch *batch, const double *const *rhs_dev, double *const *x_dev, double tol,

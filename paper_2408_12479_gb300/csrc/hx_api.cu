@@ -1603,15 +1603,20 @@ hx_status hx_batch_cg_solve(hx_batch *b, const double *const *rhs_dev, double *c
     HX_CUDA(ctx, cudaStreamSynchronize(s));
     ctx->launches += 4;
     int n_bad = 0, n_open = 0;
+    std::string bad_list;
     for (int i = 0; i < nm; ++i) {
-        const double rel = dots[3 * i + 1] > 0.0 ? std::sqrt(dots[3 * i] / dots[3 * i + 1]) : 0.0;
+        double rel = dots[3 * i + 1] > 0.0 ? std::sqrt(dots[3 * i] / dots[3 * i + 1]) : 0.0;
+        if (w.h_sc[i].bad || !(rel == rel)) {
+            rel = std::nan("");
+            if (n_bad++ < 8) bad_list += (bad_list.empty() ? "" : ", ") + std::to_string(i);
+        } else if (rel > tol) {
+            ++n_open;
+        }
         if (iters) iters[i] = w.h_sc[i].iters;
         if (rel_residual) rel_residual[i] = rel;
-        if (w.h_sc[i].bad || !(rel == rel)) ++n_bad;
-        else if (rel > tol) ++n_open;
     }
     if (n_bad) return fail(ctx, HX_ERR_NAN, "hx_batch_cg_solve: CG breakdown (NaN or non-positive curvature) on " +
-                                                std::to_string(n_bad) + " mesh(es)");
+                                                std::to_string(n_bad) + " mesh(es): " + bad_list);
     if (n_open) return fail(ctx, HX_ERR_NOT_CONVERGED, "hx_batch_cg_solve: tolerance not reached on " +
                                                            std::to_string(n_open) + " mesh(es)");
     return HX_OK;

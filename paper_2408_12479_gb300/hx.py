@@ -500,7 +500,8 @@ def hx_batch_tangent_apply(ctx, batch, dus, outs):
 def hx_batch_cg_solve(ctx, batch, rhss, xs, tol, max_iter, degree, smoothing_range, precond_prec, use_graph=True):
     """Batched FP64 CG with a per-mesh Chebyshev-Jacobi preconditioner, all
     meshes in lockstep (one CUDA graph per iteration). Returns (iters list,
-    relative residual list, status); HX_ERR_NOT_CONVERGED is returned, not
+    relative residual list, status); HX_ERR_NOT_CONVERGED and HX_ERR_NAN (a
+    mesh's breakdown: its relative residual is NaN) are returned, not
     raised."""
     n = len(xs)
     a = (C.c_void_p * n)(*[t.data_ptr() for t in rhss])
@@ -509,7 +510,7 @@ def hx_batch_cg_solve(ctx, batch, rhss, xs, tol, max_iter, degree, smoothing_ran
     rel = (C.c_double * n)()
     st = lib().hx_batch_cg_solve(batch, a, b, float(tol), int(max_iter), int(degree), float(smoothing_range),
                                  int(precond_prec), int(bool(use_graph)), it, rel)
-    if st not in (HX_OK, HX_ERR_NOT_CONVERGED):
+    if st not in (HX_OK, HX_ERR_NOT_CONVERGED, HX_ERR_NAN):
         _check(st, ctx)
     return list(it), list(rel), st
 
