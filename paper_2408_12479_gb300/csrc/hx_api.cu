@@ -1347,14 +1347,16 @@ hx_status hx_batch_tangent_apply(hx_batch *b, const void *const *du_dev, void *c
 // ---------------------------------------------------------------------------
 // K_i v_i for every mesh in one launch, from a device array of per-mesh
 // (view, du, out) entries prepared before any capture; constrained rows copied
+// (sc non-null: meshes no longer active are skipped; their role entries carry
+// the same flags)
 static hx_status batch_apply_role(hx_batch *b, const hx::BatchMesh *role, int prec, int storage, const void *du,
-                                  void *out) {
+                                  void *out, const hx::BScal *sc) {
     hx_ctx *ctx = b->ctx;
     const hx::BatchOps *ops = hx::batch_ops(prec);
     const int n = (int)b->meshes.size();
     HX_CUDA(ctx, ops->zero(role, n, ctx->stream));
     HX_CUDA(ctx, ops->apply(b->law, storage, role, b->d_items[prec][storage], b->nitems[prec][storage], ctx->stream));
-    HX_CUDA(ctx, hx::bcopy_idx(n, b->cg.d_seg, du, out, prec, ctx->stream));
+    HX_CUDA(ctx, hx::bcopy_idx(n, b->cg.d_seg, du, out, prec, sc, ctx->stream));
     ctx->launches += 3;
     return HX_OK;
 }
@@ -1465,6 +1467,8 @@ hx_status hx_batch_cg_solve(hx_batch *b, const double *const *rhs_dev, double *c
                 role[i].du = (const char *)du_base + sz * seg[i].off;
                 role[i].out = (char *)out_base + sz * seg[i].off;
                 role[i].n_dofs = seg[i].n;
+                // the iteration's applies skip converged meshes; the residual apply (k = 1) never does
+                role[i].active = k == 1 ? nullptr : &w.d_sc[i].active;
             }
             return cudaMemcpy(w.d_role[k], role.data(), sizeof(hx::BatchMesh) * nm, cudaMemcpyHostToDevice);
         };
@@ -1497,23 +1501,24 @@ hx_status hx_batch_cg_solve(hx_batch *b, const double *const *rhs_dev, double *c
     cudaStream_t s = ctx->stream;
     if (pp == HX_FP32) HX_CUDA(ctx, hx::to_f32(total, dinv, dinv32, s));
 
-    // z = Chebyshev(degree)-Jacobi applied to r, per mesh, in pp
+    // z = Chebyshev(degree)-Jacobi applied to r, per mesh, in pp (meshes no longer active skipped)
+    const hx::BScal *act = w.d_sc;
     auto precond = [&]() -> hx_status {
         for (int k = 0; k < degree; ++k) {
             if (pp == HX_FP32) {
                 if (k > 0) {
-                    hx_status q = batch_apply_role(b, w.d_role[2], HX_FP32, storage, xc32, Kx32);
+                    hx_status q = batch_apply_role(b, w.d_role[2], HX_FP32, storage, xc32, Kx32, act);
                     if (q != HX_OK) return q;
                 }
                 HX_CUDA(ctx, hx::bcheb(nm, max_n, w.d_seg, w.d_coef, degree, k, r32, k ? Kx32 : nullptr, dinv32, d32,
-                                       xc32, HX_FP32, s));
+                                       xc32, HX_FP32, act, s));
             } else {
                 if (k > 0) {
-                    hx_status q = batch_apply_role(b, w.d_role[2], HX_FP64, storage, z, Kx64);
+                    hx_status q = batch_apply_role(b, w.d_role[2], HX_FP64, storage, z, Kx64, act);
                     if (q != HX_OK) return q;
                 }
                 HX_CUDA(ctx, hx::bcheb(nm, max_n, w.d_seg, w.d_coef, degree, k, r, k ? Kx64 : nullptr, dinv, d64, z,
-                                       HX_FP64, s));
+                                       HX_FP64, act, s));
             }
             ctx->launches++;
         }
@@ -1524,10 +1529,16 @@ hx_status hx_batch_cg_solve(hx_batch *b, const double *const *rhs_dev, double *c
         return HX_OK;
     };
 
+    // every mesh active for the first preconditioner application
+    for (int i = 0; i < nm; ++i) {
+        w.h_sc[i] = hx::BScal{};
+        w.h_sc[i].active = 1;
+    }
+    HX_CUDA(ctx, cudaMemcpyAsync(w.d_sc, w.h_sc, sizeof(hx::BScal) * nm, cudaMemcpyHostToDevice, s));
     // r = b - K x; z = M r; p = zold = z
     HX_CUDA(ctx, hx::bcopy(nm, max_n, w.d_seg, xw, 0, s));
     HX_CUDA(ctx, hx::bcopy(nm, max_n, w.d_seg, bw, 2, s));
-    st = batch_apply_role(b, w.d_role[1], HX_FP64, storage, xw, Ap);
+    st = batch_apply_role(b, w.d_role[1], HX_FP64, storage, xw, Ap, nullptr);
     if (st != HX_OK) return st;
     HX_CUDA(ctx, hx::bsub(total, bw, Ap, r, s));
     if (pp == HX_FP32) HX_CUDA(ctx, hx::to_f32(total, r, r32, s));
@@ -1535,19 +1546,20 @@ hx_status hx_batch_cg_solve(hx_batch *b, const double *const *rhs_dev, double *c
     if (st != HX_OK) return st;
     HX_CUDA(ctx, cudaMemcpyAsync(p, z, total * sizeof(double), cudaMemcpyDeviceToDevice, s));
     HX_CUDA(ctx, cudaMemcpyAsync(zold, z, total * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    HX_CUDA(ctx, hx::bdots(nm, w.d_seg, 3, r, z, r, r, bw, bw, w.d_partial, w.d_dots, s));
+    HX_CUDA(ctx, hx::bdots(nm, w.d_seg, 3, r, z, r, r, bw, bw, w.d_partial, w.d_dots, nullptr, s));
     HX_CUDA(ctx, hx::bscal_init(nm, w.d_sc, w.d_dots, tol, s));
     ctx->launches += 8;
 
     auto body = [&]() -> hx_status {
-        hx_status q = batch_apply_role(b, w.d_role[0], HX_FP64, storage, p, Ap);
+        hx_status q = batch_apply_role(b, w.d_role[0], HX_FP64, storage, p, Ap, act);
         if (q != HX_OK) return q;
-        HX_CUDA(ctx, hx::bdots(nm, w.d_seg, 1, p, Ap, nullptr, nullptr, nullptr, nullptr, w.d_partial, w.d_dots, s));
+        HX_CUDA(ctx, hx::bdots(nm, w.d_seg, 1, p, Ap, nullptr, nullptr, nullptr, nullptr, w.d_partial, w.d_dots, act,
+                               s));
         HX_CUDA(ctx, hx::bscal_alpha(nm, w.d_sc, w.d_dots, s));
         HX_CUDA(ctx, hx::bxr(nm, max_n, w.d_seg, w.d_sc, p, Ap, xw, r, pp == HX_FP32 ? r32 : nullptr, s));
         q = precond();
         if (q != HX_OK) return q;
-        HX_CUDA(ctx, hx::bdots(nm, w.d_seg, 3, r, z, r, zold, r, r, w.d_partial, w.d_dots, s));
+        HX_CUDA(ctx, hx::bdots(nm, w.d_seg, 3, r, z, r, zold, r, r, w.d_partial, w.d_dots, act, s));
         HX_CUDA(ctx, hx::bscal_beta(nm, w.d_sc, w.d_dots, s));
         HX_CUDA(ctx, hx::bp(nm, max_n, w.d_seg, w.d_sc, z, p, zold, s));
         HX_CUDA(ctx, cudaMemcpyAsync(w.h_sc, w.d_sc, sizeof(hx::BScal) * nm, cudaMemcpyDeviceToHost, s));
@@ -1592,10 +1604,10 @@ hx_status hx_batch_cg_solve(hx_batch *b, const double *const *rhs_dev, double *c
         HX_CUDA(ctx, cudaStreamSynchronize(s));
     }
     // true residuals; the solutions back to the caller's vectors
-    st = batch_apply_role(b, w.d_role[1], HX_FP64, storage, xw, Ap);
+    st = batch_apply_role(b, w.d_role[1], HX_FP64, storage, xw, Ap, nullptr);
     if (st != HX_OK) return st;
     HX_CUDA(ctx, hx::bsub(total, bw, Ap, r, s));
-    HX_CUDA(ctx, hx::bdots(nm, w.d_seg, 2, r, r, bw, bw, nullptr, nullptr, w.d_partial, w.d_dots, s));
+    HX_CUDA(ctx, hx::bdots(nm, w.d_seg, 2, r, r, bw, bw, nullptr, nullptr, w.d_partial, w.d_dots, nullptr, s));
     HX_CUDA(ctx, hx::bcopy(nm, max_n, w.d_seg, xw, 1, s));
     std::vector<double> dots(3 * (size_t)nm);
     HX_CUDA(ctx, cudaMemcpyAsync(dots.data(), w.d_dots, sizeof(double) * 3 * nm, cudaMemcpyDeviceToHost, s));

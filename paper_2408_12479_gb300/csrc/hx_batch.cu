@@ -82,6 +82,7 @@ __global__ void __launch_bounds__(BT, 2) k_batch_apply(const hx::BatchMesh *__re
     __shared__ __align__(8) uint64_t bar;  // staged items' bulk copies
     if (threadIdx.x == 0) hxb1::mbar_init(&bar, 1);
     uint32_t phase = 0;
+    __shared__ int skip;
     for (int w = blockIdx.x; w < nitems; w += gridDim.x) {
         const int2 it = items[w];
         __syncthreads();  // the previous item is done with mv and the shared arrays
@@ -89,8 +90,10 @@ __global__ void __launch_bounds__(BT, 2) k_batch_apply(const hx::BatchMesh *__re
             mv = meshes[it.x].m;
             sdu = meshes[it.x].du;
             sout = meshes[it.x].out;
+            skip = meshes[it.x].active && !*meshes[it.x].active;
         }
         __syncthreads();
+        if (skip) continue;  // a mesh of the batched CG that has converged
         int r;
         switch (mv.p) {
             case 1: r = hxb1::tile<LAW, STORAGE>(mv, it.y, sdu, sout, smem_raw, &bar, phase); break;
@@ -109,6 +112,7 @@ __global__ void __launch_bounds__(BT, 2) k_batch_apply(const hx::BatchMesh *__re
 __global__ void k_batch_zero(const hx::BatchMesh *__restrict__ meshes, int nmesh) {
     const int i = blockIdx.y;
     if (i >= nmesh) return;
+    if (meshes[i].active && !*meshes[i].active) return;
     Real *o = (Real *)meshes[i].out;
     const int64_t n = meshes[i].n_dofs;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)

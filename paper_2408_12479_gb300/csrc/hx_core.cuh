@@ -1112,25 +1112,10 @@ __device__ __forceinline__ void red_add(double *p, double v, uint64_t pol) {
 }
 
 
-// One FP32 load that the compiler keeps where it is written (a volatile asm
-// with a memory clobber is not moved across other memory operations): the
-// x-rows of the next element are requested a whole element ahead.
-__device__ __forceinline__ float ld_pinned(const float *p) {
-    float v;
-    asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ double ld_pinned(const double *p) {
-    double v;
-    asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p) : "memory");
-    return v;
-}
-
 // Load the x-row (j = a0, k = a1) of element e of vector v into registers:
 // row[3*i + c] = v_c at node (i, a0, a1). In a structured box the row is 3*N
 // contiguous values; otherwise the N node ids come from the connectivity.
 // Constrained DoFs (mask) and elements past the end read zero.
-template <bool PIN = false>
 __device__ __forceinline__ void load_row(const hx::MeshView &m, int e, int64_t base, int a0, int a1,
                                          const Real *__restrict__ v, bool mask, Real *row) {
     if (e >= m.n_elem) {
@@ -1142,7 +1127,7 @@ __device__ __forceinline__ void load_row(const hx::MeshView &m, int e, int64_t b
         const int64_t off = 3 * (base + m.Nx * (a0 + m.Ny * (int64_t)a1));
         const Real *p = v + off;
 #pragma unroll
-        for (int t = 0; t < 3 * N; ++t) row[t] = PIN ? ld_pinned(p + t) : p[t];
+        for (int t = 0; t < 3 * N; ++t) row[t] = p[t];
         if (mask && m.dmask) {
             const uint8_t *q = m.dmask + off;
 #pragma unroll
@@ -1843,9 +1828,8 @@ __device__ __forceinline__ void stage_issue_elem(const hx::MeshView &m, int e, R
 // out += K(u_k) du, one warp per element with its own stage (caching
 // strategies). Warp w of a CTA takes element tile*EPB + w of each of the
 // CTA's tiles; its lane 0 issues the copies of the warp's next element as
-// soon as the warp has consumed its stage. PIN: the next element's x-rows are
-// loaded with pinned loads (ld_pinned) at the top of the current one.
-template <int EPB, int LAW, int STORAGE, bool PIN>
+// soon as the warp has consumed its stage.
+template <int EPB, int LAW, int STORAGE>
 __global__ void __launch_bounds__(EPB * 32) k_apply_wd(const hx::MeshView m, const Real *__restrict__ du,
                                                        Real *__restrict__ out, int ntiles) {
     static_assert(ROWSW && STORAGE != HX_RECOMPUTE, "one warp per element, caching strategies");
@@ -1873,14 +1857,14 @@ __global__ void __launch_bounds__(EPB * 32) k_apply_wd(const hx::MeshView m, con
     int e = blockIdx.x * EPB + el;
     if (lane == 0 && (int)blockIdx.x < ntiles && e < m.n_elem) stage_issue_elem<LAW, STORAGE>(m, e, stg, bar);
     Real row[3 * N];
-    if (act) load_row<PIN>(m, e, elem_base(m, e), a0, a1, du, true, row);
+    if (act) load_row(m, e, elem_base(m, e), a0, a1, du, true, row);
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, e += stride) {
         if (e >= m.n_elem) break;  // warp-uniform; later tiles lie further out
         const int en = e + stride;
         Real cd[3 * N];
 #pragma unroll
         for (int i = 0; i < 3 * N; ++i) cd[i] = row[i];
-        if (act) load_row<PIN>(m, en, elem_base(m, en), a0, a1, du, true, row);  // zeros past the end
+        if (act) load_row(m, en, elem_base(m, en), a0, a1, du, true, row);  // zeros past the end
         Real gz[3][N], gk[1][N];
         col_forward_c<true, true>(cd, X0, X1, X2, gz, act, eoff, lo);
         const bool ok = mbar_wait(bar, phase, m.wait_limit);

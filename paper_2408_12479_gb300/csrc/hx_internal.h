@@ -106,6 +106,7 @@ struct BatchMesh {
     const void *du;
     void *out;
     int64_t n_dofs;
+    const int *active;  // non-null: the mesh is skipped while *active == 0 (batched CG)
 };
 
 // Entry points of the batch unit of one precision (hx_batch.cu).

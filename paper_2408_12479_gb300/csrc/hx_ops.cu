@@ -90,12 +90,12 @@ cudaError_t launch_apply_t(const hx::MeshView &m, const void *du, void *out, cud
 
 // Warp-decoupled staged apply (k_apply_wd): one warp per element with its own
 // stage; FP32 at n = 5 and the caching strategies only.
-template <int EPB, int LAW, int STORAGE, bool PIN>
+template <int EPB, int LAW, int STORAGE>
 cudaError_t launch_apply_wd_t(const hx::MeshView &m, const void *du, void *out, cudaStream_t s) {
     if constexpr (!ROWSW || STORAGE == HX_RECOMPUTE) {
         return cudaErrorInvalidConfiguration;
     } else {
-        auto kern = k_apply_wd<EPB, LAW, STORAGE, PIN>;
+        auto kern = k_apply_wd<EPB, LAW, STORAGE>;
         constexpr size_t smem = ((size_t)3 * EPB * Lay<true>::ES * sizeof(Real) + 15) / 16 * 16 +
                                 (size_t)EPB * QpFields<LAW, STORAGE>::n * WIN * sizeof(Real);
         constexpr int NTH = EPB * 32;
@@ -120,8 +120,7 @@ cudaError_t launch_apply_wd_t(const hx::MeshView &m, const void *du, void *out, 
 // register prefetch one point ahead with an L2 bulk prefetch of the next tile
 // (0: default, 1: half elements per CTA), bulk copies into a shared stage one
 // tile ahead (3: default, 4: half), and the warp-decoupled staged apply with a
-// stage per warp (2; 5: the same with the next rows' loads pinned in place,
-// see ld_pinned; both with half elements per CTA). Staged variants are
+// stage per warp (2: half, 5: default elements per CTA). Staged variants are
 // not built where a tile's chunk is not a multiple of 16 bytes; the
 // warp-decoupled ones only where one warp holds one element (FP32, p = 4) and
 // not for the recompute strategy.
@@ -132,10 +131,10 @@ cudaError_t apply_variant(const hx::MeshView &m0, const void *du, void *out, cud
     constexpr int EH = EPB_A > 1 ? EPB_A / 2 : 1;
     switch (variant) {
         case 1: return launch_apply_t<EH, LAW, STORAGE, false>(m, du, out, s);
-        case 2: return launch_apply_wd_t<EH, LAW, STORAGE, false>(m, du, out, s);
+        case 2: return launch_apply_wd_t<EH, LAW, STORAGE>(m, du, out, s);
         case 3: return launch_apply_t<EPB_A, LAW, STORAGE, true>(m, du, out, s);
         case 4: return launch_apply_t<EH, LAW, STORAGE, true>(m, du, out, s);
-        case 5: return launch_apply_wd_t<EH, LAW, STORAGE, true>(m, du, out, s);
+        case 5: return launch_apply_wd_t<EPB_A, LAW, STORAGE>(m, du, out, s);
         default: return launch_apply_t<EPB_A, LAW, STORAGE, false>(m, du, out, s);
     }
 }

@@ -228,9 +228,10 @@ __global__ void __launch_bounds__(CB) k_coarse_pcg(int n, const double *__restri
 // ---- batched CG kernels ------------------------------------------------------
 template <int K>
 __global__ void k_bdots(const BSeg *__restrict__ seg, const double *a0, const double *b0, const double *a1,
-                        const double *b1, const double *a2, const double *b2, double *partial) {
+                        const double *b1, const double *a2, const double *b2, double *partial, const BScal *sc) {
     __shared__ double sh[3][VB];
     const int i = blockIdx.y;
+    if (sc && !sc[i].active) return;  // block-uniform
     const int64_t off = seg[i].off, n = seg[i].n;
     double s[3] = {0, 0, 0};
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
@@ -248,8 +249,9 @@ __global__ void k_bdots(const BSeg *__restrict__ seg, const double *a0, const do
     if (threadIdx.x < 3) partial[((int64_t)i * BRB + blockIdx.x) * 3 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
-__global__ void k_bdots_final(const double *__restrict__ partial, double *__restrict__ dots) {
+__global__ void k_bdots_final(const double *__restrict__ partial, double *__restrict__ dots, const BScal *sc) {
     const int i = blockIdx.x;
+    if (sc && !sc[i].active) return;
     if (threadIdx.x < 3) {
         double t = 0.0;
         for (int b = 0; b < BRB; ++b) t += partial[((int64_t)i * BRB + b) * 3 + threadIdx.x];
@@ -271,8 +273,10 @@ __global__ void k_bcopy(const BSeg *__restrict__ seg, double *__restrict__ y, in
 }
 
 template <typename T>
-__global__ void k_bcopy_idx(const BSeg *__restrict__ seg, const T *__restrict__ du, T *__restrict__ out) {
+__global__ void k_bcopy_idx(const BSeg *__restrict__ seg, const T *__restrict__ du, T *__restrict__ out,
+                            const BScal *sc) {
     const int i = blockIdx.y;
+    if (sc && !sc[i].active) return;
     const int64_t off = seg[i].off, n = seg[i].ncon;
     const int64_t *ci = seg[i].cidx;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
@@ -313,6 +317,7 @@ __global__ void k_bxr(const BSeg *__restrict__ seg, const BScal *__restrict__ sc
                       const double *__restrict__ Ap, double *__restrict__ x, double *__restrict__ r,
                       float *__restrict__ r32) {
     const int i = blockIdx.y;
+    if (!sc[i].active) return;  // alpha is 0 for a mesh that is not active
     const int64_t off = seg[i].off, n = seg[i].n;
     const double a = sc[i].alpha;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
@@ -350,6 +355,7 @@ __global__ void k_bscal_beta(int nm, BScal *sc, const double *dots) {
 __global__ void k_bp(const BSeg *__restrict__ seg, const BScal *__restrict__ sc, const double *__restrict__ z,
                      double *__restrict__ p, double *__restrict__ zold) {
     const int i = blockIdx.y;
+    if (!sc[i].active) return;
     const int64_t off = seg[i].off, n = seg[i].n;
     const double b = sc[i].beta;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
@@ -363,8 +369,9 @@ __global__ void k_bp(const BSeg *__restrict__ seg, const BScal *__restrict__ sc,
 template <typename T>
 __global__ void k_bcheb(const BSeg *__restrict__ seg, const double *__restrict__ coef, int degree, int step,
                         const T *__restrict__ rhs, const T *__restrict__ Kx, const T *__restrict__ dinv, T *__restrict__ d,
-                        T *__restrict__ x) {
+                        T *__restrict__ x, const BScal *sc) {
     const int i = blockIdx.y;
+    if (sc && !sc[i].active) return;
     const int64_t off = seg[i].off, n = seg[i].n;
     const T cd = (T)coef[((int64_t)i * degree + step) * 2 + 0];
     const T cr = (T)coef[((int64_t)i * degree + step) * 2 + 1];
@@ -545,16 +552,17 @@ inline dim3 bgrid(int64_t max_n, int nm) {
 }
 
 cudaError_t bdots(int nm, const BSeg *seg, int k, const double *a0, const double *b0, const double *a1,
-                  const double *b1, const double *a2, const double *b2, double *partial, double *dots, cudaStream_t s) {
+                  const double *b1, const double *a2, const double *b2, double *partial, double *dots,
+                  const BScal *sc, cudaStream_t s) {
     if (nm == 0) return cudaSuccess;
     const dim3 g(BRB, nm);
     if (k == 1)
-        k_bdots<1><<<g, VB, 0, s>>>(seg, a0, b0, a1, b1, a2, b2, partial);
+        k_bdots<1><<<g, VB, 0, s>>>(seg, a0, b0, a1, b1, a2, b2, partial, sc);
     else if (k == 2)
-        k_bdots<2><<<g, VB, 0, s>>>(seg, a0, b0, a1, b1, a2, b2, partial);
+        k_bdots<2><<<g, VB, 0, s>>>(seg, a0, b0, a1, b1, a2, b2, partial, sc);
     else
-        k_bdots<3><<<g, VB, 0, s>>>(seg, a0, b0, a1, b1, a2, b2, partial);
-    k_bdots_final<<<nm, 32, 0, s>>>(partial, dots);
+        k_bdots<3><<<g, VB, 0, s>>>(seg, a0, b0, a1, b1, a2, b2, partial, sc);
+    k_bdots_final<<<nm, 32, 0, s>>>(partial, dots, sc);
     return cudaGetLastError();
 }
 cudaError_t bcopy(int nm, int64_t max_n, const BSeg *seg, double *y, int dir, cudaStream_t s) {
@@ -562,12 +570,12 @@ cudaError_t bcopy(int nm, int64_t max_n, const BSeg *seg, double *y, int dir, cu
     k_bcopy<<<bgrid(max_n, nm), VB, 0, s>>>(seg, y, dir);
     return cudaGetLastError();
 }
-cudaError_t bcopy_idx(int nm, const BSeg *seg, const void *du, void *out, int prec, cudaStream_t s) {
+cudaError_t bcopy_idx(int nm, const BSeg *seg, const void *du, void *out, int prec, const BScal *sc, cudaStream_t s) {
     if (nm == 0) return cudaSuccess;
     if (prec == HX_FP64)
-        k_bcopy_idx<double><<<dim3(16, nm), VB, 0, s>>>(seg, (const double *)du, (double *)out);
+        k_bcopy_idx<double><<<dim3(16, nm), VB, 0, s>>>(seg, (const double *)du, (double *)out, sc);
     else
-        k_bcopy_idx<float><<<dim3(16, nm), VB, 0, s>>>(seg, (const float *)du, (float *)out);
+        k_bcopy_idx<float><<<dim3(16, nm), VB, 0, s>>>(seg, (const float *)du, (float *)out, sc);
     return cudaGetLastError();
 }
 cudaError_t bsub(int64_t n, const double *a, const double *b, double *y, cudaStream_t s) { return sub(n, a, b, y, s); }
@@ -594,14 +602,15 @@ cudaError_t bp(int nm, int64_t max_n, const BSeg *seg, const BScal *sc, const do
     return cudaGetLastError();
 }
 cudaError_t bcheb(int nm, int64_t max_n, const BSeg *seg, const double *coef, int degree, int step, const void *rhs,
-                  const void *Kx, const void *dinv, void *d, void *x, int prec, cudaStream_t s) {
+                  const void *Kx, const void *dinv, void *d, void *x, int prec, const BScal *sc, cudaStream_t s) {
     if (prec == HX_FP64)
         k_bcheb<double><<<bgrid(max_n, nm), VB, 0, s>>>(seg, coef, degree, step, (const double *)rhs,
                                                          (const double *)Kx, (const double *)dinv, (double *)d,
-                                                         (double *)x);
+                                                         (double *)x, sc);
     else
         k_bcheb<float><<<bgrid(max_n, nm), VB, 0, s>>>(seg, coef, degree, step, (const float *)rhs,
-                                                        (const float *)Kx, (const float *)dinv, (float *)d, (float *)x);
+                                                        (const float *)Kx, (const float *)dinv, (float *)d, (float *)x,
+                                                        sc);
     return cudaGetLastError();
 }
 

@@ -93,12 +93,14 @@ struct BScal {
 };
 constexpr int BRB = 64;  // reduction blocks per mesh (fixed: repeatable sums)
 // dots[3 i + j] = a_j . b_j over mesh i's segment, j < k (k <= 3)
+// (sc non-null: meshes that are no longer active are skipped, here and below)
 cudaError_t bdots(int nm, const BSeg *seg, int k, const double *a0, const double *b0, const double *a1,
-                  const double *b1, const double *a2, const double *b2, double *partial, double *dots, cudaStream_t s);
+                  const double *b1, const double *a2, const double *b2, double *partial, double *dots,
+                  const BScal *sc, cudaStream_t s);
 // y = x_i (gather, dir 0) or x_i = y (scatter, dir 1) / y = rhs_i (dir 2)
 cudaError_t bcopy(int nm, int64_t max_n, const BSeg *seg, double *y, int dir, cudaStream_t s);
 // out[cidx] = du[cidx] on every mesh's constrained DoFs (identity rows)
-cudaError_t bcopy_idx(int nm, const BSeg *seg, const void *du, void *out, int prec, cudaStream_t s);
+cudaError_t bcopy_idx(int nm, const BSeg *seg, const void *du, void *out, int prec, const BScal *sc, cudaStream_t s);
 // y = a - b over the concatenation
 cudaError_t bsub(int64_t n, const double *a, const double *b, double *y, cudaStream_t s);
 // scalars after the initial residual: rz = dots[0], rr = dots[1], bb = dots[2]
@@ -114,7 +116,7 @@ cudaError_t bp(int nm, int64_t max_n, const BSeg *seg, const BScal *sc, const do
 // Chebyshev step `step` of the per-mesh coefficients coef[(i * degree + step) * 2 + {cd, cr}]:
 // r = dinv (rhs - Kx) (Kx null: dinv rhs), d = cd d + cr r (step 0: cr r), x += d (step 0 with Kx null: x = d)
 cudaError_t bcheb(int nm, int64_t max_n, const BSeg *seg, const double *coef, int degree, int step, const void *rhs,
-                  const void *Kx, const void *dinv, void *d, void *x, int prec, cudaStream_t s);
+                  const void *Kx, const void *dinv, void *d, void *x, int prec, const BScal *sc, cudaStream_t s);
 
 // Ordered assembly (deterministic scatter): E holds every element's local
 // vector, E[3 (e NQ + a) + c] for local node a = i + n (j + n k), n = p + 1.
