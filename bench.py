@@ -506,8 +506,9 @@ def run_batch(device, steps=20, storage=None):
     return res
 
 
-def run_batch_cg(device, tol=1e-8, max_iter=5000, degree=3, smoothing_range=15.0, storage=None, strain=0.002):
-    """The 64-cube workload (cNH, n ~ U{8..24}, p ~ U{2..5}, each with its own
+def run_batch_cg(device, n_meshes=64, tol=1e-8, max_iter=5000, degree=3, smoothing_range=15.0, storage=None,
+                 strain=0.002):
+    """The first n_meshes cubes of the 64-cube workload (cNH, n ~ U{8..24}, p ~ U{2..5}, each with its own
     sine state, here scaled to 0.2 % strain: clamped on x = 0, the finest cubes'
     tangents meet negative curvature at 1 % (and most cubes' at the workload's
     5 %), where CG cannot run; the single-mesh CG reports the same meshes),
@@ -522,10 +523,10 @@ def run_batch_cg(device, tol=1e-8, max_iter=5000, degree=3, smoothing_range=15.0
     st_ = hx.HX_SPATIAL_TENSORS if storage is None else storage
     ctx = hx.hx_create(device)
     meshes, rhss, batch = [], [], None
-    res = {"workload": "64 cNH cubes, n ~ U{8..24}, p ~ U{2..5}, %g %% sine states, clamped at x=0, FP64 CG, "
-                       "FP32 Chebyshev(%d)-Jacobi, tol %g" % (100 * strain, degree, tol)}
+    res = {"workload": "%d of the 64 cNH cubes, n ~ U{8..24}, p ~ U{2..5}, %g %% sine states, clamped at x=0, "
+                       "FP64 CG, FP32 Chebyshev(%d)-Jacobi, tol %g" % (n_meshes, 100 * strain, degree, tol)}
     try:
-        for m, field, seed in I.workload_batch():
+        for m, field, seed in I.workload_batch(n_meshes):
             n = m.box[0]
             m.dirichlet = I.box_dirichlet_x0(n, n, n, m.p)
             field.amp *= strain / 0.05
@@ -1070,6 +1071,8 @@ def main():
                     help="pin the apply variant (0-5) instead of the autotuner's (profiling commands)")
     ap.add_argument("--solve-full", type=int, default=48,
                     help="the compressed-cube solve at full size with the hp-multigrid preconditioner (n given; 0: off)")
+    ap.add_argument("--batch-cg", type=int, default=16,
+                    help="batched CG over the first n cubes of the 64-cube workload, and one at a time (0: off)")
     ap.add_argument("--solve", type=int, default=16,
                     help="also run the FP32- vs FP64-preconditioned CG solve on an n^3 compressed cube (n given)")
     args = ap.parse_args()
@@ -1189,7 +1192,8 @@ def main():
         emit({"report": "law_workloads", "cases": guarded(run_law_workloads, local, hbm_peak)})
         emit({"report": "batch", "cache_F": guarded(run_batch, local, storage=hx.HX_CACHE_F),
               "spatial_tensors": guarded(run_batch, local, storage=hx.HX_SPATIAL_TENSORS)})
-        emit({"report": "batch_cg", **guarded(run_batch_cg, local)})
+        if args.batch_cg:
+            emit({"report": "batch_cg", **guarded(run_batch_cg, local, n_meshes=args.batch_cg)})
         if args.solve:
             emit({"report": "solve", **guarded(run_solve, local, n=args.solve)})
         if args.solve_full:

@@ -191,8 +191,9 @@ hx_status hx_tangent_apply_host(hx_mesh *mesh, const void *du_host, void *out_ho
  *   3, 4: bulk copies into shared memory one tile ahead, quadrature points
  *         taken in column order (default tile, half tile);
  *   2, 5: as 3/4 with a stage and an mbarrier per warp, where one warp
- *         holds one element (FP32, p = 4; caching strategies): no phase
- *         waits for more than its own warp (half tile, default tile).
+ *         holds whole elements (FP32, p <= 4: 32 / (p+1)^2 elements per
+ *         warp below p = 4, one at p = 4; caching strategies): no phase
+ *         waits for more than its own warp (small and large CTAs).
  * Returns the fastest index and the six mean times in ms (a variant that
  * cannot launch, e.g. a staged tile whose chunks would not be 16-byte aligned
  * or would not fit in shared memory, reports a negative time). Uses

@@ -302,7 +302,7 @@ size_t prec_size(int prec) { return prec == HX_FP64 ? 8 : 4; }
 
 template <typename T>
 cudaError_t dalloc(T **p, size_t n) {
-    return cudaMalloc((void **)p, n * sizeof(T) + 64);  // slack: bulk copies round up to 16 bytes
+    return cudaMalloc((void **)p, n * sizeof(T) + HX_ARRAY_SLACK);  // bulk-copy windows may reach past the end
 }
 
 void dfree(void *p) {
@@ -624,7 +624,7 @@ hx_status hx_precompute_qp(hx_mesh *m, const double *u_dev, int32_t store_prec, 
         dfree(c.buf);
         c.buf = nullptr;
         c.bytes = 0;
-        HX_CUDA(ctx, cudaMalloc(&c.buf, bytes + 64));  // slack: bulk copies round up to 16 bytes
+        HX_CUDA(ctx, cudaMalloc(&c.buf, bytes + HX_ARRAY_SLACK));  // bulk-copy windows may reach past the end
         c.bytes = bytes;
     }
     c.storage = storage;

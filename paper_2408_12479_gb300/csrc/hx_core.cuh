@@ -1794,79 +1794,102 @@ __device__ __forceinline__ bool apply_tile(const hx::MeshView &m, int tile, int 
 }
 
 // ---------------------------------------------------------------------------
-// Warp-decoupled staged apply (variants 2 and 5, FP32 at n = 5, where one
-// warp owns one element): every warp has its own stage and mbarrier, so no
-// phase needs more than a warp barrier and the warps of a CTA drift freely.
-// An element's 125-point chunk of a field is 500 bytes and starts 4 (e mod 4)
-// bytes past a 16-byte boundary, so the warp copies the 512-byte aligned
-// window around it (the neighbours' edge words come along unused; they lie
-// in sectors the neighbouring element reads anyway) and reads from word
-// e mod 4 of the window.
+// Warp-decoupled staged apply (variants 2 and 5, FP32 up to n = 5): every warp
+// owns a group of WEPW whole elements (one row-swizzled element at n = 5;
+// 32 / n^2 column-layout elements below) with its own stage and mbarrier, so
+// no phase needs more than a warp barrier and the warps of a CTA drift
+// freely. A group's chunk of a field (WEPW * NQ words) need not start on a
+// 16-byte boundary, so the warp copies the window of WWIN words that starts
+// at the chunk's first word rounded down to a multiple of 4 (the neighbours'
+// edge words come along unused; they lie in sectors the neighbouring group
+// reads anyway) and reads from word (first word mod 4) of the window.
 // ---------------------------------------------------------------------------
-constexpr int WIN = 128;  // words of one field's window in a warp's stage
+constexpr int WEPW = ROWSW ? 1 : (NN <= 32 ? 32 / NN : 0);  // elements per warp (0: not built)
+constexpr int WCH = WEPW * NQ;                              // words of a group's chunk of one field
+constexpr int WWIN = WCH % 4 == 0 ? WCH : (WCH + 6) / 4 * 4;  // window words: covers a shift of up to 3
+constexpr bool WD_OK = sizeof(Real) == 4 && WEPW > 0;
+// A window reaches at most WWIN - NQ words past the last element's points;
+// the point arrays carry HX_ARRAY_SLACK bytes after their last field.
+static_assert(!WD_OK || (WWIN - NQ) * 4 <= HX_ARRAY_SLACK, "stage windows would leave the point arrays");
 
-// Lane 0 of element e's warp: the bulk copies of e's point fields into the
-// warp's stage (one 512-byte window per field), on the warp's mbarrier. The
-// windows stay inside the arrays (64 bytes of slack after the last field).
+// Lane 0 of group g's warp: the bulk copies of the group's point fields into
+// the warp's stage (one WWIN-word window per field), on the warp's mbarrier.
 template <int LAW, int STORAGE>
-__device__ __forceinline__ void stage_issue_elem(const hx::MeshView &m, int e, Real *stg, uint64_t *bar) {
+__device__ __forceinline__ void stage_issue_group(const hx::MeshView &m, int g, Real *stg, uint64_t *bar) {
     using QF = QpFields<LAW, STORAGE>;
-    static_assert(LAW >= 0 && NQ == 125 && sizeof(Real) == 4, "the window layout is that of FP32 elements of 125 points");
+    static_assert(LAW >= 0 && WD_OK, "the window layout is that of FP32 groups of whole elements in one warp");
     if (m.skip_stage_copies) return;  // test hook: the stage never fills and the wait runs out
     const uint64_t pol = policy_evict_first();
-    const int64_t w0 = (int64_t)e * NQ - (e & 3);  // first word of the window: a multiple of 4
+    const int64_t c0 = (int64_t)g * WCH;
+    const int64_t w0 = c0 - (c0 & 3);  // first word of the window: a multiple of 4
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(bar, QF::n * WIN * 4);
+    mbar_expect_tx(bar, QF::n * WWIN * 4);
 #pragma unroll 1
     for (int f = 0; f < QF::n; ++f) {
         const Real *src = f < QF::ng ? (const Real *)m.geo + (int64_t)f * m.qs + w0
                                      : (const Real *)m.qp + (int64_t)(f - QF::ng) * m.qs + w0;
-        bulk_g2s(stg + f * WIN, src, WIN * 4, bar, pol);
+        bulk_g2s(stg + f * WWIN, src, WWIN * 4, bar, pol);
     }
 }
 
-// out += K(u_k) du, one warp per element with its own stage (caching
-// strategies). Warp w of a CTA takes element tile*EPB + w of each of the
-// CTA's tiles; its lane 0 issues the copies of the warp's next element as
-// soon as the warp has consumed its stage.
-template <int EPB, int LAW, int STORAGE>
-__global__ void __launch_bounds__(EPB * 32) k_apply_wd(const hx::MeshView m, const Real *__restrict__ du,
-                                                       Real *__restrict__ out, int ntiles) {
-    static_assert(ROWSW && STORAGE != HX_RECOMPUTE, "one warp per element, caching strategies");
+// Shared-memory bytes of a CTA of W warps: the cubes of its W * WEPW elements,
+// then the W stages.
+template <int W, int LAW, int STORAGE>
+__host__ __device__ constexpr size_t wd_cubes_bytes() {
+    return ((size_t)3 * W * WEPW * Lay<ROWSW>::ES * sizeof(Real) + 15) / 16 * 16;
+}
+template <int W, int LAW, int STORAGE>
+__host__ __device__ constexpr size_t wd_smem_bytes() {
+    return wd_cubes_bytes<W, LAW, STORAGE>() + (size_t)W * QpFields<LAW, STORAGE>::n * WWIN * sizeof(Real);
+}
+
+// out += K(u_k) du, one group of WEPW elements per warp with its own stage
+// (caching strategies). Warp w of a CTA takes group tile*W + w of each of the
+// CTA's tiles (elements g*WEPW .. g*WEPW + WEPW - 1); its lane 0 issues the
+// copies of the warp's next group as soon as the warp has consumed its stage.
+template <int W, int LAW, int STORAGE>
+__global__ void __launch_bounds__(W * 32) k_apply_wd(const hx::MeshView m, const Real *__restrict__ du,
+                                                     Real *__restrict__ out, int ntiles) {
+    static_assert(WD_OK && STORAGE != HX_RECOMPUTE, "FP32 groups of whole elements per warp, caching strategies");
+    constexpr bool SW = ROWSW;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bars[EPB];
+    __shared__ __align__(8) uint64_t bars[W];
     using QF = QpFields<LAW, STORAGE>;
-    constexpr int ES = Lay<true>::ES;
+    constexpr int ES = Lay<SW>::ES;
     const int t = threadIdx.x;
-    int el, a0, a1;
-    bool act;
-    thread_map<true>(t, EPB, el, a0, a1, act);
-    const int lane = t & 31;
-    const int eoff = el * ES;
+    const int wid = t >> 5, lane = t & 31;
+    const int sub = lane / NN;  // element of the group
+    const bool act = sub < WEPW;
+    const int a = act ? lane - sub * NN : 0;
+    const int a0 = a % N, a1 = a / N;
+    const int eoff = (wid * WEPW + (act ? sub : 0)) * ES;
     Real *X0 = (Real *)smem_raw;
-    Real *X1 = X0 + EPB * ES;
-    Real *X2 = X1 + EPB * ES;
-    Real *stg = (Real *)(smem_raw + ((size_t)3 * EPB * ES * sizeof(Real) + 15) / 16 * 16) + el * (QF::n * WIN);
-    uint64_t *bar = &bars[el];
+    Real *X1 = X0 + W * WEPW * ES;
+    Real *X2 = X1 + W * WEPW * ES;
+    Real *stg = (Real *)(smem_raw + wd_cubes_bytes<W, LAW, STORAGE>()) + wid * (QF::n * WWIN);
+    uint64_t *bar = &bars[wid];
     const uint64_t pol_keep = policy_evict_last();
-    const LineOffs<true> lo = line_offsets<true>(a0, a1);
+    const LineOffs<SW> lo = line_offsets<SW>(a0, a1);
     uint32_t phase = 0;
     if (lane == 0) mbar_init(bar, 1);
     __syncwarp();
-    const int stride = gridDim.x * EPB;
-    int e = blockIdx.x * EPB + el;
-    if (lane == 0 && (int)blockIdx.x < ntiles && e < m.n_elem) stage_issue_elem<LAW, STORAGE>(m, e, stg, bar);
+    const int stride = gridDim.x * W;  // groups
+    int g = blockIdx.x * W + wid;
+    int e = g * WEPW + sub;
+    if (lane == 0 && (int)blockIdx.x < ntiles && g * WEPW < m.n_elem) stage_issue_group<LAW, STORAGE>(m, g, stg, bar);
     Real row[3 * N];
-    if (act) load_row(m, e, elem_base(m, e), a0, a1, du, true, row);
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, e += stride) {
-        if (e >= m.n_elem) break;  // warp-uniform; later tiles lie further out
-        const int en = e + stride;
+    if (act) load_row(m, e, elem_base(m, e), a0, a1, du, true, row);  // zeros past the end
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, g += stride, e += stride * WEPW) {
+        if (g * WEPW >= m.n_elem) break;  // warp-uniform; later tiles lie further out
+        const bool valid = act && e < m.n_elem;
+        const int gn = g + stride;
+        const int en = e + stride * WEPW;
         Real cd[3 * N];
 #pragma unroll
         for (int i = 0; i < 3 * N; ++i) cd[i] = row[i];
-        if (act) load_row(m, en, elem_base(m, en), a0, a1, du, true, row);  // zeros past the end
+        if (act) load_row(m, en, elem_base(m, en), a0, a1, du, true, row);
         Real gz[3][N], gk[1][N];
-        col_forward_c<true, true>(cd, X0, X1, X2, gz, act, eoff, lo);
+        col_forward_c<SW, true>(cd, X0, X1, X2, gz, act, eoff, lo);
         const bool ok = mbar_wait(bar, phase, m.wait_limit);
         if (__any_sync(0xffffffffu, !ok)) {
             if (lane == 0) {
@@ -1877,13 +1900,13 @@ __global__ void __launch_bounds__(EPB * 32) k_apply_wd(const hx::MeshView m, con
         }
         __syncwarp();  // completes the forward sweeps
         phase ^= 1u;
-        qp_columns<LAW, STORAGE, WIN, true>(m, e, act, stg + (e & 3) + a0 + N * a1, X0, X2, nullptr, nullptr, gz,
-                                            gk, eoff, lo);
+        qp_columns<LAW, STORAGE, WWIN, SW>(m, e, valid, stg + (int)(((int64_t)g * WCH) & 3) + sub * NQ + a0 + N * a1,
+                                           X0, X2, nullptr, nullptr, gz, gk, eoff, lo);
         Real rz[3][N];
         mv3<TD, true, true>(gz, rz);
         __syncwarp();  // the stage is consumed
-        if (lane == 0 && en < m.n_elem) stage_issue_elem<LAW, STORAGE>(m, en, stg, bar);
-        col_backward_c<true, true>(m, X0, X1, X2, rz, act, act, eoff, lo, a0, a1, e, out, pol_keep);
+        if (lane == 0 && gn * WEPW < m.n_elem) stage_issue_group<LAW, STORAGE>(m, gn, stg, bar);
+        col_backward_c<SW, true>(m, X0, X1, X2, rz, act, valid, eoff, lo, a0, a1, e, out, pol_keep);
     }
 }
 

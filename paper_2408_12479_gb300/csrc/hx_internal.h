@@ -13,6 +13,9 @@
 #define HX_PMIN 1
 #define HX_PMAX 6
 #define HX_NMAX (HX_PMAX + 1)
+// bytes allocated past the end of every point array: the staged applies copy
+// whole 16-byte aligned windows, which may reach past the last point
+#define HX_ARRAY_SLACK 512
 
 namespace hx {
 

@@ -88,17 +88,20 @@ cudaError_t launch_apply_t(const hx::MeshView &m, const void *du, void *out, cud
     }
 }
 
-// Warp-decoupled staged apply (k_apply_wd): one warp per element with its own
-// stage; FP32 at n = 5 and the caching strategies only.
-template <int EPB, int LAW, int STORAGE>
+// Warp-decoupled staged apply (k_apply_wd): W warps per CTA, each with a
+// group of whole elements and its own stage; FP32 up to n = 5 and the caching
+// strategies only.
+// warps per CTA of variant 2: at n = 4 a warp's cubes and stage take 14.5 KB,
+// and two-warp CTAs pack the SM's shared memory best
+constexpr int WD_LO = N == 4 ? 2 : 4;
+template <int W, int LAW, int STORAGE>
 cudaError_t launch_apply_wd_t(const hx::MeshView &m, const void *du, void *out, cudaStream_t s) {
-    if constexpr (!ROWSW || STORAGE == HX_RECOMPUTE) {
+    if constexpr (!WD_OK || STORAGE == HX_RECOMPUTE) {
         return cudaErrorInvalidConfiguration;
     } else {
-        auto kern = k_apply_wd<EPB, LAW, STORAGE>;
-        constexpr size_t smem = ((size_t)3 * EPB * Lay<true>::ES * sizeof(Real) + 15) / 16 * 16 +
-                                (size_t)EPB * QpFields<LAW, STORAGE>::n * WIN * sizeof(Real);
-        constexpr int NTH = EPB * 32;
+        auto kern = k_apply_wd<W, LAW, STORAGE>;
+        constexpr size_t smem = wd_smem_bytes<W, LAW, STORAGE>();
+        constexpr int NTH = W * 32;
         if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
         static int per_sm = [&] {
             if (set_smem(kern, smem) != cudaSuccess) return 0;
@@ -108,7 +111,8 @@ cudaError_t launch_apply_wd_t(const hx::MeshView &m, const void *du, void *out, 
             return b;
         }();
         if (per_sm <= 0) return cudaErrorInvalidConfiguration;
-        const int ntiles = (m.n_elem + EPB - 1) / EPB;
+        const int ngroups = (m.n_elem + WEPW - 1) / WEPW;
+        const int ntiles = (ngroups + W - 1) / W;
         if (ntiles == 0) return cudaSuccess;
         const int grid = ntiles < per_sm * sm_count() ? ntiles : per_sm * sm_count();
         kern<<<grid, NTH, smem, s>>>(m, (const Real *)du, (Real *)out, ntiles);
@@ -120,10 +124,10 @@ cudaError_t launch_apply_wd_t(const hx::MeshView &m, const void *du, void *out, 
 // register prefetch one point ahead with an L2 bulk prefetch of the next tile
 // (0: default, 1: half elements per CTA), bulk copies into a shared stage one
 // tile ahead (3: default, 4: half), and the warp-decoupled staged apply with a
-// stage per warp (2: half, 5: default elements per CTA). Staged variants are
-// not built where a tile's chunk is not a multiple of 16 bytes; the
-// warp-decoupled ones only where one warp holds one element (FP32, p = 4) and
-// not for the recompute strategy.
+// stage per warp (2: WD_LO warps per CTA, 5: twice as many). Per-CTA staged variants are not
+// built where a tile's chunk is not a multiple of 16 bytes; the
+// warp-decoupled ones only where whole elements fit one warp (FP32, p <= 4)
+// and not for the recompute strategy.
 template <int LAW, int STORAGE>
 cudaError_t apply_variant(const hx::MeshView &m0, const void *du, void *out, cudaStream_t s, int variant) {
     hx::MeshView m = m0;
@@ -131,10 +135,10 @@ cudaError_t apply_variant(const hx::MeshView &m0, const void *du, void *out, cud
     constexpr int EH = EPB_A > 1 ? EPB_A / 2 : 1;
     switch (variant) {
         case 1: return launch_apply_t<EH, LAW, STORAGE, false>(m, du, out, s);
-        case 2: return launch_apply_wd_t<EH, LAW, STORAGE>(m, du, out, s);
+        case 2: return launch_apply_wd_t<WD_LO, LAW, STORAGE>(m, du, out, s);
         case 3: return launch_apply_t<EPB_A, LAW, STORAGE, true>(m, du, out, s);
         case 4: return launch_apply_t<EH, LAW, STORAGE, true>(m, du, out, s);
-        case 5: return launch_apply_wd_t<EPB_A, LAW, STORAGE>(m, du, out, s);
+        case 5: return launch_apply_wd_t<2 * WD_LO, LAW, STORAGE>(m, du, out, s);
         default: return launch_apply_t<EPB_A, LAW, STORAGE, false>(m, du, out, s);
     }
 }
