@@ -723,6 +723,82 @@ def run_solve_full(device, n=48, p=4, tol=1e-8, max_iter=500, J_target=0.9999, s
     return res
 
 
+def run_newton_full(device, n=48, p_cube=4, J_target=0.9999, p_tube=3, steps_tube=4):
+    """Newton's method (Alg. 1) end to end on the two full-size workloads.
+    (1) The compressed cube as a boundary-value problem: iNH, kappa = 1e3 mu,
+    n^3 jittered elements, p = 4, symmetry clamps and the far faces' normal
+    displacements prescribed to J = 0.9999, from u = 0 inside; FP64 CG with
+    the FP32 hp-multigrid; its exact solution is the homogeneous compression,
+    against which the result is checked. (2) The fibre tube (16 x 8 x 64
+    elements, p = 3, Q2 geometry) inflated by a dead inner pressure of 0.02 in
+    load steps, mirror-plane constraints; FP64 CG with FP32 Chebyshev(5)-
+    Jacobi."""
+    import torch
+    from paper_2408_12479_gb300 import hx
+    from paper_2408_12479_gb300 import inputs as I
+    res = {}
+    m, delta = I.workload_triaxial_compression(n=n, p=p_cube, J_target=J_target)
+    G = hx.Mesh(m, dict(I.MAT_INH), device=device)
+    mg = None
+    try:
+        rec = {"workload": f"iNH kappa=1e3 mu, {n}^3 jittered cube, p={p_cube}, triaxial compression to J={J_target}",
+               "n_dofs": m.n_dofs}
+        mg = hx.Multigrid(G, smoother_degree=3, precond_prec=hx.HX_FP32, storage=hx.HX_SPATIAL_TENSORS,
+                          lambda_iters=20, h_levels=10, coarse_cg_iters=200, coarse_cg_tol=1e-6)
+        X = G.node_coords().reshape(-1)
+        exact = delta * X
+        u = torch.where(torch.tensor(m.dirichlet, device=G.device).bool(), exact, torch.zeros_like(exact))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep, st = hx.hx_newton_solve(G.ctx, G.handle, u, None, eps_abs=1e-16, eps_rel=1e-10, max_newton=10,
+                                     storage=hx.HX_SPATIAL_TENSORS, cg_tol=1e-8, cg_max_iter=500, mg=mg)
+        torch.cuda.synchronize()
+        rec.update({"seconds": round(time.perf_counter() - t0, 3), "status": hx.STATUS_NAMES.get(st, st),
+                    "newton_iters": rep["newton_iters"], "cg_iters": rep["cg_iters"],
+                    "final_res_rel": rep["res"] / max(rep["res0"], 1e-300),
+                    "max_err_vs_closed_form_rel": float((u - exact).abs().max() / abs(delta)),
+                    "levels": ["p%d:%dx%dx%d" % mg.level(l) for l in range(len(mg.levels()))]})
+        res["cube"] = rec
+    finally:
+        if mg is not None:
+            mg.close()
+        G.close()
+        torch.cuda.empty_cache()
+    m, faces, pressure = I.workload_tube_inflation(p=p_tube)
+    G = hx.Mesh(m, dict(I.MAT_FIBER), device=device)
+    try:
+        f = torch.tensor(hx.hx_traction_load(m, faces, pressure=pressure), dtype=torch.float64, device=G.device)
+        X = G.node_coords().reshape(-1, 3)
+        u = (1e-3 * X * torch.tensor([1.0, 1.0, 0.0], dtype=torch.float64, device=G.device)).reshape(-1)
+        u[torch.tensor(m.dirichlet, device=G.device).bool()] = 0.0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        its, cg, st, rep = [], 0, hx.HX_OK, None
+        for k in range(1, steps_tube + 1):
+            rep, st = hx.hx_newton_solve(G.ctx, G.handle, u, f * (k / steps_tube), eps_abs=1e-12, eps_rel=1e-10,
+                                         max_newton=15, storage=hx.HX_SPATIAL_TENSORS, precond_prec=hx.HX_FP32,
+                                         cg_tol=1e-8, cg_max_iter=20000)
+            its.append(rep["newton_iters"])
+            cg += rep["cg_iters"]
+            if st != hx.HX_OK:
+                break
+        torch.cuda.synchronize()
+        R = torch.hypot(X[:, 0], X[:, 1])
+        U = u.reshape(-1, 3)
+        u_r = (U[:, 0] * X[:, 0] + U[:, 1] * X[:, 1]) / R
+        inner = R < 1.0 + 1e-9
+        res["tube"] = {"workload": f"fibre tube 16x8x64, p={p_tube}, inner pressure {pressure} in {steps_tube} "
+                                   f"load steps, mirror-plane constraints", "n_dofs": m.n_dofs,
+                       "seconds": round(time.perf_counter() - t0, 3), "status": hx.STATUS_NAMES.get(st, st),
+                       "newton_iters_per_step": its, "cg_iters": cg,
+                       "final_res_rel": rep["res"] / max(rep["res0"], 1e-300),
+                       "inner_radial_displacement_min_max": [float(u_r[inner].min()), float(u_r[inner].max())]}
+    finally:
+        G.close()
+        torch.cuda.empty_cache()
+    return res
+
+
 def solve_summary(r):
     """The full-size solve's key figures for the headline line."""
     if not isinstance(r, dict) or "error" in r:
@@ -1071,6 +1147,8 @@ def main():
                     help="pin the apply variant (0-5) instead of the autotuner's (profiling commands)")
     ap.add_argument("--solve-full", type=int, default=48,
                     help="the compressed-cube solve at full size with the hp-multigrid preconditioner (n given; 0: off)")
+    ap.add_argument("--no-newton-full", dest="newton_full", action="store_false",
+                    help="skip Newton's method on the full-size compressed cube and fibre tube")
     ap.add_argument("--batch-cg", type=int, default=16,
                     help="batched CG over the first n cubes of the 64-cube workload, and one at a time (0: off)")
     ap.add_argument("--solve", type=int, default=16,
@@ -1202,6 +1280,8 @@ def main():
         newton = guarded(run_newton, local)
         newton["traction"] = guarded(run_newton_traction, local)
         emit({"report": "newton", **newton})
+        if args.newton_full:
+            emit({"report": "newton_full", **guarded(run_newton_full, local)})
         emit({"report": "stability", **guarded(run_stability, local)})
         emit({"report": "paper_context", **PAPER_CONTEXT})
 

@@ -122,6 +122,21 @@ def box_dirichlet_x0(nx, ny, nz, p):
     return np.repeat(m, 3)
 
 
+def box_dirichlet_triaxial(nx, ny, nz, p):
+    """Symmetry clamps (component d on the face x_d = 0) plus component d on
+    the far face x_d = L_d, for d = x, y, z: with the far faces' normal
+    displacements prescribed this is triaxial compression (or extension),
+    whose solution is the homogeneous state."""
+    Nx, Ny, Nz = nx * p + 1, ny * p + 1, nz * p + 1
+    idx = np.arange(Nx * Ny * Nz)
+    I_, J_, K_ = idx % Nx, (idx // Nx) % Ny, idx // (Nx * Ny)
+    m = np.zeros((idx.size, 3), np.uint8)
+    m[:, 0] = (I_ == 0) | (I_ == Nx - 1)
+    m[:, 1] = (J_ == 0) | (J_ == Ny - 1)
+    m[:, 2] = (K_ == 0) | (K_ == Nz - 1)
+    return m.ravel()
+
+
 def box_boundary_faces(nx, ny, nz, side):
     """(element, local face) pairs of one side of a box: side 2d + s is the
     plane x_d = 0 (s = 0) or x_d = L_d (s = 1); the elements' local face has
@@ -199,6 +214,23 @@ def tube_mesh(p, n_r=8, n_theta=16, n_z=64, r_in=1.0, r_out=1.3, length=10.0,
                      box=None, frames=frames, name=name or f"tube_p{p}",
                      extra=dict(n_r=n_r, n_theta=n_theta, n_z=n_z, r_in=r_in, r_out=r_out,
                                 length=length))
+
+
+def tube_dirichlet_symmetry(p, n_r=8, n_theta=16, n_z=64):
+    """Constraints of a tube that leave its axisymmetric deformations free:
+    u_z = 0 on the bottom (z = 0), u_y = 0 on the nodes at theta = 0 and pi,
+    u_x = 0 on those at theta = pi/2 and 3 pi/2 (the mesh's mirror planes;
+    together they remove the rigid motions). Needs n_theta p divisible by 4."""
+    Nr, Nt, Nz = n_r * p + 1, n_theta * p, n_z * p + 1
+    if Nt % 4:
+        raise ValueError("n_theta * p must be divisible by 4")
+    idx = np.arange(Nr * Nt * Nz)
+    jt, kz = (idx // Nr) % Nt, idx // (Nr * Nt)
+    m = np.zeros((idx.size, 3), np.uint8)
+    m[:, 0] = (jt == Nt // 4) | (jt == 3 * Nt // 4)
+    m[:, 1] = (jt == 0) | (jt == Nt // 2)
+    m[:, 2] = kz == 0
+    return m.ravel()
 
 
 def tube_boundary_faces(n_r, n_theta, n_z, which):
@@ -383,6 +415,28 @@ class CompressionField:
     def __call__(self, X):
         X = np.asarray(X, dtype=np.float64)
         return self.s * X + X * self.sines(X)
+
+
+def workload_triaxial_compression(n=48, p=4, J_target=0.9999, seed=SEED_BASE + 3):
+    """The compressed cube as a boundary-value problem (iNH, kappa = 1e3 mu):
+    the n^3 jittered cube with symmetry clamps and the far faces' normal
+    displacements prescribed to (J_target^(1/3) - 1) L; returns the mesh,
+    u_0 (zero except the prescribed values) and the exact solution, the
+    homogeneous compression u = (J_target^(1/3) - 1) X, which the
+    discretisation contains (trilinear geometry)."""
+    m = box_mesh(n, p, jitter=0.1, seed=seed, name=f"cube{n}_p{p}_triaxial")
+    m.dirichlet = box_dirichlet_triaxial(n, n, n, p)
+    return m, J_target ** (1.0 / 3.0) - 1.0
+
+
+def workload_tube_inflation(p=3, n_r=8, n_theta=16, n_z=64, pressure=0.02):
+    """The fibre tube (16 x 8 x 64 elements, Q2 geometry) inflated by a dead
+    pressure on its inner surface, with the symmetry constraints of
+    tube_dirichlet_symmetry; returns the mesh, the inner faces and the
+    pressure."""
+    m = tube_mesh(p, n_r=n_r, n_theta=n_theta, n_z=n_z, name=f"tube_p{p}_inflation")
+    m.dirichlet = tube_dirichlet_symmetry(p, n_r, n_theta, n_z)
+    return m, tube_boundary_faces(n_r, n_theta, n_z, "inner"), pressure
 
 
 def workload_compressed_cube(n=48, p=4, J_target=0.9, sine_amp=0.005, seed=SEED_BASE + 3):

@@ -170,3 +170,73 @@ def test_newton_with_multigrid_matches_closed_form(law):
     finally:
         mg.close()
         G.close()
+
+
+def test_newton_triaxial_compression_with_hp_multigrid_matches_closed_form():
+    """The compressed cube as a boundary-value problem (iNH, kappa = 1e3 mu,
+    4^3 jittered cube, p = 4): symmetry clamps and the far faces' normal
+    displacements prescribed to J = 0.9999. Its solution is the homogeneous
+    compression u = (J^(1/3) - 1) X, which the discretisation holds exactly
+    (trilinear geometry; Gauss points integrate the constant stress's
+    boundary terms exactly). Newton from u = 0 inside, with linear solves by
+    FP64 CG and the FP32 hp-multigrid (p 4 -> 2 -> 1, then h-levels to the
+    coarse FP64 CG), reaches it to the solver tolerance."""
+    m, delta = I.workload_triaxial_compression(n=4, p=4)
+    G = hx.Mesh(m, dict(I.MAT_INH))
+    mg = hx.Multigrid(G, precond_prec=hx.HX_FP32, storage=hx.HX_SPATIAL_TENSORS, h_levels=1,
+                      coarse_cg_iters=200, coarse_cg_tol=1e-10)
+    try:
+        assert [mg.level(l) for l in range(len(mg.levels()))] == [(4, 4, 4, 4), (2, 4, 4, 4), (1, 4, 4, 4),
+                                                                 (1, 2, 2, 2)]
+        X = G.node_coords().cpu().numpy().reshape(-1)
+        exact = delta * X
+        u0 = np.where(m.dirichlet.astype(bool), exact, 0.0)
+        u = cuda(u0)
+        rep, st = hx.hx_newton_solve(G.ctx, G.handle, u, None, eps_abs=1e-16, eps_rel=1e-11, max_newton=10,
+                                     storage=hx.HX_SPATIAL_TENSORS, cg_tol=1e-12, cg_max_iter=2000, mg=mg)
+        assert st == hx.HX_OK and rep["converged"] and rep["newton_iters"] <= 4, rep
+        err = np.abs(u.cpu().numpy() - exact).max() / abs(delta)
+        assert err < 1e-7, (err, rep)
+    finally:
+        mg.close()
+        G.close()
+
+
+def test_tube_inflation_newton_matches_oracle_newton():
+    """The fibre tube (here 2 x 8 x 3 elements, p = 2, Q2 geometry,
+    connectivity numbering) inflated by a dead inner pressure of 0.02 in two
+    load steps, with the mirror-plane constraints that leave its axisymmetric
+    deformations free: GPU Newton (FP64 CG, FP32 Chebyshev-Jacobi) against
+    the oracle's Newton (direct solves). Both start from a small inflation,
+    where every fibre is stretched (I* > 1 at every point), so the two sides
+    take the same branch of the fibre term from the first step on."""
+    m, faces, pressure = I.workload_tube_inflation(p=2, n_r=2, n_theta=8, n_z=3)
+    M = O.OracleMesh(m)
+    mat_d = dict(I.MAT_FIBER)
+    mat_o = cases.oracle_material(mat_d)
+    f = hx.hx_traction_load(m, faces, pressure=pressure)
+    f_ref = O.traction_load(M, faces, lambda X, N: -pressure * N)
+    assert rel_inf(f, f_ref) < 1e-13
+    X = O.node_coords(M)
+    u0 = (1e-3 * X * np.array([1.0, 1.0, 0.0])).ravel()
+    u0[M.dirichlet] = 0.0
+    u_ref = u0.copy()
+    for k in (1, 2):
+        u_ref, norms = O.newton(M, mat_o, u_ref, f_ext=f_ref * (k / 2), eps_abs=1e-12, eps_rel=1e-14, max_it=30)
+        assert norms[-1] < 1e-11 * norms[0]
+    R = np.hypot(X[:, 0], X[:, 1])
+    U = u_ref.reshape(-1, 3)
+    u_r = (U[:, 0] * X[:, 0] + U[:, 1] * X[:, 1]) / R
+    assert u_r[R < 1.0 + 1e-9].min() > 2e-3  # the inner surface moved out beyond the start
+    G = hx.Mesh(m, mat_d)
+    try:
+        u = cuda(u0)
+        fg = cuda(f)
+        for k in (1, 2):
+            rep, st = hx.hx_newton_solve(G.ctx, G.handle, u, fg * (k / 2), eps_abs=1e-12, eps_rel=1e-14,
+                                         max_newton=20, storage=hx.HX_SPATIAL_TENSORS, precond_prec=hx.HX_FP32,
+                                         cg_tol=1e-12, cg_max_iter=20000)
+            assert st == hx.HX_OK and rep["converged"], rep
+        assert rel_inf(u.cpu().numpy(), u_ref) < 1e-8
+    finally:
+        G.close()
