@@ -1385,6 +1385,31 @@ __device__ __forceinline__ void stage_issue(const hx::MeshView &m, int tile, Rea
     }
 }
 
+// The same copies issued by the 32 lanes of one warp (lane f copies fields
+// f, f + 32, ...; lane 0 first posts the expected bytes); called by all lanes
+// of that warp after the CTA barrier that ends the stage's previous use.
+template <int EPB, int LAW, int STORAGE>
+__device__ __forceinline__ void stage_issue_warp(const hx::MeshView &m, int tile, Real *stg, uint64_t *bar, int lane) {
+    using QF = QpFields<LAW, STORAGE>;
+    constexpr int FE = EPB * NQ;  // stage points per field
+    const int e0 = tile * EPB;
+    const int cnt = min(EPB, m.n_elem - e0);
+    const uint32_t bytes = (uint32_t)((cnt * NQ * (int)sizeof(Real) + 15) / 16 * 16);
+    if (m.skip_stage_copies) return;  // test hook: the stage never fills and the wait runs out
+    if (lane == 0) mbar_expect_tx(bar, QF::n * bytes);
+    __syncwarp();
+    if (lane < QF::n) {
+        const uint64_t pol = policy_evict_first();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+#pragma unroll 1
+        for (int f = lane; f < QF::n; f += 32) {
+            const Real *src = f < QF::ng ? (const Real *)m.geo + (int64_t)f * m.qs + (int64_t)e0 * NQ
+                                         : (const Real *)m.qp + (int64_t)(f - QF::ng) * m.qs + (int64_t)e0 * NQ;
+            bulk_g2s(stg + f * FE, src, bytes, bar, pol);
+        }
+    }
+}
+
 // Test-gradient integration of the per-point coefficients Q (x, y, z parts in
 // X0, X1, X2, overwritten) back to nodal values and the atomic scatter into
 // out: Dz^T and Dy^T in place, then Bx^T (Dx^T Qx + .) in place, By^T, Bz^T
@@ -1459,7 +1484,8 @@ __device__ __forceinline__ void col_backward(const hx::MeshView &m, Real *X0, Re
 template <bool SW, bool WS = false>
 __device__ __forceinline__ void col_backward_c(const hx::MeshView &m, Real *X0, Real *X1, Real *X2, Real (*rz)[N],
                                                bool act, bool valid, int eoff, const LineOffs<SW> &o, int a0, int a1,
-                                               int e, Real *__restrict__ out, uint64_t pol_keep) {
+                                               int e, Real *__restrict__ out, uint64_t pol_keep,
+                                               int64_t base_e = -1) {
     constexpr int CZ = Lay<SW>::CZ;
     constexpr bool EO = true;  // even-odd sweeps in the staged apply (see mv)
     Real x[3][N], y[3][N], w[3][N];
@@ -1526,7 +1552,7 @@ __device__ __forceinline__ void col_backward_c(const hx::MeshView &m, Real *X0, 
                 for (int c = 0; c < 3; ++c) eo[3 * NN * k + c] = y[c][k];
             return;
         }
-        const int64_t base = elem_base(m, e);
+        const int64_t base = base_e >= 0 ? base_e : elem_base(m, e);  // the caller's copy, if it has one
         const bool msk = m.dmask != nullptr;
 #pragma unroll
         for (int k = 0; k < N; ++k) {
@@ -1771,7 +1797,7 @@ __device__ __forceinline__ bool apply_tile(const hx::MeshView &m, int tile, int 
         Real rz[3][N];
         mv3<TD, true, true>(gz, rz);
         __syncthreads();
-        if (t == 0 && ntile >= 0) stage_issue<EPB, LAW, STORAGE>(m, ntile, stg, bar);
+        if (t < 32 && ntile >= 0) stage_issue_warp<EPB, LAW, STORAGE>(m, ntile, stg, bar, t);
         col_backward_c<SW>(m, X0, X1, X2, rz, act, valid, eoff, lo, a0, a1, e, out, pol_keep);
         return true;
     } else {
@@ -1812,23 +1838,29 @@ constexpr bool WD_OK = sizeof(Real) == 4 && WEPW > 0;
 // the point arrays carry HX_ARRAY_SLACK bytes after their last field.
 static_assert(!WD_OK || (WWIN - NQ) * 4 <= HX_ARRAY_SLACK, "stage windows would leave the point arrays");
 
-// Lane 0 of group g's warp: the bulk copies of the group's point fields into
-// the warp's stage (one WWIN-word window per field), on the warp's mbarrier.
+// The bulk copies of group g's point fields into the warp's stage (one
+// WWIN-word window per field), on the warp's mbarrier, issued by the whole
+// warp (lane f copies fields f, f + 32, ...; lane 0 first posts the expected
+// bytes). Called by all 32 lanes after the warp barrier that ends the stage's
+// previous use.
 template <int LAW, int STORAGE>
-__device__ __forceinline__ void stage_issue_group(const hx::MeshView &m, int g, Real *stg, uint64_t *bar) {
+__device__ __forceinline__ void stage_issue_group(const hx::MeshView &m, int g, Real *stg, uint64_t *bar, int lane) {
     using QF = QpFields<LAW, STORAGE>;
     static_assert(LAW >= 0 && WD_OK, "the window layout is that of FP32 groups of whole elements in one warp");
     if (m.skip_stage_copies) return;  // test hook: the stage never fills and the wait runs out
-    const uint64_t pol = policy_evict_first();
     const int64_t c0 = (int64_t)g * WCH;
     const int64_t w0 = c0 - (c0 & 3);  // first word of the window: a multiple of 4
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(bar, QF::n * WWIN * 4);
+    if (lane == 0) mbar_expect_tx(bar, QF::n * WWIN * 4);
+    __syncwarp();
+    if (lane < QF::n) {
+        const uint64_t pol = policy_evict_first();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 #pragma unroll 1
-    for (int f = 0; f < QF::n; ++f) {
-        const Real *src = f < QF::ng ? (const Real *)m.geo + (int64_t)f * m.qs + w0
-                                     : (const Real *)m.qp + (int64_t)(f - QF::ng) * m.qs + w0;
-        bulk_g2s(stg + f * WWIN, src, WWIN * 4, bar, pol);
+        for (int f = lane; f < QF::n; f += 32) {
+            const Real *src = f < QF::ng ? (const Real *)m.geo + (int64_t)f * m.qs + w0
+                                         : (const Real *)m.qp + (int64_t)(f - QF::ng) * m.qs + w0;
+            bulk_g2s(stg + f * WWIN, src, WWIN * 4, bar, pol);
+        }
     }
 }
 
@@ -1845,8 +1877,8 @@ __host__ __device__ constexpr size_t wd_smem_bytes() {
 
 // out += K(u_k) du, one group of WEPW elements per warp with its own stage
 // (caching strategies). Warp w of a CTA takes group tile*W + w of each of the
-// CTA's tiles (elements g*WEPW .. g*WEPW + WEPW - 1); its lane 0 issues the
-// copies of the warp's next group as soon as the warp has consumed its stage.
+// CTA's tiles (elements g*WEPW .. g*WEPW + WEPW - 1); the warp issues the
+// copies of its next group as soon as it has consumed its stage.
 template <int W, int LAW, int STORAGE>
 __global__ void __launch_bounds__(W * 32) k_apply_wd(const hx::MeshView m, const Real *__restrict__ du,
                                                      Real *__restrict__ out, int ntiles) {
@@ -1876,9 +1908,10 @@ __global__ void __launch_bounds__(W * 32) k_apply_wd(const hx::MeshView m, const
     const int stride = gridDim.x * W;  // groups
     int g = blockIdx.x * W + wid;
     int e = g * WEPW + sub;
-    if (lane == 0 && (int)blockIdx.x < ntiles && g * WEPW < m.n_elem) stage_issue_group<LAW, STORAGE>(m, g, stg, bar);
+    if ((int)blockIdx.x < ntiles && g * WEPW < m.n_elem) stage_issue_group<LAW, STORAGE>(m, g, stg, bar, lane);
     Real row[3 * N];
-    if (act) load_row(m, e, elem_base(m, e), a0, a1, du, true, row);  // zeros past the end
+    int64_t base = elem_base(m, e);  // 0 past the end
+    if (act) load_row(m, e, base, a0, a1, du, true, row);  // zeros past the end
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, g += stride, e += stride * WEPW) {
         if (g * WEPW >= m.n_elem) break;  // warp-uniform; later tiles lie further out
         const bool valid = act && e < m.n_elem;
@@ -1887,7 +1920,8 @@ __global__ void __launch_bounds__(W * 32) k_apply_wd(const hx::MeshView m, const
         Real cd[3 * N];
 #pragma unroll
         for (int i = 0; i < 3 * N; ++i) cd[i] = row[i];
-        if (act) load_row(m, en, elem_base(m, en), a0, a1, du, true, row);
+        const int64_t base_n = elem_base(m, en);
+        if (act) load_row(m, en, base_n, a0, a1, du, true, row);
         Real gz[3][N], gk[1][N];
         col_forward_c<SW, true>(cd, X0, X1, X2, gz, act, eoff, lo);
         const bool ok = mbar_wait(bar, phase, m.wait_limit);
@@ -1905,8 +1939,9 @@ __global__ void __launch_bounds__(W * 32) k_apply_wd(const hx::MeshView m, const
         Real rz[3][N];
         mv3<TD, true, true>(gz, rz);
         __syncwarp();  // the stage is consumed
-        if (lane == 0 && gn * WEPW < m.n_elem) stage_issue_group<LAW, STORAGE>(m, gn, stg, bar);
-        col_backward_c<SW, true>(m, X0, X1, X2, rz, act, valid, eoff, lo, a0, a1, e, out, pol_keep);
+        if (gn * WEPW < m.n_elem) stage_issue_group<LAW, STORAGE>(m, gn, stg, bar, lane);
+        col_backward_c<SW, true>(m, X0, X1, X2, rz, act, valid, eoff, lo, a0, a1, e, out, pol_keep, base);
+        base = base_n;
     }
 }
 
@@ -2043,7 +2078,7 @@ __global__ void __launch_bounds__(apply_threads<STAGED && ROWSW>(EPB)) k_apply(c
     if constexpr (STAGED) {
         if (t == 0) mbar_init(&bar, 1);
         __syncthreads();
-        if (t == 0 && (int)blockIdx.x < ntiles) stage_issue<EPB, LAW, STORAGE>(m, blockIdx.x, stg, &bar);
+        if (t < 32 && (int)blockIdx.x < ntiles) stage_issue_warp<EPB, LAW, STORAGE>(m, blockIdx.x, stg, &bar, t);
     }
     Real rowd[3 * N], rowk[RC ? 3 * N : 1];
     if (act && (int)blockIdx.x < ntiles) {
