@@ -1363,31 +1363,12 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
         : "memory");
 }
-// Issue (one thread) the bulk copies of a tile's quadrature-point fields into
-// the stage; the stage's previous contents must have been consumed (CTA
-// barrier) -- the proxy fence orders those generic reads before the copies.
-template <int EPB, int LAW, int STORAGE>
-__device__ __forceinline__ void stage_issue(const hx::MeshView &m, int tile, Real *stg, uint64_t *bar) {
-    using QF = QpFields<LAW, STORAGE>;
-    constexpr int FE = EPB * NQ;  // stage points per field
-    const int e0 = tile * EPB;
-    const int cnt = min(EPB, m.n_elem - e0);
-    const uint32_t bytes = (uint32_t)((cnt * NQ * (int)sizeof(Real) + 15) / 16 * 16);
-    const uint64_t pol = policy_evict_first();
-    if (m.skip_stage_copies) return;  // test hook: the stage never fills and the wait runs out
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(bar, QF::n * bytes);
-#pragma unroll 1
-    for (int f = 0; f < QF::n; ++f) {
-        const Real *src = f < QF::ng ? (const Real *)m.geo + (int64_t)f * m.qs + (int64_t)e0 * NQ
-                                     : (const Real *)m.qp + (int64_t)(f - QF::ng) * m.qs + (int64_t)e0 * NQ;
-        bulk_g2s(stg + f * FE, src, bytes, bar, pol);
-    }
-}
-
-// The same copies issued by the 32 lanes of one warp (lane f copies fields
-// f, f + 32, ...; lane 0 first posts the expected bytes); called by all lanes
-// of that warp after the CTA barrier that ends the stage's previous use.
+// The bulk copies of a tile's quadrature-point fields into the CTA's stage
+// (one chunk of the tile's points per field, rounded up to 16 bytes), on the
+// CTA's mbarrier, issued by the 32 lanes of one warp (lane f copies fields
+// f, f + 32, ...; lane 0 first posts the expected bytes). Called by all lanes
+// of that warp after the CTA barrier that ends the stage's previous use; the
+// proxy fence orders those generic reads before the copies.
 template <int EPB, int LAW, int STORAGE>
 __device__ __forceinline__ void stage_issue_warp(const hx::MeshView &m, int tile, Real *stg, uint64_t *bar, int lane) {
     using QF = QpFields<LAW, STORAGE>;
@@ -2150,7 +2131,7 @@ __device__ __forceinline__ bool batch_tile_staged(const hx::MeshView &m, int til
     static_assert(SM::stageable, "bulk copies need 16-byte aligned tiles");
     Real *stg = (Real *)(smem_raw + (SM::cube_bytes + 15) / 16 * 16);
     const int t = threadIdx.x;
-    if (t == 0) stage_issue<EPB, LAW, STORAGE>(m, tile, stg, bar);
+    if (t < 32) stage_issue_warp<EPB, LAW, STORAGE>(m, tile, stg, bar, t);
     int el, a0, a1;
     bool act;
     thread_map<ROWSW>(t, EPB, el, a0, a1, act);
