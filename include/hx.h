@@ -177,10 +177,22 @@ hx_status hx_residual(hx_mesh *mesh, const void *u_dev, void *r_dev, int32_t pre
  * store_prec. du_dev and out_dev must not overlap. */
 hx_status hx_tangent_apply(hx_mesh *mesh, const void *du_dev, void *out_dev, int32_t prec);
 
-/* Same operator with host vectors: copies du to the device, applies, copies
- * the result back, all on the context stream; returns after the result is on
- * the host. Uses a device staging buffer owned by the mesh. */
+/* Same operator with host vectors; returns after the result is on the host.
+ * Uses device staging buffers owned by the mesh. On a structured box (not
+ * the fibre law, atomic assembly, at least four element layers) the work runs
+ * in z-slabs of element layers on the context stream and two copy streams
+ * owned by the mesh (created on the first call): the copy of a slab's node
+ * layers to the device overlaps the apply of the slab before it, and node
+ * layers that no later slab touches are copied back while the next slabs
+ * run. Other meshes copy the whole vectors, apply and copy back, on the
+ * context stream. du_host and out_host should be page-locked for the copies
+ * to overlap. */
 hx_status hx_tangent_apply_host(hx_mesh *mesh, const void *du_host, void *out_host, int32_t prec);
+/* slabs = 0: hx_tangent_apply_host copies whole vectors on every mesh; 1
+ * (default): slabs where they apply, at most the library's default count;
+ * 2..8: at most that many slabs (fewer where the element layers or the
+ * 16-byte alignment of the slab starts require). HX_ERR_ARG otherwise. */
+hx_status hx_set_host_apply_slabs(hx_mesh *mesh, int32_t slabs);
 
 /* Autotuner: time every compiled variant of the tangent apply for the mesh's
  * current cache at `prec` and keep the fastest for later hx_tangent_apply

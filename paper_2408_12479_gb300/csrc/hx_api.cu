@@ -234,6 +234,11 @@ struct hx_mesh {
     std::vector<void *> ws;
     void *w_cheb_d[2] = {nullptr, nullptr}, *w_cheb_Kx[2] = {nullptr, nullptr};
     void *w_stage_in = nullptr, *w_stage_out = nullptr;
+    // host-buffer apply in z-slabs: copy streams and events (created on first use)
+    cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_out = nullptr, ev_in[8] = {}, ev_done[8] = {};
+    std::vector<int64_t> h_cidx;  // the constrained DoFs, ascending (host copy of d_cidx)
+    int host_slabs = 1;           // hx_set_host_apply_slabs: 0 whole vectors, 1 automatic, n at most n slabs
     double *w_cg = nullptr;   // r z zold p Ap dinv (FP64)
     double *w_newton = nullptr;  // Newton: residual, update, inverse diagonal (FP64)
     // host copies of the description (multigrid levels are rebuilt from them)
@@ -428,6 +433,14 @@ void hx_destroy_mesh(hx_mesh *m) {
     for (void *p : ptrs) dfree(p);
     if (m->h_pinned) cudaFreeHost(m->h_pinned);
     if (m->solve_stream) cudaStreamDestroy(m->solve_stream);
+    for (cudaStream_t st : {m->s_h2d, m->s_d2h})
+        if (st) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : {m->ev_start, m->ev_out})
+        if (ev) cudaEventDestroy(ev);
+    for (int i = 0; i < 8; ++i) {
+        if (m->ev_in[i]) cudaEventDestroy(m->ev_in[i]);
+        if (m->ev_done[i]) cudaEventDestroy(m->ev_done[i]);
+    }
     delete m;
 }
 
@@ -515,6 +528,7 @@ hx_status hx_setup_mesh(hx_ctx *ctx, const hx_mesh_desc *d, const hx_material *m
             HX_MCUDA(cudaMemcpy(m->d_dmask, d->dirichlet, 3 * d->n_nodes, cudaMemcpyHostToDevice));
             HX_MCUDA(dalloc(&m->d_cidx, idx.size()));
             HX_MCUDA(cudaMemcpy(m->d_cidx, idx.data(), sizeof(int64_t) * idx.size(), cudaMemcpyHostToDevice));
+            m->h_cidx = idx;
         }
     }
     // fibre families per element: M1 and H_i = sum_k H_kk M_k (x) M_k (Sec. 3)
@@ -695,6 +709,12 @@ hx_status hx_tangent_apply(hx_mesh *m, const void *du_dev, void *out_dev, int32_
     return apply_dev(m, du_dev, out_dev, prec);
 }
 
+hx_status hx_set_host_apply_slabs(hx_mesh *m, int32_t slabs) {
+    if (!m || slabs < 0 || slabs > 8) return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_set_host_apply_slabs: bad argument");
+    m->host_slabs = slabs;
+    return HX_OK;
+}
+
 hx_status hx_set_scatter_mode(hx_mesh *m, int32_t mode) {
     if (!m || (mode != HX_SCATTER_ATOMIC && mode != HX_SCATTER_ORDERED))
         return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_set_scatter_mode: bad argument");
@@ -782,6 +802,114 @@ hx_status hx_autotune(hx_mesh *m, int32_t prec, const void *du_dev, void *out_de
     return HX_OK;
 }
 
+// The mesh view of the element layers z0 <= ez < z1 of a structured box: the
+// point arrays start at the slab's first point and the node-indexed arrays at
+// its first node layer (z0 p), so the kernels run on the slab as on a box of
+// z1 - z0 layers. Vectors passed with it must be offset by the same node
+// layer. Not for the fibre law (its per-element arrays are strided by the
+// element count) nor for ordered assembly.
+// slabs of the host-buffer apply unless the mesh sets its own limit
+constexpr int HX_HOST_SLABS = 4;
+
+hx::MeshView slab_view(const hx_mesh *m, int prec, int z0, int z1) {
+    hx::MeshView v = view(m, prec);
+    const size_t sz = prec_size(prec);
+    const int64_t nq = (int64_t)(m->p + 1) * (m->p + 1) * (m->p + 1);
+    const int64_t e0 = (int64_t)z0 * m->nx * m->ny;
+    const int64_t node0 = (int64_t)z0 * m->p * v.Nx * v.Ny;
+    v.n_elem = (z1 - z0) * m->nx * m->ny;
+    v.nz = z1 - z0;
+    v.n_nodes = v.Nx * v.Ny * ((int64_t)(z1 - z0) * m->p + 1);
+    v.n_qp = (int64_t)v.n_elem * nq;
+    v.geo = (const char *)v.geo + e0 * nq * sz;
+    v.geo64 = v.geo64 + e0 * nq;
+    v.qp = (const char *)v.qp + e0 * nq * sz;  // point-indexed caches
+    v.uk = (const char *)v.uk + 3 * node0 * sz;  // the recompute strategy's node vector u_k
+    if (v.dmask) v.dmask += 3 * node0;
+    return v;
+}
+
+// out = K(u_k) du from host vectors on a structured box, in z-slabs of element
+// layers on three streams: the copy of slab s + 1's node layers to the device
+// overlaps the apply of slab s, and the node layers that no later slab touches
+// are fixed on constrained rows and copied back while the next slabs run.
+// Sets *done = false, doing nothing, where it does not apply (connectivity
+// meshes, the fibre law, ordered assembly, fewer than four element layers, or
+// no slab split whose point chunks start on 16-byte boundaries).
+hx_status apply_host_slabs(hx_mesh *m, const void *du_host, void *out_host, int prec, bool *done) {
+    *done = false;
+    hx_ctx *ctx = m->ctx;
+    const QpCache &c = m->cache[prec];
+    if (!m->structured || m->scatter_ordered || m->law == HX_FIBER || !c.valid || m->nz < 4) return HX_OK;
+    const size_t sz = prec_size(prec);
+    const int64_t nq = (int64_t)(m->p + 1) * (m->p + 1) * (m->p + 1);
+    const int64_t lay = (int64_t)m->nx * m->ny;
+    int k = 0;  // element layers per slab
+    const int most = m->host_slabs >= 2 ? m->host_slabs : HX_HOST_SLABS;
+    for (int ns = std::min(most, m->nz / 2); ns >= 2 && !k; --ns) {
+        const int kk = (m->nz + ns - 1) / ns;
+        bool ok = true;
+        for (int z0 = kk; z0 < m->nz; z0 += kk) ok = ok && ((int64_t)z0 * lay * nq * (int64_t)sz) % 16 == 0;
+        if (ok) k = kk;
+    }
+    if (!k) return HX_OK;
+    if (!m->s_h2d) {
+        DeviceGuard dg(ctx->device);
+        HX_CUDA(ctx, cudaStreamCreateWithFlags(&m->s_h2d, cudaStreamNonBlocking));
+        HX_CUDA(ctx, cudaStreamCreateWithFlags(&m->s_d2h, cudaStreamNonBlocking));
+        HX_CUDA(ctx, cudaEventCreateWithFlags(&m->ev_start, cudaEventDisableTiming));
+        HX_CUDA(ctx, cudaEventCreateWithFlags(&m->ev_out, cudaEventDisableTiming));
+        for (int i = 0; i < 8; ++i) {
+            HX_CUDA(ctx, cudaEventCreateWithFlags(&m->ev_in[i], cudaEventDisableTiming));
+            HX_CUDA(ctx, cudaEventCreateWithFlags(&m->ev_done[i], cudaEventDisableTiming));
+        }
+    }
+    const int64_t Nx = (int64_t)m->nx * m->p + 1, Ny = (int64_t)m->ny * m->p + 1;
+    const int64_t Nz = (int64_t)m->nz * m->p + 1;
+    const int64_t lv = 3 * Nx * Ny;  // values per node layer
+    const char *hin = (const char *)du_host;
+    char *hout = (char *)out_host;
+    char *din = (char *)m->w_stage_in, *dout = (char *)m->w_stage_out;
+    const int variant = m->variant[prec][c.storage];
+    HX_CUDA(ctx, cudaEventRecord(m->ev_start, ctx->stream));
+    HX_CUDA(ctx, cudaStreamWaitEvent(m->s_h2d, m->ev_start, 0));
+    HX_CUDA(ctx, cudaStreamWaitEvent(m->s_d2h, m->ev_start, 0));
+    HX_CUDA(ctx, cudaMemsetAsync(dout, 0, (size_t)(lv * Nz) * sz, ctx->stream));
+    int64_t in_done = 0, out_done = 0;  // node layers copied in and out so far
+    for (int z0 = 0, s = 0; z0 < m->nz; z0 += k, ++s) {
+        const int z1 = std::min(z0 + k, m->nz);
+        const int64_t need = (int64_t)z1 * m->p + 1;  // node layers this slab reads
+        HX_CUDA(ctx, cudaMemcpyAsync(din + in_done * lv * sz, hin + in_done * lv * sz, (size_t)((need - in_done) * lv) * sz,
+                                     cudaMemcpyHostToDevice, m->s_h2d));
+        in_done = need;
+        HX_CUDA(ctx, cudaEventRecord(m->ev_in[s], m->s_h2d));
+        HX_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, m->ev_in[s], 0));
+        const hx::MeshView v = slab_view(m, prec, z0, z1);
+        const int64_t off = (int64_t)z0 * m->p * lv;
+        HX_CUDA(ctx, hx::prec_ops(m->p, prec)->apply(v, c.storage, din + off * sz, dout + off * sz, ctx->stream, variant));
+        ctx->launches++;
+        HX_CUDA(ctx, cudaEventRecord(m->ev_done[s], ctx->stream));
+        HX_CUDA(ctx, cudaStreamWaitEvent(m->s_d2h, m->ev_done[s], 0));
+        const int64_t ready = z1 == m->nz ? Nz : (int64_t)z1 * m->p;  // node layers no later slab touches
+        if (m->n_constrained) {  // constrained rows: out = du
+            const auto lo = std::lower_bound(m->h_cidx.begin(), m->h_cidx.end(), out_done * lv);
+            const auto hi = std::lower_bound(m->h_cidx.begin(), m->h_cidx.end(), ready * lv);
+            if (hi > lo) {
+                HX_CUDA(ctx, hx::copy_idx(m->d_cidx + (lo - m->h_cidx.begin()), hi - lo, din, dout, prec, m->s_d2h));
+                ctx->launches++;
+            }
+        }
+        HX_CUDA(ctx, cudaMemcpyAsync(hout + out_done * lv * sz, dout + out_done * lv * sz,
+                                     (size_t)((ready - out_done) * lv) * sz, cudaMemcpyDeviceToHost, m->s_d2h));
+        out_done = ready;
+    }
+    HX_CUDA(ctx, cudaEventRecord(m->ev_out, m->s_d2h));
+    HX_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, m->ev_out, 0));
+    HX_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    *done = true;
+    return HX_OK;
+}
+
 hx_status hx_tangent_apply_host(hx_mesh *m, const void *du_host, void *out_host, int32_t prec) {
     if (!m || !du_host || !out_host || bad_prec(prec))
         return fail(m ? m->ctx : nullptr, HX_ERR_ARG, "hx_tangent_apply_host: bad argument");
@@ -790,6 +918,11 @@ hx_status hx_tangent_apply_host(hx_mesh *m, const void *du_host, void *out_host,
     if (!m->w_stage_in) {
         HX_CUDA(ctx, cudaMalloc(&m->w_stage_in, 3 * (size_t)m->n_nodes * 8 + 16));
         HX_CUDA(ctx, cudaMalloc(&m->w_stage_out, 3 * (size_t)m->n_nodes * 8 + 16));
+    }
+    if (m->host_slabs) {
+        bool done = false;
+        const hx_status st = apply_host_slabs(m, du_host, out_host, prec, &done);
+        if (st != HX_OK || done) return st;
     }
     HX_CUDA(ctx, cudaMemcpyAsync(m->w_stage_in, du_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
     hx_status st = apply_dev(m, m->w_stage_in, m->w_stage_out, prec);

@@ -38,7 +38,7 @@ EXPORTS = ["hx_create", "hx_destroy", "hx_set_stream", "hx_last_error", "hx_sync
            "hx_mg_destroy", "hx_mg_info", "hx_mg_setup", "hx_mg_vcycle", "hx_mg_transfer", "hx_mg_cg_solve", "hx_fibre_dispersion", "hx_batch_create",
            "hx_batch_destroy", "hx_batch_tangent_apply", "hx_measure_fma_peak", "hx_launch_count",
            "hx_autotune", "hx_set_apply_variant", "hx_chebyshev_smooth_noalloc", "hx_traction_load",
-           "hx_set_wait_test", "hx_set_scatter_mode", "hx_mg_level", "hx_mg_coarse_iters", "hx_batch_cg_solve"]
+           "hx_set_wait_test", "hx_set_scatter_mode", "hx_set_host_apply_slabs", "hx_mg_level", "hx_mg_coarse_iters", "hx_batch_cg_solve"]
 
 
 class HxError(RuntimeError):
@@ -138,6 +138,7 @@ def lib():
             "hx_traction_load": (I32, [C.POINTER(hx_mesh_desc), I32, P, I32, C.POINTER(D), P]),
             "hx_set_wait_test": (I32, [P, I32, C.c_int64]),
             "hx_set_scatter_mode": (I32, [P, I32]),
+            "hx_set_host_apply_slabs": (I32, [P, I32]),
             "hx_mg_level": (I32, [P, I32, C.POINTER(I32), C.POINTER(I32), C.POINTER(I32), C.POINTER(I32)]),
             "hx_mg_coarse_iters": (I32, [P, C.POINTER(I32)]),
             "hx_batch_cg_solve": (I32, [P, C.POINTER(P), C.POINTER(P), D, I32, I32, D, I32, I32, C.POINTER(I32),
@@ -455,6 +456,12 @@ def hx_set_apply_variant(ctx, mesh, prec, storage, variant):
 
 
 HX_SCATTER_ATOMIC, HX_SCATTER_ORDERED = 0, 1
+
+
+def hx_set_host_apply_slabs(ctx, mesh, slabs):
+    """0: hx_tangent_apply_host copies whole vectors; 1 (default): z-slabs
+    with overlapped copies where they apply; 2..8: at most that many slabs."""
+    _check(lib().hx_set_host_apply_slabs(mesh, int(slabs)), ctx)
 
 
 def hx_set_scatter_mode(ctx, mesh, mode):
