@@ -270,6 +270,15 @@ hx_status cuda_fail(hx_ctx *ctx, cudaError_t e, const char *where) {
         if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);   \
     } while (0)
 
+// multiplier and shifts of the division by d >= 1 (see hx::FastDiv)
+hx::FastDiv fast_div_of(int d) {
+    const uint64_t dd = d > 0 ? (uint64_t)d : 1;
+    int l = 0;
+    while ((1ull << l) < dd) ++l;
+    const uint64_t mm = (((1ull << 32) * ((1ull << l) - dd)) / dd) + 1;
+    return hx::FastDiv{(uint32_t)mm, (uint32_t)(l < 1 ? l : 1), (uint32_t)(l > 1 ? l - 1 : 0)};
+}
+
 hx::MeshView view(const hx_mesh *m, int prec) {
     hx::MeshView v{};
     v.p = m->p;
@@ -279,6 +288,8 @@ hx::MeshView view(const hx_mesh *m, int prec) {
     v.qs = m->qs;
     v.structured = m->structured;
     v.nx = m->nx;
+    v.fnx = fast_div_of(m->nx);
+    v.fny = fast_div_of(m->ny);
     v.ny = m->ny;
     v.nz = m->nz;
     v.Nx = (int64_t)m->nx * m->p + 1;

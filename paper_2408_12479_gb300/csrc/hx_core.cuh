@@ -222,11 +222,23 @@ __device__ __forceinline__ void backward_int(T *G, T *W, T *U, int nc) {
 // ---------------------------------------------------------------------------
 // gather / scatter
 // ---------------------------------------------------------------------------
+// n / d for 0 <= n < 2^31 (see hx::FastDiv)
+__device__ __forceinline__ int fast_div(int n, const hx::FastDiv &f) {
+    const uint32_t t = __umulhi(f.m, (uint32_t)n);
+    return (int)((t + (((uint32_t)n - t) >> f.s1)) >> f.s2);
+}
+// element lattice indices of element e of a structured box
+__device__ __forceinline__ void elem_xyz(const hx::MeshView &m, int e, int &ex, int &ey, int &ez) {
+    const int t = fast_div(e, m.fnx);
+    ex = e - t * m.nx;
+    ez = fast_div(t, m.fny);
+    ey = t - ez * m.ny;
+}
+
 __device__ __forceinline__ int64_t node_of(const hx::MeshView &m, int e, int i, int j, int k) {
     if (m.structured) {
-        const int ex = e % m.nx;
-        const int t = e / m.nx;
-        const int ey = t % m.ny, ez = t / m.ny;
+        int ex, ey, ez;
+        elem_xyz(m, e, ex, ey, ez);
         return (int64_t)(ex * HX_P + i) + m.Nx * ((int64_t)(ey * HX_P + j) + m.Ny * (int64_t)(ez * HX_P + k));
     }
     return m.dof_conn[(int64_t)e * NQ + i + N * (j + N * k)];
@@ -1065,9 +1077,8 @@ struct F2 {
 __device__ __forceinline__ int64_t elem_base(const hx::MeshView &m, int e) {
     if (e >= m.n_elem) return 0;
     if (m.structured) {
-        const int ex = e % m.nx;
-        const int t = e / m.nx;
-        const int ey = t % m.ny, ez = t / m.ny;
+        int ex, ey, ez;
+        elem_xyz(m, e, ex, ey, ez);
         return (int64_t)ex * HX_P + m.Nx * ((int64_t)ey * HX_P + m.Ny * (int64_t)ez * HX_P);
     }
     return e;

@@ -38,12 +38,22 @@ struct MatParamsF {
     float mu, lambda, kappa, k1, k2;
 };
 
+// Division of 0 <= n < 2^31 by a divisor fixed per mesh, with a multiply-high
+// and two shifts instead of an integer division (Granlund and Montgomery,
+// "Division by invariant integers using multiplication", PLDI 1994, the
+// unsigned case): with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+// t = mulhi(m, n) and n / d = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0).
+struct FastDiv {
+    uint32_t m, s1, s2;
+};
+
 // Plain-old-data view of a device mesh, passed by value to every kernel.
 struct MeshView {
     int p, n_elem;
     int64_t n_nodes, n_qp;
     int64_t qs;                  // field stride of the SoA point arrays: n_qp rounded up to 32
     int structured, nx, ny, nz;
+    FastDiv fnx, fny;            // division by nx and by ny (structured boxes)
     int64_t Nx, Ny;              // node lattice extents of a structured box
     const int32_t *dof_conn;     // [n_elem][(p+1)^3] or null (structured)
     const void *geo;             // [10][qs] of T: (J0^-1)_{ed} at field 3e+d, JxW at field 9
