@@ -211,3 +211,65 @@ def test_full_size_tube_sampled():
         assert np.abs(r[dofs] - ref[dofs]).max() / np.abs(ref[dofs]).max() < 1e-12
     finally:
         G.close()
+
+
+def test_full_size_compressed_cube_sampled():
+    """The solver workload at its full size: 48^3 jittered cube, p = 4, iNH at
+    kappa = 1e3 mu compressed to J ~ 0.9 (21.6 M DoFs, every DoF free), on
+    sampled DoFs (random nodes, corners, face nodes) against the oracle over
+    the elements around them: the FP32 spatial-tensor apply in every variant
+    that launches, the FP64 one in the autotuned variant, and the FP64
+    residual. (The FP32 residual is left out at this size: it takes Grad u of
+    the smooth compression field from nodal values in FP32, a sum of terms
+    about |u| / h, here ~200 times |Grad u|, so H and, through kappa = 1e3 mu,
+    the pressure carry relative errors near 1e-5 before the residual's own
+    cancellation between elements. The tangent's state comes from the FP64
+    precompute, and the residual in the solvers is FP64.)"""
+    p = 4
+    m, field, seed = I.workload_compressed_cube(n=48, p=p, J_target=0.9)
+    m.dirichlet = np.zeros_like(m.dirichlet)
+    assert m.n_dofs == 21567171
+    M = O.OracleMesh(m)
+    X = O.node_coords(M)
+    u = field(X).ravel()
+    du = I.random_direction(m.n_dofs, seed + 41)
+    mat_d = dict(I.MAT_INH)
+    mat = cases.oracle_material(mat_d)
+    g = np.random.Generator(np.random.PCG64(seed + 42))
+    Np = 48 * p + 1
+    corners = [i + Np * (j + Np * k) for i in (0, Np - 1) for j in (0, Np - 1) for k in (0, Np - 1)]
+    faces = [Np // 2 + Np * (Np // 3), 7 + Np * Np * (Np // 2), Np - 1 + Np * (5 + Np * 9)]
+    nodes = np.unique(np.concatenate([g.choice(m.n_nodes, size=48, replace=False), corners, faces]))
+    elems = np.where(np.isin(m.dof_conn, nodes).any(axis=1))[0].astype(np.int32)
+    dofs = (3 * nodes[:, None] + np.arange(3)).ravel()
+    G = hx.Mesh(m, mat_d)
+    try:
+        for prec in (hx.HX_FP32, hx.HX_FP64):
+            G.precompute(cuda(u), prec, hx.HX_SPATIAL_TENSORS)
+            du_t = cuda(du, prec)
+            ref = O.apply(M, mat, u, host(du_t), elems=elems)
+            scale = np.abs(ref[dofs]).max()
+            out = torch.empty_like(du_t)
+            hx.hx_autotune(G.ctx, G.handle, du_t, out, reps=1)
+            res = host(G.apply(du_t))
+            G.sync(120000)
+            assert np.abs(res[dofs] - ref[dofs]).max() / scale < TOL[prec], prec
+            if prec == hx.HX_FP32:
+                ran = []
+                for variant in range(6):
+                    hx.hx_set_apply_variant(G.ctx, G.handle, prec, hx.HX_SPATIAL_TENSORS, variant)
+                    try:
+                        res = host(G.apply(du_t))
+                    except hx.HxError as e:
+                        assert variant >= 2 and e.status == hx.HX_ERR_CUDA, (variant, str(e))
+                        continue
+                    G.sync(120000)
+                    assert np.abs(res[dofs] - ref[dofs]).max() / scale < TOL[prec], variant
+                    ran.append(variant)
+                assert 0 in ran and 2 in ran, ran
+        r = host(G.residual(cuda(u)))
+        G.sync(120000)
+        ref_r = O.residual(M, mat, u, elems=elems)
+        assert np.abs(r[dofs] - ref_r[dofs]).max() / np.abs(ref_r[dofs]).max() < TOL[hx.HX_FP64]
+    finally:
+        G.close()
