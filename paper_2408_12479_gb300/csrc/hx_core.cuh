@@ -1159,6 +1159,25 @@ __device__ __forceinline__ void load_row(const hx::MeshView &m, int e, int64_t b
     }
 }
 
+// Subtract from a thread's x-row of v (3 N values, load_row layout) the value
+// of v at its element's node (0, 0, 0). For rows of a field whose gradient is
+// all that is needed (u in the residual, u_k in the recompute strategy): a
+// smooth field's nodal values are about |v| / h times its gradient, and
+// differentiating them directly in FP32 would lose that factor to
+// cancellation; the gradient of the shifted rows is the same.
+__device__ __forceinline__ void shift_row(const hx::MeshView &m, int e, int64_t base, const Real *__restrict__ v,
+                                          Real *row) {
+    if (e >= m.n_elem) return;
+    const int64_t d = 3 * node_at(m, base, 0, 0, 0);
+    const Real s0 = v[d], s1 = v[d + 1], s2 = v[d + 2];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        row[3 * i + 0] -= s0;
+        row[3 * i + 1] -= s1;
+        row[3 * i + 2] -= s2;
+    }
+}
+
 // forward sum factorization of an element whose x-rows are in the threads'
 // registers (row[3*i + c], x-line (a0, a1)): leaves the x-, y- and
 // z-reference derivatives at the Gauss points in X0, X1 and X2, which also
@@ -2024,10 +2043,12 @@ __global__ void __launch_bounds__(col_threads(EPB)) k_residual_col(const hx::Mes
     const bool act = el < EPB;
     const uint64_t pol_keep = policy_evict_last();
     const uint64_t pol_stream = policy_evict_first();
-    Real row[3 * N];
+    Real row[3 * N];  // R needs only Grad u: rows relative to the element's first node (shift_row)
     if (act && (int)blockIdx.x < ntiles) {
         const int e1 = blockIdx.x * EPB + el;
-        load_row(m, e1, elem_base(m, e1), a0, a1, u, false, row);
+        const int64_t base = elem_base(m, e1);
+        load_row(m, e1, base, a0, a1, u, false, row);
+        shift_row(m, e1, base, u, row);
     }
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int ntile = tile + gridDim.x;
@@ -2036,7 +2057,9 @@ __global__ void __launch_bounds__(col_threads(EPB)) k_residual_col(const hx::Mes
         for (int i = 0; i < 3 * N; ++i) cu[i] = row[i];
         if (act && ntile < ntiles) {
             const int e1 = ntile * EPB + el;
-            load_row(m, e1, elem_base(m, e1), a0, a1, u, false, row);
+            const int64_t base = elem_base(m, e1);
+            load_row(m, e1, base, a0, a1, u, false, row);
+            shift_row(m, e1, base, u, row);
         }
         // no barrier: the previous tile's last phase reads X1 only, the first
         // phase of this one writes X0 only
@@ -2077,7 +2100,10 @@ __global__ void __launch_bounds__(apply_threads<STAGED && ROWSW>(EPB)) k_apply(c
         const int e1 = blockIdx.x * EPB + el;
         const int64_t b1 = elem_base(m, e1);
         load_row(m, e1, b1, a0, a1, du, true, rowd);
-        if constexpr (RC) load_row(m, e1, b1, a0, a1, (const Real *)m.uk, false, rowk);
+        if constexpr (RC) {  // only Grad u_k is needed (shift_row)
+            load_row(m, e1, b1, a0, a1, (const Real *)m.uk, false, rowk);
+            shift_row(m, e1, b1, (const Real *)m.uk, rowk);
+        }
     }
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int ntile = tile + gridDim.x;
@@ -2094,7 +2120,10 @@ __global__ void __launch_bounds__(apply_threads<STAGED && ROWSW>(EPB)) k_apply(c
             const int e1 = ntile * EPB + el;
             const int64_t b1 = elem_base(m, e1);
             load_row(m, e1, b1, a0, a1, du, true, rowd);
-            if constexpr (RC) load_row(m, e1, b1, a0, a1, (const Real *)m.uk, false, rowk);
+            if constexpr (RC) {
+                load_row(m, e1, b1, a0, a1, (const Real *)m.uk, false, rowk);
+                shift_row(m, e1, b1, (const Real *)m.uk, rowk);
+            }
         }
         // no barrier: the previous tile's last phase reads X1 only, the first
         // phase of this one writes X0 (and K0) only
@@ -2121,7 +2150,10 @@ __device__ __forceinline__ void batch_tile(const hx::MeshView &m, int tile, cons
         const int e1 = tile * EPB + el;
         const int64_t b1 = elem_base(m, e1);
         load_row(m, e1, b1, a0, a1, du, true, cd);
-        if constexpr (RC) load_row(m, e1, b1, a0, a1, (const Real *)m.uk, false, ck);
+        if constexpr (RC) {  // only Grad u_k is needed (shift_row)
+            load_row(m, e1, b1, a0, a1, (const Real *)m.uk, false, ck);
+            shift_row(m, e1, b1, (const Real *)m.uk, ck);
+        }
     }
     uint32_t phase = 0;
     apply_tile<EPB, NT, LAW, STORAGE, false>(m, tile, -1, out, cd, ck, smem_raw, nullptr, nullptr, phase,
