@@ -218,8 +218,9 @@ def test_full_size_compressed_cube_sampled():
     kappa = 1e3 mu compressed to J ~ 0.9 (21.6 M DoFs, every DoF free), on
     sampled DoFs (random nodes, corners, face nodes) against the oracle over
     the elements around them: the FP32 spatial-tensor apply in every variant
-    that launches, the FP64 one in the autotuned variant, and the residual in
-    both precisions. The FP32 residual holds 1e-5 here only because each
+    that launches, the FP64 one in the autotuned variant, the FP32 apply of
+    the recompute strategy (state rebuilt from FP32 u_k, so the oracle takes
+    the FP32-rounded u_k) and the residual in both precisions. The FP32 residual holds 1e-5 here only because each
     element's nodal values are taken relative to its first node before they
     are differentiated: the smooth compression field's values are about |u| /
     h, some 200 times |Grad u| at h = 1/48, and differentiated directly in FP32
@@ -268,6 +269,13 @@ def test_full_size_compressed_cube_sampled():
                     assert np.abs(res[dofs] - ref[dofs]).max() / scale < TOL[prec], variant
                     ran.append(variant)
                 assert 0 in ran and 2 in ran, ran
+        # the recompute strategy in FP32 rebuilds the state from FP32 u_k at every point
+        G.precompute(cuda(u), hx.HX_FP32, hx.HX_RECOMPUTE)
+        du_t = cuda(du, hx.HX_FP32)
+        ref = O.apply(M, mat, host(cuda(u, hx.HX_FP32)), host(du_t), elems=elems)
+        res = host(G.apply(du_t))
+        G.sync(120000)
+        assert np.abs(res[dofs] - ref[dofs]).max() / np.abs(ref[dofs]).max() < TOL[hx.HX_FP32]
         for prec in (hx.HX_FP64, hx.HX_FP32):
             u_t = cuda(u, prec)
             r = host(G.residual(u_t))
