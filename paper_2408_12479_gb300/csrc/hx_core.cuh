@@ -1351,10 +1351,13 @@ struct ApplySmem {
     static constexpr int arrays = STORAGE == HX_RECOMPUTE ? 6 : 3;
     static constexpr bool SW = STAGED && ROWSW;
     static constexpr size_t cube_bytes = (size_t)arrays * EPB * Lay<SW>::ES * sizeof(Real);
-    static constexpr size_t field_bytes = (size_t)EPB * NQ * sizeof(Real);
-    // bulk copies need 16-byte aligned starts: every tile offset is a
-    // multiple of field_bytes, and the field strides are padded to 32 points
-    static constexpr bool stageable = field_bytes % 16 == 0;
+    // stage words per field: a tile's chunk of EPB NQ points, or, where chunks
+    // do not start on 16-byte boundaries, the window that starts at the chunk's
+    // first word rounded down to one and ends on one (the field strides are
+    // padded to 32 points, and the point arrays carry slack behind the last)
+    static constexpr int VW = 16 / (int)sizeof(Real);
+    static constexpr int FE = (EPB * NQ) % VW == 0 ? EPB * NQ : (EPB * NQ + 2 * VW - 2) / VW * VW;
+    static constexpr size_t field_bytes = (size_t)FE * sizeof(Real);
     static constexpr size_t bytes =
         (cube_bytes + 15) / 16 * 16 + (STAGED ? (size_t)QpFields<LAW, STORAGE>::n * field_bytes : 0);
 };
@@ -1394,7 +1397,8 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 // The bulk copies of a tile's quadrature-point fields into the CTA's stage
-// (one chunk of the tile's points per field, rounded up to 16 bytes), on the
+// (per field, the tile's chunk of points widened to 16-byte boundaries: it
+// starts (e0 NQ) mod (16 / sizeof(Real)) words into the stage field), on the
 // CTA's mbarrier, issued by the 32 lanes of one warp (lane f copies fields
 // f, f + 32, ...; lane 0 first posts the expected bytes). Called by all lanes
 // of that warp after the CTA barrier that ends the stage's previous use; the
@@ -1402,10 +1406,17 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 template <int EPB, int LAW, int STORAGE>
 __device__ __forceinline__ void stage_issue_warp(const hx::MeshView &m, int tile, Real *stg, uint64_t *bar, int lane) {
     using QF = QpFields<LAW, STORAGE>;
-    constexpr int FE = EPB * NQ;  // stage points per field
+    using SM = ApplySmem<EPB, LAW, STORAGE, true>;
+    constexpr int FE = SM::FE;  // stage words per field
     const int e0 = tile * EPB;
     const int cnt = min(EPB, m.n_elem - e0);
-    const uint32_t bytes = (uint32_t)((cnt * NQ * (int)sizeof(Real) + 15) / 16 * 16);
+    const int64_t c0 = (int64_t)e0 * NQ;
+    const int off = FE == EPB * NQ ? 0 : (int)(c0 % SM::VW);  // the chunk's first word in its window
+    const uint32_t bytes = (uint32_t)(((off + cnt * NQ) * (int)sizeof(Real) + 15) / 16 * 16);
+    static_assert((((FE == EPB * NQ ? 0 : SM::VW - 1) + EPB * NQ) * (int)sizeof(Real) + 15) / 16 * 16 <=
+                      FE * (int)sizeof(Real),
+                  "the widest window fits its stage field");
+    static_assert(2 * SM::VW * (int)sizeof(Real) <= HX_ARRAY_SLACK, "windows stay inside the point arrays");
     if (m.skip_stage_copies) return;  // test hook: the stage never fills and the wait runs out
     if (lane == 0) mbar_expect_tx(bar, QF::n * bytes);
     __syncwarp();
@@ -1414,8 +1425,8 @@ __device__ __forceinline__ void stage_issue_warp(const hx::MeshView &m, int tile
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 #pragma unroll 1
         for (int f = lane; f < QF::n; f += 32) {
-            const Real *src = f < QF::ng ? (const Real *)m.geo + (int64_t)f * m.qs + (int64_t)e0 * NQ
-                                         : (const Real *)m.qp + (int64_t)(f - QF::ng) * m.qs + (int64_t)e0 * NQ;
+            const Real *src = f < QF::ng ? (const Real *)m.geo + (int64_t)f * m.qs + (c0 - off)
+                                         : (const Real *)m.qp + (int64_t)(f - QF::ng) * m.qs + (c0 - off);
             bulk_g2s(stg + f * FE, src, bytes, bar, pol);
         }
     }
@@ -1803,8 +1814,10 @@ __device__ __forceinline__ bool apply_tile(const hx::MeshView &m, int tile, int 
             return false;
         }
         phase ^= 1u;
-        qp_columns<LAW, STORAGE, EPB * NQ, SW>(m, e, valid, stg + el * NQ + a0 + N * a1, X0, X2, K0, K2, gz, gk,
-                                               eoff, lo);
+        using SMS = ApplySmem<EPB, LAW, STORAGE, true>;
+        const int soff = SMS::FE == EPB * NQ ? 0 : (int)(((int64_t)tile * EPB * NQ) % SMS::VW);  // chunk in its window
+        qp_columns<LAW, STORAGE, SMS::FE, SW>(m, e, valid, stg + soff + el * NQ + a0 + N * a1, X0, X2, K0, K2, gz,
+                                              gk, eoff, lo);
         Real rz[3][N];
         mv3<TD, true, true>(gz, rz);
         __syncthreads();
@@ -2171,7 +2184,6 @@ __device__ __forceinline__ bool batch_tile_staged(const hx::MeshView &m, int til
                                                   uint32_t phase) {
     static_assert(STORAGE != HX_RECOMPUTE, "the staged tile runs the caching strategies");
     using SM = ApplySmem<EPB, LAW, STORAGE, true>;
-    static_assert(SM::stageable, "bulk copies need 16-byte aligned tiles");
     Real *stg = (Real *)(smem_raw + (SM::cube_bytes + 15) / 16 * 16);
     const int t = threadIdx.x;
     if (t < 32) stage_issue_warp<EPB, LAW, STORAGE>(m, tile, stg, bar, t);

@@ -65,27 +65,43 @@ int sm_count() {
 template <int EPB, int LAW, int STORAGE, bool STAGED>
 cudaError_t launch_apply_t(const hx::MeshView &m, const void *du, void *out, cudaStream_t s) {
     using SM = ApplySmem<EPB, LAW, STORAGE, STAGED>;
-    if constexpr (STAGED && !SM::stageable) {
-        return cudaErrorInvalidConfiguration;  // tile chunks would not start on 16-byte boundaries
-    } else {
-        auto kern = k_apply<EPB, LAW, STORAGE, STAGED>;
-        constexpr size_t smem = SM::bytes;
-        constexpr int NTH = apply_threads<STAGED && ROWSW>(EPB);
-        if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
-        static int per_sm = [&] {
-            if (set_smem(kern, smem) != cudaSuccess) return 0;
-            cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-            int b = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, NTH, smem) != cudaSuccess) return 0;
-            return b;
-        }();
-        if (per_sm <= 0) return cudaErrorInvalidConfiguration;
-        const int ntiles = (m.n_elem + EPB - 1) / EPB;
-        if (ntiles == 0) return cudaSuccess;
-        const int grid = ntiles < per_sm * sm_count() ? ntiles : per_sm * sm_count();
-        kern<<<grid, NTH, smem, s>>>(m, (const Real *)du, (Real *)out, ntiles);
-        return cudaGetLastError();
+    auto kern = k_apply<EPB, LAW, STORAGE, STAGED>;
+    constexpr size_t smem = SM::bytes;
+    constexpr int NTH = apply_threads<STAGED && ROWSW>(EPB);
+    if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+    static int per_sm = [&] {
+        if (set_smem(kern, smem) != cudaSuccess) return 0;
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, NTH, smem) != cudaSuccess) return 0;
+        return b;
+    }();
+    if (per_sm <= 0) return cudaErrorInvalidConfiguration;
+    const int ntiles = (m.n_elem + EPB - 1) / EPB;
+    if (ntiles == 0) return cudaSuccess;
+    const int grid = ntiles < per_sm * sm_count() ? ntiles : per_sm * sm_count();
+    kern<<<grid, NTH, smem, s>>>(m, (const Real *)du, (Real *)out, ntiles);
+    return cudaGetLastError();
+}
+
+// Elements per CTA of the half-tile staged variant at n >= 6, where a
+// staged element takes 24-38 KB of shared memory: the tile size, up to the
+// default, that keeps the most elements resident per SM.
+template <int LAW, int STORAGE>
+constexpr int epb_resident() {
+    int best = 1, most = 0;
+    for (int e = 1; e <= EPB_A; ++e) {
+        const int vw = 16 / (int)sizeof(Real);
+        const int fe = (e * NQ) % vw == 0 ? e * NQ : (e * NQ + 2 * vw - 2) / vw * vw;
+        const size_t b = ((size_t)(STORAGE == HX_RECOMPUTE ? 6 : 3) * e * CES * sizeof(Real) + 15) / 16 * 16 +
+                         (size_t)QpFields<LAW, STORAGE>::n * fe * sizeof(Real);
+        const int ctas = (int)((size_t)227 * 1024 / b);
+        if (e * ctas >= most) {
+            most = e * ctas;
+            best = e;
+        }
     }
+    return best;
 }
 
 // Warp-decoupled staged apply (k_apply_wd): W warps per CTA, each with a
@@ -123,11 +139,12 @@ cudaError_t launch_apply_wd_t(const hx::MeshView &m, const void *du, void *out, 
 // variants: how the quadrature-point fields arrive and the tile shape:
 // register prefetch one point ahead with an L2 bulk prefetch of the next tile
 // (0: default, 1: half elements per CTA), bulk copies into a shared stage one
-// tile ahead (3: default, 4: half), and the warp-decoupled staged apply with a
-// stage per warp (2: WD_LO warps per CTA, 5: twice as many). Per-CTA staged variants are not
-// built where a tile's chunk is not a multiple of 16 bytes; the
-// warp-decoupled ones only where whole elements fit one warp (FP32, p <= 4)
-// and not for the recompute strategy.
+// tile ahead (3: default, 4: half; from n = 6 on, the tile that keeps the most
+// elements resident; chunks that do not start on 16-byte boundaries are
+// copied as aligned windows), and the warp-decoupled staged apply with a
+// stage per warp (2: WD_LO warps per CTA, 5: twice as many), built only where
+// whole elements fit one warp (FP32, p <= 4) and not for the recompute
+// strategy.
 template <int LAW, int STORAGE>
 cudaError_t apply_variant(const hx::MeshView &m0, const void *du, void *out, cudaStream_t s, int variant) {
     hx::MeshView m = m0;
@@ -137,7 +154,7 @@ cudaError_t apply_variant(const hx::MeshView &m0, const void *du, void *out, cud
         case 1: return launch_apply_t<EH, LAW, STORAGE, false>(m, du, out, s);
         case 2: return launch_apply_wd_t<WD_LO, LAW, STORAGE>(m, du, out, s);
         case 3: return launch_apply_t<EPB_A, LAW, STORAGE, true>(m, du, out, s);
-        case 4: return launch_apply_t<EH, LAW, STORAGE, true>(m, du, out, s);
+        case 4: return launch_apply_t<(N >= 6 ? epb_resident<LAW, STORAGE>() : EH), LAW, STORAGE, true>(m, du, out, s);
         case 5: return launch_apply_wd_t<2 * WD_LO, LAW, STORAGE>(m, du, out, s);
         default: return launch_apply_t<EPB_A, LAW, STORAGE, false>(m, du, out, s);
     }
